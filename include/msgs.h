@@ -1,0 +1,244 @@
+/*
+ * msgs.h -- multi-scale selective Gaussian splatting on one GPU (sm_103a).
+ *
+ * C ABI of libmsgs.so: the rendering path of "Multi-Scale 3D Gaussian
+ * Splatting for Anti-Aliased Rendering" (arXiv 2311.17089):
+ *
+ *   ms_scene_prepare  per-scene activations (exp(log_scale), ln(255 sigma))
+ *   ms_project        EWA splat, pixel coverage, selection, SH colour
+ *   ms_select         re-run the selection predicate on stored coverage
+ *   ms_update_range   UpdateRange of the coverage bounds
+ *   ms_bin            16x16 tile binning with a stable (tile, depth) order
+ *   ms_raster         per-pixel front-to-back blend with early termination
+ *
+ * Conventions shared by every call:
+ *   - Every pointer inside ms_scene_t, ms_proj_t, ms_bins_t and every
+ *     image pointer is DEVICE memory owned by the caller; the library never
+ *     allocates, frees or retains a pointer past the call.  Arrays are
+ *     dense, row-major, FP32 unless stated.  ms_camera_t is a host struct
+ *     passed by value inside the call.
+ *   - `stream` is a cudaStream_t (0 = legacy default stream).  Calls only
+ *     enqueue work on it and return; nothing is synchronised unless the
+ *     entry point says so.
+ *   - Return value: MS_OK or an ms_status_t error; ms_last_error() gives a
+ *     message for the calling thread.  Argument errors are detected before
+ *     any work is enqueued.  Device-side conditions (duplicate capacity
+ *     overflow, a bounded wait that gave up) are recorded in the device
+ *     status word of ms_bins_t and reported by ms_bin_counts().
+ *   - Camera: OpenCV axes (x right, y down, z forward), X_cam = R X_world + t,
+ *     pixel (i, j) covers [i, i+1) x [j, j+1) and is sampled at its centre.
+ */
+#ifndef MSGS_H
+#define MSGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MS_OK = 0,
+    MS_ERR_INVALID_ARG = 1, /* bad size, null pointer, misaligned buffer */
+    MS_ERR_CAPACITY = 2,    /* more tile duplicates than dup_capacity    */
+    MS_ERR_CUDA = 3,        /* a CUDA runtime call failed                */
+    MS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up        */
+    MS_ERR_NO_DEVICE = 5    /* no usable sm_103 device                   */
+} ms_status_t;
+
+/* Which Gaussians are rendered (Eq. 6 and the "Filter Small" ablation). */
+typedef enum {
+    MS_SELECTIVE = 0,    /* Eq. 6 with the level exemptions of Sec. 4.1    */
+    MS_ALL_LEVELS = 1,   /* every valid Gaussian, all levels together      */
+    MS_FILTER_SMALL = 2  /* second clause of Eq. 6 only, no exemption      */
+} ms_mode_t;
+
+/*
+ * A scene of n 3D Gaussians (Sec. 3.1: centre, covariance from scale and
+ * rotation, opacity, colour; Sec. 4.1: level and coverage range).
+ *   mean[n*3]       world centre
+ *   log_scale[n*3]  log of the per-axis standard deviation
+ *   quat[n*4]       rotation (w, x, y, z); any non-zero length; 16-B aligned
+ *   opacity[n]      activated opacity sigma
+ *   color           sh_degree >= 0: SH coefficients [n][(deg+1)^2][3],
+ *                   16-B aligned; sh_degree == -1: plain RGB [n][3]
+ *   level[n]        uint8 level, 1 (finest) .. n_levels (coarsest)
+ *   s_max[n], s_min[n]  coverage range (read by ms_project, written by
+ *                   ms_update_range); S_max = 0, S_min = +inf before any
+ *                   update
+ *   scale[n*3], lnop[n]  derived, written by ms_scene_prepare:
+ *                   exp(log_scale) and ln(255 sigma), each evaluated in
+ *                   FP64 and rounded to FP32
+ * n <= 2^31 - 1, n_levels in 1..255, sh_degree in -1..3.
+ */
+typedef struct {
+    int64_t n;
+    int32_t n_levels;
+    int32_t sh_degree;
+    const float *mean;
+    const float *log_scale;
+    const float *quat;
+    const float *opacity;
+    const float *color;
+    const uint8_t *level;
+    float *s_max;
+    float *s_min;
+    float *scale;
+    float *lnop;
+} ms_scene_t;
+
+/* Pinhole camera, host struct.  width, height >= 1; near_plane > 0. */
+typedef struct {
+    float R[9];      /* world -> camera rotation, row-major */
+    float t[3];      /* world -> camera translation         */
+    float campos[3]; /* camera centre in world coordinates  */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_plane;
+    float bg[3];     /* background colour added as T_final * bg */
+} ms_camera_t;
+
+/*
+ * Output of ms_project; device buffers sized for the scene's n.
+ *   rec[n*12]     48-byte raster record of every listed Gaussian (selected
+ *                 and touching >= 1 tile): ux, uy, conic a, conic b |
+ *                 conic c, opacity, r, g | b, 0, 0, 0.  16-B aligned.
+ *                 Entries of other Gaussians are left untouched.
+ *   rect[n*2]     listed Gaussians: tile rectangle packed as
+ *                 (x0 | y0 << 16), (x1 | y1 << 16), inclusive
+ *   n_tiles[n]    tiles covered if listed, else 0 (always written)
+ *   depth[n]      listed Gaussians: bit pattern of view-space z (> 0)
+ *   cover[n]      optional (may be NULL): pixel coverage S of every valid
+ *                 Gaussian, -1 for invalid ones
+ *   mask[(n+31)/32]  optional (may be NULL): selection bitset, bit i%32 of
+ *                 word i/32 set iff Gaussian i is valid and selected
+ *   stats[MS_STATS_WORDS]  uint32 counters written by ms_project and read
+ *                 by ms_bin: survivors, duplicates, depth-digit histograms
+ *   n             number of Gaussians the arrays hold (>= the scene's n);
+ *                 kernels never index past it
+ */
+#define MS_STATS_WORDS 1040
+typedef struct {
+    float *rec;
+    uint32_t *rect;
+    uint32_t *n_tiles;
+    uint32_t *depth;
+    float *cover;
+    uint32_t *mask;
+    uint32_t *stats;
+    int64_t n;
+} ms_proj_t;
+
+/*
+ * Output of ms_bin.
+ *   gauss_idx[dup_capacity]  Gaussian indices, grouped by tile in
+ *                 row-major tile order, each group ordered by depth bits
+ *                 then index
+ *   ranges[tiles*2]  [start, end) of each tile's group in gauss_idx
+ *   counts[4]     uint64 device words: [0] duplicates D (the number
+ *                 needed, even when it exceeds the capacity), [1] survivor
+ *                 count, [2] status bits (1 = capacity overflow, 2 = a
+ *                 bounded wait gave up), [3] reserved
+ *   dup_capacity  entries gauss_idx can hold, 1 .. 2^30
+ */
+typedef struct {
+    uint32_t *gauss_idx;
+    uint32_t *ranges;
+    uint64_t *counts;
+    int64_t dup_capacity;
+} ms_bins_t;
+
+/* Message describing the last error returned on the calling thread. */
+const char *ms_last_error(void);
+
+/* Library version, 100 * major + minor. */
+int ms_version(void);
+
+/*
+ * Per-scene activations: scale = exp(log_scale), lnop = ln(255 * opacity)
+ * = ln(sigma / sigma_T) with sigma_T = 1/255 (Sec. 4.1), both in FP64 then
+ * rounded to FP32, so no transcendental enters the per-view footprint.
+ * Run once per scene (and after the parameters change).
+ */
+int ms_scene_prepare(const ms_scene_t *scene, void *stream);
+
+/*
+ * Splat and select (Sec. 3.1, Sec. 3.2 Eq. 4, Sec. 4.1, Eq. 6; in Alg. 2 the
+ * pixel coverage and the sets G1, G2).  For every Gaussian, in FP32 with a fixed
+ * operation order: view transform, quaternion -> rotation, Sigma = R S^2
+ * R^T, V = J W Sigma W^T J^T (Jacobian with the view ratio clamped to 1.3x
+ * the half field of view), coverage S = sqrt(8 L det V / max(V_xx, V_yy))
+ * on the undilated V, selection by `mode`, dilated V' = V + 0.3 I, its
+ * conic, the level-set tile rectangle and, for listed Gaussians only, the
+ * colour (SH of degree sh_degree evaluated towards the camera, + 0.5,
+ * clamped at 0).  Valid = view z > near_plane, lnop > 0, det V' > 0 and
+ * finite intermediates.
+ */
+int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
+               ms_mode_t mode, const ms_proj_t *out, void *stream);
+
+/*
+ * Selection predicate alone (Eq. 6, Sec. 4.1 exemptions) on a coverage
+ * array produced by ms_project for the same scene: writes the bitset
+ * mask[(n+31)/32].  cover < 0 marks invalid Gaussians (never selected).
+ */
+int ms_select(const ms_scene_t *scene, const float *cover, ms_mode_t mode,
+              uint32_t *mask, void *stream);
+
+/*
+ * UpdateRange (Eq. 5, Alg. 2): for every valid Gaussian of level `level_r`
+ * whose level-set rectangle touches the image of `cam`,
+ *   s_max = max(0.95 s_max, S),  s_min = min(1.05 s_min, S).
+ * The caller renders level l at its creation scale 4^(l-1) (Sec. 4.1).
+ */
+int ms_update_range(const ms_scene_t *scene, const ms_camera_t *cam,
+                    int32_t level_r, void *stream);
+
+/* Workspace bytes ms_bin needs for n Gaussians, `tiles` tiles and a
+ * duplicate capacity; 0 on invalid sizes. */
+size_t ms_bin_workspace_bytes(int64_t n, int64_t tiles, int64_t dup_capacity);
+
+/*
+ * Tile binning (Sec. 3.1: "all 2D Gaussians touching each tile are sorted
+ * based on their original depth").  Listed Gaussians are sorted by depth
+ * bits with a stable LSD radix sort (ties keep index order), expanded to
+ * one entry per covered tile in that order, and stably radix-sorted by tile
+ * id, which yields every tile's list in (depth, index) order.  Fully
+ * asynchronous; D is only known on the device: entries beyond
+ * dup_capacity are dropped and status bit 1 set.  `ws` (16-B aligned) of
+ * ms_bin_workspace_bytes(n, tiles, dup_capacity) bytes is scratch owned by
+ * the call until the stream passes it.
+ */
+int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
+           const ms_bins_t *out, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Copy the counts of a finished ms_bin to the host (synchronises
+ * `stream`).  Returns MS_ERR_CAPACITY if D exceeded the capacity
+ * (*d_needed tells how many are needed), MS_ERR_TIMEOUT if a bounded wait
+ * gave up, else MS_OK.  Either pointer may be NULL.
+ */
+int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed,
+                  int64_t *survivors, void *stream);
+
+/*
+ * Front-to-back blend (Sec. 3.1, Eq. 3): one 256-thread CTA per 16x16 tile,
+ * one thread per pixel, sampled at the pixel centre.  For each Gaussian of
+ * the tile's list in order: power = -(a dx^2 + c dy^2)/2 - b dx dy; skip if
+ * power > 0; alpha = min(0.99, sigma e^power); skip if alpha < 1/255; stop
+ * before a Gaussian that would bring T below 1e-4; C += alpha T rgb,
+ * T *= 1 - alpha.  Writes image[3][H][W] (planar, C + T bg), final_t[H][W]
+ * and n_contrib[H][W] (1 + list position of the last blended Gaussian, 0 if
+ * none).  n_eval[H][W] receives the number of list entries the pixel
+ * evaluated up to and including the one that ended it (the algorithmic
+ * work, for measurement).  final_t, n_contrib and n_eval may be NULL.
+ */
+int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins,
+              const ms_camera_t *cam, float *image, float *final_t,
+              uint32_t *n_contrib, uint32_t *n_eval, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,317 @@
+"""Python binding of libmsgs (include/msgs.h): multi-scale selective
+Gaussian splatting on one GPU.
+
+Argument marshalling only: every step of the rendering path runs in the
+CUDA kernels of libmsgs.so.  PyTorch provides device memory and streams.
+The functions `ms_*` mirror the C entry points one to one and raise
+`MsError` on a non-zero status.  `DeviceScene` and `Renderer` hold the
+torch-allocated buffers a frame needs and chain the calls.
+
+There is no CPU fallback: if libmsgs.so cannot be built or loaded, or no
+CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmsgs.so")
+
+MS_OK, MS_ERR_INVALID_ARG, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_TIMEOUT = 0, 1, 2, 3, 4
+MS_SELECTIVE, MS_ALL_LEVELS, MS_FILTER_SMALL = 0, 1, 2
+MODES = {"selective": MS_SELECTIVE, "all_levels": MS_ALL_LEVELS,
+         "filter_small": MS_FILTER_SMALL}
+MS_STATS_WORDS = 1040
+REC_FLOATS = 12
+
+P = ctypes.c_void_p
+
+
+class MsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"msgs error {code}: {msg}")
+        self.code = code
+
+
+class ms_scene_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_levels", ctypes.c_int32),
+                ("sh_degree", ctypes.c_int32), ("mean", P), ("log_scale", P),
+                ("quat", P), ("opacity", P), ("color", P), ("level", P),
+                ("s_max", P), ("s_min", P), ("scale", P), ("lnop", P)]
+
+
+class ms_camera_t(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3),
+                ("campos", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("near_plane", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+class ms_proj_t(ctypes.Structure):
+    _fields_ = [("rec", P), ("rect", P), ("n_tiles", P), ("depth", P),
+                ("cover", P), ("mask", P), ("stats", P), ("n", ctypes.c_int64)]
+
+
+class ms_bins_t(ctypes.Structure):
+    _fields_ = [("gauss_idx", P), ("ranges", P), ("counts", P),
+                ("dup_capacity", ctypes.c_int64)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/msgs.h
+_SIGNATURES = [
+    ("ms_last_error", ctypes.c_char_p, []),
+    ("ms_version", ctypes.c_int, []),
+    ("ms_scene_prepare", ctypes.c_int, [ctypes.POINTER(ms_scene_t), P]),
+    ("ms_project", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
+                                  ctypes.c_int, ctypes.POINTER(ms_proj_t), P]),
+    ("ms_select", ctypes.c_int, [ctypes.POINTER(ms_scene_t), P, ctypes.c_int, P, P]),
+    ("ms_update_range", ctypes.c_int, [ctypes.POINTER(ms_scene_t),
+                                       ctypes.POINTER(ms_camera_t), ctypes.c_int32, P]),
+    ("ms_bin_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.c_int64]),
+    ("ms_bin", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.c_int64,
+                              ctypes.POINTER(ms_camera_t), ctypes.POINTER(ms_bins_t),
+                              P, ctypes.c_size_t, P]),
+    ("ms_bin_counts", ctypes.c_int, [ctypes.POINTER(ms_bins_t),
+                                     ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int64), P]),
+    ("ms_raster", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
+                                 ctypes.POINTER(ms_camera_t), P, P, P, P, P]),
+]
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def lib():
+    """Load libmsgs.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        from . import _build
+        if not _build.up_to_date():
+            _build.build()
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != MS_OK:
+        raise MsError(rc, lib().ms_last_error().decode())
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream=None) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def camera_struct(cam: inputs.Camera) -> ms_camera_t:
+    c = ms_camera_t()
+    c.R[:] = [float(v) for v in np.asarray(cam.R, np.float32).reshape(9)]
+    c.t[:] = [float(v) for v in np.asarray(cam.t, np.float32)]
+    c.campos[:] = [float(v) for v in np.asarray(cam.campos, np.float32)]
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.width, c.height = cam.width, cam.height
+    c.near_plane = cam.near
+    c.bg[:] = [float(v) for v in np.asarray(cam.bg, np.float32)]
+    return c
+
+
+# ------------------------------------------------ one-to-one entry points
+
+def ms_version() -> int:
+    return lib().ms_version()
+
+
+def ms_scene_prepare(scene: ms_scene_t, stream=None):
+    _check(lib().ms_scene_prepare(ctypes.byref(scene), P(_stream(stream))))
+
+
+def ms_project(scene: ms_scene_t, cam: ms_camera_t, mode: int, out: ms_proj_t, stream=None):
+    _check(lib().ms_project(ctypes.byref(scene), ctypes.byref(cam), int(mode),
+                            ctypes.byref(out), P(_stream(stream))))
+
+
+def ms_select(scene: ms_scene_t, cover_ptr: int, mode: int, mask_ptr: int, stream=None):
+    _check(lib().ms_select(ctypes.byref(scene), P(cover_ptr), int(mode), P(mask_ptr),
+                           P(_stream(stream))))
+
+
+def ms_update_range(scene: ms_scene_t, cam: ms_camera_t, level_r: int, stream=None):
+    _check(lib().ms_update_range(ctypes.byref(scene), ctypes.byref(cam), int(level_r),
+                                 P(_stream(stream))))
+
+
+def ms_bin_workspace_bytes(n: int, tiles: int, dup_capacity: int) -> int:
+    return int(lib().ms_bin_workspace_bytes(n, tiles, dup_capacity))
+
+
+def ms_bin(proj: ms_proj_t, n: int, cam: ms_camera_t, out: ms_bins_t, ws_ptr: int,
+           ws_bytes: int, stream=None):
+    _check(lib().ms_bin(ctypes.byref(proj), int(n), ctypes.byref(cam), ctypes.byref(out),
+                        P(ws_ptr), ws_bytes, P(_stream(stream))))
+
+
+def ms_bin_counts(bins: ms_bins_t, stream=None):
+    """(status, D needed, survivors); synchronises the stream."""
+    d = ctypes.c_int64()
+    s = ctypes.c_int64()
+    rc = lib().ms_bin_counts(ctypes.byref(bins), ctypes.byref(d), ctypes.byref(s),
+                             P(_stream(stream)))
+    if rc not in (MS_OK, MS_ERR_CAPACITY):
+        _check(rc)
+    return rc, d.value, s.value
+
+
+def ms_raster(proj: ms_proj_t, bins: ms_bins_t, cam: ms_camera_t, image_ptr: int,
+              final_t_ptr: int = 0, n_contrib_ptr: int = 0, n_eval_ptr: int = 0,
+              stream=None):
+    _check(lib().ms_raster(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam),
+                           P(image_ptr), P(final_t_ptr), P(n_contrib_ptr), P(n_eval_ptr),
+                           P(_stream(stream))))
+
+
+# ------------------------------------------------------ buffer helpers
+
+class DeviceScene:
+    """A scene's arrays resident in device memory plus its ms_scene_t."""
+
+    def __init__(self, scene: inputs.Scene, device="cuda", prepare: bool = True):
+        import torch
+        dev = torch.device(device)
+
+        def f32(a):
+            return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+
+        self.n = scene.n
+        self.n_levels = scene.n_levels
+        self.sh_degree = scene.sh_degree
+        self.mean = f32(scene.mean)
+        self.log_scale = f32(scene.log_scale)
+        self.quat = f32(scene.quat)
+        self.opacity = f32(scene.opacity)
+        self.color = f32(scene.color)
+        self.level = torch.from_numpy(np.ascontiguousarray(scene.level, np.uint8)).to(dev)
+        self.s_max = f32(scene.s_max)
+        self.s_min = f32(scene.s_min)
+        self.scale = torch.empty((max(self.n, 1), 3), dtype=torch.float32, device=dev)
+        self.lnop = torch.empty(max(self.n, 1), dtype=torch.float32, device=dev)
+        self.struct = ms_scene_t(
+            self.n, self.n_levels, self.sh_degree, _ptr(self.mean), _ptr(self.log_scale),
+            _ptr(self.quat), _ptr(self.opacity), _ptr(self.color), _ptr(self.level),
+            _ptr(self.s_max), _ptr(self.s_min), _ptr(self.scale), _ptr(self.lnop))
+        if prepare:
+            ms_scene_prepare(self.struct)
+
+    def set_range(self, s_max, s_min):
+        import torch
+        self.s_max.copy_(torch.as_tensor(np.ascontiguousarray(s_max, np.float32)))
+        self.s_min.copy_(torch.as_tensor(np.ascontiguousarray(s_min, np.float32)))
+
+    def calibrate(self, cams):
+        """UpdateRange at each level's creation scale 4^(l-1) (Sec. 4.1) for
+        every camera in order, on the device."""
+        for cam in cams:
+            for l in range(1, self.n_levels + 1):
+                ms_update_range(self.struct, camera_struct(inputs.downscale(cam, 4 ** (l - 1))), l)
+
+
+class Renderer:
+    """Buffers for rendering one scene at images up to `max_tiles` tiles."""
+
+    def __init__(self, n: int, max_tiles: int, dup_capacity: int, device="cuda",
+                 with_cover: bool = True, with_mask: bool = True):
+        import torch
+        dev = torch.device(device)
+        nn = max(n, 1)
+        self.n = n
+        self.max_tiles = max_tiles
+        self.dup_capacity = dup_capacity
+        self.rec = torch.empty(nn * REC_FLOATS, dtype=torch.float32, device=dev)
+        self.rect = torch.empty(nn * 2, dtype=torch.int32, device=dev)
+        self.n_tiles = torch.empty(nn, dtype=torch.int32, device=dev)
+        self.depth = torch.empty(nn, dtype=torch.int32, device=dev)
+        self.cover = torch.empty(nn, dtype=torch.float32, device=dev) if with_cover else None
+        self.mask = (torch.empty((nn + 31) // 32, dtype=torch.int32, device=dev)
+                     if with_mask else None)
+        self.stats = torch.empty(MS_STATS_WORDS, dtype=torch.int32, device=dev)
+        self.proj = ms_proj_t(_ptr(self.rec), _ptr(self.rect), _ptr(self.n_tiles),
+                              _ptr(self.depth), _ptr(self.cover), _ptr(self.mask),
+                              _ptr(self.stats), nn)
+        self.gauss_idx = torch.empty(dup_capacity, dtype=torch.int32, device=dev)
+        self.ranges = torch.empty(max_tiles * 2, dtype=torch.int32, device=dev)
+        self.counts = torch.zeros(4, dtype=torch.int64, device=dev)
+        self.bins = ms_bins_t(_ptr(self.gauss_idx), _ptr(self.ranges), _ptr(self.counts),
+                              dup_capacity)
+        self.ws_bytes = ms_bin_workspace_bytes(n, max_tiles, dup_capacity)
+        if self.ws_bytes == 0:
+            raise MsError(MS_ERR_INVALID_ARG, "invalid workspace sizes")
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+
+    def images(self, cam: inputs.Camera, device="cuda"):
+        import torch
+        H, W = cam.height, cam.width
+        return (torch.empty((3, H, W), dtype=torch.float32, device=device),
+                torch.empty((H, W), dtype=torch.float32, device=device),
+                torch.empty((H, W), dtype=torch.int32, device=device))
+
+    def render(self, scene: DeviceScene, cam: inputs.Camera, mode="selective", out=None,
+               stream=None, n_eval=None):
+        """Enqueue project -> bin -> raster.  Returns (image, final_t,
+        n_contrib) device tensors; call `check()` after to learn D and
+        whether the capacity sufficed."""
+        if cam.tiles_x * cam.tiles_y > self.max_tiles:
+            raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
+        cs = camera_struct(cam)
+        m = MODES.get(mode, mode)
+        ms_project(scene.struct, cs, m, self.proj, stream)
+        ms_bin(self.proj, scene.n, cs, self.bins, _ptr(self.ws), self.ws_bytes, stream)
+        image, final_t, n_contrib = out if out is not None else self.images(cam)
+        ms_raster(self.proj, self.bins, cs, _ptr(image), _ptr(final_t), _ptr(n_contrib),
+                  _ptr(n_eval), stream)
+        return image, final_t, n_contrib
+
+    def check(self, stream=None):
+        rc, d, s = ms_bin_counts(self.bins, stream)
+        if rc == MS_ERR_CAPACITY:
+            raise MsError(rc, f"tile duplicates {d} exceed capacity {self.dup_capacity}")
+        return d, s
+
+
+def render(scene: inputs.Scene, cam: inputs.Camera, mode="selective", dup_capacity=None):
+    """One-shot convenience: upload, render, return numpy (image, final_t,
+    n_contrib).  Retries once with the exact duplicate count if the first
+    capacity guess was too small."""
+    import torch
+    ds = DeviceScene(scene)
+    cap = dup_capacity or max(1024, 8 * scene.n)
+    for _ in range(2):
+        r = Renderer(scene.n, cam.tiles_x * cam.tiles_y, cap)
+        img, ft, nc = r.render(ds, cam, mode)
+        rc, d, _ = ms_bin_counts(r.bins)
+        if rc == MS_OK:
+            torch.cuda.synchronize()
+            return img.cpu().numpy(), ft.cpu().numpy(), nc.cpu().numpy()
+        cap = d
+    raise MsError(MS_ERR_CAPACITY, "duplicate capacity retry failed")

@@ -1,0 +1,546 @@
+// Tile binning (Sec. 3.1: every 2D Gaussian touching a 16x16 tile is listed
+// for it, and each list is sorted by the Gaussians' view-space depth).
+//
+// Design: instead of one radix sort of D 64-bit (tile, depth) keys, the
+// listed Gaussians are first sorted by their 32-bit depth bits (4 onesweep
+// passes over the N_s survivors; the first pass also compacts them out of
+// the N-long footprint arrays), then expanded to one (tile, index) entry per
+// covered tile in depth order, then stably sorted by tile id (1-2 passes
+// over D entries).  Stability gives every tile's list in (depth, index)
+// order, exactly the order of a (tile, depth, index) sort.
+//
+// Onesweep pass (single-pass LSD radix step): each CTA takes a 4096-item
+// partition by atomic ticket, ranks its items stably per 8-bit digit with
+// warp match, publishes its per-digit counts and obtains the counts of all
+// earlier partitions by decoupled look-back, then scatters through shared
+// memory.  Every wait on another CTA is bounded; a wait that gives up sets
+// a status bit and the CTA carries on, so a kernel can never hang.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace msgs {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortIPT = 16;
+constexpr int kPart = kSortThreads * kSortIPT;  // items per partition
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPre = 2u << 30;
+constexpr uint32_t kFlagMask = 3u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+
+constexpr int kDupThreads = 256;
+constexpr int kDupIPT = 4;
+constexpr int kDupPart = kDupThreads * kDupIPT;
+constexpr unsigned long long kDupFlagAgg = 1ull << 62;
+constexpr unsigned long long kDupFlagPre = 2ull << 62;
+constexpr unsigned long long kDupValMask = (1ull << 62) - 1;
+
+struct PassArgs {
+    const uint32_t *keys_in;
+    const uint32_t *vals_in;    // nullptr: value = item index
+    const uint32_t *filter;     // nullptr, or item valid iff filter[i] > 0
+    uint32_t *keys_out;         // nullptr: keys not written
+    uint32_t *vals_out;
+    const uint32_t *n32;        // device item count (u32) or nullptr
+    const unsigned long long *n64;  // device item count (u64) or nullptr
+    uint64_t n_cap;             // count = min(device count, n_cap); or n_cap alone
+    int shift;
+    const uint32_t *hist;       // [256] digit totals of this pass
+    uint32_t *status;           // [partitions][256]
+    uint32_t *ticket;
+    unsigned long long *err;    // status word (bit kStatusTimeout)
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *s_warp,
+                                                       uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) {
+        uint32_t t = s_warp[w];
+        if (w < warp) wpre += t;
+        total += t;
+    }
+    __syncthreads();
+    return wpre + x - v;
+}
+
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ uint64_t pass_count(const PassArgs &a) {
+    uint64_t n = a.n_cap;
+    if (a.n32) n = umin64(n, *a.n32);
+    if (a.n64) n = umin64(n, *a.n64);
+    return n;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+onesweep_pass(PassArgs a) {
+    __shared__ uint32_t s_whist[kSortWarps][256];
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_excl[256];
+    __shared__ uint32_t s_prefix[256];
+    __shared__ uint32_t s_keys[kPart];
+    __shared__ uint32_t s_vals[kPart];
+    __shared__ uint32_t s_warp[kSortWarps];
+    __shared__ uint32_t s_part;
+    __shared__ uint32_t s_total;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t n = pass_count(a);
+    const uint64_t parts = (n + kPart - 1) / kPart;
+    {
+        uint32_t tot;
+        uint32_t b = block_excl_scan256(a.hist[tid], s_warp, tot);
+        s_base[tid] = b;
+    }
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_part = atomicAdd(a.ticket, 1u);
+        for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+        __syncthreads();
+        const uint32_t p = s_part;
+        if (p >= parts) break;
+        // ---- load and rank (warp-striped, rounds in item order)
+        uint32_t key[kSortIPT], val[kSortIPT], rank[kSortIPT];
+        const uint64_t wbase = (uint64_t)p * kPart + (uint64_t)warp * 32 * kSortIPT;
+#pragma unroll
+        for (int r = 0; r < kSortIPT; r++) {
+            uint64_t i = wbase + (uint64_t)r * 32 + lane;
+            bool valid = i < n;
+            if (valid && a.filter) valid = a.filter[i] > 0;
+            uint32_t k = valid ? a.keys_in[i] : 0u;
+            uint32_t v = valid ? (a.vals_in ? a.vals_in[i] : (uint32_t)i) : 0u;
+            uint32_t d = (k >> a.shift) & 255u;
+            uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u);
+            uint32_t before = 0;
+            if (valid) before = s_whist[warp][d] + __popc(peers & lanemask_lt());
+            __syncwarp();
+            if (valid && lane == 31 - __clz(peers)) s_whist[warp][d] += __popc(peers);
+            __syncwarp();
+            key[r] = k;
+            val[r] = v;
+            rank[r] = valid ? ((d << 16) | before) : 0xffffffffu;
+        }
+        __syncthreads();
+        // ---- per digit: warp prefix, partition count, publish, look back
+        const uint32_t d = tid;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++) {
+            uint32_t c = s_whist[w][d];
+            s_whist[w][d] = run;
+            run += c;
+        }
+        const uint32_t local = run;
+        uint32_t *st = a.status + (uint64_t)p * 256 + d;
+        if (p == 0) {
+            st_release(st, kFlagPre | local);
+            s_prefix[d] = 0;
+        } else {
+            st_release(st, kFlagAgg | local);
+            uint32_t excl = 0;
+            int64_t k = (int64_t)p - 1;
+            uint32_t spins = 0;
+            while (k >= 0) {
+                uint32_t s = ld_acquire(a.status + (uint64_t)k * 256 + d);
+                if ((s & kFlagMask) == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += s & kValMask;
+                if (s & kFlagPre) break;
+                k--;
+            }
+            st_release(st, kFlagPre | ((excl + local) & kValMask));
+            s_prefix[d] = excl;
+        }
+        uint32_t tot;
+        s_excl[d] = block_excl_scan256(local, s_warp, tot);
+        if (tid == 0) s_total = tot;
+        __syncthreads();
+        // ---- stage digit-sorted in shared memory
+#pragma unroll
+        for (int r = 0; r < kSortIPT; r++) {
+            if (rank[r] == 0xffffffffu) continue;
+            uint32_t dd = rank[r] >> 16;
+            uint32_t pos = s_excl[dd] + s_whist[warp][dd] + (rank[r] & 0xffffu);
+            s_keys[pos] = key[r];
+            s_vals[pos] = val[r];
+        }
+        __syncthreads();
+        // ---- coalesced scatter
+        const uint32_t total = s_total;
+        for (uint32_t j = tid; j < total; j += kSortThreads) {
+            uint32_t k = s_keys[j];
+            uint32_t dd = (k >> a.shift) & 255u;
+            uint64_t g = (uint64_t)s_base[dd] + s_prefix[dd] + (j - s_excl[dd]);
+            if (g >= n) {  // only reachable after a wait gave up
+                atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                continue;
+            }
+            if (a.keys_out) a.keys_out[g] = k;
+            a.vals_out[g] = s_vals[j];
+        }
+    }
+}
+
+// Duplication: exclusive scan of n_tiles in depth order (decoupled look-back
+// across partitions), then one (tile id, Gaussian index) entry per covered
+// tile, emitted with a block-wide load-balanced search so writes are
+// contiguous.  Also accumulates the tile-id digit histograms of the
+// following radix passes.
+struct DupArgs {
+    const uint32_t *order;       // Gaussian indices in depth order
+    const uint32_t *n_tiles;
+    const uint2 *rect;
+    const uint32_t *n32;         // survivors (device)
+    uint64_t n_max;              // length of n_tiles / rect
+    int tiles_x;
+    uint32_t tiles;
+    uint64_t cap;
+    uint32_t *keys_out, *vals_out;
+    uint32_t *hist;              // [2][256]
+    unsigned long long *status;  // [partitions]
+    uint32_t *ticket;
+    unsigned long long *err;
+};
+
+__global__ void __launch_bounds__(kDupThreads)
+duplicate_kernel(DupArgs a) {
+    __shared__ uint32_t s_off[kDupPart + 1];
+    __shared__ uint32_t s_idx[kDupPart];
+    __shared__ uint2 s_rect[kDupPart];
+    __shared__ uint32_t s_hist[2][256];
+    __shared__ uint32_t s_warp[kSortWarps];
+    __shared__ uint32_t s_part;
+    __shared__ unsigned long long s_prefix;
+    const int tid = threadIdx.x;
+    const uint64_t n = umin64(*a.n32, a.n_max);
+    const uint64_t parts = (n + kDupPart - 1) / kDupPart;
+    for (int i = tid; i < 512; i += kDupThreads) (&s_hist[0][0])[i] = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_part = atomicAdd(a.ticket, 1u);
+        __syncthreads();
+        const uint32_t p = s_part;
+        if (p >= parts) break;
+        uint32_t nt[kDupIPT];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int r = 0; r < kDupIPT; r++) {
+            uint64_t j = (uint64_t)p * kDupPart + tid * kDupIPT + r;
+            uint32_t g = 0, c = 0;
+            uint2 rc = make_uint2(0, 0);
+            if (j < n) {
+                g = a.order[j];
+                if (g < a.n_max) {
+                    c = a.n_tiles[g];
+                    rc = a.rect[g];
+                } else {
+                    atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                }
+            }
+            s_idx[tid * kDupIPT + r] = g;
+            s_rect[tid * kDupIPT + r] = rc;
+            nt[r] = c;
+            sum += c;
+        }
+        uint32_t total;
+        uint32_t excl = block_excl_scan256(sum, s_warp, total);
+#pragma unroll
+        for (int r = 0; r < kDupIPT; r++) {
+            s_off[tid * kDupIPT + r] = excl;
+            excl += nt[r];
+        }
+        if (tid == 0) {
+            s_off[kDupPart] = total;
+            unsigned long long *st = a.status + p;
+            unsigned long long pre = 0;
+            if (p == 0) {
+                st_release64(st, kDupFlagPre | total);
+            } else {
+                st_release64(st, kDupFlagAgg | total);
+                int64_t k = (int64_t)p - 1;
+                uint32_t spins = 0;
+                while (k >= 0) {
+                    unsigned long long s = ld_acquire64(a.status + k);
+                    if ((s >> 62) == 0) {
+                        if (++spins > kSpinLimit) {
+                            atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    pre += s & kDupValMask;
+                    if (s & kDupFlagPre) break;
+                    k--;
+                }
+                st_release64(st, kDupFlagPre | ((pre + total) & kDupValMask));
+            }
+            s_prefix = pre;
+        }
+        __syncthreads();
+        const uint64_t base = s_prefix;
+        for (uint32_t k = tid; k < total; k += kDupThreads) {
+            // last item whose offset is <= k
+            int lo = 0, hi = kDupPart;  // invariant s_off[lo] <= k < s_off[hi]
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (s_off[mid] <= k) lo = mid;
+                else hi = mid;
+            }
+            uint32_t m = k - s_off[lo];
+            uint2 rc = s_rect[lo];
+            uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+            uint32_t w = x1 - x0 + 1;
+            uint32_t tile = (y0 + m / w) * (uint32_t)a.tiles_x + x0 + m % w;
+            uint64_t g = base + k;
+            if (tile >= a.tiles) {
+                atomicOr(a.err, (unsigned long long)kStatusTimeout);
+            } else if (g < a.cap) {
+                a.keys_out[g] = tile;
+                a.vals_out[g] = s_idx[lo];
+                atomicAdd(&s_hist[0][tile & 255u], 1u);
+                atomicAdd(&s_hist[1][(tile >> 8) & 255u], 1u);
+            } else {
+                atomicOr(a.err, (unsigned long long)kStatusOverflow);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < 512; i += kDupThreads) {
+        uint32_t v = (&s_hist[0][0])[i];
+        if (v) atomicAdd(&a.hist[i], v);
+    }
+}
+
+// [start, end) of every tile's run in the tile-sorted keys.
+__global__ void ranges_kernel(const uint32_t *__restrict__ keys,
+                              const unsigned long long *__restrict__ dup, uint64_t cap,
+                              uint32_t tiles, uint32_t *__restrict__ ranges) {
+    const uint64_t n = umin64(*dup, cap);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t k = keys[i];
+        if (k >= tiles) continue;
+        if (i == 0 || keys[i - 1] != k) ranges[2 * (uint64_t)k] = (uint32_t)i;
+        if (i + 1 == n || keys[i + 1] != k) ranges[2 * (uint64_t)k + 1] = (uint32_t)(i + 1);
+    }
+}
+
+__global__ void finish_counts_kernel(const uint32_t *__restrict__ stats,
+                                     unsigned long long *__restrict__ counts,
+                                     uint64_t cap) {
+    unsigned long long d = *reinterpret_cast<const unsigned long long *>(stats + kStatDup);
+    counts[kCntDup] = d;
+    counts[kCntSurvivors] = stats[kStatSurvivors];
+    if (d > cap) atomicOr(counts + kCntStatus, (unsigned long long)kStatusOverflow);
+}
+
+// ------------------------------------------------------------ workspace
+
+struct BinLayout {
+    size_t dkeys_a, dvals_a, dkeys_b, dvals_b;
+    size_t tkeys_a, tvals_a, tkeys_b, tvals_b;
+    size_t zero_begin;  // everything from here to total is zeroed per call
+    size_t tickets, thist, dup_status, dstatus, tstatus;
+    size_t total;
+    int64_t dparts, tparts, dupparts;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static bool layout(int64_t n, int64_t cap, BinLayout &L) {
+    if (n < 0 || n > INT32_MAX || cap < 1 || cap > (1ll << 30)) return false;
+    int64_t nn = n > 0 ? n : 1;
+    L.dparts = ceil_div(nn, kPart);
+    L.tparts = ceil_div(cap, kPart);
+    L.dupparts = ceil_div(nn, kDupPart);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    L.dkeys_a = take(nn * 4);
+    L.dvals_a = take(nn * 4);
+    L.dkeys_b = take(nn * 4);
+    L.dvals_b = take(nn * 4);
+    L.tkeys_a = take(cap * 4);
+    L.tvals_a = take(cap * 4);
+    L.tkeys_b = take(cap * 4);
+    L.tvals_b = take(cap * 4);
+    L.zero_begin = o;
+    L.tickets = take(16 * 4);
+    L.thist = take(512 * 4);
+    L.dup_status = take(L.dupparts * 8);
+    L.dstatus = take((size_t)4 * L.dparts * 256 * 4);
+    L.tstatus = take((size_t)2 * L.tparts * 256 * 4);
+    L.total = o;
+    return true;
+}
+
+}  // namespace msgs
+
+using namespace msgs;
+
+extern "C" size_t ms_bin_workspace_bytes(int64_t n, int64_t tiles, int64_t dup_capacity) {
+    BinLayout L;
+    if (tiles < 1 || tiles > 65536 || !layout(n, dup_capacity, L)) return 0;
+    return L.total;
+}
+
+extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
+                      const ms_bins_t *out, void *ws, size_t ws_bytes, void *stream) {
+    if (!proj || !out || !cam) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+        return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
+    const int tiles_x = (cam->width + 15) / 16, tiles_y = (cam->height + 15) / 16;
+    const int64_t tiles = (int64_t)tiles_x * tiles_y;
+    if (tiles > 65536) return fail(MS_ERR_INVALID_ARG, "more than 65536 tiles");
+    BinLayout L;
+    if (!layout(n, out->dup_capacity, L))
+        return fail(MS_ERR_INVALID_ARG, "n or dup_capacity out of range");
+    if (!ws || ws_bytes < L.total || !aligned(ws, 16))
+        return fail(MS_ERR_INVALID_ARG, "workspace missing, too small or misaligned");
+    if (!out->gauss_idx || !out->ranges || !out->counts || !aligned(out->counts, 8))
+        return fail(MS_ERR_INVALID_ARG, "ms_bins_t has a NULL or misaligned buffer");
+    if (n > 0 && (!proj->n_tiles || !proj->depth || !proj->rect || !proj->stats))
+        return fail(MS_ERR_INVALID_ARG, "ms_proj_t has a NULL buffer");
+    if (proj->n < n) return fail(MS_ERR_INVALID_ARG, "ms_proj_t holds fewer Gaussians than n");
+    cudaStream_t st = as_stream(stream);
+    char *w = static_cast<char *>(ws);
+    int rc;
+    if ((rc = cuda_check(cudaMemsetAsync(w + L.zero_begin, 0, L.total - L.zero_begin, st),
+                         "workspace memset")))
+        return rc;
+    if ((rc = cuda_check(cudaMemsetAsync(out->ranges, 0, (size_t)tiles * 2 * sizeof(uint32_t), st),
+                         "ranges memset")))
+        return rc;
+    if ((rc = cuda_check(cudaMemsetAsync(out->counts, 0, 4 * sizeof(uint64_t), st), "counts memset")))
+        return rc;
+    if (n == 0) return MS_OK;
+    auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(w + off); };
+    uint32_t *tickets = U32(L.tickets);
+    unsigned long long *err = reinterpret_cast<unsigned long long *>(out->counts) + kCntStatus;
+    const int per_sm = 2;
+    const int sms = num_sms();
+
+    finish_counts_kernel<<<1, 1, 0, st>>>(proj->stats, reinterpret_cast<unsigned long long *>(out->counts),
+                                          (uint64_t)out->dup_capacity);
+    // ---- depth sort: 4 passes over the listed Gaussians
+    const uint32_t *survivors = proj->stats + kStatSurvivors;
+    const unsigned long long *dup64 =
+        reinterpret_cast<const unsigned long long *>(proj->stats + kStatDup);
+    uint32_t *dk[2] = {U32(L.dkeys_a), U32(L.dkeys_b)};
+    uint32_t *dv[2] = {U32(L.dvals_a), U32(L.dvals_b)};
+    int dgrid = (int)std::min<int64_t>(L.dparts, (int64_t)sms * per_sm);
+    for (int pass = 0; pass < 4; pass++) {
+        PassArgs a;
+        a.keys_in = pass == 0 ? proj->depth : dk[(pass - 1) & 1];
+        a.vals_in = pass == 0 ? nullptr : dv[(pass - 1) & 1];
+        a.filter = pass == 0 ? proj->n_tiles : nullptr;
+        a.keys_out = pass == 3 ? nullptr : dk[pass & 1];
+        a.vals_out = dv[pass & 1];
+        a.n32 = pass == 0 ? nullptr : survivors;
+        a.n64 = nullptr;
+        a.n_cap = (uint64_t)n;
+        a.shift = 8 * pass;
+        a.hist = proj->stats + kStatHist + 256 * pass;
+        a.status = U32(L.dstatus) + (size_t)pass * L.dparts * 256;
+        a.ticket = tickets + pass;
+        a.err = err;
+        onesweep_pass<<<dgrid, kSortThreads, 0, st>>>(a);
+    }
+    // after 4 passes (out: a, b, a, b) the depth-ordered indices are in dv[1]
+    // ---- duplicate into (tile, index) entries
+    DupArgs da;
+    da.order = dv[1];
+    da.n_tiles = proj->n_tiles;
+    da.rect = reinterpret_cast<const uint2 *>(proj->rect);
+    da.n32 = survivors;
+    da.n_max = (uint64_t)n;
+    da.tiles_x = tiles_x;
+    da.tiles = (uint32_t)tiles;
+    da.cap = (uint64_t)out->dup_capacity;
+    da.keys_out = U32(L.tkeys_a);
+    da.vals_out = U32(L.tvals_a);
+    da.hist = U32(L.thist);
+    da.status = reinterpret_cast<unsigned long long *>(w + L.dup_status);
+    da.ticket = tickets + 4;
+    da.err = err;
+    int dupgrid = (int)std::min<int64_t>(L.dupparts, (int64_t)sms * 4);
+    duplicate_kernel<<<dupgrid, kDupThreads, 0, st>>>(da);
+    // ---- stable sort by tile id
+    const int tpasses = tiles <= 256 ? 1 : 2;
+    int tgrid = (int)std::min<int64_t>(L.tparts, (int64_t)sms * per_sm);
+    uint32_t *final_keys = U32(L.tkeys_b);
+    for (int pass = 0; pass < tpasses; pass++) {
+        PassArgs a;
+        a.keys_in = pass == 0 ? U32(L.tkeys_a) : U32(L.tkeys_b);
+        a.vals_in = pass == 0 ? U32(L.tvals_a) : U32(L.tvals_b);
+        a.filter = nullptr;
+        bool last = pass == tpasses - 1;
+        a.keys_out = pass == 0 ? U32(L.tkeys_b) : U32(L.tkeys_a);
+        a.vals_out = last ? out->gauss_idx : U32(L.tvals_b);
+        final_keys = a.keys_out;
+        a.n32 = nullptr;
+        a.n64 = dup64;
+        a.n_cap = (uint64_t)out->dup_capacity;
+        a.shift = 8 * pass;
+        a.hist = U32(L.thist) + 256 * pass;
+        a.status = U32(L.tstatus) + (size_t)pass * L.tparts * 256;
+        a.ticket = tickets + 5 + pass;
+        a.err = err;
+        onesweep_pass<<<tgrid, kSortThreads, 0, st>>>(a);
+    }
+    ranges_kernel<<<sms * 4, 256, 0, st>>>(final_keys, dup64, (uint64_t)out->dup_capacity,
+                                           (uint32_t)tiles, out->ranges);
+    return cuda_check(cudaGetLastError(), "ms_bin launches");
+}
+
+extern "C" int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed, int64_t *survivors,
+                             void *stream) {
+    if (!bins || !bins->counts) return fail(MS_ERR_INVALID_ARG, "NULL bins");
+    uint64_t h[4];
+    cudaStream_t st = as_stream(stream);
+    int rc;
+    if ((rc = cuda_check(cudaMemcpyAsync(h, bins->counts, sizeof(h), cudaMemcpyDeviceToHost, st),
+                         "counts copy")))
+        return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(st), "stream sync"))) return rc;
+    if (d_needed) *d_needed = (int64_t)h[kCntDup];
+    if (survivors) *survivors = (int64_t)h[kCntSurvivors];
+    if (h[kCntStatus] & kStatusTimeout)
+        return fail(MS_ERR_TIMEOUT, "a bounded device wait gave up during ms_bin");
+    if (h[kCntStatus] & kStatusOverflow)
+        return fail(MS_ERR_CAPACITY, "tile duplicates exceed dup_capacity");
+    return MS_OK;
+}

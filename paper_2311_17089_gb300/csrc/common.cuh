@@ -1,0 +1,71 @@
+// Internal helpers of libmsgs (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "msgs.h"
+
+namespace msgs {
+
+// ---------------------------------------------------------------- errors
+int fail(int code, const std::string &msg);  // records msg, returns code
+int cuda_check(cudaError_t e, const char *what);
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+bool aligned(const void *p, size_t a);
+
+// ------------------------------------------- single-rounding FP32 operations
+// Each is exactly one IEEE-754 round-to-nearest operation; the compiler may
+// not fuse or reorder them, which keeps the footprint reproducible
+// bit-for-bit by any implementation doing the same operations in order.
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
+
+// ----------------------------------------------------------- stats layout
+// ms_proj_t::stats words
+constexpr int kStatSurvivors = 0;  // uint32 listed Gaussians
+constexpr int kStatDup = 2;        // uint64 (words 2-3) sum of n_tiles
+constexpr int kStatHist = 16;      // 4 x 256 uint32 depth-digit histograms
+static_assert(kStatHist + 1024 <= MS_STATS_WORDS, "stats layout");
+
+// ms_bins_t::counts words (uint64)
+constexpr int kCntDup = 0;
+constexpr int kCntSurvivors = 1;
+constexpr int kCntStatus = 2;
+constexpr uint64_t kStatusOverflow = 1;
+constexpr uint64_t kStatusTimeout = 2;
+
+// Raster record: three float4 per Gaussian.
+//   r0 = (ux, uy, conic a, conic b)
+//   r1 = (conic c, opacity, r, g)
+//   r2 = (b, 0, 0, 0)
+constexpr int kRecFloats = 12;
+
+// Bounded waits: spin iterations before giving up (each ~100 ns).
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int num_sms();
+
+}  // namespace msgs

@@ -1,0 +1,507 @@
+// Per-Gaussian kernels: scene activations, splat + coverage + selection
+// (the K1 "project" stage), stand-alone selection and UpdateRange.
+//
+// The footprint below performs the operations of the FP32 footprint
+// definition in a fixed order with single-rounding intrinsics, so masks,
+// coverage, depth keys and tile rectangles are reproducible bit-for-bit.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace msgs {
+
+struct CamK {
+    float W[9], t[3], campos[3];
+    float fx, fy, cx, cy, near_plane;
+    int width, height, tiles_x, tiles_y;
+};
+
+static CamK make_cam(const ms_camera_t &c) {
+    CamK k;
+    for (int i = 0; i < 9; i++) k.W[i] = c.R[i];
+    for (int i = 0; i < 3; i++) {
+        k.t[i] = c.t[i];
+        k.campos[i] = c.campos[i];
+    }
+    k.fx = c.fx;
+    k.fy = c.fy;
+    k.cx = c.cx;
+    k.cy = c.cy;
+    k.near_plane = c.near_plane;
+    k.width = c.width;
+    k.height = c.height;
+    k.tiles_x = (c.width + 15) / 16;
+    k.tiles_y = (c.height + 15) / 16;
+    return k;
+}
+
+struct Foot {
+    bool valid;
+    float S, ux, uy, ca, cb, cc;
+    uint32_t depth;
+    int x0, y0, x1, y1;
+    uint32_t ntiles;
+};
+
+__device__ __forceinline__ bool fin(float v) { return isfinite(v); }
+
+// FP32 footprint (Sec. 3.1 EWA splat, Eq. 4 dilation by 0.3 px^2,
+// Sec. 4.1 pixel coverage, Sec. 3.1 16x16 tiles).
+__device__ __forceinline__ void footprint(const float m[3], const float s[3],
+                                          float4 q, float L, const CamK &c,
+                                          Foot &o) {
+    o.valid = false;
+    o.S = -1.0f;
+    o.ntiles = 0;
+    o.x0 = o.y0 = 0;
+    o.x1 = o.y1 = -1;
+    const float *W = c.W;
+    float tx = fa(fa(fa(fm(W[0], m[0]), fm(W[1], m[1])), fm(W[2], m[2])), c.t[0]);
+    float ty = fa(fa(fa(fm(W[3], m[0]), fm(W[4], m[1])), fm(W[5], m[2])), c.t[1]);
+    float tz = fa(fa(fa(fm(W[6], m[0]), fm(W[7], m[1])), fm(W[8], m[2])), c.t[2]);
+    o.depth = __float_as_uint(tz);
+    float n2 = fa(fa(fa(fm(q.x, q.x), fm(q.y, q.y)), fm(q.z, q.z)), fm(q.w, q.w));
+    if (!(L > 0.0f) || !fin(L) || !(tz > c.near_plane) || !fin(tz) ||
+        !(n2 > 0.0f) || !fin(n2))
+        return;
+    float rn = fdv(1.0f, fsq(n2));
+    float w = fm(q.x, rn), x = fm(q.y, rn), y = fm(q.z, rn), z = fm(q.w, rn);
+    float xx = fm(x, x), yy = fm(y, y), zz = fm(z, z);
+    float xy = fm(x, y), xz = fm(x, z), yz = fm(y, z);
+    float wx = fm(w, x), wy = fm(w, y), wz = fm(w, z);
+    float R[9];
+    R[0] = fs(1.0f, fm(2.0f, fa(yy, zz)));
+    R[1] = fm(2.0f, fs(xy, wz));
+    R[2] = fm(2.0f, fa(xz, wy));
+    R[3] = fm(2.0f, fa(xy, wz));
+    R[4] = fs(1.0f, fm(2.0f, fa(xx, zz)));
+    R[5] = fm(2.0f, fs(yz, wx));
+    R[6] = fm(2.0f, fs(xz, wy));
+    R[7] = fm(2.0f, fa(yz, wx));
+    R[8] = fs(1.0f, fm(2.0f, fa(xx, yy)));
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) M[3 * r + k] = fm(R[3 * r + k], s[k]);
+    float S3[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int k = r; k < 3; k++) {
+            float v = fa(fa(fm(M[3 * r], M[3 * k]), fm(M[3 * r + 1], M[3 * k + 1])),
+                         fm(M[3 * r + 2], M[3 * k + 2]));
+            S3[3 * r + k] = v;
+            S3[3 * k + r] = v;
+        }
+    float limx = fm(1.3f, fdv(fm(0.5f, (float)c.width), c.fx));
+    float limy = fm(1.3f, fdv(fm(0.5f, (float)c.height), c.fy));
+    float xr = fdv(tx, tz), yr = fdv(ty, tz);
+    float xc = fminf(limx, fmaxf(-limx, xr));
+    float yc = fminf(limy, fmaxf(-limy, yr));
+    float J00 = fdv(c.fx, tz);
+    float J02 = fdv(-fm(c.fx, xc), tz);
+    float J11 = fdv(c.fy, tz);
+    float J12 = fdv(-fm(c.fy, yc), tz);
+    float T[6];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        T[k] = fa(fm(J00, W[k]), fm(J02, W[6 + k]));
+        T[3 + k] = fa(fm(J11, W[3 + k]), fm(J12, W[6 + k]));
+    }
+    float U[6];
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            U[3 * r + k] = fa(fa(fm(T[3 * r], S3[k]), fm(T[3 * r + 1], S3[3 + k])),
+                              fm(T[3 * r + 2], S3[6 + k]));
+    float V00 = fa(fa(fm(U[0], T[0]), fm(U[1], T[1])), fm(U[2], T[2]));
+    float V01 = fa(fa(fm(U[0], T[3]), fm(U[1], T[4])), fm(U[2], T[5]));
+    float V11 = fa(fa(fm(U[3], T[3]), fm(U[4], T[4])), fm(U[5], T[5]));
+    float a = fa(V00, 0.3f), b = V01, cc = fa(V11, 0.3f);
+    float detd = fs(fm(a, cc), fm(b, b));
+    float ux = fa(fm(c.fx, xr), c.cx);
+    float uy = fa(fm(c.fy, yr), c.cy);
+    if (!fin(V00) || !fin(V01) || !fin(V11) || !(detd > 0.0f) || !fin(detd) ||
+        !fin(ux) || !fin(uy))
+        return;
+    o.valid = true;
+    float det = fs(fm(V00, V11), fm(V01, V01));
+    float mx = fmaxf(V00, V11);
+    float S = 0.0f;
+    if (det > 0.0f && mx > 0.0f) S = fsq(fdv(fm(fm(8.0f, L), det), mx));
+    o.S = S;
+    o.ux = ux;
+    o.uy = uy;
+    o.ca = fdv(cc, detd);
+    o.cb = fdv(-b, detd);
+    o.cc = fdv(a, detd);
+    float ex = fsq(fm(fm(2.0f, L), a));
+    float ey = fsq(fm(fm(2.0f, L), cc));
+    float x0 = floorf(fm(fs(ux, ex), 0.0625f)), x1 = floorf(fm(fa(ux, ex), 0.0625f));
+    float y0 = floorf(fm(fs(uy, ey), 0.0625f)), y1 = floorf(fm(fa(uy, ey), 0.0625f));
+    x0 = fmaxf(x0, 0.0f);
+    y0 = fmaxf(y0, 0.0f);
+    x1 = fminf(x1, (float)(c.tiles_x - 1));
+    y1 = fminf(y1, (float)(c.tiles_y - 1));
+    if (x0 <= x1 && y0 <= y1) {
+        o.x0 = (int)x0;
+        o.y0 = (int)y0;
+        o.x1 = (int)x1;
+        o.y1 = (int)y1;
+        o.ntiles = (uint32_t)((o.x1 - o.x0 + 1) * (o.y1 - o.y0 + 1));
+    }
+}
+
+// Eq. 6 (S_rel^max = 1.5, S_rel^min = 0.5, S_T = 2 px) with the level
+// exemptions of Sec. 4.1: the finest level is never dropped as too large,
+// the coarsest never as too small.
+__device__ __forceinline__ bool select_pred(float S, int level, int n_levels,
+                                            float smax, float smin, int mode) {
+    if (mode == MS_ALL_LEVELS) return true;
+    bool small_ok = (fdv(S, smin) >= 0.5f) || (S >= 2.0f);
+    if (mode == MS_FILTER_SMALL) return small_ok;
+    bool large_ok = (level == 1) || (fdv(S, smax) <= 1.5f);
+    return large_ok && ((level == n_levels) || small_ok);
+}
+
+// Real SH basis to degree 3 (orthonormal, k = l^2 + l + m), colour =
+// max(0, sum_k f_k Y_k + 0.5) per channel; coef is [K][3].
+template <int DEG>
+__device__ __forceinline__ float3 sh_color(const float *__restrict__ coef, float dx,
+                                           float dy, float dz) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float c[3 * K];
+    if constexpr ((3 * K) % 4 == 0) {
+        const float4 *src = reinterpret_cast<const float4 *>(coef);
+#pragma unroll
+        for (int k = 0; k < (3 * K) / 4; k++) {
+            float4 v = __ldg(src + k);
+            c[4 * k] = v.x;
+            c[4 * k + 1] = v.y;
+            c[4 * k + 2] = v.z;
+            c[4 * k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3 * K; k++) c[k] = __ldg(coef + k);
+    }
+    float r = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    float x = dx * r, y = dy * r, z = dz * r;
+    float Y[K];
+    Y[0] = 0.28209479177387814f;
+    if constexpr (DEG >= 1) {
+        Y[1] = 0.4886025119029199f * y;
+        Y[2] = 0.4886025119029199f * z;
+        Y[3] = 0.4886025119029199f * x;
+    }
+    if constexpr (DEG >= 2) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;
+        Y[5] = 1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+        Y[7] = 1.0925484305920792f * x * z;
+        Y[8] = 0.5462742152960396f * (xx - yy);
+        if constexpr (DEG >= 3) {
+            Y[9] = 0.5900435899266435f * y * (3.0f * xx - yy);
+            Y[10] = 2.890611442640554f * x * y * z;
+            Y[11] = 0.4570457994644658f * y * (4.0f * zz - xx - yy);
+            Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = 0.4570457994644658f * x * (4.0f * zz - xx - yy);
+            Y[14] = 1.445305721320277f * z * (xx - yy);
+            Y[15] = 0.5900435899266435f * x * (xx - 3.0f * yy);
+        }
+    }
+    float3 out = make_float3(0.5f, 0.5f, 0.5f);
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        out.x = fmaf(c[3 * k + 0], Y[k], out.x);
+        out.y = fmaf(c[3 * k + 1], Y[k], out.y);
+        out.z = fmaf(c[3 * k + 2], Y[k], out.z);
+    }
+    out.x = fmaxf(out.x, 0.0f);
+    out.y = fmaxf(out.y, 0.0f);
+    out.z = fmaxf(out.z, 0.0f);
+    return out;
+}
+
+__device__ __forceinline__ float3 gaussian_color(const float *__restrict__ color, int deg,
+                                                 int64_t i, float dx, float dy, float dz) {
+    switch (deg) {
+    case 0: return sh_color<0>(color + i * 3, dx, dy, dz);
+    case 1: return sh_color<1>(color + i * 12, dx, dy, dz);
+    case 2: return sh_color<2>(color + i * 27, dx, dy, dz);
+    case 3: return sh_color<3>(color + i * 48, dx, dy, dz);
+    default:
+        return make_float3(__ldg(color + 3 * i), __ldg(color + 3 * i + 1), __ldg(color + 3 * i + 2));
+    }
+}
+
+// ------------------------------------------------------------- kernels
+
+__global__ void prepare_kernel(int64_t n, const float *__restrict__ log_scale,
+                               const float *__restrict__ opacity,
+                               float *__restrict__ scale, float *__restrict__ lnop) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < 3; k++)
+            scale[3 * i + k] = (float)exp((double)log_scale[3 * i + k]);
+        lnop[i] = (float)log(255.0 * (double)opacity[i]);
+    }
+}
+
+struct SceneK {
+    int64_t n;
+    int n_levels, sh_degree;
+    const float *mean, *quat, *opacity, *color, *scale, *lnop;
+    const uint8_t *level;
+    const float *s_max, *s_min;
+};
+
+static SceneK make_scene(const ms_scene_t &s) {
+    SceneK k;
+    k.n = s.n;
+    k.n_levels = s.n_levels;
+    k.sh_degree = s.sh_degree;
+    k.mean = s.mean;
+    k.quat = s.quat;
+    k.opacity = s.opacity;
+    k.color = s.color;
+    k.scale = s.scale;
+    k.lnop = s.lnop;
+    k.level = s.level;
+    k.s_max = s.s_max;
+    k.s_min = s.s_min;
+    return k;
+}
+
+constexpr int kProjThreads = 256;
+
+// K1: one thread per Gaussian (grid-stride), writes the footprint outputs,
+// the raster record of listed Gaussians, and accumulates the survivor
+// count, the duplicate count and the four depth-digit histograms that the
+// binning stage's radix sort needs.
+__global__ void __launch_bounds__(kProjThreads)
+project_kernel(SceneK sc, CamK cam, int mode, float4 *__restrict__ rec,
+               uint2 *__restrict__ rect, uint32_t *__restrict__ n_tiles,
+               uint32_t *__restrict__ depth, float *__restrict__ cover,
+               uint32_t *__restrict__ mask, uint32_t *__restrict__ stats) {
+    __shared__ uint32_t s_hist[4][256];
+    __shared__ uint32_t s_surv;
+    __shared__ unsigned long long s_dup;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+    if (threadIdx.x == 0) {
+        s_surv = 0;
+        s_dup = 0;
+    }
+    __syncthreads();
+    uint32_t my_surv = 0;
+    unsigned long long my_dup = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // all threads of a warp iterate together so warp ballots stay full
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < sc.n; base += stride) {
+        int64_t i = base + threadIdx.x;
+        bool in = i < sc.n;
+        Foot f;
+        f.valid = false;
+        f.ntiles = 0;
+        f.S = -1.0f;
+        bool sel = false;
+        if (in) {
+            float m[3] = {sc.mean[3 * i], sc.mean[3 * i + 1], sc.mean[3 * i + 2]};
+            float s[3] = {sc.scale[3 * i], sc.scale[3 * i + 1], sc.scale[3 * i + 2]};
+            float4 q = reinterpret_cast<const float4 *>(sc.quat)[i];
+            footprint(m, s, q, sc.lnop[i], cam, f);
+            if (f.valid)
+                sel = select_pred(f.S, sc.level[i], sc.n_levels, sc.s_max[i],
+                                  sc.s_min[i], mode);
+            bool listed = sel && f.ntiles > 0;
+            n_tiles[i] = listed ? f.ntiles : 0u;
+            if (cover) cover[i] = f.S;
+            if (listed) {
+                float op = sc.opacity[i];
+                float3 col = gaussian_color(sc.color, sc.sh_degree, i, m[0] - cam.campos[0],
+                                            m[1] - cam.campos[1], m[2] - cam.campos[2]);
+                rec[3 * i + 0] = make_float4(f.ux, f.uy, f.ca, f.cb);
+                rec[3 * i + 1] = make_float4(f.cc, op, col.x, col.y);
+                rec[3 * i + 2] = make_float4(col.z, 0.0f, 0.0f, 0.0f);
+                rect[i] = make_uint2((uint32_t)f.x0 | ((uint32_t)f.y0 << 16),
+                                     (uint32_t)f.x1 | ((uint32_t)f.y1 << 16));
+                depth[i] = f.depth;
+                my_surv++;
+                my_dup += f.ntiles;
+                atomicAdd(&s_hist[0][f.depth & 255], 1u);
+                atomicAdd(&s_hist[1][(f.depth >> 8) & 255], 1u);
+                atomicAdd(&s_hist[2][(f.depth >> 16) & 255], 1u);
+                atomicAdd(&s_hist[3][f.depth >> 24], 1u);
+            }
+        }
+        if (mask) {
+            uint32_t bits = __ballot_sync(0xffffffffu, in && sel);
+            if ((threadIdx.x & 31) == 0 && in) mask[i >> 5] = bits;
+        }
+    }
+    // block reduction of the counters
+    for (int o = 16; o > 0; o >>= 1) {
+        my_surv += __shfl_xor_sync(0xffffffffu, my_surv, o);
+        my_dup += __shfl_xor_sync(0xffffffffu, my_dup, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (my_surv) atomicAdd(&s_surv, my_surv);
+        if (my_dup) atomicAdd(&s_dup, my_dup);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
+        uint32_t v = (&s_hist[0][0])[k];
+        if (v) atomicAdd(&stats[kStatHist + k], v);
+    }
+    if (threadIdx.x == 0) {
+        if (s_surv) atomicAdd(&stats[kStatSurvivors], s_surv);
+        if (s_dup)
+            atomicAdd(reinterpret_cast<unsigned long long *>(stats + kStatDup), s_dup);
+    }
+}
+
+__global__ void select_kernel(int64_t n, const float *__restrict__ cover,
+                              const uint8_t *__restrict__ level, int n_levels,
+                              const float *__restrict__ smax,
+                              const float *__restrict__ smin, int mode,
+                              uint32_t *__restrict__ mask) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        int64_t i = base + threadIdx.x;
+        bool sel = false;
+        if (i < n) {
+            float S = cover[i];
+            sel = (S >= 0.0f) && select_pred(S, level[i], n_levels, smax[i], smin[i], mode);
+        }
+        uint32_t bits = __ballot_sync(0xffffffffu, sel);
+        if ((threadIdx.x & 31) == 0 && i < n) mask[i >> 5] = bits;
+    }
+}
+
+// Eq. 5: S_max' = max(0.95 S_max, S), S_min' = min(1.05 S_min, S) for the
+// Gaussians of level_r that are valid and touch the image.
+__global__ void update_range_kernel(SceneK sc, CamK cam, int level_r,
+                                    float *__restrict__ smax,
+                                    float *__restrict__ smin) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sc.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (sc.level[i] != level_r) continue;
+        float m[3] = {sc.mean[3 * i], sc.mean[3 * i + 1], sc.mean[3 * i + 2]};
+        float s[3] = {sc.scale[3 * i], sc.scale[3 * i + 1], sc.scale[3 * i + 2]};
+        float4 q = reinterpret_cast<const float4 *>(sc.quat)[i];
+        Foot f;
+        footprint(m, s, q, sc.lnop[i], cam, f);
+        if (!f.valid || f.ntiles == 0) continue;
+        smax[i] = fmaxf(fm(0.95f, smax[i]), f.S);
+        smin[i] = fminf(fm(1.05f, smin[i]), f.S);
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+static int check_scene(const ms_scene_t *s, bool need_prepared) {
+    if (!s) return fail(MS_ERR_INVALID_ARG, "scene is NULL");
+    if (s->n < 0 || s->n > INT32_MAX) return fail(MS_ERR_INVALID_ARG, "scene n out of range");
+    if (s->n == 0) return MS_OK;
+    if (!s->mean || !s->quat || !s->opacity || !s->level)
+        return fail(MS_ERR_INVALID_ARG, "scene has a NULL array");
+    if (!aligned(s->quat, 16)) return fail(MS_ERR_INVALID_ARG, "quat must be 16-byte aligned");
+    if (s->n_levels < 1 || s->n_levels > 255)
+        return fail(MS_ERR_INVALID_ARG, "n_levels must be in 1..255");
+    if (s->sh_degree < -1 || s->sh_degree > 3)
+        return fail(MS_ERR_INVALID_ARG, "sh_degree must be in -1..3");
+    if (!s->color) return fail(MS_ERR_INVALID_ARG, "scene color is NULL");
+    if (s->sh_degree >= 0 && !aligned(s->color, 16))
+        return fail(MS_ERR_INVALID_ARG, "SH coefficients must be 16-byte aligned");
+    if (!s->s_max || !s->s_min) return fail(MS_ERR_INVALID_ARG, "s_max/s_min is NULL");
+    if (need_prepared && (!s->scale || !s->lnop))
+        return fail(MS_ERR_INVALID_ARG, "scene scale/lnop is NULL (run ms_scene_prepare)");
+    return MS_OK;
+}
+
+static int check_cam(const ms_camera_t *c) {
+    if (!c) return fail(MS_ERR_INVALID_ARG, "camera is NULL");
+    if (c->width < 1 || c->height < 1 || c->width > 32768 || c->height > 32768)
+        return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
+    if (!(c->near_plane > 0.0f)) return fail(MS_ERR_INVALID_ARG, "near_plane must be > 0");
+    if (!(c->fx > 0.0f) || !(c->fy > 0.0f)) return fail(MS_ERR_INVALID_ARG, "focal length must be > 0");
+    return MS_OK;
+}
+
+static int grid_for(int64_t n, int threads, int per_sm) {
+    int64_t g = ceil_div(n, threads);
+    int64_t cap = (int64_t)num_sms() * per_sm;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace msgs
+
+using namespace msgs;
+
+extern "C" int ms_scene_prepare(const ms_scene_t *scene, void *stream) {
+    if (!scene) return fail(MS_ERR_INVALID_ARG, "scene is NULL");
+    if (scene->n < 0 || scene->n > INT32_MAX) return fail(MS_ERR_INVALID_ARG, "scene n out of range");
+    if (scene->n == 0) return MS_OK;
+    if (!scene->log_scale || !scene->opacity || !scene->scale || !scene->lnop)
+        return fail(MS_ERR_INVALID_ARG, "scene log_scale/opacity/scale/lnop is NULL");
+    prepare_kernel<<<grid_for(scene->n, 256, 8), 256, 0, as_stream(stream)>>>(
+        scene->n, scene->log_scale, scene->opacity, scene->scale, scene->lnop);
+    return cuda_check(cudaGetLastError(), "prepare_kernel launch");
+}
+
+extern "C" int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
+                          ms_mode_t mode, const ms_proj_t *out, void *stream) {
+    int rc = check_scene(scene, true);
+    if (rc) return rc;
+    if ((rc = check_cam(cam))) return rc;
+    if (mode != MS_SELECTIVE && mode != MS_ALL_LEVELS && mode != MS_FILTER_SMALL)
+        return fail(MS_ERR_INVALID_ARG, "unknown mode");
+    if (!out || !out->rec || !out->rect || !out->n_tiles || !out->depth || !out->stats)
+        return fail(MS_ERR_INVALID_ARG, "ms_proj_t has a NULL required buffer");
+    if (out->n < scene->n) return fail(MS_ERR_INVALID_ARG, "ms_proj_t holds fewer Gaussians than the scene");
+    if (!aligned(out->rec, 16) || !aligned(out->rect, 8) || !aligned(out->stats, 16))
+        return fail(MS_ERR_INVALID_ARG, "rec must be 16-B, rect 8-B, stats 16-B aligned");
+    cudaStream_t st = as_stream(stream);
+    if ((rc = cuda_check(cudaMemsetAsync(out->stats, 0, MS_STATS_WORDS * sizeof(uint32_t), st),
+                         "stats memset")))
+        return rc;
+    if (scene->n == 0) return MS_OK;
+    project_kernel<<<grid_for(scene->n, kProjThreads, 8), kProjThreads, 0, st>>>(
+        make_scene(*scene), make_cam(*cam), (int)mode, reinterpret_cast<float4 *>(out->rec),
+        reinterpret_cast<uint2 *>(out->rect), out->n_tiles, out->depth, out->cover, out->mask,
+        out->stats);
+    return cuda_check(cudaGetLastError(), "project_kernel launch");
+}
+
+extern "C" int ms_select(const ms_scene_t *scene, const float *cover, ms_mode_t mode,
+                         uint32_t *mask, void *stream) {
+    int rc = check_scene(scene, false);
+    if (rc) return rc;
+    if (mode != MS_SELECTIVE && mode != MS_ALL_LEVELS && mode != MS_FILTER_SMALL)
+        return fail(MS_ERR_INVALID_ARG, "unknown mode");
+    if (scene->n == 0) return MS_OK;
+    if (!cover || !mask) return fail(MS_ERR_INVALID_ARG, "cover/mask is NULL");
+    select_kernel<<<grid_for(scene->n, 256, 8), 256, 0, as_stream(stream)>>>(
+        scene->n, cover, scene->level, scene->n_levels, scene->s_max, scene->s_min, (int)mode,
+        mask);
+    return cuda_check(cudaGetLastError(), "select_kernel launch");
+}
+
+extern "C" int ms_update_range(const ms_scene_t *scene, const ms_camera_t *cam,
+                               int32_t level_r, void *stream) {
+    int rc = check_scene(scene, true);
+    if (rc) return rc;
+    if ((rc = check_cam(cam))) return rc;
+    if (scene->n == 0) return MS_OK;
+    if (level_r < 1 || level_r > scene->n_levels)
+        return fail(MS_ERR_INVALID_ARG, "level_r must be in 1..n_levels");
+    update_range_kernel<<<grid_for(scene->n, 256, 8), 256, 0, as_stream(stream)>>>(
+        make_scene(*scene), make_cam(*cam), level_r, scene->s_max, scene->s_min);
+    return cuda_check(cudaGetLastError(), "update_range_kernel launch");
+}

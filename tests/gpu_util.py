@@ -1,0 +1,112 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the
+C-ABI binding and compare with the oracle on the same seeded inputs."""
+import numpy as np
+
+import oracle
+import paper_2311_17089_gb300 as msgs
+from paper_2311_17089_gb300 import inputs
+
+IMAGE_ATOL = 2e-4      # max abs per colour channel (FP32 path vs FP64 oracle)
+
+
+def require_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("GPU parity tests need a CUDA device")
+    return torch
+
+
+def calibrated(scene, cams):
+    """Coverage ranges written by the oracle (never by the CUDA path)."""
+    return oracle.calibrate(scene.copy(), cams)
+
+
+def gpu_frame(scene, cam, mode="selective", cap=None, ds=None):
+    """Run ms_project -> ms_bin -> ms_raster; return host copies."""
+    torch = require_cuda()
+    ds = ds or msgs.DeviceScene(scene)
+    cap = cap or max(4096, 16 * scene.n)
+    r = msgs.Renderer(scene.n, cam.tiles_x * cam.tiles_y, cap)
+    img, ft, nc = r.render(ds, cam, mode)
+    rc, d, surv = msgs.ms_bin_counts(r.bins)
+    if rc == msgs.MS_ERR_CAPACITY:
+        r = msgs.Renderer(scene.n, cam.tiles_x * cam.tiles_y, max(d, 1))
+        img, ft, nc = r.render(ds, cam, mode)
+        rc, d, surv = msgs.ms_bin_counts(r.bins)
+    assert rc == msgs.MS_OK, rc
+    torch.cuda.synchronize()
+    n = max(scene.n, 1)
+    rec = r.rec.cpu().numpy().reshape(n, 12)
+    out = dict(
+        image=img.cpu().numpy(), final_t=ft.cpu().numpy(),
+        n_contrib=nc.cpu().numpy().view(np.uint32),
+        n_tiles=r.n_tiles.cpu().numpy().view(np.uint32)[:scene.n],
+        depth=r.depth.cpu().numpy().view(np.uint32)[:scene.n],
+        rect=r.rect.cpu().numpy().view(np.uint32).reshape(n, 2)[:scene.n],
+        cover=r.cover.cpu().numpy()[:scene.n],
+        mask=r.mask.cpu().numpy().view(np.uint32),
+        rec=rec[:scene.n], D=d, survivors=surv,
+        gauss_idx=r.gauss_idx.cpu().numpy().view(np.uint32)[:d],
+        ranges=r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)[:cam.tiles_x * cam.tiles_y],
+    )
+    return out
+
+
+def mask_bits(mask_words, n):
+    bits = np.unpackbits(mask_words.view(np.uint8), bitorder="little")
+    return bits[:n].astype(bool)
+
+
+def assert_footprints_equal(g, fp, scene, cam):
+    """K1 outputs bit-exact against the oracle's FP32 footprint."""
+    n = scene.n
+    listed = (fp["selected"] == 1) & (fp["ntiles"] > 0)
+    np.testing.assert_array_equal(g["n_tiles"], np.where(listed, fp["ntiles"], 0))
+    np.testing.assert_array_equal(g["cover"].view(np.uint32), fp["cover"].view(np.uint32))
+    np.testing.assert_array_equal(mask_bits(g["mask"], n), fp["selected"] == 1)
+    li = np.nonzero(listed)[0]
+    np.testing.assert_array_equal(g["depth"][li], fp["depth"][li])
+    r = fp["rect"][li].astype(np.uint32)
+    np.testing.assert_array_equal(g["rect"][li, 0], r[:, 0] | (r[:, 1] << 16))
+    np.testing.assert_array_equal(g["rect"][li, 1], r[:, 2] | (r[:, 3] << 16))
+    rec = g["rec"][li]
+    for col, want in ((0, fp["ux"][li]), (1, fp["uy"][li]), (2, fp["conic"][li, 0]),
+                      (3, fp["conic"][li, 1]), (4, fp["conic"][li, 2]),
+                      (5, scene.opacity[li])):
+        np.testing.assert_array_equal(rec[:, col].view(np.uint32),
+                                      np.ascontiguousarray(want, np.float32).view(np.uint32))
+    rgb = oracle.colors(scene, cam)[li]
+    np.testing.assert_allclose(rec[:, [6, 7, 8]], rgb, rtol=0, atol=2e-6)
+    return li
+
+
+def assert_lists_equal(g, offsets, idx):
+    D = len(idx)
+    assert g["D"] == D
+    np.testing.assert_array_equal(g["gauss_idx"], idx)
+    counts = np.diff(offsets)
+    got = g["ranges"][:, 1].astype(np.int64) - g["ranges"][:, 0]
+    np.testing.assert_array_equal(got, counts)
+    ne = counts > 0
+    np.testing.assert_array_equal(g["ranges"][ne, 0], offsets[:-1][ne])
+
+
+def assert_image_close(g, o, tiles=None, cam=None, atol=IMAGE_ATOL, max_flagged=0.02):
+    """Colour within atol on pixels where no evaluation sat on the alpha
+    threshold; final T and the contributor count on pixels with no flag."""
+    flags = o["flags"]
+    region = np.ones_like(flags, bool)
+    if tiles is not None:
+        region[:] = False
+        for t in tiles:
+            tx, ty = t % cam.tiles_x, t // cam.tiles_x
+            region[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16] = True
+    ok = region & ((flags & 1) == 0)
+    assert ok.sum() >= (1 - max_flagged) * region.sum(), (ok.sum(), region.sum())
+    err = np.abs(g["image"] - o["image"])[:, ok]
+    assert err.size == 0 or err.max() <= atol, err.max()
+    clean = region & (flags == 0)
+    terr = np.abs(g["final_t"] - o["final_t"])[clean]
+    assert terr.size == 0 or terr.max() <= atol, terr.max()
+    np.testing.assert_array_equal(g["n_contrib"][clean], o["n_contrib"][clean])
+    return float(err.max()) if err.size else 0.0, int(region.sum() - ok.sum())

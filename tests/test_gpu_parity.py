@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Footprints, selection masks and per-tile sorted index lists must be
+bit-exact; images within 2e-4 max abs per channel on pixels where no
+Gaussian sits on the alpha threshold (the oracle flags those)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2311_17089_gb300 as msgs
+from paper_2311_17089_gb300 import inputs
+
+from gpu_util import (assert_footprints_equal, assert_image_close, assert_lists_equal,
+                      calibrated, gpu_frame, mask_bits, require_cuda)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    return require_cuda()
+
+
+@pytest.fixture(scope="module")
+def ms_scene_50k():
+    sc = inputs.multiscale_scene(n=50_000, seed=0)
+    return calibrated(sc, inputs.orbit_cameras(8, seed=1, radius=25.0))
+
+
+def test_scene_prepare_matches_oracle(cuda):
+    sc = inputs.multiscale_scene(n=200_000, seed=3)
+    ds = msgs.DeviceScene(sc)
+    cuda.cuda.synchronize()
+    scale, lnop = oracle.prepare(sc)
+    np.testing.assert_array_equal(ds.scale.cpu().numpy(), scale)
+    np.testing.assert_array_equal(ds.lnop.cpu().numpy(), lnop)
+
+
+@pytest.mark.parametrize("mode", ["all_levels", "selective"])
+def test_single_level_config_full_parity(cuda, mode):
+    """10k single-level Gaussians, 256x256 (16x16 tiles)."""
+    sc = inputs.single_level_scene()
+    cam = inputs.config1_camera()
+    g = gpu_frame(sc, cam, mode)
+    o = oracle.render(sc, cam, mode)
+    assert_footprints_equal(g, o["fp"], sc, cam)
+    assert_lists_equal(g, o["offsets"], o["idx"])
+    err, flagged = assert_image_close(g, o)
+    assert flagged < 0.01 * cam.width * cam.height
+
+
+@pytest.mark.parametrize("scale", [1, 2, 4, 8, 16, 32, 64, 128])
+@pytest.mark.parametrize("mode", ["selective", "all_levels", "filter_small"])
+def test_multiscale_all_scales(cuda, ms_scene_50k, mode, scale):
+    """50k-Gaussian 4-level scene at every evaluation scale of 1256x832
+    (ragged right-hand tiles at most scales)."""
+    sc = ms_scene_50k
+    cam = inputs.downscale(inputs.config2_camera(), scale)
+    g = gpu_frame(sc, cam, mode)
+    o = oracle.render(sc, cam, mode)
+    assert_footprints_equal(g, o["fp"], sc, cam)
+    assert_lists_equal(g, o["offsets"], o["idx"])
+    assert_image_close(g, o)
+
+
+def test_selective_differs_from_all_levels_and_skips_levels(cuda, ms_scene_50k):
+    """Sanity of the workload: at 1x most coarse Gaussians are filtered,
+    at 64x most fine ones are."""
+    sc = ms_scene_50k
+    for s, dropped_level in ((1, 4), (64, 1)):
+        cam = inputs.downscale(inputs.config2_camera(), s)
+        g = gpu_frame(sc, cam, "selective")
+        sel = mask_bits(g["mask"], sc.n)
+        lv = sc.level == dropped_level
+        assert sel[lv].mean() < 0.5
+
+
+def test_select_entry_point_matches_project_mask(cuda, ms_scene_50k):
+    torch = cuda
+    sc = ms_scene_50k
+    cam = inputs.downscale(inputs.config2_camera(), 4)
+    ds = msgs.DeviceScene(sc)
+    r = msgs.Renderer(sc.n, cam.tiles_x * cam.tiles_y, 16 * sc.n)
+    for mode in ("selective", "all_levels", "filter_small"):
+        msgs.ms_project(ds.struct, msgs.camera_struct(cam), msgs.MODES[mode], r.proj)
+        m2 = torch.empty_like(r.mask)
+        msgs.ms_select(ds.struct, msgs._ptr(r.cover), msgs.MODES[mode], msgs._ptr(m2))
+        torch.cuda.synchronize()
+        assert torch.equal(r.mask, m2)
+
+
+def test_update_range_matches_oracle(cuda):
+    """Device UpdateRange over a calibration sequence (8 cameras x 4 levels at
+    each level's creation scale) equals the oracle's, bit for bit."""
+    sc = inputs.multiscale_scene(n=100_000, seed=5)
+    cams = inputs.orbit_cameras(8, seed=2, radius=25.0)
+    ds = msgs.DeviceScene(sc)
+    ds.calibrate(cams)
+    want = oracle.calibrate(sc.copy(), cams)
+    np.testing.assert_array_equal(ds.s_max.cpu().numpy(), want.s_max)
+    np.testing.assert_array_equal(ds.s_min.cpu().numpy(), want.s_min)
+
+
+def test_full_size_multiscale_sampled(cuda):
+    """1M Gaussians (700k/200k/70k/30k) at 1256x832, the launch shape the
+    benchmark times: every footprint and every tile list bit-exact; the
+    image on 48 sampled tiles plus the longest list's tile."""
+    sc = inputs.multiscale_scene(n=1_000_000, seed=0)
+    sc = calibrated(sc, inputs.orbit_cameras(8, seed=1, radius=25.0))
+    rng = np.random.default_rng(0)
+    for mode in ("selective", "all_levels"):
+        for s in (1, 16, 128):
+            cam = inputs.downscale(inputs.config2_camera(), s)
+            g = gpu_frame(sc, cam, mode)
+            fp = oracle.footprints(sc, cam, mode)
+            assert_footprints_equal(g, fp, sc, cam)
+            off, idx = oracle.tile_lists(fp, cam)
+            assert_lists_equal(g, off, idx)
+            ntiles = cam.tiles_x * cam.tiles_y
+            tiles = sorted(set(rng.choice(ntiles, min(48, ntiles), replace=False).tolist()
+                               + [int(np.argmax(np.diff(off)))]))
+            o = oracle.render(sc, cam, mode, tiles=tiles)
+            assert_image_close(g, o, tiles=tiles, cam=cam)
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_empty_scene(cuda):
+    sc = inputs.single_level_scene(n=0)
+    cam = inputs.config1_camera(40, 24)
+    cam.bg[:] = [0.25, 0.5, 1.0]
+    g = gpu_frame(sc, cam, "selective")
+    assert g["D"] == 0
+    np.testing.assert_array_equal(g["image"], np.broadcast_to(cam.bg[:, None, None], (3, 24, 40)))
+    assert np.all(g["final_t"] == 1.0) and np.all(g["n_contrib"] == 0)
+
+
+def test_everything_culled(cuda):
+    sc = inputs.single_level_scene(n=5000)
+    cam = inputs.pinhole((0, 0, -3), (0, 0, -6), (0, -1, 0), 64, 64, 60.0)  # looks away
+    g = gpu_frame(sc, cam, "all_levels")
+    o = oracle.render(sc, cam, "all_levels")
+    assert g["D"] == 0 and len(o["idx"]) == 0
+    assert_footprints_equal(g, o["fp"], sc, cam)
+    assert np.all(g["image"] == 0.0)
+
+
+@pytest.mark.parametrize("wh", [(1, 1), (33, 17), (16, 16), (17, 1), (300, 7)])
+def test_ragged_sizes(cuda, wh):
+    sc = inputs.single_level_scene(n=3000, seed=4)
+    cam = inputs.config1_camera(*wh)
+    cam.bg[:] = [0.1, 0.2, 0.3]
+    g = gpu_frame(sc, cam, "all_levels")
+    o = oracle.render(sc, cam, "all_levels")
+    assert_footprints_equal(g, o["fp"], sc, cam)
+    assert_lists_equal(g, o["offsets"], o["idx"])
+    assert_image_close(g, o)
+
+
+def test_degenerate_and_nonfinite_inputs(cuda):
+    sc = inputs.single_level_scene(n=2000, seed=6)
+    sc.quat[0:10] = 0.0                       # no rotation -> invalid
+    sc.mean[10:20, 0] = np.nan                # NaN centre -> invalid
+    sc.log_scale[20:30] = -30.0               # vanishing scale
+    sc.log_scale[30:35] = 30.0                # enormous scale
+    sc.opacity[35:45] = 1.0 / 255.0           # no level set
+    sc.opacity[45:50] = 1e-6
+    sc.mean[50:60, 2] = -3.0                  # exactly at the camera plane
+    cam = inputs.config1_camera(96, 80)
+    g = gpu_frame(sc, cam, "all_levels")
+    o = oracle.render(sc, cam, "all_levels")
+    assert_footprints_equal(g, o["fp"], sc, cam)
+    assert not o["fp"]["valid"][:20].any()
+    assert_lists_equal(g, o["offsets"], o["idx"])
+    assert_image_close(g, o)
+
+
+def test_depth_ties_order_by_index(cuda):
+    """Many Gaussians on one depth plane: lists order ties by index."""
+    sc = inputs.single_level_scene(n=20_000, seed=8)
+    sc.mean[:, 2] = np.round(sc.mean[:, 2] * 4) / 4   # 9 depth planes
+    cam = inputs.config1_camera(128, 96)
+    g = gpu_frame(sc, cam, "all_levels")
+    o = oracle.render(sc, cam, "all_levels")
+    assert_lists_equal(g, o["offsets"], o["idx"])
+    assert_image_close(g, o)
+
+
+def test_huge_gaussian_covers_every_tile(cuda):
+    sc = inputs.single_level_scene(n=200, seed=9)
+    sc.log_scale[7] = 1.0
+    sc.mean[7] = 0.0
+    cam = inputs.config1_camera(256, 192)
+    g = gpu_frame(sc, cam, "all_levels")
+    o = oracle.render(sc, cam, "all_levels")
+    assert o["fp"]["ntiles"][7] == cam.tiles_x * cam.tiles_y
+    assert_lists_equal(g, o["offsets"], o["idx"])
+    assert_image_close(g, o)
+
+
+def test_capacity_overflow_reported_then_retry(cuda):
+    torch = cuda
+    sc = inputs.single_level_scene(n=10_000)
+    cam = inputs.config1_camera()
+    ds = msgs.DeviceScene(sc)
+    r = msgs.Renderer(sc.n, cam.tiles_x * cam.tiles_y, 1000)
+    r.render(ds, cam, "all_levels")
+    rc, d, _ = msgs.ms_bin_counts(r.bins)
+    assert rc == msgs.MS_ERR_CAPACITY and d > 1000
+    o = oracle.render(sc, cam, "all_levels")
+    assert d == len(o["idx"])
+    g = gpu_frame(sc, cam, "all_levels", cap=d)
+    assert_lists_equal(g, o["offsets"], o["idx"])
