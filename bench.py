@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""Throughput of multi-scale selective Gaussian-splat rendering on GB300.
+
+Workload (one "step"): a 1M-Gaussian, four-level scene (700k/200k/70k/30k,
+SH degree 3, 64 clusters in a 20-unit box; coverage ranges calibrated on
+the device with UpdateRange from 8 orbit cameras) rendered from one camera
+at 1256x832 and at 2, 4, 8, 16, 32, 64, 128x downscale -- 8 frames.
+
+`value` is frames/s of the selective path (Eq. 6) over that sweep with the
+scene resident in device memory; the same sweep with every level rendered
+(no selection) is reported beside it, per scale too.  `e2e` is the same
+metric through the public API with the scene uploaded from pinned host
+memory and every image read back inside each step.  The scene (about
+250 MB) is larger than L2, so the timed steps do not flush L2.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2311_17089_gb300 import inputs  # noqa: E402
+
+METRIC = ("frames/s at 1x-128x downscale, selective vs all-levels; "
+          "serve p50/p99 ms; bwd it/s")
+N_GAUSS = 1_000_000
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+OPS_PER_EVAL = 16          # FP32 operations per pixel-Gaussian evaluation
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_GAUSS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def workload(n):
+    sc = inputs.multiscale_scene(n=n, seed=0)
+    cams = [inputs.downscale(inputs.config2_camera(), s) for s in inputs.SCALES]
+    calib = inputs.orbit_cameras(8, seed=1, radius=25.0)
+    return sc, cams, calib
+
+
+def config(n, extra=None):
+    c = {"workload": f"multiscale-{n // 1000}k-4level-sh3-1256x832-sweep8",
+         "gaussians": n, "levels": [0.70, 0.20, 0.07, 0.03], "sh_degree": 3,
+         "image": [1256, 832], "scales": list(inputs.SCALES),
+         "frames_per_step": len(inputs.SCALES), "parallelism": "replicas",
+         "l2": "inputs larger than L2 (scene ~250 MB), no flush",
+         "launch": "each 8-frame sweep replayed as one CUDA graph"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle arm
+
+def oracle_scene(sc):
+    """The oracle's own calibration of the coverage ranges (same cameras)."""
+    import oracle
+    calibrated = oracle.calibrate(sc.copy(), inputs.orbit_cameras(8, seed=1, radius=25.0))
+    return calibrated, oracle.prepare(calibrated)
+
+
+def oracle_sweep(scene, cams, budget_s):
+    """Time the oracle on the workload's frames, coarse to fine, until the
+    time budget is spent; returns (frames, seconds, threads, widths)."""
+    import oracle
+    calibrated, prepared = scene
+    frames, spent, done = 0, 0.0, []
+    for cam in reversed(cams):
+        t0 = time.perf_counter()
+        oracle.render(calibrated, cam, "selective", prepared=prepared)
+        dt = time.perf_counter() - t0
+        frames += 1
+        spent += dt
+        done.append(cam.width)
+        if spent > budget_s:
+            break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return frames, spent, threads, done
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, cams, _ = workload(args.n)
+    scene = oracle_scene(sc)
+    budget = max(0.5, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sweep(scene, cams, budget)
+    frames, secs = 0, 0.0
+    threads, scales = 1, []
+    for _ in range(args.steps):
+        f, s, threads, scales = oracle_sweep(scene, cams, budget)
+        frames += f
+        secs += s
+    value = frames / secs
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config(args.n),
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads,
+                         "kind": "oracle",
+                         "sample": f"selective frames at widths {scales} per step "
+                                   f"(coarse to fine until {budget:.1f} s)"},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_2311_17089_gb300 as msgs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    sc, cams, calib = workload(args.n)
+    ds = msgs.DeviceScene(sc, device=dev)
+    ds.calibrate(calib)
+    max_tiles = cams[0].tiles_x * cams[0].tiles_y
+    # size the duplicate capacity from one pass of both modes
+    probe = msgs.Renderer(sc.n, max_tiles, 4 * sc.n, device=dev, with_cover=False,
+                          with_mask=False)
+    dmax = {}
+    for mode in ("selective", "all_levels"):
+        for cam in cams:
+            probe.render(ds, cam, mode)
+            rc, d, _ = msgs.ms_bin_counts(probe.bins)
+            dmax[(mode, cam.width)] = d
+    cap = int(max(dmax.values()) * 1.05) + 1024
+    del probe
+    r = msgs.Renderer(sc.n, max_tiles, cap, device=dev, with_cover=False, with_mask=False)
+    bufs = [r.images(cam, device=dev) for cam in cams]
+    neval = [torch.empty((c.height, c.width), dtype=torch.int32, device=dev) for c in cams]
+    def step(mode):
+        for cam, out in zip(cams, bufs):
+            r.render(ds, cam, mode, out=out)
+
+    # counts: duplicates, survivors, evaluations per frame
+    stats = {}
+    for mode in ("selective", "all_levels"):
+        for cam, out, ne in zip(cams, bufs, neval):
+            r.render(ds, cam, mode, out=out, n_eval=ne)
+            rc, d, s = msgs.ms_bin_counts(r.bins)
+            if rc != msgs.MS_OK:
+                raise msgs.MsError(rc, "capacity")
+            stats[(mode, cam.width)] = dict(D=d, survivors=s,
+                                            P_eval=int(ne.sum(dtype=torch.int64).item()))
+
+    # CUDA graphs: one per 8-frame sweep, and one per stage of every frame
+    # (the per-scale breakdown); the same kernels run on every replay
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    g_step = {m: capture(lambda m=m: step(m)) for m in ("selective", "all_levels")}
+    g_stage = {}
+    for mode in ("selective", "all_levels"):
+        for cam, out in zip(cams, bufs):
+            cs = msgs.camera_struct(cam)
+            md = msgs.MODES[mode]
+            g_stage[(mode, cam.width)] = (
+                capture(lambda cs=cs, md=md: msgs.ms_project(ds.struct, cs, md, r.proj)),
+                capture(lambda cs=cs: msgs.ms_bin(r.proj, sc.n, cs, r.bins, msgs._ptr(r.ws),
+                                                  r.ws_bytes)),
+                capture(lambda cs=cs, out=out: msgs.ms_raster(
+                    r.proj, r.bins, cs, msgs._ptr(out[0]), msgs._ptr(out[1]),
+                    msgs._ptr(out[2]), 0, msgs._ptr(r.rws), r.rws_bytes)))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        g_step["selective"].replay()
+        g_step["all_levels"].replay()
+    torch.cuda.synchronize()
+
+    def timed(mode, k):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            g_step[mode].replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t_sel = timed("selective", args.steps)
+    t_all = timed("all_levels", args.steps)
+
+    frames = len(cams)
+    value = world * frames * args.steps / t_sel
+    value_all = world * frames * args.steps / t_all
+
+    # per-scale and per-stage timing (events on the launching stream)
+    per_scale = {"selective": {}, "all_levels": {}}
+    stage_ms = {"project": 0.0, "bin": 0.0, "raster": 0.0}
+    reps = max(20, args.steps)
+    for mode in ("selective", "all_levels"):
+        for cam in cams:
+            graphs = g_stage[(mode, cam.width)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            tot = [0.0, 0.0, 0.0]
+            for _ in range(reps):
+                for k in range(3):
+                    ev[k].record(stream)
+                    graphs[k].replay()
+                ev[3].record(stream)
+                torch.cuda.synchronize()
+                for k in range(3):
+                    tot[k] += ev[k].elapsed_time(ev[k + 1])
+            ms = [t / reps for t in tot]
+            per_scale[mode][f"{cam.width}x{cam.height}"] = {
+                "fps": 1e3 / sum(ms), "project_ms": ms[0], "bin_ms": ms[1],
+                "raster_ms": ms[2], **stats[(mode, cam.width)]}
+            if mode == "selective":
+                for k, name in enumerate(("project", "bin", "raster")):
+                    stage_ms[name] += ms[k]
+    clk = clocks.stop()
+
+    # roofline of the dominant stage of the selective step
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    n = sc.n
+    proj_bytes = 0
+    evals = 0
+    for cam in cams:
+        s = stats[("selective", cam.width)]
+        proj_bytes += 57 * n + (192 + 4 + 48) * s["survivors"]
+        evals += s["P_eval"]
+    proj_s = stage_ms["project"] / 1e3
+    raster_s = stage_ms["raster"] / 1e3
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2070.0e6 / 1e12   # T ops/s at max clock
+    roof_project = {"bound": "hbm", "kernel": "project_kernel",
+                    "achieved": proj_bytes / proj_s / 1e9, "peak": hbm_peak, "unit": "GB/s"}
+    roof_project["frac"] = roof_project["achieved"] / roof_project["peak"]
+    roof_raster = {"bound": "alu", "kernel": "raster_kernel",
+                   "achieved": OPS_PER_EVAL * evals / raster_s / 1e12, "peak": alu_peak,
+                   "unit": "Tops/s"}
+    roof_raster["frac"] = roof_raster["achieved"] / roof_raster["peak"]
+    dominant = max(stage_ms, key=stage_ms.get)
+    roof = roof_raster if dominant == "raster" else roof_project
+    if dominant == "bin":
+        roof = dict(roof_project)
+        roof["note"] = "binning dominates; project roofline shown"
+    roof = dict(roof, traffic=None, stage_ms_per_step=stage_ms)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).pin_memory()
+                for k in ("mean", "log_scale", "quat", "opacity", "color", "level")}
+        host["s_max"] = ds.s_max.cpu().pin_memory()
+        host["s_min"] = ds.s_min.cpu().pin_memory()
+        outs = [torch.empty((3, c.height, c.width), dtype=torch.float32).pin_memory()
+                for c in cams]
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        d2h = sum(t.numel() * t.element_size() for t in outs)
+
+        def e2e_step():
+            for k, t in host.items():
+                getattr(ds, k).copy_(t, non_blocking=True)
+            msgs.ms_scene_prepare(ds.struct)
+            for cam, out, hb in zip(cams, bufs, outs):
+                r.render(ds, cam, "selective", out=out)
+                hb.copy_(out[0], non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        barrier()
+        e2e = {"value": world * frames * args.steps / t_e2e, "unit": "frames/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # kernels of libmsgs per frame: project; finish_counts, 4 depth passes,
+    # duplicate, 1-2 tile passes, ranges; chunk offsets, raster
+    launches_per_step = 0
+    for cam in cams:
+        tiles = cam.tiles_x * cam.tiles_y
+        launches_per_step += 1 + (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        f, s, threads, scales = oracle_sweep(oracle_scene(sc), cams, args.cpu_budget_s)
+        cpu = {"value": f / s, "unit": "frames/s", "cores": threads, "kind": "oracle",
+               "sample": f"{f} selective frames of the same scene at widths {scales}"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_sel / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config(sc.n), "clocks": clk, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "roofline": roof,
+            "cpu_baseline": cpu,
+            "all_levels": {"value": value_all, "unit": "frames/s",
+                           "ms_per_step": 1e3 * t_all / args.steps},
+            "per_scale": per_scale,
+            "roofline_all": {"project": roof_project, "raster": roof_raster},
+        }))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

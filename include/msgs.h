@@ -102,8 +102,11 @@ typedef struct {
 /*
  * Output of ms_project; device buffers sized for the scene's n.
  *   rec[n*12]     48-byte raster record of every listed Gaussian (selected
- *                 and touching >= 1 tile): ux, uy, conic a, conic b |
- *                 conic c, opacity, r, g | b, 0, 0, 0.  16-B aligned.
+ *                 and touching >= 1 tile): ux, uy, A, B | C, opacity, r, g |
+ *                 b, 0, 0, 0, where (A, B, C) = (k a, 2k b, k c), k =
+ *                 -log2(e)/2 as an FP32 constant, each one FP32 product of
+ *                 the conic (a, b, c) = inverse dilated covariance, so that
+ *                 power * log2(e) = A dx^2 + B dx dy + C dy^2.  16-B aligned.
  *                 Entries of other Gaussians are left untouched.
  *   rect[n*2]     listed Gaussians: tile rectangle packed as
  *                 (x0 | y0 << 16), (x1 | y1 << 16), inclusive
@@ -222,9 +225,15 @@ int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
 int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed,
                   int64_t *survivors, void *stream);
 
+/* Workspace bytes ms_raster needs for `tiles` tiles and the binning's
+ * duplicate capacity; 0 on invalid sizes. */
+size_t ms_raster_workspace_bytes(int64_t tiles, int64_t dup_capacity);
+
 /*
- * Front-to-back blend (Sec. 3.1, Eq. 3): one 256-thread CTA per 16x16 tile,
- * one thread per pixel, sampled at the pixel centre.  For each Gaussian of
+ * Front-to-back blend (Sec. 3.1, Eq. 3): 256-thread CTAs, one thread per
+ * pixel of a 16x16 tile, sampled at the pixel centre.  Lists longer than
+ * 512 entries are split across CTAs and merged exactly (the result of one
+ * sequential walk, up to FP32 rounding).  For each Gaussian of
  * the tile's list in order: power = -(a dx^2 + c dy^2)/2 - b dx dy; skip if
  * power > 0; alpha = min(0.99, sigma e^power); skip if alpha < 1/255; stop
  * before a Gaussian that would bring T below 1e-4; C += alpha T rgb,
@@ -233,10 +242,14 @@ int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed,
  * none).  n_eval[H][W] receives the number of list entries the pixel
  * evaluated up to and including the one that ended it (the algorithmic
  * work, for measurement).  final_t, n_contrib and n_eval may be NULL.
+ * `ws` (16-B aligned) of ms_raster_workspace_bytes(tiles, dup_capacity)
+ * bytes is scratch owned by the call until the stream passes it.  A
+ * bounded wait that gives up sets status bit 2 in bins->counts.
  */
 int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins,
               const ms_camera_t *cam, float *image, float *final_t,
-              uint32_t *n_contrib, uint32_t *n_eval, void *stream);
+              uint32_t *n_contrib, uint32_t *n_eval, void *ws,
+              size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

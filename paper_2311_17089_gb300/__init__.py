@@ -82,8 +82,10 @@ _SIGNATURES = [
     ("ms_bin_counts", ctypes.c_int, [ctypes.POINTER(ms_bins_t),
                                      ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64), P]),
+    ("ms_raster_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     ("ms_raster", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
-                                 ctypes.POINTER(ms_camera_t), P, P, P, P, P]),
+                                 ctypes.POINTER(ms_camera_t), P, P, P, P, P,
+                                 ctypes.c_size_t, P]),
 ]
 
 _lib = None
@@ -184,12 +186,16 @@ def ms_bin_counts(bins: ms_bins_t, stream=None):
     return rc, d.value, s.value
 
 
+def ms_raster_workspace_bytes(tiles: int, dup_capacity: int) -> int:
+    return int(lib().ms_raster_workspace_bytes(tiles, dup_capacity))
+
+
 def ms_raster(proj: ms_proj_t, bins: ms_bins_t, cam: ms_camera_t, image_ptr: int,
-              final_t_ptr: int = 0, n_contrib_ptr: int = 0, n_eval_ptr: int = 0,
-              stream=None):
+              final_t_ptr: int, n_contrib_ptr: int, n_eval_ptr: int, ws_ptr: int,
+              ws_bytes: int, stream=None):
     _check(lib().ms_raster(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam),
                            P(image_ptr), P(final_t_ptr), P(n_contrib_ptr), P(n_eval_ptr),
-                           P(_stream(stream))))
+                           P(ws_ptr), ws_bytes, P(_stream(stream))))
 
 
 # ------------------------------------------------------ buffer helpers
@@ -268,6 +274,10 @@ class Renderer:
         if self.ws_bytes == 0:
             raise MsError(MS_ERR_INVALID_ARG, "invalid workspace sizes")
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.rws_bytes = ms_raster_workspace_bytes(max_tiles, dup_capacity)
+        if self.rws_bytes == 0:
+            raise MsError(MS_ERR_INVALID_ARG, "invalid raster workspace sizes")
+        self.rws = torch.empty(self.rws_bytes, dtype=torch.uint8, device=dev)
 
     def images(self, cam: inputs.Camera, device="cuda"):
         import torch
@@ -289,7 +299,7 @@ class Renderer:
         ms_bin(self.proj, scene.n, cs, self.bins, _ptr(self.ws), self.ws_bytes, stream)
         image, final_t, n_contrib = out if out is not None else self.images(cam)
         ms_raster(self.proj, self.bins, cs, _ptr(image), _ptr(final_t), _ptr(n_contrib),
-                  _ptr(n_eval), stream)
+                  _ptr(n_eval), _ptr(self.rws), self.rws_bytes, stream)
         return image, final_t, n_contrib
 
     def check(self, stream=None):

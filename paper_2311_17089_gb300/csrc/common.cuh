@@ -40,8 +40,8 @@ constexpr uint64_t kStatusOverflow = 1;
 constexpr uint64_t kStatusTimeout = 2;
 
 // Raster record: three float4 per Gaussian.
-//   r0 = (ux, uy, conic a, conic b)
-//   r1 = (conic c, opacity, r, g)
+//   r0 = (ux, uy, A, B)      A = -log2(e)/2 conic a, B = -log2(e) conic b
+//   r1 = (C, opacity, r, g)  C = -log2(e)/2 conic c
 //   r2 = (b, 0, 0, 0)
 constexpr int kRecFloats = 12;
 

@@ -69,7 +69,9 @@ def test_argument_errors_need_no_device():
     bins = msgs.ms_bins_t()
     bins.dup_capacity = 16
     assert lib.ms_bin(ctypes.byref(proj), 10, ctypes.byref(cam), ctypes.byref(bins), None, 0, None) == msgs.MS_ERR_INVALID_ARG
-    assert lib.ms_raster(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam), None, None, None, None, None) == msgs.MS_ERR_INVALID_ARG
+    assert lib.ms_raster(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam), None, None, None, None, None, 0, None) == msgs.MS_ERR_INVALID_ARG
+    assert msgs.ms_raster_workspace_bytes(4108, 1 << 20) > 0
+    assert msgs.ms_raster_workspace_bytes(0, 1 << 20) == 0
 
 
 def test_inputs_module_stands_alone():
