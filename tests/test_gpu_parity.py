@@ -213,18 +213,21 @@ def test_capacity_overflow_reported_then_retry(cuda):
     assert_lists_equal(g, o["offsets"], o["idx"])
 
 
-@pytest.mark.parametrize("wh,n", [((16, 16), 6000), ((48, 32), 9000), ((16, 16), 1500)])
-def test_long_lists_split_across_ctas(cuda, wh, n):
+@pytest.mark.parametrize("wh,n,op", [((16, 16), 6000, (0.008, 0.014)),
+                                     ((48, 32), 9000, (0.008, 0.014)),
+                                     ((16, 16), 1500, (0.0050, 0.0058))])
+def test_long_lists_split_across_ctas(cuda, wh, n, op):
     """Thousands of faint, wide Gaussians on few tiles: lists are split into
-    512-entry chunks blended by different CTAs; pixels terminate inside a
-    later chunk (T falls by about 1% per Gaussian) or never, and the merge
-    must reproduce the sequential blend."""
+    512-entry chunks blended by different CTAs.  With opacity ~0.01 every
+    pixel's T falls about 1% per Gaussian and it terminates inside a later
+    chunk; with opacity ~0.005 over 1500 entries no pixel terminates.  The
+    merge must reproduce the sequential blend."""
     rng = np.random.default_rng(n)
     mean = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.4, 0.4, n),
                      rng.uniform(-1.0, 1.0, n)], 1).astype(np.float32)
-    log_scale = rng.normal(np.log(2.0), 0.1, (n, 3)).astype(np.float32)
+    log_scale = rng.normal(np.log(6.0), 0.05, (n, 3)).astype(np.float32)
     quat = rng.standard_normal((n, 4)).astype(np.float32)
-    opacity = rng.uniform(0.006, 0.014, n).astype(np.float32)
+    opacity = rng.uniform(op[0], op[1], n).astype(np.float32)
     color = rng.uniform(0, 1, (n, 3)).astype(np.float32)
     sc = inputs.Scene(mean, log_scale, quat, opacity, color, np.ones(n, np.uint8), 1, -1,
                       np.zeros(n, np.float32), np.full(n, np.inf, np.float32))
@@ -233,7 +236,8 @@ def test_long_lists_split_across_ctas(cuda, wh, n):
     o = oracle.render(sc, cam, "all_levels")
     assert_lists_equal(g, o["offsets"], o["idx"])
     assert np.diff(o["offsets"]).max() > 1024
-    if n > 2000:
-        # some pixels end beyond the first chunk, some never terminate
-        assert (o["n_contrib"] > 600).any()
-    assert_image_close(g, o)
+    if op[0] > 0.007:
+        assert (o["n_contrib"] > 600).all() and (o["final_t"] < 1.1e-2).all()
+    else:
+        assert (o["n_contrib"] == n).all()
+    assert_image_close(g, o, max_flagged=0.15)
