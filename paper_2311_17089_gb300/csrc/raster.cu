@@ -1,22 +1,28 @@
 // Front-to-back blending per 16x16 tile (Sec. 3.1; Eq. 3 with incremental
-// transmittance T_k): one 256-thread CTA walks a chunk of a tile's sorted
+// transmittance T_k): a 256-thread CTA walks a segment of a tile's sorted
 // list, one thread per pixel.
 //
-// Long lists (low resolutions put thousands of splats on one tile; Sec. 3.2,
-// item 2) are cut into chunks of kChunk records that different CTAs blend
-// concurrently.  The blend stays exactly sequential:
-//   - a chunk whose predecessor has already finished starts from the
+// Load balance: low resolutions put thousands of splats on a few tiles
+// (Sec. 3.2, item 2), so one CTA per tile would leave most SMs idle.  Each
+// tile's list is cut into segments of seg_len = max(kChunk, D / resident
+// CTAs) entries; only tiles longer than a fair share of the work are split.
+// A CTA walks its segment in sub-batches of kChunk records, double-buffered:
+// the next sub-batch arrives in shared memory by per-record bulk copies
+// (cp.async.bulk) on an mbarrier while the current one is blended.
+//
+// The blend stays exactly sequential across segments:
+//   - a segment whose predecessor has already finished starts from the
 //     predecessor's per-pixel (C, T) and applies the termination rule
 //     directly;
 //   - otherwise it blends from T = 1 into local (C_l, T_l), then waits for
 //     the predecessor's (C_in, T_in).  If no termination can fall inside the
-//     chunk (T_in T_l >= 1e-4, T being monotone) the result is
-//     C_in + T_in C_l, T_in T_l; otherwise the chunk is re-walked from
-//     shared memory starting at T_in, which finds the exact stopping point.
-// Records reach shared memory by per-record bulk copies (cp.async.bulk)
-// completing on an mbarrier; each persistent CTA prefetches its next chunk
-// into the second buffer while it blends the current one.  Every wait is
-// bounded; a wait that gives up sets a status bit and the CTA carries on.
+//     segment (T_in T_l >= 1e-4, T being monotone) the result is
+//     C_in + T_in C_l, T_in T_l; otherwise the segment is walked again from
+//     T_in, which finds the exact stopping point.
+// The first segment whose result has every pixel terminated writes the
+// tile's image and marks the tile done; later segments of that tile stop
+// as soon as they see the mark.  Every wait is bounded; a wait that gives
+// up sets a status bit and the CTA carries on.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,7 +31,7 @@
 namespace msgs {
 
 constexpr int kRasterThreads = 256;
-constexpr int kChunk = 512;                  // records per chunk
+constexpr int kChunk = 256;                  // records per staged sub-batch
 constexpr int kRecBytes = 48;                // one raster record
 constexpr int kBufBytes = kChunk * kRecBytes;
 constexpr float kAlphaMin = 1.0f / 255.0f;
@@ -86,48 +92,64 @@ struct RasterArgs {
     float *final_t;
     uint32_t *n_contrib;
     uint32_t *n_eval;
-    uint32_t *chunk_off;  // [tiles + 1]
+    uint32_t *seg_off;    // [tiles + 1] exclusive prefix of segments per tile
+    uint32_t *seg_len;    // [1] entries per segment (a multiple of kChunk)
     uint32_t *ticket;
-    uint32_t *flags;      // [max_chunks]
-    float4 *state;        // [max_chunks][256] (C0, C1, C2, T)
-    uint2 *state2;        // [max_chunks][256] (n_contrib, n_eval | term bit)
+    uint32_t *flags;      // [max_segs] predecessor state published
+    uint32_t *tile_done;  // [tiles] every pixel terminated, image written
+    float4 *state;        // [max_segs][256] (C0, C1, C2, T)
+    uint2 *state2;        // [max_segs][256] (n_contrib, n_eval | term bit)
     unsigned long long *err;
 };
 
-struct Chunk {
-    uint32_t t, k, nk, start, cnt;
+struct Seg {
+    uint32_t t, k, nk, start, len;
 };
 
-__device__ __forceinline__ Chunk chunk_of(const RasterArgs &a, uint32_t c) {
-    int lo = 0, hi = a.tiles;  // chunk_off[lo] <= c < chunk_off[hi]
+__device__ __forceinline__ Seg seg_of(const RasterArgs &a, uint32_t c, uint32_t L) {
+    int lo = 0, hi = a.tiles;  // seg_off[lo] <= c < seg_off[hi]
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
-        if (a.chunk_off[mid] <= c) lo = mid;
+        if (a.seg_off[mid] <= c) lo = mid;
         else hi = mid;
     }
-    Chunk ch;
-    ch.t = lo;
-    ch.k = c - a.chunk_off[lo];
-    ch.nk = a.chunk_off[lo + 1] - a.chunk_off[lo];
+    Seg sg;
+    sg.t = lo;
+    sg.k = c - a.seg_off[lo];
+    sg.nk = a.seg_off[lo + 1] - a.seg_off[lo];
     uint32_t s = a.ranges[2 * lo], e = a.ranges[2 * lo + 1];
-    ch.start = s + ch.k * kChunk;
-    uint32_t stop = min(e, ch.start + kChunk);
-    ch.cnt = stop > ch.start ? stop - ch.start : 0;
-    return ch;
+    sg.start = s + sg.k * L;
+    uint32_t stop = min(e, sg.start + L);
+    sg.len = stop > sg.start ? stop - sg.start : 0;
+    return sg;
 }
 
-// Number of chunks of every tile (at least one, so empty tiles still write
-// the background), exclusive-scanned by one block.
+// One block: D = sum of list lengths, segment length L = max(kChunk,
+// ceil(D / resident) rounded up to kChunk), then the number of segments of
+// every tile (at least one, so empty tiles still write the background),
+// exclusive-scanned.
 __global__ void __launch_bounds__(1024)
-chunk_offsets_kernel(const uint32_t *__restrict__ ranges, int tiles, uint32_t *__restrict__ off) {
+segment_offsets_kernel(const uint32_t *__restrict__ ranges, int tiles, uint32_t resident,
+                       uint32_t *__restrict__ off, uint32_t *__restrict__ seg_len) {
     __shared__ uint32_t s_warp[32];
+    __shared__ unsigned long long s_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (tiles + 1023) / 1024;
     const int t0 = tid * per;
+    if (tid == 0) s_total = 0;
+    __syncthreads();
+    unsigned long long d = 0;
+    for (int t = t0; t < t0 + per && t < tiles; t++) d += ranges[2 * t + 1] - ranges[2 * t];
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0 && d) atomicAdd(&s_total, d);
+    __syncthreads();
+    unsigned long long share = (s_total + resident - 1) / (resident > 0 ? resident : 1);
+    uint32_t L = (uint32_t)(((share + kChunk - 1) / kChunk) * kChunk);
+    if (L < (uint32_t)kChunk) L = kChunk;
     uint32_t sum = 0;
     for (int t = t0; t < t0 + per && t < tiles; t++) {
         uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
-        sum += len > 0 ? (len + kChunk - 1) / kChunk : 1u;
+        sum += len > 0 ? (len + L - 1) / L : 1u;
     }
     uint32_t x = sum;
     for (int o = 1; o < 32; o <<= 1) {
@@ -149,9 +171,12 @@ chunk_offsets_kernel(const uint32_t *__restrict__ ranges, int tiles, uint32_t *_
     for (int t = t0; t < t0 + per && t < tiles; t++) {
         off[t] = run;
         uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
-        run += len > 0 ? (len + kChunk - 1) / kChunk : 1u;
+        run += len > 0 ? (len + L - 1) / L : 1u;
     }
-    if (tid == 1023) off[tiles] = run;
+    if (tid == 1023) {
+        off[tiles] = run;
+        seg_len[0] = L;
+    }
 }
 
 struct PixelState {
@@ -160,9 +185,9 @@ struct PixelState {
     bool term;
 };
 
-// Blend records [0, cnt) of a staged chunk into s, starting from s's state.
-// pos0 is the list position of record 0 of the chunk.
-__device__ __forceinline__ void blend_chunk(const float4 *__restrict__ buf, uint32_t cnt,
+// Blend records [0, cnt) of a staged sub-batch into s, starting from s's
+// state.  pos0 is the list position of record 0 of the sub-batch.
+__device__ __forceinline__ void blend_batch(const float4 *__restrict__ buf, uint32_t cnt,
                                             uint32_t pos0, float fx, float fy, PixelState &s) {
     for (uint32_t i = 0; i < cnt; i++) {
         const float4 r0 = buf[3 * i];
@@ -190,22 +215,21 @@ __device__ __forceinline__ void blend_chunk(const float4 *__restrict__ buf, uint
     s.evals = pos0 + cnt;
 }
 
-// All threads: arm the buffer's mbarrier with the chunk's byte count, then
-// each thread issues bulk copies of its share of the gathered records.
-__device__ __forceinline__ void issue_chunk(const RasterArgs &a, const Chunk &ch, float4 *buf,
-                                            uint64_t *bar) {
-    if (ch.cnt == 0) return;
-    if (threadIdx.x == 0) mbar_expect_tx(bar, ch.cnt * kRecBytes);
+// All threads: arm the buffer's mbarrier with the sub-batch's byte count,
+// then each thread issues bulk copies of its share of the gathered records.
+__device__ __forceinline__ void issue_batch(const RasterArgs &a, uint32_t first, uint32_t cnt,
+                                            float4 *buf, uint64_t *bar) {
+    if (threadIdx.x == 0) mbar_expect_tx(bar, cnt * kRecBytes);
     __syncthreads();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (uint32_t i = threadIdx.x; i < ch.cnt; i += kRasterThreads) {
-        uint32_t g = a.gidx[ch.start + i];
+    for (uint32_t i = threadIdx.x; i < cnt; i += kRasterThreads) {
+        uint32_t g = a.gidx[first + i];
         if (g >= a.n_rec) g = 0;  // unreachable unless binning reported an error
         bulk_copy_g2s(buf + 3 * i, a.rec + 3 * (size_t)g, kRecBytes, bar);
     }
 }
 
-__device__ __forceinline__ bool wait_chunk(const RasterArgs &a, uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool wait_batch(const RasterArgs &a, uint64_t *bar, uint32_t parity) {
     for (uint32_t spins = 0; spins < kSpinLimit; spins++)
         if (mbar_try_wait(bar, parity)) return true;
     atomicOr(a.err, (unsigned long long)kStatusTimeout);
@@ -221,77 +245,139 @@ __device__ __forceinline__ PixelState load_state(const RasterArgs &a, uint32_t c
     return s;
 }
 
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
+    return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+
+// Double-buffer bookkeeping: bit i of `parity` is the phase parity of
+// buffer i's mbarrier, `b` the buffer holding the current sub-batch, `ok`
+// false once a copy wait gave up.
+struct Staging {
+    uint32_t parity;
+    uint32_t b;
+    uint32_t ok;
+};
+
+__device__ __forceinline__ float4 *stage_buf(unsigned char *smem, uint32_t i) {
+    return reinterpret_cast<float4 *>(smem + i * kBufBytes);
+}
+
+__device__ __forceinline__ bool stage_wait(const RasterArgs &a, uint64_t *bars, Staging &stg,
+                                           uint32_t i) {
+    bool r = wait_batch(a, bars + i, (stg.parity >> i) & 1u);
+    stg.parity ^= 1u << i;
+    if (!r) stg.ok = 0u;
+    return r;
+}
+
+// Walk one segment in double-buffered sub-batches.  In local mode
+// (`exact` false) the walk stops as soon as the tile is marked done, and
+// returns true (the partial result is then irrelevant).  The CTA stops
+// early once every pixel has terminated.
+__device__ __forceinline__ bool run_segment(const RasterArgs &a, const Seg &sg, uint32_t L,
+                                            bool exact, bool inside, float fx, float fy,
+                                            PixelState &s, unsigned char *smem, uint64_t *bars,
+                                            Staging &stg, uint32_t *s_abort) {
+    const uint32_t pos0 = sg.k * L;
+    if (sg.len == 0) return false;
+    const uint32_t nb = (sg.len + kChunk - 1) / kChunk;
+    issue_batch(a, sg.start, min(sg.len, (uint32_t)kChunk), stage_buf(smem, stg.b), bars + stg.b);
+    bool abort = false;
+    for (uint32_t j = 0; j < nb; j++) {
+        const uint32_t off = j * kChunk;
+        const uint32_t cnt = min(sg.len - off, (uint32_t)kChunk);
+        const bool more = j + 1 < nb;
+        if (more)
+            issue_batch(a, sg.start + off + kChunk, min(sg.len - off - kChunk, (uint32_t)kChunk),
+                        stage_buf(smem, stg.b ^ 1u), bars + (stg.b ^ 1u));
+        if (!stage_wait(a, bars, stg, stg.b)) {
+            if (more) stage_wait(a, bars, stg, stg.b ^ 1u);
+            return true;
+        }
+        if (inside && !s.term) blend_batch(stage_buf(smem, stg.b), cnt, pos0 + off, fx, fy, s);
+        if (threadIdx.x == 0) *s_abort = exact ? 0u : ld_volatile(a.tile_done + sg.t);
+        const int done = __syncthreads_count(s.term || !inside);
+        abort = *s_abort != 0;
+        stg.b ^= 1u;
+        if (done == kRasterThreads || abort) {
+            if (more) stage_wait(a, bars, stg, stg.b);  // drain the prefetched sub-batch
+            break;
+        }
+    }
+    return abort;
+}
+
 __global__ void __launch_bounds__(kRasterThreads)
 raster_kernel(RasterArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ uint32_t s_next;
     __shared__ uint32_t s_flag;
+    __shared__ uint32_t s_abort;
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_next = atomicAdd(a.ticket, 1u);
     }
     __syncthreads();
-    const uint32_t total = a.chunk_off[a.tiles];
-    uint32_t cur = s_next;
-    uint32_t parity = 0u;  // bit b: phase parity of buffer b's mbarrier
-    int b = 0;
-    auto buf = [&](int i) { return reinterpret_cast<float4 *>(smem + i * kBufBytes); };
-    Chunk ch = {0, 0, 0, 0, 0};
-    if (cur < total) {
-        ch = chunk_of(a, cur);
-        issue_chunk(a, ch, buf(b), &bars[b]);
-    }
-    while (cur < total) {
-        // prefetch the next chunk into the other buffer
+    const uint32_t total = a.seg_off[a.tiles];
+    const uint32_t L = a.seg_len[0];
+    Staging stg = {0u, 0u, 1u};
+    for (;;) {
         __syncthreads();
         if (tid == 0) s_next = atomicAdd(a.ticket, 1u);
         __syncthreads();
-        const uint32_t nxt = s_next;
-        Chunk nch = {0, 0, 0, 0, 0};
-        if (nxt < total) {
-            nch = chunk_of(a, nxt);
-            issue_chunk(a, nch, buf(b ^ 1), &bars[b ^ 1]);
+        const uint32_t c = s_next;
+        if (c >= total || !stg.ok) break;
+        const Seg sg = seg_of(a, c, L);
+        const uint32_t prev = c - 1;
+        bool exact = sg.k == 0;
+        if (!exact) {
+            if (tid == 0)
+                s_flag = ld_volatile(a.tile_done + sg.t) ? 2u : ld_acquire(a.flags + prev);
+            __syncthreads();
+            if (s_flag == 2u) continue;  // an earlier segment finished the tile
+            exact = s_flag != 0;
         }
-        if (ch.cnt > 0) {
-            if (!wait_chunk(a, &bars[b], (parity >> b) & 1u)) return;
-            parity ^= 1u << b;
-        }
-        // ---- blend this chunk
-        const int tx = ch.t % a.tiles_x, ty = ch.t / a.tiles_x;
+        const int tx = sg.t % a.tiles_x, ty = sg.t / a.tiles_x;
         const int px = tx * 16 + (tid & 15), py = ty * 16 + (tid >> 4);
         const bool inside = px < a.W && py < a.H;
         const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-        const uint32_t pos0 = ch.k * kChunk;
-        PixelState s = {0.0f, 0.0f, 0.0f, 1.0f, 0u, pos0, false};
-        bool exact = ch.k == 0;
-        const uint32_t prev = cur - 1;
-        if (!exact) {
-            if (tid == 0) s_flag = ld_acquire(a.flags + prev);
-            __syncthreads();
-            if (s_flag) {
-                exact = true;
-                s = load_state(a, prev);
+        PixelState s = {0.0f, 0.0f, 0.0f, 1.0f, 0u, sg.k * L, false};
+        if (sg.k > 0 && exact) s = load_state(a, prev);
+        // pass 0 walks the segment (exact, or locally from T = 1); pass 1
+        // re-walks it from the predecessor's state for the pixels whose
+        // termination falls inside the segment
+        bool active = inside, skip = false;
+        for (int pass = 0; pass < 2; pass++) {
+            if (run_segment(a, sg, L, exact || pass == 1, active, fx, fy, s, smem, bars, stg,
+                            &s_abort)) {
+                skip = true;  // an earlier segment finished the tile
+                break;
             }
-        }
-        if (inside && !s.term) blend_chunk(buf(b), ch.cnt, pos0, fx, fy, s);
-        if (!exact) {
-            // wait for the predecessor's inclusive state, then merge
+            if (exact || pass == 1) break;
+            // wait for the predecessor's inclusive state (or the tile's end)
             if (tid == 0) {
-                uint32_t spins = 0;
-                while (ld_acquire(a.flags + prev) == 0) {
+                uint32_t spins = 0, f = 0;
+                for (;;) {
+                    if (ld_acquire(a.flags + prev)) { f = 1; break; }
+                    if (ld_volatile(a.tile_done + sg.t)) { f = 2; break; }
                     if (++spins > kSpinLimit) {
                         atomicOr(a.err, (unsigned long long)kStatusTimeout);
                         break;
                     }
                     __nanosleep(64);
                 }
+                s_flag = f;
             }
             __syncthreads();
-            PixelState in = load_state(a, prev);
+            if (s_flag == 2u) {
+                skip = true;
+                break;
+            }
+            const PixelState in = load_state(a, prev);
+            bool redo = false;
             if (in.term) {
                 s = in;
             } else if (!s.term && in.T * s.T >= kTStop) {
@@ -299,61 +385,73 @@ raster_kernel(RasterArgs a) {
                 s.C1 = fmaf(in.T, s.C1, in.C1);
                 s.C2 = fmaf(in.T, s.C2, in.C2);
                 s.T = in.T * s.T;
-                if (s.last <= pos0) s.last = in.last;
+                if (s.last <= sg.k * L) s.last = in.last;
             } else {
-                s = in;
-                if (inside) blend_chunk(buf(b), ch.cnt, pos0, fx, fy, s);
+                s = in;  // termination falls inside this segment
+                redo = inside;
             }
+            active = redo;
+            if (!__syncthreads_or(redo)) break;
         }
-        if (ch.k + 1 < ch.nk) {
-            a.state[(size_t)cur * kRasterThreads + tid] = make_float4(s.C0, s.C1, s.C2, s.T);
-            a.state2[(size_t)cur * kRasterThreads + tid] =
+        if (skip) continue;
+        const bool all_done = __syncthreads_and(s.term || !inside);
+        if (sg.k + 1 < sg.nk && !all_done) {
+            a.state[(size_t)c * kRasterThreads + tid] = make_float4(s.C0, s.C1, s.C2, s.T);
+            a.state2[(size_t)c * kRasterThreads + tid] =
                 make_uint2(s.last, s.evals | (s.term ? kTermBit : 0u));
             __threadfence();
             __syncthreads();
-            if (tid == 0) st_release(a.flags + cur, 1u);
-        } else if (inside) {
-            const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
-            a.image[p] = fmaf(s.T, a.bg0, s.C0);
-            a.image[plane + p] = fmaf(s.T, a.bg1, s.C1);
-            a.image[2 * plane + p] = fmaf(s.T, a.bg2, s.C2);
-            if (a.final_t) a.final_t[p] = s.T;
-            if (a.n_contrib) a.n_contrib[p] = s.last;
-            if (a.n_eval) a.n_eval[p] = s.evals;
+            if (tid == 0) st_release(a.flags + c, 1u);
+        } else {
+            if (inside) {
+                const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+                a.image[p] = fmaf(s.T, a.bg0, s.C0);
+                a.image[plane + p] = fmaf(s.T, a.bg1, s.C1);
+                a.image[2 * plane + p] = fmaf(s.T, a.bg2, s.C2);
+                if (a.final_t) a.final_t[p] = s.T;
+                if (a.n_contrib) a.n_contrib[p] = s.last;
+                if (a.n_eval) a.n_eval[p] = s.evals;
+            }
+            if (sg.k + 1 < sg.nk) {
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) st_release(a.tile_done + sg.t, 1u);
+            }
         }
-        cur = nxt;
-        ch = nch;
-        b ^= 1;
     }
 }
 
 struct RasterLayout {
-    size_t ticket, chunk_off, flags, state, state2, total, zero_bytes;
-    int64_t max_chunks;
+    size_t ticket, seg_len, flags, tile_done, seg_off, state, state2, total, zero_bytes;
+    int64_t max_segs;
 };
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {
     if (tiles < 1 || tiles > 65536 || cap < 1 || cap > (1ll << 30)) return false;
-    L.max_chunks = tiles + ceil_div(cap, kChunk);
+    L.max_segs = tiles + ceil_div(cap, kChunk);
     size_t o = 0;
     L.ticket = o;
     o = al256(o + 4);
     L.flags = o;
-    o = al256(o + (size_t)L.max_chunks * 4);
+    o = al256(o + (size_t)L.max_segs * 4);
+    L.tile_done = o;
+    o = al256(o + (size_t)tiles * 4);
     L.zero_bytes = o;
-    L.chunk_off = o;
+    L.seg_len = o;
+    o = al256(o + 4);
+    L.seg_off = o;
     o = al256(o + (size_t)(tiles + 1) * 4);
     L.state = o;
-    o = al256(o + (size_t)L.max_chunks * kRasterThreads * sizeof(float4));
+    o = al256(o + (size_t)L.max_segs * kRasterThreads * sizeof(float4));
     L.state2 = o;
-    o = al256(o + (size_t)L.max_chunks * kRasterThreads * sizeof(uint2));
+    o = al256(o + (size_t)L.max_segs * kRasterThreads * sizeof(uint2));
     L.total = o;
     return true;
 }
 
-static int raster_grid() {
+static int raster_blocks_per_sm() {
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
         int v = 0;
@@ -363,7 +461,7 @@ static int raster_grid() {
             v = 1;
         blocks_per_sm = v;
     }
-    return blocks_per_sm * num_sms();
+    return blocks_per_sm;
 }
 
 }  // namespace msgs
@@ -424,13 +522,17 @@ extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_
     a.final_t = final_t;
     a.n_contrib = n_contrib;
     a.n_eval = n_eval;
-    a.chunk_off = reinterpret_cast<uint32_t *>(w + L.chunk_off);
+    a.seg_off = reinterpret_cast<uint32_t *>(w + L.seg_off);
+    a.seg_len = reinterpret_cast<uint32_t *>(w + L.seg_len);
     a.ticket = reinterpret_cast<uint32_t *>(w + L.ticket);
     a.flags = reinterpret_cast<uint32_t *>(w + L.flags);
+    a.tile_done = reinterpret_cast<uint32_t *>(w + L.tile_done);
     a.state = reinterpret_cast<float4 *>(w + L.state);
     a.state2 = reinterpret_cast<uint2 *>(w + L.state2);
     a.err = reinterpret_cast<unsigned long long *>(bins->counts) + kCntStatus;
-    chunk_offsets_kernel<<<1, 1024, 0, st>>>(bins->ranges, (int)tiles, a.chunk_off);
-    raster_kernel<<<raster_grid(), kRasterThreads, 2 * kBufBytes, st>>>(a);
+    const int resident = raster_blocks_per_sm() * num_sms();
+    segment_offsets_kernel<<<1, 1024, 0, st>>>(bins->ranges, (int)tiles, (uint32_t)resident,
+                                               a.seg_off, a.seg_len);
+    raster_kernel<<<resident, kRasterThreads, 2 * kBufBytes, st>>>(a);
     return cuda_check(cudaGetLastError(), "raster launches");
 }
