@@ -4,8 +4,9 @@
 //
 // Load balance: low resolutions put thousands of splats on a few tiles
 // (Sec. 3.2, item 2), so one CTA per tile would leave most SMs idle.  Each
-// tile's list is cut into segments of seg_len = max(kChunk, D / resident
-// CTAs) entries; only tiles longer than a fair share of the work are split.
+// tile's list is cut into segments of seg_len = max(kMinSegment, D /
+// resident CTAs) entries; only tiles longer than a fair share of the work
+// are split.
 // A CTA walks its segment in sub-batches of kChunk records, double-buffered:
 // the next sub-batch arrives in shared memory by per-record bulk copies
 // (cp.async.bulk) on an mbarrier while the current one is blended.
@@ -17,11 +18,13 @@
 //   - otherwise it blends from T = 1 into local (C_l, T_l), then waits for
 //     the predecessor's (C_in, T_in).  If no termination can fall inside the
 //     segment (T_in T_l >= 1e-4, T being monotone) the result is
-//     C_in + T_in C_l, T_in T_l; otherwise the segment is walked again from
-//     T_in, which finds the exact stopping point.
-// The first segment whose result has every pixel terminated writes the
-// tile's image and marks the tile done; later segments of that tile stop
-// as soon as they see the mark.  Every wait is bounded; a wait that gives
+//     C_in + T_in C_l, T_in T_l; otherwise the pixel terminates inside the
+//     segment: it is handed on as terminated at once, and the segment is
+//     walked again from T_in to find the exact stopping point.
+// Each pixel is written by the segment it terminates in, or by its tile's
+// last segment.  A segment after which every pixel has terminated marks
+// the tile done; later segments of that tile stop as soon as they see the
+// mark.  Every wait is bounded; a wait that gives
 // up sets a status bit and the CTA carries on.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -32,6 +35,7 @@ namespace msgs {
 
 constexpr int kRasterThreads = 256;
 constexpr int kChunk = 256;                  // records per staged sub-batch
+constexpr uint32_t kMinSegment = 4 * kChunk; // shortest segment a tile is cut into
 constexpr int kRecBytes = 48;                // one raster record
 constexpr int kBufBytes = kChunk * kRecBytes;
 constexpr float kAlphaMin = 1.0f / 255.0f;
@@ -145,7 +149,7 @@ segment_offsets_kernel(const uint32_t *__restrict__ ranges, int tiles, uint32_t 
     __syncthreads();
     unsigned long long share = (s_total + resident - 1) / (resident > 0 ? resident : 1);
     uint32_t L = (uint32_t)(((share + kChunk - 1) / kChunk) * kChunk);
-    if (L < (uint32_t)kChunk) L = kChunk;
+    if (L < kMinSegment) L = kMinSegment;
     uint32_t sum = 0;
     for (int t = t0; t < t0 + per && t < tiles; t++) {
         uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
@@ -345,78 +349,92 @@ raster_kernel(RasterArgs a) {
         const bool inside = px < a.W && py < a.H;
         const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
         PixelState s = {0.0f, 0.0f, 0.0f, 1.0f, 0u, sg.k * L, false};
-        if (sg.k > 0 && exact) s = load_state(a, prev);
+        bool was_term = false;  // terminated in an earlier segment (already written)
+        if (sg.k > 0 && exact) {
+            s = load_state(a, prev);
+            was_term = s.term;
+        }
         // pass 0 walks the segment (exact, or locally from T = 1); pass 1
-        // re-walks it from the predecessor's state for the pixels whose
-        // termination falls inside the segment
-        bool active = inside, skip = false;
+        // re-walks it from the predecessor's state for the pixels that
+        // terminate inside it, after the state has been handed on
+        bool active = inside, skip = false, redone = false;
+        const bool last_seg = sg.k + 1 == sg.nk;
         for (int pass = 0; pass < 2; pass++) {
             if (run_segment(a, sg, L, exact || pass == 1, active, fx, fy, s, smem, bars, stg,
                             &s_abort)) {
                 skip = true;  // an earlier segment finished the tile
                 break;
             }
-            if (exact || pass == 1) break;
-            // wait for the predecessor's inclusive state (or the tile's end)
-            if (tid == 0) {
-                uint32_t spins = 0, f = 0;
-                for (;;) {
-                    if (ld_acquire(a.flags + prev)) { f = 1; break; }
-                    if (ld_volatile(a.tile_done + sg.t)) { f = 2; break; }
-                    if (++spins > kSpinLimit) {
-                        atomicOr(a.err, (unsigned long long)kStatusTimeout);
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-                s_flag = f;
-            }
-            __syncthreads();
-            if (s_flag == 2u) {
-                skip = true;
-                break;
-            }
-            const PixelState in = load_state(a, prev);
+            if (pass == 1) break;
             bool redo = false;
-            if (in.term) {
-                s = in;
-            } else if (!s.term && in.T * s.T >= kTStop) {
-                s.C0 = fmaf(in.T, s.C0, in.C0);
-                s.C1 = fmaf(in.T, s.C1, in.C1);
-                s.C2 = fmaf(in.T, s.C2, in.C2);
-                s.T = in.T * s.T;
-                if (s.last <= sg.k * L) s.last = in.last;
-            } else {
-                s = in;  // termination falls inside this segment
-                redo = inside;
+            PixelState in = s;
+            if (!exact) {
+                // wait for the predecessor's inclusive state (or the tile's end)
+                if (tid == 0) {
+                    uint32_t spins = 0, f = 0;
+                    for (;;) {
+                        if (ld_acquire(a.flags + prev)) { f = 1; break; }
+                        if (ld_volatile(a.tile_done + sg.t)) { f = 2; break; }
+                        if (++spins > kSpinLimit) {
+                            atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                    s_flag = f;
+                }
+                __syncthreads();
+                if (s_flag == 2u) {
+                    skip = true;
+                    break;
+                }
+                in = load_state(a, prev);
+                if (in.term) {
+                    s = in;
+                    was_term = true;
+                } else if (!s.term && in.T * s.T >= kTStop) {
+                    s.C0 = fmaf(in.T, s.C0, in.C0);
+                    s.C1 = fmaf(in.T, s.C1, in.C1);
+                    s.C2 = fmaf(in.T, s.C2, in.C2);
+                    s.T = in.T * s.T;
+                    if (s.last <= sg.k * L) s.last = in.last;
+                } else {
+                    // the pixel terminates inside this segment: successors
+                    // only need to know that; its exact result comes next
+                    redo = inside;
+                    s.term = true;
+                }
             }
-            active = redo;
-            if (!__syncthreads_or(redo)) break;
-        }
-        if (skip) continue;
-        const bool all_done = __syncthreads_and(s.term || !inside);
-        if (sg.k + 1 < sg.nk && !all_done) {
-            a.state[(size_t)c * kRasterThreads + tid] = make_float4(s.C0, s.C1, s.C2, s.T);
-            a.state2[(size_t)c * kRasterThreads + tid] =
-                make_uint2(s.last, s.evals | (s.term ? kTermBit : 0u));
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) st_release(a.flags + c, 1u);
-        } else {
-            if (inside) {
-                const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
-                a.image[p] = fmaf(s.T, a.bg0, s.C0);
-                a.image[plane + p] = fmaf(s.T, a.bg1, s.C1);
-                a.image[2 * plane + p] = fmaf(s.T, a.bg2, s.C2);
-                if (a.final_t) a.final_t[p] = s.T;
-                if (a.n_contrib) a.n_contrib[p] = s.last;
-                if (a.n_eval) a.n_eval[p] = s.evals;
-            }
-            if (sg.k + 1 < sg.nk) {
+            // hand the state on before any re-walk, so the chain never
+            // waits for one
+            const bool all_done = __syncthreads_and(s.term || !inside);
+            if (!last_seg) {
+                if (!all_done) {
+                    a.state[(size_t)c * kRasterThreads + tid] =
+                        make_float4(s.C0, s.C1, s.C2, s.T);
+                    a.state2[(size_t)c * kRasterThreads + tid] =
+                        make_uint2(s.last, s.evals | (s.term ? kTermBit : 0u));
+                }
                 __threadfence();
                 __syncthreads();
-                if (tid == 0) st_release(a.tile_done + sg.t, 1u);
+                if (tid == 0) st_release(all_done ? a.tile_done + sg.t : a.flags + c, 1u);
             }
+            if (!__syncthreads_or(redo)) break;
+            if (redo) s = in;
+            active = redo;
+            redone = redo;
+        }
+        if (skip) continue;
+        // every pixel is written once: by the segment it terminates in, or
+        // by the tile's last segment
+        if (inside && !was_term && (s.term || last_seg || redone)) {
+            const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+            a.image[p] = fmaf(s.T, a.bg0, s.C0);
+            a.image[plane + p] = fmaf(s.T, a.bg1, s.C1);
+            a.image[2 * plane + p] = fmaf(s.T, a.bg2, s.C2);
+            if (a.final_t) a.final_t[p] = s.T;
+            if (a.n_contrib) a.n_contrib[p] = s.last;
+            if (a.n_eval) a.n_eval[p] = s.evals;
         }
     }
 }
