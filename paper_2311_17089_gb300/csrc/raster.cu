@@ -11,16 +11,18 @@
 // the next sub-batch arrives in shared memory by per-record bulk copies
 // (cp.async.bulk) on an mbarrier while the current one is blended.
 //
-// The blend stays exactly sequential across segments:
-//   - a segment whose predecessor has already finished starts from the
-//     predecessor's per-pixel (C, T) and applies the termination rule
+// The blend stays exactly sequential across segments (decoupled look-back):
+//   - a segment whose predecessor has published its inclusive prefix
+//     starts from that per-pixel (C, T) and applies the termination rule
 //     directly;
-//   - otherwise it blends from T = 1 into local (C_l, T_l), then waits for
-//     the predecessor's (C_in, T_in).  If no termination can fall inside the
-//     segment (T_in T_l >= 1e-4, T being monotone) the result is
-//     C_in + T_in C_l, T_in T_l; otherwise the pixel terminates inside the
-//     segment: it is handed on as terminated at once, and the segment is
-//     walked again from T_in to find the exact stopping point.
+//   - otherwise it blends from T = 1 into a local aggregate (C_l, T_l),
+//     publishes it, and folds forward from the nearest published prefix
+//     over the aggregates after it to get its exact (C_in, T_in).  If no
+//     termination can fall inside the segment (T_in T_l >= 1e-4, T being
+//     monotone) the result is C_in + T_in C_l, T_in T_l; otherwise the pixel
+//     terminates inside the segment: it is handed on as terminated at once,
+//     and the segment is walked again from T_in to find the exact stopping
+//     point.
 // Each pixel is written by the segment it terminates in, or by its tile's
 // last segment.  A segment after which every pixel has terminated marks
 // the tile done; later segments of that tile stop as soon as they see the
@@ -42,6 +44,8 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
 constexpr uint32_t kTermBit = 0x80000000u;
+constexpr uint32_t kAgg = 1u;                // segment flag: local aggregate published
+constexpr uint32_t kPre = 2u;                // segment flag: inclusive prefix published
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -99,10 +103,12 @@ struct RasterArgs {
     uint32_t *seg_off;    // [tiles + 1] exclusive prefix of segments per tile
     uint32_t *seg_len;    // [1] entries per segment (a multiple of kChunk)
     uint32_t *ticket;
-    uint32_t *flags;      // [max_segs] predecessor state published
+    uint32_t *flags;      // [max_segs] 0, kAgg (local aggregate), kPre (prefix)
     uint32_t *tile_done;  // [tiles] every pixel terminated, image written
-    float4 *state;        // [max_segs][256] (C0, C1, C2, T)
-    uint2 *state2;        // [max_segs][256] (n_contrib, n_eval | term bit)
+    float4 *agg;          // [max_segs][256] local (C0, C1, C2, T) from T = 1
+    uint2 *agg2;          // [max_segs][256] (n_contrib, n_eval | term bit)
+    float4 *pre;          // [max_segs][256] inclusive (C0, C1, C2, T)
+    uint2 *pre2;          // [max_segs][256] (n_contrib, n_eval | term bit)
     unsigned long long *err;
 };
 
@@ -242,11 +248,40 @@ __device__ __forceinline__ bool wait_batch(const RasterArgs &a, uint64_t *bar, u
     return false;
 }
 
-__device__ __forceinline__ PixelState load_state(const RasterArgs &a, uint32_t c) {
-    float4 st = __ldcg(a.state + (size_t)c * kRasterThreads + threadIdx.x);
-    uint2 st2 = __ldcg(a.state2 + (size_t)c * kRasterThreads + threadIdx.x);
+__device__ __forceinline__ PixelState load_state(const float4 *v, const uint2 *v2, uint32_t c) {
+    float4 st = __ldcg(v + (size_t)c * kRasterThreads + threadIdx.x);
+    uint2 st2 = __ldcg(v2 + (size_t)c * kRasterThreads + threadIdx.x);
     PixelState s = {st.x, st.y, st.z, st.w, st2.x, st2.y & ~kTermBit, (st2.y & kTermBit) != 0};
     return s;
+}
+
+__device__ __forceinline__ void store_state(float4 *v, uint2 *v2, uint32_t c,
+                                            const PixelState &s) {
+    v[(size_t)c * kRasterThreads + threadIdx.x] = make_float4(s.C0, s.C1, s.C2, s.T);
+    v2[(size_t)c * kRasterThreads + threadIdx.x] =
+        make_uint2(s.last, s.evals | (s.term ? kTermBit : 0u));
+}
+
+// The exact state after one more segment, from the state P before it and
+// the segment's local result X (blended from T = 1).  A pixel terminates in
+// the segment when X terminated locally or P.T X.T < 1e-4 (T is monotone);
+// its colour then needs a re-walk, the fold only records the termination.
+// Every segment folds with this one function in list order, so all of them
+// reach bit-identical prefixes and the same termination decisions.
+__device__ __forceinline__ PixelState fold(const PixelState &P, const PixelState &X) {
+    if (P.term) return P;
+    PixelState r = P;
+    if (X.term || P.T * X.T < kTStop) {
+        r.term = true;
+        return r;
+    }
+    r.C0 = fmaf(P.T, X.C0, P.C0);
+    r.C1 = fmaf(P.T, X.C1, P.C1);
+    r.C2 = fmaf(P.T, X.C2, P.C2);
+    r.T = P.T * X.T;
+    r.last = X.last != 0 ? X.last : P.last;
+    r.evals = X.evals;
+    return r;
 }
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
@@ -339,10 +374,10 @@ raster_kernel(RasterArgs a) {
         bool exact = sg.k == 0;
         if (!exact) {
             if (tid == 0)
-                s_flag = ld_volatile(a.tile_done + sg.t) ? 2u : ld_acquire(a.flags + prev);
+                s_flag = ld_volatile(a.tile_done + sg.t) ? 3u : ld_acquire(a.flags + prev);
             __syncthreads();
-            if (s_flag == 2u) continue;  // an earlier segment finished the tile
-            exact = s_flag != 0;
+            if (s_flag == 3u) continue;  // an earlier segment finished the tile
+            exact = s_flag == kPre;
         }
         const int tx = sg.t % a.tiles_x, ty = sg.t / a.tiles_x;
         const int px = tx * 16 + (tid & 15), py = ty * 16 + (tid >> 4);
@@ -351,12 +386,12 @@ raster_kernel(RasterArgs a) {
         PixelState s = {0.0f, 0.0f, 0.0f, 1.0f, 0u, sg.k * L, false};
         bool was_term = false;  // terminated in an earlier segment (already written)
         if (sg.k > 0 && exact) {
-            s = load_state(a, prev);
+            s = load_state(a.pre, a.pre2, prev);
             was_term = s.term;
         }
-        // pass 0 walks the segment (exact, or locally from T = 1); pass 1
-        // re-walks it from the predecessor's state for the pixels that
-        // terminate inside it, after the state has been handed on
+        // pass 0 walks the segment (exact from the predecessor's prefix, or
+        // locally from T = 1); pass 1 re-walks it from the exact prefix for
+        // the pixels that terminate inside it, after the prefix is published
         bool active = inside, skip = false, redone = false;
         const bool last_seg = sg.k + 1 == sg.nk;
         for (int pass = 0; pass < 2; pass++) {
@@ -369,35 +404,49 @@ raster_kernel(RasterArgs a) {
             bool redo = false;
             PixelState in = s;
             if (!exact) {
-                // wait for the predecessor's inclusive state (or the tile's end)
+                // publish the local aggregate, then look back: the nearest
+                // predecessor with a published prefix, and the aggregates
+                // after it
+                store_state(a.agg, a.agg2, c, s);
+                __threadfence();
+                __syncthreads();
                 if (tid == 0) {
-                    uint32_t spins = 0, f = 0;
+                    st_release(a.flags + c, kAgg);
+                    uint32_t j = prev, spins = 0, res = 0;
                     for (;;) {
-                        if (ld_acquire(a.flags + prev)) { f = 1; break; }
-                        if (ld_volatile(a.tile_done + sg.t)) { f = 2; break; }
-                        if (++spins > kSpinLimit) {
-                            atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                        const uint32_t f = ld_acquire(a.flags + j);
+                        if (f == kPre) break;
+                        if (f == kAgg) {
+                            j--;  // segment 0 of a tile always publishes a prefix
+                            continue;
+                        }
+                        if (ld_volatile(a.tile_done + sg.t)) {
+                            res = 1u;
                             break;
                         }
-                        __nanosleep(64);
+                        if (++spins > kSpinLimit) {
+                            atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                            res = 1u;
+                            break;
+                        }
+                        __nanosleep(32);
                     }
-                    s_flag = f;
+                    s_flag = res;
+                    s_next = j;
                 }
                 __syncthreads();
-                if (s_flag == 2u) {
+                if (s_flag) {
                     skip = true;
                     break;
                 }
-                in = load_state(a, prev);
+                const uint32_t j = s_next;
+                in = load_state(a.pre, a.pre2, j);
+                for (uint32_t i = j + 1; i < c; i++) in = fold(in, load_state(a.agg, a.agg2, i));
                 if (in.term) {
                     s = in;
                     was_term = true;
                 } else if (!s.term && in.T * s.T >= kTStop) {
-                    s.C0 = fmaf(in.T, s.C0, in.C0);
-                    s.C1 = fmaf(in.T, s.C1, in.C1);
-                    s.C2 = fmaf(in.T, s.C2, in.C2);
-                    s.T = in.T * s.T;
-                    if (s.last <= sg.k * L) s.last = in.last;
+                    s = fold(in, s);
                 } else {
                     // the pixel terminates inside this segment: successors
                     // only need to know that; its exact result comes next
@@ -405,19 +454,15 @@ raster_kernel(RasterArgs a) {
                     s.term = true;
                 }
             }
-            // hand the state on before any re-walk, so the chain never
-            // waits for one
+            // publish the inclusive prefix before any re-walk, so no
+            // successor ever waits for one
             const bool all_done = __syncthreads_and(s.term || !inside);
             if (!last_seg) {
-                if (!all_done) {
-                    a.state[(size_t)c * kRasterThreads + tid] =
-                        make_float4(s.C0, s.C1, s.C2, s.T);
-                    a.state2[(size_t)c * kRasterThreads + tid] =
-                        make_uint2(s.last, s.evals | (s.term ? kTermBit : 0u));
-                }
+                if (!all_done) store_state(a.pre, a.pre2, c, s);
                 __threadfence();
                 __syncthreads();
-                if (tid == 0) st_release(all_done ? a.tile_done + sg.t : a.flags + c, 1u);
+                if (tid == 0) st_release(all_done ? a.tile_done + sg.t : a.flags + c,
+                                         all_done ? 1u : kPre);
             }
             if (!__syncthreads_or(redo)) break;
             if (redo) s = in;
@@ -440,7 +485,7 @@ raster_kernel(RasterArgs a) {
 }
 
 struct RasterLayout {
-    size_t ticket, seg_len, flags, tile_done, seg_off, state, state2, total, zero_bytes;
+    size_t ticket, seg_len, flags, tile_done, seg_off, agg, agg2, pre, pre2, total, zero_bytes;
     int64_t max_segs;
 };
 
@@ -448,7 +493,7 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {
     if (tiles < 1 || tiles > 65536 || cap < 1 || cap > (1ll << 30)) return false;
-    L.max_segs = tiles + ceil_div(cap, kChunk);
+    L.max_segs = tiles + ceil_div(cap, kMinSegment);
     size_t o = 0;
     L.ticket = o;
     o = al256(o + 4);
@@ -461,10 +506,16 @@ static bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {
     o = al256(o + 4);
     L.seg_off = o;
     o = al256(o + (size_t)(tiles + 1) * 4);
-    L.state = o;
-    o = al256(o + (size_t)L.max_segs * kRasterThreads * sizeof(float4));
-    L.state2 = o;
-    o = al256(o + (size_t)L.max_segs * kRasterThreads * sizeof(uint2));
+    const size_t per4 = (size_t)L.max_segs * kRasterThreads * sizeof(float4);
+    const size_t per2 = (size_t)L.max_segs * kRasterThreads * sizeof(uint2);
+    L.agg = o;
+    o = al256(o + per4);
+    L.agg2 = o;
+    o = al256(o + per2);
+    L.pre = o;
+    o = al256(o + per4);
+    L.pre2 = o;
+    o = al256(o + per2);
     L.total = o;
     return true;
 }
@@ -545,8 +596,10 @@ extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_
     a.ticket = reinterpret_cast<uint32_t *>(w + L.ticket);
     a.flags = reinterpret_cast<uint32_t *>(w + L.flags);
     a.tile_done = reinterpret_cast<uint32_t *>(w + L.tile_done);
-    a.state = reinterpret_cast<float4 *>(w + L.state);
-    a.state2 = reinterpret_cast<uint2 *>(w + L.state2);
+    a.agg = reinterpret_cast<float4 *>(w + L.agg);
+    a.agg2 = reinterpret_cast<uint2 *>(w + L.agg2);
+    a.pre = reinterpret_cast<float4 *>(w + L.pre);
+    a.pre2 = reinterpret_cast<uint2 *>(w + L.pre2);
     a.err = reinterpret_cast<unsigned long long *>(bins->counts) + kCntStatus;
     const int resident = raster_blocks_per_sm() * num_sms();
     segment_offsets_kernel<<<1, 1024, 0, st>>>(bins->ranges, (int)tiles, (uint32_t)resident,
