@@ -103,7 +103,9 @@ typedef struct {
  * Output of ms_project; device buffers sized for the scene's n.
  *   rec[n*12]     48-byte raster record of every listed Gaussian (selected
  *                 and touching >= 1 tile): ux, uy, A, B | C, opacity, r, g |
- *                 b, 0, 0, 0, where (A, B, C) = (k a, 2k b, k c), k =
+ *                 b, thr, 0, 0, where thr = -log2(e) ln(255 opacity) (so
+ *                 alpha >= 1/255 exactly when power log2(e) >= thr) and
+ *                 (A, B, C) = (k a, 2k b, k c), k =
  *                 -log2(e)/2 as an FP32 constant, each one FP32 product of
  *                 the conic (a, b, c) = inverse dilated covariance, so that
  *                 power * log2(e) = A dx^2 + B dx dy + C dy^2.  16-B aligned.

@@ -122,25 +122,33 @@ onesweep_pass(PassArgs a) {
         __syncthreads();
         const uint32_t p = s_part;
         if (p >= parts) break;
-        // ---- load and rank (warp-striped, rounds in item order)
+        // ---- load every item first (all loads in flight together), then
+        // rank (warp-striped, rounds in item order)
         uint32_t key[kSortIPT], val[kSortIPT], rank[kSortIPT];
+        bool ok[kSortIPT];
         const uint64_t wbase = (uint64_t)p * kPart + (uint64_t)warp * 32 * kSortIPT;
 #pragma unroll
         for (int r = 0; r < kSortIPT; r++) {
-            uint64_t i = wbase + (uint64_t)r * 32 + lane;
-            bool valid = i < n;
-            if (valid && a.filter) valid = a.filter[i] > 0;
-            uint32_t k = valid ? a.keys_in[i] : 0u;
-            uint32_t v = valid ? (a.vals_in ? a.vals_in[i] : (uint32_t)i) : 0u;
-            uint32_t d = (k >> a.shift) & 255u;
-            uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u);
+            const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+            ok[r] = i < n;
+            if (a.filter && ok[r]) ok[r] = __ldg(a.filter + i) > 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kSortIPT; r++) {
+            const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+            key[r] = ok[r] ? a.keys_in[i] : 0u;
+            val[r] = ok[r] ? (a.vals_in ? a.vals_in[i] : (uint32_t)i) : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kSortIPT; r++) {
+            const bool valid = ok[r];
+            const uint32_t d = (key[r] >> a.shift) & 255u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u);
             uint32_t before = 0;
             if (valid) before = s_whist[warp][d] + __popc(peers & lanemask_lt());
             __syncwarp();
             if (valid && lane == 31 - __clz(peers)) s_whist[warp][d] += __popc(peers);
             __syncwarp();
-            key[r] = k;
-            val[r] = v;
             rank[r] = valid ? ((d << 16) | before) : 0xffffffffu;
         }
         __syncthreads();
@@ -229,6 +237,9 @@ struct DupArgs {
     unsigned long long *status;  // [partitions]
     uint32_t *ticket;
     unsigned long long *err;
+    const unsigned long long *dup;  // duplicates D (device)
+    uint32_t *tstatus;           // tile-pass look-back words, zeroed here
+    uint64_t tstride;            // words per tile pass in tstatus
 };
 
 __global__ void __launch_bounds__(kDupThreads)
@@ -244,21 +255,35 @@ duplicate_kernel(DupArgs a) {
     const uint64_t n = umin64(*a.n32, a.n_max);
     const uint64_t parts = (n + kDupPart - 1) / kDupPart;
     for (int i = tid; i < 512; i += kDupThreads) (&s_hist[0][0])[i] = 0;
+    {
+        // clear the look-back words the tile passes will use (only as many
+        // partitions as D needs; the passes start after this kernel ends)
+        const uint64_t words = ((umin64(*a.dup, a.cap) + kPart - 1) / kPart) * 256;
+        for (uint64_t w = blockIdx.x * (uint64_t)kDupThreads + tid; w < words;
+             w += (uint64_t)gridDim.x * kDupThreads) {
+            a.tstatus[w] = 0u;
+            a.tstatus[a.tstride + w] = 0u;
+        }
+    }
     for (;;) {
         __syncthreads();
         if (tid == 0) s_part = atomicAdd(a.ticket, 1u);
         __syncthreads();
         const uint32_t p = s_part;
         if (p >= parts) break;
-        uint32_t nt[kDupIPT];
+        uint32_t nt[kDupIPT], gi[kDupIPT];
         uint32_t sum = 0;
 #pragma unroll
         for (int r = 0; r < kDupIPT; r++) {
-            uint64_t j = (uint64_t)p * kDupPart + tid * kDupIPT + r;
-            uint32_t g = 0, c = 0;
+            const uint64_t j = (uint64_t)p * kDupPart + tid * kDupIPT + r;
+            gi[r] = j < n ? a.order[j] : 0xffffffffu;
+        }
+#pragma unroll
+        for (int r = 0; r < kDupIPT; r++) {
+            const uint32_t g = gi[r];
+            uint32_t c = 0;
             uint2 rc = make_uint2(0, 0);
-            if (j < n) {
-                g = a.order[j];
+            if (g != 0xffffffffu) {
                 if (g < a.n_max) {
                     c = a.n_tiles[g];
                     rc = a.rect[g];
@@ -397,12 +422,12 @@ static bool layout(int64_t n, int64_t cap, BinLayout &L) {
     L.tvals_a = take(cap * 4);
     L.tkeys_b = take(cap * 4);
     L.tvals_b = take(cap * 4);
+    L.tstatus = take((size_t)2 * L.tparts * 256 * 4);  // cleared by duplicate_kernel
     L.zero_begin = o;
     L.tickets = take(16 * 4);
     L.thist = take(512 * 4);
     L.dup_status = take(L.dupparts * 8);
     L.dstatus = take((size_t)4 * L.dparts * 256 * 4);
-    L.tstatus = take((size_t)2 * L.tparts * 256 * 4);
     L.total = o;
     return true;
 }
@@ -496,6 +521,9 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     da.status = reinterpret_cast<unsigned long long *>(w + L.dup_status);
     da.ticket = tickets + 4;
     da.err = err;
+    da.dup = dup64;
+    da.tstatus = U32(L.tstatus);
+    da.tstride = (uint64_t)L.tparts * 256;
     int dupgrid = (int)std::min<int64_t>(L.dupparts, (int64_t)sms * 4);
     duplicate_kernel<<<dupgrid, kDupThreads, 0, st>>>(da);
     // ---- stable sort by tile id

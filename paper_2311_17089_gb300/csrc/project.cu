@@ -281,6 +281,7 @@ static SceneK make_scene(const ms_scene_t &s) {
 constexpr int kProjThreads = 256;
 constexpr float kConicA = -0.72134752044448170f;   // -log2(e) / 2
 constexpr float kConicB = -1.4426950408889634f;    // -log2(e)
+constexpr float kLog2e = 1.4426950408889634f;
 
 // K1: one thread per Gaussian (grid-stride), writes the footprint outputs,
 // the raster record of listed Gaussians, and accumulates the survivor
@@ -330,7 +331,8 @@ project_kernel(SceneK sc, CamK cam, int mode, float4 *__restrict__ rec,
                 // conic pre-scaled so power * log2(e) = A dx^2 + B dx dy + C dy^2
                 rec[3 * i + 0] = make_float4(f.ux, f.uy, fm(kConicA, f.ca), fm(kConicB, f.cb));
                 rec[3 * i + 1] = make_float4(fm(kConicA, f.cc), op, col.x, col.y);
-                rec[3 * i + 2] = make_float4(col.z, 0.0f, 0.0f, 0.0f);
+                // alpha >= 1/255 <=> power * log2(e) >= -ln(255 sigma) log2(e)
+                rec[3 * i + 2] = make_float4(col.z, fm(-kLog2e, sc.lnop[i]), 0.0f, 0.0f);
                 rect[i] = make_uint2((uint32_t)f.x0 | ((uint32_t)f.y0 << 16),
                                      (uint32_t)f.x1 | ((uint32_t)f.y1 << 16));
                 depth[i] = f.depth;

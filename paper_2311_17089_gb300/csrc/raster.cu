@@ -39,7 +39,8 @@ constexpr int kRasterThreads = 256;
 constexpr int kChunk = 256;                  // records per staged sub-batch
 constexpr uint32_t kMinSegment = 4 * kChunk; // shortest segment a tile is cut into
 constexpr int kRecBytes = 48;                // one raster record
-constexpr int kBufBytes = kChunk * kRecBytes;
+constexpr int kBufBytes = kChunk * kRecBytes;  // staged records, as copied
+constexpr int kPairs = kChunk / 2;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
@@ -195,38 +196,126 @@ struct PixelState {
     bool term;
 };
 
-// Blend records [0, cnt) of a staged sub-batch into s, starting from s's
-// state.  pos0 is the list position of record 0 of the sub-batch.
-__device__ __forceinline__ void blend_batch(const float4 *__restrict__ buf, uint32_t cnt,
-                                            uint32_t pos0, float fx, float fy, PixelState &s) {
-    for (uint32_t i = 0; i < cnt; i++) {
-        const float4 r0 = buf[3 * i];
-        const float4 r1 = buf[3 * i + 1];
-        const float dx = fx - r0.x, dy = fy - r0.y;
-        const float u = fmaf(r0.w, dy, r0.z * dx);
-        const float p = fmaf(r1.x * dy, dy, dx * u);
-        if (p > 0.0f) continue;
-        const float al = fminf(kAlphaMax, r1.y * ex2_approx(p));
-        if (al < kAlphaMin) continue;
-        const float Tn = fmaf(-al, s.T, s.T);
-        if (Tn < kTStop) {
-            s.term = true;
-            s.evals = pos0 + i + 1;
-            return;
-        }
-        const float w = al * s.T;
-        const float rb = reinterpret_cast<const float *>(buf)[12 * i + 8];
-        s.C0 = fmaf(w, r1.z, s.C0);
-        s.C1 = fmaf(w, r1.w, s.C1);
-        s.C2 = fmaf(w, rb, s.C2);
-        s.T = Tn;
-        s.last = pos0 + i + 1;
+// A staged sub-batch regrouped in record pairs (2m, 2m+1) with each field
+// of the two records side by side, so one packed FP32x2 instruction
+// evaluates both records' power terms.
+struct PairBuf {
+    float4 q0[kPairs];  // ux0 ux1 uy0 uy1
+    float4 q1[kPairs];  // A0 A1 B0 B1
+    float4 q2[kPairs];  // C0 C1 thr0 thr1
+    float4 q3[kPairs];  // opacity0 opacity1 r0 r1
+    float4 q4[kPairs];  // g0 g1 b0 b1
+};
+constexpr int kSmemBytes = kBufBytes + (int)sizeof(PairBuf);
+
+typedef unsigned long long f32x2;  // two FP32 values in one 64-bit register pair
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+    f32x2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Regroup records [0, cnt) of the copied sub-batch into pairs; an odd
+// count is padded with a record that no pixel accepts (thr = +inf).
+__device__ __forceinline__ void regroup(const float4 *__restrict__ aos, uint32_t cnt,
+                                        PairBuf &pb) {
+    const uint32_t i = threadIdx.x;
+    if (i >= ((cnt + 1u) & ~1u)) return;
+    float4 r0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), r1 = r0, r2 = r0;
+    r2.y = __int_as_float(0x7f800000);
+    if (i < cnt) {
+        r0 = aos[3 * i];
+        r1 = aos[3 * i + 1];
+        r2 = aos[3 * i + 2];
+    }
+    const uint32_t m = i >> 1, h = i & 1u;
+    float *q0 = reinterpret_cast<float *>(&pb.q0[m]);
+    float *q1 = reinterpret_cast<float *>(&pb.q1[m]);
+    float *q2 = reinterpret_cast<float *>(&pb.q2[m]);
+    float *q3 = reinterpret_cast<float *>(&pb.q3[m]);
+    float *q4 = reinterpret_cast<float *>(&pb.q4[m]);
+    q0[h] = r0.x;
+    q0[2 + h] = r0.y;
+    q1[h] = r0.z;
+    q1[2 + h] = r0.w;
+    q2[h] = r1.x;
+    q2[2 + h] = r2.y;
+    q3[h] = r1.y;
+    q3[2 + h] = r1.z;
+    q4[h] = r1.w;
+    q4[2 + h] = r2.x;
+}
+
+// One record's contribution once it passed the alpha test: stop before a
+// Gaussian that would bring T below 1e-4, else accumulate and advance T.
+// Returns true when the pixel terminated.
+__device__ __forceinline__ bool blend_one(float p, float opacity, float r, float g, float b,
+                                          uint32_t pos, PixelState &s) {
+    const float al = fminf(kAlphaMax, opacity * ex2_approx(p));
+    const float Tn = fmaf(-al, s.T, s.T);
+    if (Tn < kTStop) {
+        s.term = true;
+        s.evals = pos;
+        return true;
+    }
+    const float w = al * s.T;
+    s.C0 = fmaf(w, r, s.C0);
+    s.C1 = fmaf(w, g, s.C1);
+    s.C2 = fmaf(w, b, s.C2);
+    s.T = Tn;
+    s.last = pos;
+    return false;
+}
+
+// Blend the regrouped records [0, cnt) into s.  pos0 is the list position
+// of record 0.  power * log2(e) = A dx^2 + B dx dy + C dy^2 is evaluated
+// for both records of a pair at once; a record is skipped when the power
+// is positive or alpha would stay below 1/255 (power * log2(e) < thr).
+__device__ __forceinline__ void blend_pairs(const PairBuf &pb, uint32_t cnt, uint32_t pos0,
+                                            f32x2 fx2, f32x2 fy2, PixelState &s) {
+    const uint32_t np = (cnt + 1) >> 1;
+    for (uint32_t m = 0; m < np; m++) {
+        const ulonglong2 v0 = *reinterpret_cast<const ulonglong2 *>(&pb.q0[m]);
+        const ulonglong2 v1 = *reinterpret_cast<const ulonglong2 *>(&pb.q1[m]);
+        const ulonglong2 v2 = *reinterpret_cast<const ulonglong2 *>(&pb.q2[m]);
+        const f32x2 dx = sub2(fx2, v0.x), dy = sub2(fy2, v0.y);
+        const f32x2 u = fma2(v1.y, dy, mul2(v1.x, dx));
+        const f32x2 pw = fma2(mul2(v2.x, dy), dy, mul2(dx, u));
+        float p0, p1, t0, t1;
+        unpack2(pw, p0, p1);
+        unpack2(v2.y, t0, t1);
+        const bool h0 = p0 <= 0.0f && p0 >= t0;
+        const bool h1 = p1 <= 0.0f && p1 >= t1;
+        if (!(h0 || h1)) continue;
+        const float4 w3 = pb.q3[m], w4 = pb.q4[m];
+        const uint32_t pos = pos0 + 2 * m;
+        if (h0 && blend_one(p0, w3.x, w3.z, w4.x, w4.z, pos + 1, s)) return;
+        if (h1 && blend_one(p1, w3.y, w3.w, w4.y, w4.w, pos + 2, s)) return;
     }
     s.evals = pos0 + cnt;
 }
 
-// All threads: arm the buffer's mbarrier with the sub-batch's byte count,
-// then each thread issues bulk copies of its share of the gathered records.
+// All threads: arm the mbarrier with the sub-batch's byte count, then each
+// thread issues a bulk copy of its gathered record.
 __device__ __forceinline__ void issue_batch(const RasterArgs &a, uint32_t first, uint32_t cnt,
                                             float4 *buf, uint64_t *bar) {
     if (threadIdx.x == 0) mbar_expect_tx(bar, cnt * kRecBytes);
@@ -288,87 +377,76 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
     return *reinterpret_cast<const volatile uint32_t *>(p);
 }
 
-// Double-buffer bookkeeping: bit i of `parity` is the phase parity of
-// buffer i's mbarrier, `b` the buffer holding the current sub-batch, `ok`
-// false once a copy wait gave up.
-struct Staging {
-    uint32_t parity;
-    uint32_t b;
-    uint32_t ok;
-};
-
-__device__ __forceinline__ float4 *stage_buf(unsigned char *smem, uint32_t i) {
-    return reinterpret_cast<float4 *>(smem + i * kBufBytes);
-}
-
-__device__ __forceinline__ bool stage_wait(const RasterArgs &a, uint64_t *bars, Staging &stg,
-                                           uint32_t i) {
-    bool r = wait_batch(a, bars + i, (stg.parity >> i) & 1u);
-    stg.parity ^= 1u << i;
-    if (!r) stg.ok = 0u;
-    return r;
-}
-
-// Walk one segment in double-buffered sub-batches.  In local mode
-// (`exact` false) the walk stops as soon as the tile is marked done, and
-// returns true (the partial result is then irrelevant).  The CTA stops
-// early once every pixel has terminated.
-__device__ __forceinline__ bool run_segment(const RasterArgs &a, const Seg &sg, uint32_t L,
+// Walk one segment in sub-batches: while the CTA blends sub-batch j from the
+// regrouped buffer, the bulk copies of sub-batch j+1 land in the copy
+// buffer.  In local mode (`exact` false) the walk stops as soon as the tile
+// is marked done, and returns true (the partial result is then
+// irrelevant).  The CTA stops early once every pixel has terminated.
+// Returns kWalked, kAborted, or kFailed when a copy wait gave up (the CTA
+// must then stop).
+constexpr int kWalked = 0, kAborted = 1, kFailed = 2;
+__device__ __forceinline__ int run_segment(const RasterArgs &a, const Seg &sg, uint32_t L,
                                             bool exact, bool inside, float fx, float fy,
-                                            PixelState &s, unsigned char *smem, uint64_t *bars,
-                                            Staging &stg, uint32_t *s_abort) {
+                                            PixelState &s, float4 *aos, PairBuf &pb,
+                                            uint64_t *bar, uint32_t &parity,
+                                            uint32_t *s_abort) {
     const uint32_t pos0 = sg.k * L;
-    if (sg.len == 0) return false;
+    if (sg.len == 0) return kWalked;
     const uint32_t nb = (sg.len + kChunk - 1) / kChunk;
-    issue_batch(a, sg.start, min(sg.len, (uint32_t)kChunk), stage_buf(smem, stg.b), bars + stg.b);
+    const f32x2 fx2 = pack2(fx, fx), fy2 = pack2(fy, fy);
+    issue_batch(a, sg.start, min(sg.len, (uint32_t)kChunk), aos, bar);
     bool abort = false;
     for (uint32_t j = 0; j < nb; j++) {
         const uint32_t off = j * kChunk;
         const uint32_t cnt = min(sg.len - off, (uint32_t)kChunk);
+        const bool ok = wait_batch(a, bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) return kFailed;
+        regroup(aos, cnt, pb);
+        __syncthreads();
         const bool more = j + 1 < nb;
         if (more)
             issue_batch(a, sg.start + off + kChunk, min(sg.len - off - kChunk, (uint32_t)kChunk),
-                        stage_buf(smem, stg.b ^ 1u), bars + (stg.b ^ 1u));
-        if (!stage_wait(a, bars, stg, stg.b)) {
-            if (more) stage_wait(a, bars, stg, stg.b ^ 1u);
-            return true;
-        }
-        if (inside && !s.term) blend_batch(stage_buf(smem, stg.b), cnt, pos0 + off, fx, fy, s);
+                        aos, bar);
+        if (inside && !s.term) blend_pairs(pb, cnt, pos0 + off, fx2, fy2, s);
         if (threadIdx.x == 0) *s_abort = exact ? 0u : ld_volatile(a.tile_done + sg.t);
         const int done = __syncthreads_count(s.term || !inside);
         abort = *s_abort != 0;
-        stg.b ^= 1u;
         if (done == kRasterThreads || abort) {
-            if (more) stage_wait(a, bars, stg, stg.b);  // drain the prefetched sub-batch
+            if (more) {  // drain the copies already issued
+                wait_batch(a, bar, parity);
+                parity ^= 1u;
+            }
             break;
         }
     }
-    return abort;
+    return abort ? kAborted : kWalked;
 }
 
 __global__ void __launch_bounds__(kRasterThreads)
 raster_kernel(RasterArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t s_next;
     __shared__ uint32_t s_flag;
     __shared__ uint32_t s_abort;
+    float4 *aos = reinterpret_cast<float4 *>(smem);
+    PairBuf &pb = *reinterpret_cast<PairBuf *>(smem + kBufBytes);
     const int tid = threadIdx.x;
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const uint32_t total = a.seg_off[a.tiles];
     const uint32_t L = a.seg_len[0];
-    Staging stg = {0u, 0u, 1u};
+    uint32_t parity = 0u;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_next = atomicAdd(a.ticket, 1u);
         __syncthreads();
         const uint32_t c = s_next;
-        if (c >= total || !stg.ok) break;
+        if (c >= total) break;
         const Seg sg = seg_of(a, c, L);
         const uint32_t prev = c - 1;
         bool exact = sg.k == 0;
@@ -395,8 +473,10 @@ raster_kernel(RasterArgs a) {
         bool active = inside, skip = false, redone = false;
         const bool last_seg = sg.k + 1 == sg.nk;
         for (int pass = 0; pass < 2; pass++) {
-            if (run_segment(a, sg, L, exact || pass == 1, active, fx, fy, s, smem, bars, stg,
-                            &s_abort)) {
+            const int rc = run_segment(a, sg, L, exact || pass == 1, active, fx, fy, s, aos,
+                                       pb, &bar, parity, &s_abort);
+            if (rc == kFailed) return;
+            if (rc == kAborted) {
                 skip = true;  // an earlier segment finished the tile
                 break;
             }
@@ -525,7 +605,7 @@ static int raster_blocks_per_sm() {
     if (blocks_per_sm == 0) {
         int v = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_kernel, kRasterThreads,
-                                                          2 * kBufBytes) != cudaSuccess ||
+                                                          kSmemBytes) != cudaSuccess ||
             v < 1)
             v = 1;
         blocks_per_sm = v;
@@ -568,7 +648,7 @@ extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_
     if (!attr_set) {
         if ((rc = cuda_check(cudaFuncSetAttribute(raster_kernel,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  2 * kBufBytes),
+                                                  kSmemBytes),
                              "raster smem attribute")))
             return rc;
         attr_set = true;
@@ -604,6 +684,6 @@ extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_
     const int resident = raster_blocks_per_sm() * num_sms();
     segment_offsets_kernel<<<1, 1024, 0, st>>>(bins->ranges, (int)tiles, (uint32_t)resident,
                                                a.seg_off, a.seg_len);
-    raster_kernel<<<resident, kRasterThreads, 2 * kBufBytes, st>>>(a);
+    raster_kernel<<<resident, kRasterThreads, kSmemBytes, st>>>(a);
     return cuda_check(cudaGetLastError(), "raster launches");
 }
