@@ -492,24 +492,36 @@ raster_kernel(RasterArgs a) {
                 __syncthreads();
                 if (tid == 0) {
                     st_release(a.flags + c, kAgg);
+                    // batched look-back over the flags of up to 16
+                    // predecessors; the tile's first segment never publishes
+                    // an aggregate, so the walk ends there at the latest
+                    const uint32_t c0 = c - sg.k;
                     uint32_t j = prev, spins = 0, res = 0;
                     for (;;) {
-                        const uint32_t f = ld_acquire(a.flags + j);
-                        if (f == kPre) break;
-                        if (f == kAgg) {
-                            j--;  // segment 0 of a tile always publishes a prefix
-                            continue;
+                        uint32_t pre_mask = 0, agg_mask = 0;
+#pragma unroll
+                        for (int i = 0; i < 16; i++) {
+                            const uint32_t f = (j >= c0 + i) ? ld_acquire(a.flags + j - i) : 0u;
+                            pre_mask |= (uint32_t)(f == kPre) << i;
+                            agg_mask |= (uint32_t)(f == kAgg) << i;
                         }
-                        if (ld_volatile(a.tile_done + sg.t)) {
-                            res = 1u;
-                            break;
+                        // leading run of aggregates, then a prefix or a gap
+                        const uint32_t run = __ffs(~agg_mask) - 1;
+                        j -= run;
+                        if (run < 16 && ((pre_mask >> run) & 1u)) break;
+                        if (run < 16) {
+                            // j has published nothing yet
+                            if (ld_volatile(a.tile_done + sg.t)) {
+                                res = 1u;
+                                break;
+                            }
+                            if (++spins > kSpinLimit) {
+                                atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                                res = 1u;
+                                break;
+                            }
+                            __nanosleep(32);
                         }
-                        if (++spins > kSpinLimit) {
-                            atomicOr(a.err, (unsigned long long)kStatusTimeout);
-                            res = 1u;
-                            break;
-                        }
-                        __nanosleep(32);
                     }
                     s_flag = res;
                     s_next = j;
@@ -521,7 +533,16 @@ raster_kernel(RasterArgs a) {
                 }
                 const uint32_t j = s_next;
                 in = load_state(a.pre, a.pre2, j);
-                for (uint32_t i = j + 1; i < c; i++) in = fold(in, load_state(a.agg, a.agg2, i));
+                // fold the aggregates after j, four loads in flight at a time
+                uint32_t i = j + 1;
+                for (; i + 4 <= c; i += 4) {
+                    PixelState x0 = load_state(a.agg, a.agg2, i);
+                    PixelState x1 = load_state(a.agg, a.agg2, i + 1);
+                    PixelState x2 = load_state(a.agg, a.agg2, i + 2);
+                    PixelState x3 = load_state(a.agg, a.agg2, i + 3);
+                    in = fold(fold(fold(fold(in, x0), x1), x2), x3);
+                }
+                for (; i < c; i++) in = fold(in, load_state(a.agg, a.agg2, i));
                 if (in.term) {
                     s = in;
                     was_term = true;
