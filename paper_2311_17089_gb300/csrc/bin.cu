@@ -26,7 +26,7 @@ namespace msgs {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortIPT = 16;
+constexpr int kSortIPT = 4;
 constexpr int kPart = kSortThreads * kSortIPT;  // items per partition
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPre = 2u << 30;
@@ -475,7 +475,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(w + off); };
     uint32_t *tickets = U32(L.tickets);
     unsigned long long *err = reinterpret_cast<unsigned long long *>(out->counts) + kCntStatus;
-    const int per_sm = 2;
+    const int per_sm = 6;
     const int sms = num_sms();
 
     finish_counts_kernel<<<1, 1, 0, st>>>(proj->stats, reinterpret_cast<unsigned long long *>(out->counts),

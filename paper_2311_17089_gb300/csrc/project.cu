@@ -279,6 +279,7 @@ static SceneK make_scene(const ms_scene_t &s) {
 }
 
 constexpr int kProjThreads = 256;
+constexpr int kProjBlocksPerSM = 4;  // 64 registers: the footprint fits without spills
 constexpr float kConicA = -0.72134752044448170f;   // -log2(e) / 2
 constexpr float kConicB = -1.4426950408889634f;    // -log2(e)
 constexpr float kLog2e = 1.4426950408889634f;
@@ -287,7 +288,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 // the raster record of listed Gaussians, and accumulates the survivor
 // count, the duplicate count and the four depth-digit histograms that the
 // binning stage's radix sort needs.
-__global__ void __launch_bounds__(kProjThreads)
+__global__ void __launch_bounds__(kProjThreads, kProjBlocksPerSM)
 project_kernel(SceneK sc, CamK cam, int mode, float4 *__restrict__ rec,
                uint2 *__restrict__ rect, uint32_t *__restrict__ n_tiles,
                uint32_t *__restrict__ depth, float *__restrict__ cover,
@@ -477,7 +478,7 @@ extern "C" int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
                          "stats memset")))
         return rc;
     if (scene->n == 0) return MS_OK;
-    project_kernel<<<grid_for(scene->n, kProjThreads, 8), kProjThreads, 0, st>>>(
+    project_kernel<<<grid_for(scene->n, kProjThreads, kProjBlocksPerSM), kProjThreads, 0, st>>>(
         make_scene(*scene), make_cam(*cam), (int)mode, reinterpret_cast<float4 *>(out->rec),
         reinterpret_cast<uint2 *>(out->rect), out->n_tiles, out->depth, out->cover, out->mask,
         out->stats);
