@@ -24,14 +24,17 @@
 
 namespace msgs {
 
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 1024;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortIPT = 4;
 constexpr int kPart = kSortThreads * kSortIPT;  // items per partition
+constexpr int kDigits = 256;
+constexpr int kScanWarps = kDigits / 32;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPre = 2u << 30;
 constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr int kLookback = 16;  // predecessors polled per look-back step
 
 constexpr int kDupThreads = 256;
 constexpr int kDupIPT = 4;
@@ -62,7 +65,9 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Exclusive scan of one value per thread over a 256-thread block.
+// Exclusive scan of one value per thread over the first 256 threads of the
+// block (the other threads pass 0 and get their result ignored); every
+// thread of the block must call it.
 __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *s_warp,
                                                        uint32_t &total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -72,12 +77,12 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *s_w
         uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) s_warp[warp] = x;
+    if (lane == 31 && warp < kScanWarps) s_warp[warp] = x;
     __syncthreads();
     uint32_t wpre = 0;
     total = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; w++) {
+    for (int w = 0; w < kScanWarps; w++) {
         uint32_t t = s_warp[w];
         if (w < warp) wpre += t;
         total += t;
@@ -95,15 +100,18 @@ __device__ __forceinline__ uint64_t pass_count(const PassArgs &a) {
     return n;
 }
 
+constexpr int kSortSmem = (kSortWarps * kDigits + 2 * kPart) * 4;
+
 __global__ void __launch_bounds__(kSortThreads)
 onesweep_pass(PassArgs a) {
-    __shared__ uint32_t s_whist[kSortWarps][256];
-    __shared__ uint32_t s_base[256];
-    __shared__ uint32_t s_excl[256];
-    __shared__ uint32_t s_prefix[256];
-    __shared__ uint32_t s_keys[kPart];
-    __shared__ uint32_t s_vals[kPart];
-    __shared__ uint32_t s_warp[kSortWarps];
+    extern __shared__ __align__(16) uint32_t sort_smem[];
+    uint32_t(*s_whist)[kDigits] = reinterpret_cast<uint32_t(*)[kDigits]>(sort_smem);
+    uint32_t *s_keys = sort_smem + kSortWarps * kDigits;
+    uint32_t *s_vals = s_keys + kPart;
+    __shared__ uint32_t s_base[kDigits];
+    __shared__ uint32_t s_excl[kDigits];
+    __shared__ uint32_t s_prefix[kDigits];
+    __shared__ uint32_t s_warp[kScanWarps];
     __shared__ uint32_t s_part;
     __shared__ uint32_t s_total;
 
@@ -112,13 +120,13 @@ onesweep_pass(PassArgs a) {
     const uint64_t parts = (n + kPart - 1) / kPart;
     {
         uint32_t tot;
-        uint32_t b = block_excl_scan256(a.hist[tid], s_warp, tot);
-        s_base[tid] = b;
+        uint32_t b = block_excl_scan256(tid < kDigits ? a.hist[tid] : 0u, s_warp, tot);
+        if (tid < kDigits) s_base[tid] = b;
     }
     for (;;) {
         __syncthreads();
         if (tid == 0) s_part = atomicAdd(a.ticket, 1u);
-        for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+        for (int i = tid; i < kSortWarps * kDigits; i += kSortThreads) (&s_whist[0][0])[i] = 0;
         __syncthreads();
         const uint32_t p = s_part;
         if (p >= parts) break;
@@ -152,44 +160,63 @@ onesweep_pass(PassArgs a) {
             rank[r] = valid ? ((d << 16) | before) : 0xffffffffu;
         }
         __syncthreads();
-        // ---- per digit: warp prefix, partition count, publish, look back
+        // ---- per digit (threads 0..255): warp prefix, partition count,
+        // publish, look back
         const uint32_t d = tid;
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < kSortWarps; w++) {
-            uint32_t c = s_whist[w][d];
-            s_whist[w][d] = run;
-            run += c;
-        }
-        const uint32_t local = run;
-        uint32_t *st = a.status + (uint64_t)p * 256 + d;
-        if (p == 0) {
-            st_release(st, kFlagPre | local);
-            s_prefix[d] = 0;
-        } else {
-            st_release(st, kFlagAgg | local);
-            uint32_t excl = 0;
-            int64_t k = (int64_t)p - 1;
-            uint32_t spins = 0;
-            while (k >= 0) {
-                uint32_t s = ld_acquire(a.status + (uint64_t)k * 256 + d);
-                if ((s & kFlagMask) == 0) {
-                    if (++spins > kSpinLimit) {
-                        atomicOr(a.err, (unsigned long long)kStatusTimeout);
-                        break;
-                    }
-                    __nanosleep(32);
-                    continue;
-                }
-                excl += s & kValMask;
-                if (s & kFlagPre) break;
-                k--;
+        uint32_t local = 0;
+        if (tid < kDigits) {
+            uint32_t run = 0;
+#pragma unroll 8
+            for (int w = 0; w < kSortWarps; w++) {
+                uint32_t c = s_whist[w][d];
+                s_whist[w][d] = run;
+                run += c;
             }
-            st_release(st, kFlagPre | ((excl + local) & kValMask));
-            s_prefix[d] = excl;
+            local = run;
+            uint32_t *st = a.status + (uint64_t)p * kDigits + d;
+            if (p == 0) {
+                st_release(st, kFlagPre | local);
+                s_prefix[d] = 0;
+            } else {
+                st_release(st, kFlagAgg | local);
+                // batched look-back: poll up to kLookback predecessors at
+                // once, add aggregates until the nearest inclusive prefix
+                uint32_t excl = 0;
+                int64_t k = (int64_t)p - 1;
+                uint32_t spins = 0;
+                while (k >= 0) {
+                    uint32_t v[kLookback];
+#pragma unroll
+                    for (int i = 0; i < kLookback; i++)
+                        v[i] = (k - i >= 0) ? ld_acquire(a.status + (uint64_t)(k - i) * kDigits + d)
+                                            : kFlagPre;
+                    int i = 0;
+                    bool stop = false;
+                    for (; i < kLookback; i++) {
+                        if ((v[i] & kFlagMask) == 0) break;  // not published yet: poll again
+                        excl += v[i] & kValMask;
+                        if (v[i] & kFlagPre) {
+                            stop = true;
+                            break;
+                        }
+                    }
+                    if (stop) break;
+                    k -= i;
+                    if (i == 0) {
+                        if (++spins > kSpinLimit) {
+                            atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+                st_release(st, kFlagPre | ((excl + local) & kValMask));
+                s_prefix[d] = excl;
+            }
         }
         uint32_t tot;
-        s_excl[d] = block_excl_scan256(local, s_warp, tot);
+        const uint32_t ex = block_excl_scan256(local, s_warp, tot);
+        if (tid < kDigits) s_excl[d] = ex;
         if (tid == 0) s_total = tot;
         __syncthreads();
         // ---- stage digit-sorted in shared memory
@@ -311,21 +338,33 @@ duplicate_kernel(DupArgs a) {
                 st_release64(st, kDupFlagPre | total);
             } else {
                 st_release64(st, kDupFlagAgg | total);
+                // batched look-back over up to kLookback predecessors
                 int64_t k = (int64_t)p - 1;
                 uint32_t spins = 0;
                 while (k >= 0) {
-                    unsigned long long s = ld_acquire64(a.status + k);
-                    if ((s >> 62) == 0) {
+                    unsigned long long v[kLookback];
+#pragma unroll
+                    for (int i = 0; i < kLookback; i++)
+                        v[i] = (k - i >= 0) ? ld_acquire64(a.status + (k - i)) : kDupFlagPre;
+                    int i = 0;
+                    bool stop = false;
+                    for (; i < kLookback; i++) {
+                        if ((v[i] >> 62) == 0) break;
+                        pre += v[i] & kDupValMask;
+                        if (v[i] & kDupFlagPre) {
+                            stop = true;
+                            break;
+                        }
+                    }
+                    if (stop) break;
+                    k -= i;
+                    if (i == 0) {
                         if (++spins > kSpinLimit) {
                             atomicOr(a.err, (unsigned long long)kStatusTimeout);
                             break;
                         }
                         __nanosleep(32);
-                        continue;
                     }
-                    pre += s & kDupValMask;
-                    if (s & kDupFlagPre) break;
-                    k--;
                 }
                 st_release64(st, kDupFlagPre | ((pre + total) & kDupValMask));
             }
@@ -463,6 +502,15 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     cudaStream_t st = as_stream(stream);
     char *w = static_cast<char *>(ws);
     int rc;
+    static bool attr_set = false;
+    if (!attr_set) {
+        if ((rc = cuda_check(cudaFuncSetAttribute(onesweep_pass,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kSortSmem),
+                             "radix smem attribute")))
+            return rc;
+        attr_set = true;
+    }
     if ((rc = cuda_check(cudaMemsetAsync(w + L.zero_begin, 0, L.total - L.zero_begin, st),
                          "workspace memset")))
         return rc;
@@ -475,7 +523,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(w + off); };
     uint32_t *tickets = U32(L.tickets);
     unsigned long long *err = reinterpret_cast<unsigned long long *>(out->counts) + kCntStatus;
-    const int per_sm = 6;
+    const int per_sm = 1;
     const int sms = num_sms();
 
     finish_counts_kernel<<<1, 1, 0, st>>>(proj->stats, reinterpret_cast<unsigned long long *>(out->counts),
@@ -502,7 +550,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
         a.status = U32(L.dstatus) + (size_t)pass * L.dparts * 256;
         a.ticket = tickets + pass;
         a.err = err;
-        onesweep_pass<<<dgrid, kSortThreads, 0, st>>>(a);
+        onesweep_pass<<<dgrid, kSortThreads, kSortSmem, st>>>(a);
     }
     // after 4 passes (out: a, b, a, b) the depth-ordered indices are in dv[1]
     // ---- duplicate into (tile, index) entries
@@ -547,7 +595,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
         a.status = U32(L.tstatus) + (size_t)pass * L.tparts * 256;
         a.ticket = tickets + 5 + pass;
         a.err = err;
-        onesweep_pass<<<tgrid, kSortThreads, 0, st>>>(a);
+        onesweep_pass<<<tgrid, kSortThreads, kSortSmem, st>>>(a);
     }
     ranges_kernel<<<sms * 4, 256, 0, st>>>(final_keys, dup64, (uint64_t)out->dup_capacity,
                                            (uint32_t)tiles, out->ranges);
