@@ -24,9 +24,9 @@
 
 namespace msgs {
 
-constexpr int kSortThreads = 1024;
+constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortIPT = 4;
+constexpr int kSortIPT = 16;
 constexpr int kPart = kSortThreads * kSortIPT;  // items per partition
 constexpr int kDigits = 256;
 constexpr int kScanWarps = kDigits / 32;
@@ -523,7 +523,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(w + off); };
     uint32_t *tickets = U32(L.tickets);
     unsigned long long *err = reinterpret_cast<unsigned long long *>(out->counts) + kCntStatus;
-    const int per_sm = 1;
+    const int per_sm = 2;
     const int sms = num_sms();
 
     finish_counts_kernel<<<1, 1, 0, st>>>(proj->stats, reinterpret_cast<unsigned long long *>(out->counts),
