@@ -13,7 +13,8 @@
 // partition by atomic ticket, ranks its items stably per 8-bit digit with
 // warp match, publishes its per-digit counts and obtains the counts of all
 // earlier partitions by decoupled look-back, then scatters through shared
-// memory.  Every wait on another CTA is bounded; a wait that gives up sets
+// memory.  A look-back word carries its own count, so it is published and
+// polled with relaxed accesses (no fences; many polls in flight at once).  Every wait on another CTA is bounded; a wait that gives up sets
 // a status bit and the CTA carries on, so a kernel can never hang.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -175,10 +176,10 @@ onesweep_pass(PassArgs a) {
             local = run;
             uint32_t *st = a.status + (uint64_t)p * kDigits + d;
             if (p == 0) {
-                st_release(st, kFlagPre | local);
+                st_relaxed(st, kFlagPre | local);
                 s_prefix[d] = 0;
             } else {
-                st_release(st, kFlagAgg | local);
+                st_relaxed(st, kFlagAgg | local);
                 // batched look-back: poll up to kLookback predecessors at
                 // once, add aggregates until the nearest inclusive prefix
                 uint32_t excl = 0;
@@ -188,7 +189,7 @@ onesweep_pass(PassArgs a) {
                     uint32_t v[kLookback];
 #pragma unroll
                     for (int i = 0; i < kLookback; i++)
-                        v[i] = (k - i >= 0) ? ld_acquire(a.status + (uint64_t)(k - i) * kDigits + d)
+                        v[i] = (k - i >= 0) ? ld_relaxed(a.status + (uint64_t)(k - i) * kDigits + d)
                                             : kFlagPre;
                     int i = 0;
                     bool stop = false;
@@ -210,7 +211,7 @@ onesweep_pass(PassArgs a) {
                         __nanosleep(32);
                     }
                 }
-                st_release(st, kFlagPre | ((excl + local) & kValMask));
+                st_relaxed(st, kFlagPre | ((excl + local) & kValMask));
                 s_prefix[d] = excl;
             }
         }
@@ -335,9 +336,9 @@ duplicate_kernel(DupArgs a) {
             unsigned long long *st = a.status + p;
             unsigned long long pre = 0;
             if (p == 0) {
-                st_release64(st, kDupFlagPre | total);
+                st_relaxed64(st, kDupFlagPre | total);
             } else {
-                st_release64(st, kDupFlagAgg | total);
+                st_relaxed64(st, kDupFlagAgg | total);
                 // batched look-back over up to kLookback predecessors
                 int64_t k = (int64_t)p - 1;
                 uint32_t spins = 0;
@@ -345,7 +346,7 @@ duplicate_kernel(DupArgs a) {
                     unsigned long long v[kLookback];
 #pragma unroll
                     for (int i = 0; i < kLookback; i++)
-                        v[i] = (k - i >= 0) ? ld_acquire64(a.status + (k - i)) : kDupFlagPre;
+                        v[i] = (k - i >= 0) ? ld_relaxed64(a.status + (k - i)) : kDupFlagPre;
                     int i = 0;
                     bool stop = false;
                     for (; i < kLookback; i++) {
@@ -366,7 +367,7 @@ duplicate_kernel(DupArgs a) {
                         __nanosleep(32);
                     }
                 }
-                st_release64(st, kDupFlagPre | ((pre + total) & kDupValMask));
+                st_relaxed64(st, kDupFlagPre | ((pre + total) & kDupValMask));
             }
             s_prefix = pre;
         }

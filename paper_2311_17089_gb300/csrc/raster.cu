@@ -501,14 +501,17 @@ raster_kernel(RasterArgs a) {
                         uint32_t pre_mask = 0, agg_mask = 0;
 #pragma unroll
                         for (int i = 0; i < 16; i++) {
-                            const uint32_t f = (j >= c0 + i) ? ld_acquire(a.flags + j - i) : 0u;
+                            const uint32_t f = (j >= c0 + i) ? ld_relaxed(a.flags + j - i) : 0u;
                             pre_mask |= (uint32_t)(f == kPre) << i;
                             agg_mask |= (uint32_t)(f == kAgg) << i;
                         }
                         // leading run of aggregates, then a prefix or a gap
                         const uint32_t run = __ffs(~agg_mask) - 1;
                         j -= run;
-                        if (run < 16 && ((pre_mask >> run) & 1u)) break;
+                        if (run < 16 && ((pre_mask >> run) & 1u)) {
+                            fence_acquire();  // the states behind the flags seen
+                            break;
+                        }
                         if (run < 16) {
                             // j has published nothing yet
                             if (ld_volatile(a.tile_done + sg.t)) {
