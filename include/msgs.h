@@ -219,6 +219,32 @@ int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
            const ms_bins_t *out, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * ms_bin for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment aid).  Examples are an engine plugin
+ * whose host application owns every device allocation, and a render loop
+ * under a fixed memory budget or a no-allocation rule on its frame thread.
+ * Such callers cannot provide ms_bin's workspace.  This entry point takes
+ * the same projection and output buffers as ms_bin, but its scratch space
+ * is a static 16 MiB device array inside this library.  Every GPU that
+ * loads the library keeps that array until the process exits.
+ *   - Sizes whose ms_bin_workspace_bytes(n, tiles, dup_capacity) exceeds
+ *     16 MiB are rejected with MS_ERR_INVALID_ARG and a message; nothing
+ *     is enqueued.  For example, n = 262144 Gaussians with dup_capacity =
+ *     524288 fits; larger scenes must use ms_bin with their own workspace.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current.  Make that first
+ *     call before any stream capture on the device.
+ *   - All calls share the one array.  Each call clears the parts that must
+ *     start at zero, so nothing carries over between calls that run one
+ *     after the other.  Calls that overlap on the GPU (different streams
+ *     with no ordering between them) race on the array and corrupt each
+ *     other's results.
+ *   - No device memory is allocated or freed.
+ */
+int ms_bin_noalloc(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
+                   const ms_bins_t *out, void *stream);
+
+/*
  * Copy the counts of a finished ms_bin to the host (synchronises
  * `stream`).  Returns MS_ERR_CAPACITY if D exceeded the capacity
  * (*d_needed tells how many are needed), MS_ERR_TIMEOUT if a bounded wait

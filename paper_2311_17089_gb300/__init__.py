@@ -79,6 +79,9 @@ _SIGNATURES = [
     ("ms_bin", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.c_int64,
                               ctypes.POINTER(ms_camera_t), ctypes.POINTER(ms_bins_t),
                               P, ctypes.c_size_t, P]),
+    ("ms_bin_noalloc", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.c_int64,
+                                      ctypes.POINTER(ms_camera_t), ctypes.POINTER(ms_bins_t),
+                                      P]),
     ("ms_bin_counts", ctypes.c_int, [ctypes.POINTER(ms_bins_t),
                                      ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64), P]),
@@ -173,6 +176,13 @@ def ms_bin(proj: ms_proj_t, n: int, cam: ms_camera_t, out: ms_bins_t, ws_ptr: in
            ws_bytes: int, stream=None):
     _check(lib().ms_bin(ctypes.byref(proj), int(n), ctypes.byref(cam), ctypes.byref(out),
                         P(ws_ptr), ws_bytes, P(_stream(stream))))
+
+
+def ms_bin_noalloc(proj: ms_proj_t, n: int, cam: ms_camera_t, out: ms_bins_t, stream=None):
+    """ms_bin with the library's static scratch array instead of a caller
+    workspace, for callers that cannot allocate device memory."""
+    _check(lib().ms_bin_noalloc(ctypes.byref(proj), int(n), ctypes.byref(cam),
+                                ctypes.byref(out), P(_stream(stream))))
 
 
 def ms_bin_counts(bins: ms_bins_t, stream=None):

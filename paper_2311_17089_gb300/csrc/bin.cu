@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <string>
 
 #include "common.cuh"
 
@@ -620,4 +621,49 @@ extern "C" int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed, int64_t *
     if (h[kCntStatus] & kStatusOverflow)
         return fail(MS_ERR_CAPACITY, "tile duplicates exceed dup_capacity");
     return MS_OK;
+}
+
+// ------------------------------------------------ binning without allocation
+//
+// For callers that cannot allocate device memory: an engine plugin whose
+// host application owns every device allocation, a render loop that runs
+// under a fixed memory budget or a no-allocation rule on its frame thread,
+// or a runtime that hands the library only the buffers it must fill.  They
+// still pass the projection and the output buffers; the scratch space of the
+// binning lives in this library's own static device array.
+
+namespace msgs {
+
+constexpr size_t kStaticScratchBytes = 16u << 20;  // 16 MiB per device
+static __device__ __align__(256) unsigned char g_bin_scratch[kStaticScratchBytes];
+
+}  // namespace msgs
+
+extern "C" int ms_bin_noalloc(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
+                              const ms_bins_t *out, void *stream) {
+    static void *addr[64] = {nullptr};
+    if (!cam || !out) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+        return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
+    const int64_t tiles = (int64_t)((cam->width + 15) / 16) * ((cam->height + 15) / 16);
+    const size_t need = ms_bin_workspace_bytes(n, tiles, out->dup_capacity);
+    if (need == 0) return fail(MS_ERR_INVALID_ARG, "n, tiles or dup_capacity out of range");
+    if (need > kStaticScratchBytes)
+        return fail(MS_ERR_INVALID_ARG,
+                    "ms_bin_noalloc: n / tiles / dup_capacity need " + std::to_string(need) +
+                        " bytes of scratch, more than the static " +
+                        std::to_string(kStaticScratchBytes) + " (use ms_bin with a workspace)");
+    int dev = 0;
+    int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    if (dev < 0 || dev >= 64) return fail(MS_ERR_INVALID_ARG, "device index beyond 63");
+    if (!addr[dev]) {
+        // first call on this device: the array's device address (the host
+        // symbol is only a stand-in and must never reach a kernel)
+        void *p = nullptr;
+        if ((rc = cuda_check(cudaGetSymbolAddress(&p, g_bin_scratch), "cudaGetSymbolAddress")))
+            return rc;
+        addr[dev] = p;
+    }
+    return ms_bin(proj, n, cam, out, addr[dev], kStaticScratchBytes, stream);
 }
