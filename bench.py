@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--profile", default=None, choices=["selective", "all_levels"],
+                    help="for profilers: two warm-up sweeps, then one sweep of this mode "
+                         "inside the NVTX range 'sweep'; prints no JSON")
     return ap.parse_args()
 
 
@@ -221,6 +224,21 @@ def main():
     ds = msgs.DeviceScene(sc, device=dev)
     ds.calibrate(calib)
     max_tiles = cams[0].tiles_x * cams[0].tiles_y
+    if args.profile:
+        cap = 4_000_000 if args.profile == "selective" else 60_000_000
+        r = msgs.Renderer(sc.n, max_tiles, cap, device=dev, with_cover=False, with_mask=False)
+        bufs = [r.images(cam, device=dev) for cam in cams]
+        for it in range(3):
+            if it == 2:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push("sweep")
+            for cam, out in zip(cams, bufs):
+                r.render(ds, cam, args.profile, out=out)
+            if it == 2:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_pop()
+        r.check()
+        return
     # size the duplicate capacity from one pass of both modes
     probe = msgs.Renderer(sc.n, max_tiles, 4 * sc.n, device=dev, with_cover=False,
                           with_mask=False)
