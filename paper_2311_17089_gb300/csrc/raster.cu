@@ -458,7 +458,11 @@ raster_kernel(RasterArgs a) {
             exact = s_flag == kPre;
         }
         const int tx = sg.t % a.tiles_x, ty = sg.t / a.tiles_x;
-        const int px = tx * 16 + (tid & 15), py = ty * 16 + (tid >> 4);
+        // each warp covers an 8x4 pixel block (2 x 4 blocks per tile): close
+        // pixels accept and terminate alike, which keeps lanes converged
+        const int wid = tid >> 5, lid = tid & 31;
+        const int px = tx * 16 + (wid & 1) * 8 + (lid & 7);
+        const int py = ty * 16 + (wid >> 1) * 4 + (lid >> 3);
         const bool inside = px < a.W && py < a.H;
         const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
         PixelState s = {0.0f, 0.0f, 0.0f, 1.0f, 0u, sg.k * L, false};
