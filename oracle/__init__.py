@@ -5,7 +5,7 @@ CPU-baseline leg may import this package.  It shares no code with the CUDA
 library (paper_2311_17089_gb300); the two meet only through the seeded
 inputs of paper_2311_17089_gb300.inputs.
 
-The C sources (footprint32.c, render64.c, sh64.c, range.c) hold
+The C sources (footprint32.c, render64.c, sh64.c, range.c, grad64.c) hold
 the arithmetic; this module compiles them with gcc and marshals numpy
 arrays through ctypes.
 
@@ -21,7 +21,7 @@ import sys
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["footprint32.c", "render64.c", "sh64.c", "range.c"]
+_SOURCES = ["footprint32.c", "render64.c", "sh64.c", "range.c", "grad64.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 SELECTIVE, ALL_LEVELS, FILTER_SMALL = 0, 1, 2
@@ -85,6 +85,9 @@ def lib():
         L.or_render64_brute.restype = I64
         L.or_update_range.argtypes = [I64, P, P, P, P, P, I32, I32, P, P, P]
         L.or_coverage64.argtypes = [I64, P, P, P, P, P, P, P, P, P]
+        L.or_forward64_full.argtypes = [I64, P, P, P, P, P, I32, P, P, P, P, P, P, P]
+        L.or_grad64.argtypes = [I64, P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P]
+        L.or_grad64.restype = I64
         _lib = L
     return _lib
 
@@ -239,3 +242,37 @@ def coverage64(scene, cam):
                         _p(_f32(scene.quat)), _p(_f32(scene.opacity)),
                         ctypes.byref(cs), _p(cover), _p(ux), _p(uy), _p(cov2d))
     return cover, ux, uy, cov2d
+
+
+def forward64(scene, cam, offsets, idx):
+    """FP64 render with an FP64 projection over fixed tile lists (the
+    function the gradient differentiates)."""
+    H, W = cam.height, cam.width
+    image = np.zeros((3, H, W))
+    final_t = np.zeros((H, W))
+    n_contrib = np.zeros((H, W), np.uint32)
+    n_blend = np.zeros((H, W), np.uint32)
+    cs = camera_struct(cam)
+    lib().or_forward64_full(scene.n, _p(_f32(scene.mean)), _p(_f32(scene.log_scale)),
+                            _p(_f32(scene.quat)), _p(_f32(scene.opacity)),
+                            _p(_f32(scene.color)), scene.sh_degree, ctypes.byref(cs),
+                            _p(np.ascontiguousarray(offsets, np.int64)),
+                            _p(np.ascontiguousarray(idx if len(idx) else np.zeros(1), np.uint32)),
+                            _p(image), _p(final_t), _p(n_contrib), _p(n_blend))
+    return dict(image=image, final_t=final_t, n_contrib=n_contrib, n_blend=n_blend)
+
+
+def grad64(scene, cam, offsets, idx, dl_dimage):
+    """Analytic FP64 gradient of sum(dl_dimage * image) with respect to
+    mean, log_scale, quat, opacity and colour (tile lists held fixed)."""
+    n = scene.n
+    g = dict(mean=np.zeros((n, 3)), log_scale=np.zeros((n, 3)), quat=np.zeros((n, 4)),
+             opacity=np.zeros(n), color=np.zeros(scene.color.shape))
+    cs = camera_struct(cam)
+    lib().or_grad64(n, _p(_f32(scene.mean)), _p(_f32(scene.log_scale)), _p(_f32(scene.quat)),
+                    _p(_f32(scene.opacity)), _p(_f32(scene.color)), scene.sh_degree,
+                    ctypes.byref(cs), _p(np.ascontiguousarray(offsets, np.int64)),
+                    _p(np.ascontiguousarray(idx if len(idx) else np.zeros(1), np.uint32)),
+                    _p(np.ascontiguousarray(dl_dimage, np.float64)), _p(g["mean"]),
+                    _p(g["log_scale"]), _p(g["quat"]), _p(g["opacity"]), _p(g["color"]))
+    return g

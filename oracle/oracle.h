@@ -14,6 +14,8 @@
  *                  blend (Sec. 3.1, Eq. 3), brute-force variant without tiles
  *   sh64.c         real spherical harmonics from the Legendre recurrence
  *   range.c        UpdateRange (Eq. 5), FP64 coverage for pins
+ *   grad64.c       FP64 forward with an FP64 projection, and its analytic
+ *                  gradient (reverse replay, chain rule to the parameters)
  *
  * Parity unpinned: nothing here reproduces the paper's PSNR/LPIPS tables
  * (they need the datasets and trained models).
@@ -94,6 +96,18 @@ void or_coverage64(int64_t n, const float *mean, const float *log_scale,
                    const float *quat, const float *opacity,
                    const or_camera *cam, double *cover, double *ux,
                    double *uy, double *cov2d);
+
+void or_forward64_full(int64_t n, const float *mean, const float *log_scale,
+                       const float *quat, const float *opacity, const float *color,
+                       int32_t sh_degree, const or_camera *cam, const int64_t *offsets,
+                       const uint32_t *idx, double *image, double *final_t,
+                       uint32_t *n_contrib, uint32_t *n_blend);
+
+int64_t or_grad64(int64_t n, const float *mean, const float *log_scale, const float *quat,
+                  const float *opacity, const float *color, int32_t sh_degree,
+                  const or_camera *cam, const int64_t *offsets, const uint32_t *idx,
+                  const double *dl_dimage, double *dmean, double *dlog_scale,
+                  double *dquat, double *dopacity, double *dcolor);
 
 #ifdef __cplusplus
 }
