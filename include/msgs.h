@@ -10,6 +10,7 @@
  *   ms_update_range   UpdateRange of the coverage bounds
  *   ms_bin            16x16 tile binning with a stable (tile, depth) order
  *   ms_raster         per-pixel front-to-back blend with early termination
+ *   ms_raster_bwd     gradient of the image with respect to the scene
  *
  * Conventions shared by every call:
  *   - Every pointer inside ms_scene_t, ms_proj_t, ms_bins_t and every
@@ -278,6 +279,50 @@ int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins,
               const ms_camera_t *cam, float *image, float *final_t,
               uint32_t *n_contrib, uint32_t *n_eval, void *ws,
               size_t ws_bytes, void *stream);
+
+/*
+ * Gradients of a loss with respect to the scene parameters, outputs of
+ * ms_raster_bwd; device buffers with the scene's shapes: dmean[n*3],
+ * dlog_scale[n*3], dquat[n*4] (with respect to the unnormalised
+ * quaternion), dopacity[n], dcolor (same layout as scene color).
+ */
+typedef struct {
+    float *dmean;
+    float *dlog_scale;
+    float *dquat;
+    float *dopacity;
+    float *dcolor;
+} ms_grads_t;
+
+/* Workspace bytes ms_raster_bwd needs for n Gaussians (9 floats each). */
+size_t ms_raster_bwd_workspace_bytes(int64_t n);
+
+/*
+ * Backward of ms_project -> ms_bin -> ms_raster for one frame (the gradient
+ * a multi-scale training step propagates, Sec. 4.1 "Multi-Scale
+ * Training").  Inputs: the frame's proj and bins as the forward left them,
+ * dl_dimage[3][H][W] (dL/d image, planar), and the forward's final_t and
+ * n_contrib.  Each tile's list is replayed backwards per pixel from its
+ * final transmittance, recomputing every alpha with the forward's exact
+ * FP32 operations (so the same Gaussians contribute):
+ *   dC/dalpha_k = T_k c_k - R_k / (1 - alpha_k),  dC/dc_k = alpha_k T_k,
+ * with R_k the colour behind Gaussian k (including T_final bg), then
+ * through alpha = min(0.99, sigma e^power) (no gradient when clamped), the
+ * centre and conic, V' = V + 0.3 I, the EWA covariance, the rotation of
+ * the normalised quaternion, exp(log_scale) and the SH colour (direction
+ * term included, zero where the colour was clamped at 0).  Gaussians the
+ * frame did not blend get zero.  Selection and coverage are not
+ * differentiated (the mask is discrete).  `ws` of
+ * ms_raster_bwd_workspace_bytes(n) bytes (16-B aligned) holds the
+ * per-Gaussian 2D gradients; every output and the workspace are
+ * overwritten.  Sums are accumulated with float atomics, so the last bits
+ * of a gradient may vary from run to run.
+ */
+int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
+                  const ms_proj_t *proj, const ms_bins_t *bins,
+                  const float *dl_dimage, const float *final_t,
+                  const uint32_t *n_contrib, const ms_grads_t *grads, void *ws,
+                  size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -59,6 +59,11 @@ class ms_proj_t(ctypes.Structure):
                 ("cover", P), ("mask", P), ("stats", P), ("n", ctypes.c_int64)]
 
 
+class ms_grads_t(ctypes.Structure):
+    _fields_ = [("dmean", P), ("dlog_scale", P), ("dquat", P), ("dopacity", P),
+                ("dcolor", P)]
+
+
 class ms_bins_t(ctypes.Structure):
     _fields_ = [("gauss_idx", P), ("ranges", P), ("counts", P),
                 ("dup_capacity", ctypes.c_int64)]
@@ -86,6 +91,11 @@ _SIGNATURES = [
                                      ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64), P]),
     ("ms_raster_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
+    ("ms_raster_bwd_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64]),
+    ("ms_raster_bwd", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
+                                     ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
+                                     P, P, P, ctypes.POINTER(ms_grads_t), P, ctypes.c_size_t,
+                                     P]),
     ("ms_raster", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
                                  ctypes.POINTER(ms_camera_t), P, P, P, P, P,
                                  ctypes.c_size_t, P]),
@@ -206,6 +216,19 @@ def ms_raster(proj: ms_proj_t, bins: ms_bins_t, cam: ms_camera_t, image_ptr: int
     _check(lib().ms_raster(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam),
                            P(image_ptr), P(final_t_ptr), P(n_contrib_ptr), P(n_eval_ptr),
                            P(ws_ptr), ws_bytes, P(_stream(stream))))
+
+
+def ms_raster_bwd_workspace_bytes(n: int) -> int:
+    return int(lib().ms_raster_bwd_workspace_bytes(n))
+
+
+def ms_raster_bwd(scene: ms_scene_t, cam: ms_camera_t, proj: ms_proj_t, bins: ms_bins_t,
+                  dl_ptr: int, final_t_ptr: int, n_contrib_ptr: int, grads: ms_grads_t,
+                  ws_ptr: int, ws_bytes: int, stream=None):
+    _check(lib().ms_raster_bwd(ctypes.byref(scene), ctypes.byref(cam), ctypes.byref(proj),
+                               ctypes.byref(bins), P(dl_ptr), P(final_t_ptr),
+                               P(n_contrib_ptr), ctypes.byref(grads), P(ws_ptr), ws_bytes,
+                               P(_stream(stream))))
 
 
 # ------------------------------------------------------ buffer helpers

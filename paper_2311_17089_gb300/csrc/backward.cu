@@ -1,0 +1,531 @@
+// Gradient of the rendered image with respect to the scene parameters
+// (the back-propagation a multi-scale training step runs, Sec. 4.1
+// "Multi-Scale Training").
+//
+// raster_bwd_kernel: one CTA per tile replays the tile's list backwards for
+// every pixel, from its final transmittance and its last contributor
+// (both stored by ms_raster), recomputing each alpha with exactly the
+// forward's FP32 operations, so the same Gaussians contribute.  With R the
+// colour behind Gaussian k (including T_final * bg):
+//   dC/dalpha_k = T_k c_k - R / (1 - alpha_k),  dC/dc_k = alpha_k T_k,
+//   T_k = T_{k+1} / (1 - alpha_k),  R += alpha_k T_k c_k.
+// alpha = sigma e^power (below the 0.99 clamp) gives dsigma and dpower, and
+// power = -(a dx^2 + c dy^2)/2 - b dx dy gives the centre and conic
+// gradients.  Per record, a warp sums its pixels' contributions with
+// shuffles, warps meet in shared memory, and the CTA adds its sums to the
+// per-Gaussian 2D gradient with one atomic per value.
+//
+// project_bwd_kernel: per Gaussian, the chain rule from (centre, conic,
+// opacity, colour) through V' = V + 0.3 I, V = J W Sigma W^T J^T, the
+// Jacobian, Sigma = R diag(e^s)^2 R^T, the normalised quaternion and the
+// SH colour (basis derivatives in closed form, projected on the sphere).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace msgs {
+
+constexpr int kBwdThreads = 256;
+constexpr int kBwdBatch = 256;
+constexpr int kG2 = 9;  // dux, duy, da, db, dc, dsigma, dr, dg, db
+constexpr float kLog2eB = 1.4426950408889634f;
+constexpr float kInvConicA = -1.3862943611198906f;  // 1 / (-log2(e)/2)
+constexpr float kInvConicB = -0.6931471805599453f;  // 1 / (-log2(e))
+
+__device__ __forceinline__ float ex2_approx_b(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct BwdArgs {
+    const uint32_t *ranges;
+    const uint32_t *gidx;
+    const float4 *rec;
+    uint32_t n_rec;
+    int W, H, tiles_x;
+    float bg0, bg1, bg2;
+    const float *dl;        // [3][H][W]
+    const float *final_t;   // [H][W]
+    const uint32_t *n_contrib;
+    float *g2;              // [n][kG2]
+};
+
+__global__ void __launch_bounds__(kBwdThreads)
+raster_bwd_kernel(BwdArgs a) {
+    __shared__ float4 s_r0[kBwdBatch], s_r1[kBwdBatch];
+    __shared__ float2 s_r2[kBwdBatch];
+    __shared__ uint32_t s_idx[kBwdBatch];
+    __shared__ float s_acc[kBwdBatch][kG2 + 1];
+    __shared__ uint32_t s_max;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int px = tx * 16 + (wid & 1) * 8 + (lane & 7);
+    const int py = ty * 16 + (wid >> 1) * 4 + (lane >> 3);
+    const bool inside = px < a.W && py < a.H;
+    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const uint32_t start = a.ranges[2 * tile];
+    uint32_t nc = 0;
+    float T = 1.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+    if (inside) {
+        const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+        nc = a.n_contrib[p];
+        T = a.final_t[p];
+        d0 = a.dl[p];
+        d1 = a.dl[plane + p];
+        d2 = a.dl[2 * plane + p];
+    }
+    float R0 = T * a.bg0, R1 = T * a.bg1, R2 = T * a.bg2;
+    if (tid == 0) s_max = 0;
+    for (int i = tid; i < kBwdBatch * (kG2 + 1); i += kBwdThreads) (&s_acc[0][0])[i] = 0.0f;
+    __syncthreads();
+    atomicMax(&s_max, nc);
+    __syncthreads();
+    const uint32_t top = s_max;
+    for (int64_t hi = top; hi > 0; hi -= kBwdBatch) {
+        const uint32_t lo = hi > kBwdBatch ? (uint32_t)hi - kBwdBatch : 0u;
+        const uint32_t cnt = (uint32_t)hi - lo;
+        if ((uint32_t)tid < cnt) {
+            uint32_t g = a.gidx[start + lo + tid];
+            if (g >= a.n_rec) g = 0;  // unreachable unless binning reported an error
+            s_idx[tid] = g;
+            s_r0[tid] = a.rec[3 * (size_t)g];
+            s_r1[tid] = a.rec[3 * (size_t)g + 1];
+            const float4 r2 = a.rec[3 * (size_t)g + 2];
+            s_r2[tid] = make_float2(r2.x, r2.y);
+        }
+        __syncthreads();
+        for (int j = (int)cnt - 1; j >= 0; j--) {
+            const uint32_t pos = lo + (uint32_t)j;  // list position of the record
+            float v[kG2];
+#pragma unroll
+            for (int q = 0; q < kG2; q++) v[q] = 0.0f;
+            bool acc = false;
+            if (pos < nc) {
+                const float4 r0 = s_r0[j], r1 = s_r1[j];
+                const float2 r2 = s_r2[j];
+                // the forward's exact FP32 operations
+                const float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
+                const float u = __fmaf_rn(r0.w, dy, __fmul_rn(r0.z, dx));
+                const float pw = __fmaf_rn(__fmul_rn(r1.x, dy), dy, __fmul_rn(dx, u));
+                if (pw <= 0.0f && pw >= r2.y) {
+                    acc = true;
+                    const float e = ex2_approx_b(pw);
+                    const float G = r1.y * e;
+                    const float al = fminf(0.99f, G);
+                    const float om = 1.0f - al;
+                    const float Tk = T / om;
+                    const float dal = d0 * (Tk * r1.z - R0 / om) + d1 * (Tk * r1.w - R1 / om) +
+                                      d2 * (Tk * r2.x - R2 / om);
+                    const float w = al * Tk;
+                    v[6] = w * d0;
+                    v[7] = w * d1;
+                    v[8] = w * d2;
+                    R0 = fmaf(w, r1.z, R0);
+                    R1 = fmaf(w, r1.w, R1);
+                    R2 = fmaf(w, r2.x, R2);
+                    T = Tk;
+                    if (G < 0.99f) {
+                        v[5] = dal * e;
+                        const float dpow = dal * al;
+                        const float ca = r0.z * kInvConicA, cb = r0.w * kInvConicB,
+                                    cc = r1.x * kInvConicA;
+                        v[0] = dpow * (ca * dx + cb * dy);
+                        v[1] = dpow * (cc * dy + cb * dx);
+                        v[2] = dpow * (-0.5f * dx * dx);
+                        v[3] = dpow * (-dx * dy);
+                        v[4] = dpow * (-0.5f * dy * dy);
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, acc)) {
+#pragma unroll
+                for (int q = 0; q < kG2; q++) {
+                    float x = v[q];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    v[q] = x;
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int q = 0; q < kG2; q++) atomicAdd(&s_acc[j][q], v[q]);
+                    s_acc[j][kG2] = 1.0f;
+                }
+            }
+        }
+        __syncthreads();
+        if ((uint32_t)tid < cnt && s_acc[tid][kG2] != 0.0f) {
+            float *dst = a.g2 + (size_t)s_idx[tid] * kG2;
+#pragma unroll
+            for (int q = 0; q < kG2; q++) {
+                if (s_acc[tid][q] != 0.0f) atomicAdd(dst + q, s_acc[tid][q]);
+                s_acc[tid][q] = 0.0f;
+            }
+            s_acc[tid][kG2] = 0.0f;
+        }
+        __syncthreads();
+    }
+}
+
+struct SceneB {
+    int64_t n;
+    int sh_degree;
+    const float *mean, *quat, *color, *scale;
+};
+
+struct CamB {
+    float W[9], t[3], campos[3];
+    float fx, fy, width, height;
+};
+
+// d/d(x, y, z) of the real SH basis polynomials (degree <= 3), k = l^2 + l + m
+template <int DEG>
+__device__ __forceinline__ void sh_grad(float x, float y, float z, const float *coef,
+                                        const float dr[3], float g[3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float Dx[K], Dy[K], Dz[K];
+    Dx[0] = Dy[0] = Dz[0] = 0.0f;
+    if constexpr (DEG >= 1) {
+        const float c1 = 0.4886025119029199f;
+        Dx[1] = 0; Dy[1] = c1; Dz[1] = 0;
+        Dx[2] = 0; Dy[2] = 0; Dz[2] = c1;
+        Dx[3] = c1; Dy[3] = 0; Dz[3] = 0;
+    }
+    if constexpr (DEG >= 2) {
+        const float k4 = 1.0925484305920792f, k6 = 0.31539156525252005f,
+                    k8 = 0.5462742152960396f;
+        Dx[4] = k4 * y; Dy[4] = k4 * x; Dz[4] = 0;
+        Dx[5] = 0; Dy[5] = k4 * z; Dz[5] = k4 * y;
+        Dx[6] = -2 * k6 * x; Dy[6] = -2 * k6 * y; Dz[6] = 4 * k6 * z;
+        Dx[7] = k4 * z; Dy[7] = 0; Dz[7] = k4 * x;
+        Dx[8] = 2 * k8 * x; Dy[8] = -2 * k8 * y; Dz[8] = 0;
+    }
+    if constexpr (DEG >= 3) {
+        const float k9 = 0.5900435899266435f, k10 = 2.890611442640554f,
+                    k11 = 0.4570457994644658f, k12 = 0.3731763325901154f,
+                    k14 = 1.445305721320277f;
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Dx[9] = 6 * k9 * x * y; Dy[9] = 3 * k9 * (xx - yy); Dz[9] = 0;
+        Dx[10] = k10 * y * z; Dy[10] = k10 * x * z; Dz[10] = k10 * x * y;
+        Dx[11] = -2 * k11 * x * y; Dy[11] = k11 * (4 * zz - xx - 3 * yy); Dz[11] = 8 * k11 * y * z;
+        Dx[12] = -6 * k12 * x * z; Dy[12] = -6 * k12 * y * z; Dz[12] = k12 * (6 * zz - 3 * xx - 3 * yy);
+        Dx[13] = k11 * (4 * zz - 3 * xx - yy); Dy[13] = -2 * k11 * x * y; Dz[13] = 8 * k11 * x * z;
+        Dx[14] = 2 * k14 * x * z; Dy[14] = -2 * k14 * y * z; Dz[14] = k14 * (xx - yy);
+        Dx[15] = 3 * k9 * (xx - yy); Dy[15] = -6 * k9 * x * y; Dz[15] = 0;
+    }
+    g[0] = g[1] = g[2] = 0.0f;
+#pragma unroll
+    for (int k = 1; k < K; k++) {
+        const float s = dr[0] * coef[3 * k] + dr[1] * coef[3 * k + 1] + dr[2] * coef[3 * k + 2];
+        g[0] = fmaf(s, Dx[k], g[0]);
+        g[1] = fmaf(s, Dy[k], g[1]);
+        g[2] = fmaf(s, Dz[k], g[2]);
+    }
+}
+
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
+    Y[0] = 0.28209479177387814f;
+    if constexpr (DEG >= 1) {
+        Y[1] = 0.4886025119029199f * y;
+        Y[2] = 0.4886025119029199f * z;
+        Y[3] = 0.4886025119029199f * x;
+    }
+    if constexpr (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;
+        Y[5] = 1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+        Y[7] = 1.0925484305920792f * x * z;
+        Y[8] = 0.5462742152960396f * (xx - yy);
+        if constexpr (DEG >= 3) {
+            Y[9] = 0.5900435899266435f * y * (3.0f * xx - yy);
+            Y[10] = 2.890611442640554f * x * y * z;
+            Y[11] = 0.4570457994644658f * y * (4.0f * zz - xx - yy);
+            Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = 0.4570457994644658f * x * (4.0f * zz - xx - yy);
+            Y[14] = 1.445305721320277f * z * (xx - yy);
+            Y[15] = 0.5900435899266435f * x * (xx - 3.0f * yy);
+        }
+    }
+}
+
+// Colour backward: SH coefficient gradients and the view-direction term of
+// the mean gradient.  Returns the latter in dmu.
+template <int DEG>
+__device__ __forceinline__ void color_bwd(int64_t i, const SceneB &sc, const CamB &cam,
+                                          const float *g2, float *dcolor, float dmu[3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const float *coef = sc.color + i * K * 3;
+    float dx = sc.mean[3 * i] - cam.campos[0], dy = sc.mean[3 * i + 1] - cam.campos[1],
+          dz = sc.mean[3 * i + 2] - cam.campos[2];
+    const float r = sqrtf(dx * dx + dy * dy + dz * dz), ir = 1.0f / r;
+    const float x = dx * ir, y = dy * ir, z = dz * ir;
+    float Y[K];
+    sh_basis<DEG>(x, y, z, Y);
+    float pre[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        pre[0] = fmaf(coef[3 * k], Y[k], pre[0]);
+        pre[1] = fmaf(coef[3 * k + 1], Y[k], pre[1]);
+        pre[2] = fmaf(coef[3 * k + 2], Y[k], pre[2]);
+    }
+    float dr[3];
+    for (int c = 0; c < 3; c++) dr[c] = pre[c] > 0.0f ? g2[6 + c] : 0.0f;
+    float *dst = dcolor + i * K * 3;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        dst[3 * k] = dr[0] * Y[k];
+        dst[3 * k + 1] = dr[1] * Y[k];
+        dst[3 * k + 2] = dr[2] * Y[k];
+    }
+    dmu[0] = dmu[1] = dmu[2] = 0.0f;
+    if constexpr (DEG >= 1) {
+        float gd[3];
+        sh_grad<DEG>(x, y, z, coef, dr, gd);
+        // project on the sphere's tangent plane, then through d / |d|
+        const float dd = gd[0] * x + gd[1] * y + gd[2] * z;
+        dmu[0] = (gd[0] - x * dd) * ir;
+        dmu[1] = (gd[1] - y * dd) * ir;
+        dmu[2] = (gd[2] - z * dd) * ir;
+    }
+}
+
+struct GradsK {
+    float *dmean, *dlog_scale, *dquat, *dopacity, *dcolor;
+};
+
+__global__ void __launch_bounds__(256)
+project_bwd_kernel(SceneB sc, CamB cam, const float *__restrict__ g2all, GradsK out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sc.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float *g2 = g2all + i * kG2;
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < kG2; q++) any |= g2[q] != 0.0f;
+        if (!any) continue;
+        const float *W = cam.W;
+        const float m0 = sc.mean[3 * i], m1 = sc.mean[3 * i + 1], m2 = sc.mean[3 * i + 2];
+        const float tx = W[0] * m0 + W[1] * m1 + W[2] * m2 + cam.t[0];
+        const float ty = W[3] * m0 + W[4] * m1 + W[5] * m2 + cam.t[1];
+        const float tz = W[6] * m0 + W[7] * m1 + W[8] * m2 + cam.t[2];
+        const float4 q4 = reinterpret_cast<const float4 *>(sc.quat)[i];
+        const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+        const float iq = 1.0f / qn;
+        const float w = q4.x * iq, x = q4.y * iq, y = q4.z * iq, z = q4.w * iq;
+        float R[9];
+        R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+        R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+        R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+        const float se[3] = {sc.scale[3 * i], sc.scale[3 * i + 1], sc.scale[3 * i + 2]};
+        float M[9], Sg[9];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) M[3 * r + c] = R[3 * r + c] * se[c];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++)
+                Sg[3 * r + c] = M[3 * r] * M[3 * c] + M[3 * r + 1] * M[3 * c + 1] +
+                                M[3 * r + 2] * M[3 * c + 2];
+        const float limx = 1.3f * (0.5f * cam.width / cam.fx);
+        const float limy = 1.3f * (0.5f * cam.height / cam.fy);
+        const float xr = tx / tz, yr = ty / tz;
+        const bool clx = fabsf(xr) > limx, cly = fabsf(yr) > limy;
+        const float xc = fminf(limx, fmaxf(-limx, xr)), yc = fminf(limy, fmaxf(-limy, yr));
+        const float J00 = cam.fx / tz, J02 = -cam.fx * xc / tz;
+        const float J11 = cam.fy / tz, J12 = -cam.fy * yc / tz;
+        float T[6];
+        for (int c = 0; c < 3; c++) {
+            T[c] = J00 * W[c] + J02 * W[6 + c];
+            T[3 + c] = J11 * W[3 + c] + J12 * W[6 + c];
+        }
+        // V' and its inverse (the conic)
+        float TS[6];
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 3; c++)
+                TS[3 * r + c] = T[3 * r] * Sg[c] + T[3 * r + 1] * Sg[3 + c] + T[3 * r + 2] * Sg[6 + c];
+        const float va = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + 0.3f;
+        const float vb = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+        const float vc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + 0.3f;
+        const float idet = 1.0f / (va * vc - vb * vb);
+        const float Qa = vc * idet, Qb = -vb * idet, Qc = va * idet;
+        float dt0 = 0.0f, dt1 = 0.0f, dt2 = 0.0f;
+        // centre
+        dt0 += g2[0] * cam.fx / tz;
+        dt2 += -g2[0] * cam.fx * tx / (tz * tz);
+        dt1 += g2[1] * cam.fy / tz;
+        dt2 += -g2[1] * cam.fy * ty / (tz * tz);
+        // G_V = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]]
+        const float ga = g2[2], gb = 0.5f * g2[3], gc = g2[4];
+        const float A00 = Qa * ga + Qb * gb, A01 = Qa * gb + Qb * gc;
+        const float A10 = Qb * ga + Qc * gb, A11 = Qb * gb + Qc * gc;
+        const float GV0 = -(A00 * Qa + A01 * Qb), GV1 = -(A00 * Qb + A01 * Qc),
+                    GV2 = -(A10 * Qb + A11 * Qc);
+        const float GVm[4] = {GV0, GV1, GV1, GV2};
+        // G_Sigma = T^T G_V T ; G_T = 2 G_V T Sigma
+        float GS[9];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) {
+                float v = 0.0f;
+                for (int p = 0; p < 2; p++)
+                    for (int q = 0; q < 2; q++) v += T[3 * p + r] * GVm[2 * p + q] * T[3 * q + c];
+                GS[3 * r + c] = v;
+            }
+        float GT[6];
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 3; c++)
+                GT[3 * r + c] = 2.0f * (GVm[2 * r] * TS[c] + GVm[2 * r + 1] * TS[3 + c]);
+        // G_J = G_T W^T
+        float GJ[6];
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 3; c++)
+                GJ[3 * r + c] = GT[3 * r] * W[3 * c] + GT[3 * r + 1] * W[3 * c + 1] +
+                                GT[3 * r + 2] * W[3 * c + 2];
+        const float itz2 = 1.0f / (tz * tz);
+        dt2 += GJ[0] * (-cam.fx * itz2) + GJ[4] * (-cam.fy * itz2) + GJ[2] * (cam.fx * xc * itz2) +
+               GJ[5] * (cam.fy * yc * itz2);
+        const float dxc = GJ[2] * (-cam.fx / tz), dyc = GJ[5] * (-cam.fy / tz);
+        if (!clx) {
+            dt0 += dxc / tz;
+            dt2 += -dxc * tx * itz2;
+        }
+        if (!cly) {
+            dt1 += dyc / tz;
+            dt2 += -dyc * ty * itz2;
+        }
+        float dmu[3] = {0.0f, 0.0f, 0.0f};
+        switch (sc.sh_degree) {
+        case 0: color_bwd<0>(i, sc, cam, g2, out.dcolor, dmu); break;
+        case 1: color_bwd<1>(i, sc, cam, g2, out.dcolor, dmu); break;
+        case 2: color_bwd<2>(i, sc, cam, g2, out.dcolor, dmu); break;
+        case 3: color_bwd<3>(i, sc, cam, g2, out.dcolor, dmu); break;
+        default:
+            out.dcolor[3 * i] = g2[6];
+            out.dcolor[3 * i + 1] = g2[7];
+            out.dcolor[3 * i + 2] = g2[8];
+        }
+        for (int c = 0; c < 3; c++)
+            out.dmean[3 * i + c] = W[c] * dt0 + W[3 + c] * dt1 + W[6 + c] * dt2 + dmu[c];
+        // Sigma = M M^T: G_M = 2 G_Sigma M;  M = R diag(se)
+        float GM[9];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++)
+                GM[3 * r + c] = 2.0f * (GS[3 * r] * M[c] + GS[3 * r + 1] * M[3 + c] +
+                                        GS[3 * r + 2] * M[6 + c]);
+        float GR[9];
+        for (int c = 0; c < 3; c++) {
+            float gs = 0.0f;
+            for (int r = 0; r < 3; r++) {
+                gs += R[3 * r + c] * GM[3 * r + c];
+                GR[3 * r + c] = GM[3 * r + c] * se[c];
+            }
+            out.dlog_scale[3 * i + c] = gs * se[c];
+        }
+        float dq[4];
+        dq[0] = GR[1] * (-2 * z) + GR[2] * (2 * y) + GR[3] * (2 * z) + GR[5] * (-2 * x) +
+                GR[6] * (-2 * y) + GR[7] * (2 * x);
+        dq[1] = GR[1] * (2 * y) + GR[2] * (2 * z) + GR[3] * (2 * y) + GR[4] * (-4 * x) +
+                GR[5] * (-2 * w) + GR[6] * (2 * z) + GR[7] * (2 * w) + GR[8] * (-4 * x);
+        dq[2] = GR[0] * (-4 * y) + GR[1] * (2 * x) + GR[2] * (2 * w) + GR[3] * (2 * x) +
+                GR[5] * (2 * z) + GR[6] * (-2 * w) + GR[7] * (2 * z) + GR[8] * (-4 * y);
+        dq[3] = GR[0] * (-4 * z) + GR[1] * (-2 * w) + GR[2] * (2 * x) + GR[3] * (2 * w) +
+                GR[4] * (-4 * z) + GR[5] * (2 * y) + GR[6] * (2 * x) + GR[7] * (2 * y);
+        const float dot = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+        out.dquat[4 * i] = (dq[0] - w * dot) * iq;
+        out.dquat[4 * i + 1] = (dq[1] - x * dot) * iq;
+        out.dquat[4 * i + 2] = (dq[2] - y * dot) * iq;
+        out.dquat[4 * i + 3] = (dq[3] - z * dot) * iq;
+        out.dopacity[i] = g2[5];
+    }
+}
+
+}  // namespace msgs
+
+using namespace msgs;
+
+extern "C" size_t ms_raster_bwd_workspace_bytes(int64_t n) {
+    if (n < 0 || n > INT32_MAX) return 0;
+    return (size_t)(n > 0 ? n : 1) * kG2 * sizeof(float);
+}
+
+extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
+                             const ms_proj_t *proj, const ms_bins_t *bins,
+                             const float *dl_dimage, const float *final_t,
+                             const uint32_t *n_contrib, const ms_grads_t *grads, void *ws,
+                             size_t ws_bytes, void *stream) {
+    if (!scene || !cam || !proj || !bins || !grads)
+        return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (scene->n < 0 || scene->n > INT32_MAX) return fail(MS_ERR_INVALID_ARG, "scene n out of range");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+        return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
+    if (!dl_dimage || !final_t || !n_contrib)
+        return fail(MS_ERR_INVALID_ARG, "dl_dimage, final_t and n_contrib are required");
+    if (scene->n > 0 && (!grads->dmean || !grads->dlog_scale || !grads->dquat ||
+                         !grads->dopacity || !grads->dcolor))
+        return fail(MS_ERR_INVALID_ARG, "ms_grads_t has a NULL buffer");
+    if (scene->n > 0 && (!scene->mean || !scene->quat || !scene->scale || !scene->color))
+        return fail(MS_ERR_INVALID_ARG, "scene mean/quat/scale/color is NULL");
+    if (scene->sh_degree < -1 || scene->sh_degree > 3)
+        return fail(MS_ERR_INVALID_ARG, "sh_degree must be in -1..3");
+    if (proj->n < scene->n || !proj->rec) return fail(MS_ERR_INVALID_ARG, "ms_proj_t too small");
+    const size_t need = ms_raster_bwd_workspace_bytes(scene->n);
+    if (!ws || ws_bytes < need || !aligned(ws, 16))
+        return fail(MS_ERR_INVALID_ARG, "backward workspace missing, too small or misaligned");
+    cudaStream_t st = as_stream(stream);
+    const int64_t n = scene->n;
+    const int K = scene->sh_degree < 0 ? 1 : (scene->sh_degree + 1) * (scene->sh_degree + 1);
+    int rc;
+    if ((rc = cuda_check(cudaMemsetAsync(ws, 0, need, st), "bwd workspace memset"))) return rc;
+    if (n > 0) {
+        if ((rc = cuda_check(cudaMemsetAsync(grads->dmean, 0, n * 3 * sizeof(float), st), "memset")) ||
+            (rc = cuda_check(cudaMemsetAsync(grads->dlog_scale, 0, n * 3 * sizeof(float), st), "memset")) ||
+            (rc = cuda_check(cudaMemsetAsync(grads->dquat, 0, n * 4 * sizeof(float), st), "memset")) ||
+            (rc = cuda_check(cudaMemsetAsync(grads->dopacity, 0, n * sizeof(float), st), "memset")) ||
+            (rc = cuda_check(cudaMemsetAsync(grads->dcolor, 0, n * K * 3 * sizeof(float), st), "memset")))
+            return rc;
+    }
+    const int tiles_x = (cam->width + 15) / 16, tiles_y = (cam->height + 15) / 16;
+    BwdArgs a;
+    a.ranges = bins->ranges;
+    a.gidx = bins->gauss_idx;
+    a.rec = reinterpret_cast<const float4 *>(proj->rec);
+    a.n_rec = (uint32_t)proj->n;
+    a.W = cam->width;
+    a.H = cam->height;
+    a.tiles_x = tiles_x;
+    a.bg0 = cam->bg[0];
+    a.bg1 = cam->bg[1];
+    a.bg2 = cam->bg[2];
+    a.dl = dl_dimage;
+    a.final_t = final_t;
+    a.n_contrib = n_contrib;
+    a.g2 = static_cast<float *>(ws);
+    raster_bwd_kernel<<<tiles_x * tiles_y, kBwdThreads, 0, st>>>(a);
+    if (n > 0) {
+        SceneB sb;
+        sb.n = n;
+        sb.sh_degree = scene->sh_degree;
+        sb.mean = scene->mean;
+        sb.quat = scene->quat;
+        sb.color = scene->color;
+        sb.scale = scene->scale;
+        CamB cb;
+        for (int k = 0; k < 9; k++) cb.W[k] = cam->R[k];
+        for (int k = 0; k < 3; k++) {
+            cb.t[k] = cam->t[k];
+            cb.campos[k] = cam->campos[k];
+        }
+        cb.fx = cam->fx;
+        cb.fy = cam->fy;
+        cb.width = (float)cam->width;
+        cb.height = (float)cam->height;
+        GradsK gk = {grads->dmean, grads->dlog_scale, grads->dquat, grads->dopacity,
+                     grads->dcolor};
+        int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
+        project_bwd_kernel<<<grid, 256, 0, st>>>(sb, cb, static_cast<const float *>(ws), gk);
+    }
+    return cuda_check(cudaGetLastError(), "backward launches");
+}

@@ -293,6 +293,7 @@ __device__ __forceinline__ bool blend_one(float p, float opacity, float r, float
 __device__ __forceinline__ void blend_pairs(const PairBuf &pb, uint32_t cnt, uint32_t pos0,
                                             f32x2 fx2, f32x2 fy2, PixelState &s) {
     const uint32_t np = (cnt + 1) >> 1;
+#pragma unroll 2
     for (uint32_t m = 0; m < np; m++) {
         const ulonglong2 v0 = *reinterpret_cast<const ulonglong2 *>(&pb.q0[m]);
         const ulonglong2 v1 = *reinterpret_cast<const ulonglong2 *>(&pb.q1[m]);
