@@ -11,6 +11,7 @@
  *   ms_bin            16x16 tile binning with a stable (tile, depth) order
  *   ms_raster         per-pixel front-to-back blend with early termination
  *   ms_raster_bwd     gradient of the image with respect to the scene
+ *   ms_l1_loss_grad   L1 image loss and its gradient (training step)
  *
  * Conventions shared by every call:
  *   - Every pointer inside ms_scene_t, ms_proj_t, ms_bins_t and every
@@ -314,15 +315,32 @@ size_t ms_raster_bwd_workspace_bytes(int64_t n);
  * frame did not blend get zero.  Selection and coverage are not
  * differentiated (the mask is discrete).  `ws` of
  * ms_raster_bwd_workspace_bytes(n) bytes (16-B aligned) holds the
- * per-Gaussian 2D gradients; every output and the workspace are
- * overwritten.  Sums are accumulated with float atomics, so the last bits
- * of a gradient may vary from run to run.
+ * per-Gaussian 2D gradients and is overwritten.  `flags` = 0 overwrites
+ * every output (zero for Gaussians the frame did not blend);
+ * MS_BWD_ACCUMULATE adds this frame's gradient to the outputs instead (a
+ * batch of views: the first call overwrites, the others accumulate).
+ * Sums are accumulated with float atomics, so the last bits of a gradient
+ * may vary from run to run.
  */
+#define MS_BWD_ACCUMULATE 1u
 int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
                   const ms_proj_t *proj, const ms_bins_t *bins,
                   const float *dl_dimage, const float *final_t,
-                  const uint32_t *n_contrib, const ms_grads_t *grads, void *ws,
-                  size_t ws_bytes, void *stream);
+                  const uint32_t *n_contrib, const ms_grads_t *grads, uint32_t flags,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * L1 photometric loss of a training step (Sec. 4.1 trains with the image
+ * loss of the single-scale method; its L1 term):
+ *   dl_dimage[i] = weight * sign(image[i] - target[i])   (sign(0) = 0)
+ *   *loss_sum   += weight * sum_i |image[i] - target[i]|  (if loss_sum)
+ * over `count` FP32 values.  weight = 1 / count gives the mean.  All
+ * pointers are device memory; loss_sum may be NULL, and it is accumulated
+ * with atomics (zero it before the first view of a batch).  count = 0 is a
+ * no-op.
+ */
+int ms_l1_loss_grad(const float *image, const float *target, int64_t count, float weight,
+                    float *dl_dimage, float *loss_sum, void *stream);
 
 #ifdef __cplusplus
 }

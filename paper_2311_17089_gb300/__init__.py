@@ -27,6 +27,7 @@ MS_SELECTIVE, MS_ALL_LEVELS, MS_FILTER_SMALL = 0, 1, 2
 MODES = {"selective": MS_SELECTIVE, "all_levels": MS_ALL_LEVELS,
          "filter_small": MS_FILTER_SMALL}
 MS_STATS_WORDS = 1040
+MS_BWD_ACCUMULATE = 1
 REC_FLOATS = 12
 
 P = ctypes.c_void_p
@@ -94,8 +95,9 @@ _SIGNATURES = [
     ("ms_raster_bwd_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64]),
     ("ms_raster_bwd", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
                                      ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
-                                     P, P, P, ctypes.POINTER(ms_grads_t), P, ctypes.c_size_t,
-                                     P]),
+                                     P, P, P, ctypes.POINTER(ms_grads_t), ctypes.c_uint32, P,
+                                     ctypes.c_size_t, P]),
+    ("ms_l1_loss_grad", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_float, P, P, P]),
     ("ms_raster", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
                                  ctypes.POINTER(ms_camera_t), P, P, P, P, P,
                                  ctypes.c_size_t, P]),
@@ -224,11 +226,17 @@ def ms_raster_bwd_workspace_bytes(n: int) -> int:
 
 def ms_raster_bwd(scene: ms_scene_t, cam: ms_camera_t, proj: ms_proj_t, bins: ms_bins_t,
                   dl_ptr: int, final_t_ptr: int, n_contrib_ptr: int, grads: ms_grads_t,
-                  ws_ptr: int, ws_bytes: int, stream=None):
+                  flags: int, ws_ptr: int, ws_bytes: int, stream=None):
     _check(lib().ms_raster_bwd(ctypes.byref(scene), ctypes.byref(cam), ctypes.byref(proj),
                                ctypes.byref(bins), P(dl_ptr), P(final_t_ptr),
-                               P(n_contrib_ptr), ctypes.byref(grads), P(ws_ptr), ws_bytes,
-                               P(_stream(stream))))
+                               P(n_contrib_ptr), ctypes.byref(grads), int(flags), P(ws_ptr),
+                               ws_bytes, P(_stream(stream))))
+
+
+def ms_l1_loss_grad(image_ptr: int, target_ptr: int, count: int, weight: float, dl_ptr: int,
+                    loss_sum_ptr: int, stream=None):
+    _check(lib().ms_l1_loss_grad(P(image_ptr), P(target_ptr), int(count), float(weight),
+                                 P(dl_ptr), P(loss_sum_ptr), P(_stream(stream))))
 
 
 # ------------------------------------------------------ buffer helpers

@@ -80,7 +80,7 @@ class GaussianRender(torch.autograd.Function):
                            _ptr(g["opacity"]), _ptr(g["color"]))
         ms_raster_bwd(sc, camera_struct(frame.cam), r.proj, r.bins,
                       _ptr(grad_image.contiguous()), _ptr(frame.final_t),
-                      _ptr(frame.n_contrib), grads, _ptr(frame.bwd_ws), frame.bwd_ws_bytes)
+                      _ptr(frame.n_contrib), grads, 0, _ptr(frame.bwd_ws), frame.bwd_ws_bytes)
         return (g["mean"], g["log_scale"], g["quat"], g["opacity"], g["color"], None, None,
                 None, None, None, None, None)
 

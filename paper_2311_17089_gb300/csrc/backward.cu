@@ -255,11 +255,15 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
     }
 }
 
+// Store or accumulate one gradient entry.
+__device__ __forceinline__ void put(float *p, float v, bool acc) { *p = acc ? *p + v : v; }
+
 // Colour backward: SH coefficient gradients and the view-direction term of
 // the mean gradient.  Returns the latter in dmu.
 template <int DEG>
 __device__ __forceinline__ void color_bwd(int64_t i, const SceneB &sc, const CamB &cam,
-                                          const float *g2, float *dcolor, float dmu[3]) {
+                                          const float *g2, float *dcolor, bool acc,
+                                          float dmu[3]) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const float *coef = sc.color + i * K * 3;
     float dx = sc.mean[3 * i] - cam.campos[0], dy = sc.mean[3 * i + 1] - cam.campos[1],
@@ -280,9 +284,9 @@ __device__ __forceinline__ void color_bwd(int64_t i, const SceneB &sc, const Cam
     float *dst = dcolor + i * K * 3;
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        dst[3 * k] = dr[0] * Y[k];
-        dst[3 * k + 1] = dr[1] * Y[k];
-        dst[3 * k + 2] = dr[2] * Y[k];
+        put(dst + 3 * k, dr[0] * Y[k], acc);
+        put(dst + 3 * k + 1, dr[1] * Y[k], acc);
+        put(dst + 3 * k + 2, dr[2] * Y[k], acc);
     }
     dmu[0] = dmu[1] = dmu[2] = 0.0f;
     if constexpr (DEG >= 1) {
@@ -298,7 +302,9 @@ __device__ __forceinline__ void color_bwd(int64_t i, const SceneB &sc, const Cam
 
 struct GradsK {
     float *dmean, *dlog_scale, *dquat, *dopacity, *dcolor;
+    bool acc;  // add to the outputs instead of overwriting them
 };
+
 
 __global__ void __launch_bounds__(256)
 project_bwd_kernel(SceneB sc, CamB cam, const float *__restrict__ g2all, GradsK out) {
@@ -398,17 +404,18 @@ project_bwd_kernel(SceneB sc, CamB cam, const float *__restrict__ g2all, GradsK 
         }
         float dmu[3] = {0.0f, 0.0f, 0.0f};
         switch (sc.sh_degree) {
-        case 0: color_bwd<0>(i, sc, cam, g2, out.dcolor, dmu); break;
-        case 1: color_bwd<1>(i, sc, cam, g2, out.dcolor, dmu); break;
-        case 2: color_bwd<2>(i, sc, cam, g2, out.dcolor, dmu); break;
-        case 3: color_bwd<3>(i, sc, cam, g2, out.dcolor, dmu); break;
+        case 0: color_bwd<0>(i, sc, cam, g2, out.dcolor, out.acc, dmu); break;
+        case 1: color_bwd<1>(i, sc, cam, g2, out.dcolor, out.acc, dmu); break;
+        case 2: color_bwd<2>(i, sc, cam, g2, out.dcolor, out.acc, dmu); break;
+        case 3: color_bwd<3>(i, sc, cam, g2, out.dcolor, out.acc, dmu); break;
         default:
-            out.dcolor[3 * i] = g2[6];
-            out.dcolor[3 * i + 1] = g2[7];
-            out.dcolor[3 * i + 2] = g2[8];
+            put(out.dcolor + 3 * i, g2[6], out.acc);
+            put(out.dcolor + 3 * i + 1, g2[7], out.acc);
+            put(out.dcolor + 3 * i + 2, g2[8], out.acc);
         }
         for (int c = 0; c < 3; c++)
-            out.dmean[3 * i + c] = W[c] * dt0 + W[3 + c] * dt1 + W[6 + c] * dt2 + dmu[c];
+            put(out.dmean + 3 * i + c, W[c] * dt0 + W[3 + c] * dt1 + W[6 + c] * dt2 + dmu[c],
+                out.acc);
         // Sigma = M M^T: G_M = 2 G_Sigma M;  M = R diag(se)
         float GM[9];
         for (int r = 0; r < 3; r++)
@@ -422,7 +429,7 @@ project_bwd_kernel(SceneB sc, CamB cam, const float *__restrict__ g2all, GradsK 
                 gs += R[3 * r + c] * GM[3 * r + c];
                 GR[3 * r + c] = GM[3 * r + c] * se[c];
             }
-            out.dlog_scale[3 * i + c] = gs * se[c];
+            put(out.dlog_scale + 3 * i + c, gs * se[c], out.acc);
         }
         float dq[4];
         dq[0] = GR[1] * (-2 * z) + GR[2] * (2 * y) + GR[3] * (2 * z) + GR[5] * (-2 * x) +
@@ -434,17 +441,70 @@ project_bwd_kernel(SceneB sc, CamB cam, const float *__restrict__ g2all, GradsK 
         dq[3] = GR[0] * (-4 * z) + GR[1] * (-2 * w) + GR[2] * (2 * x) + GR[3] * (2 * w) +
                 GR[4] * (-4 * z) + GR[5] * (2 * y) + GR[6] * (2 * x) + GR[7] * (2 * y);
         const float dot = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
-        out.dquat[4 * i] = (dq[0] - w * dot) * iq;
-        out.dquat[4 * i + 1] = (dq[1] - x * dot) * iq;
-        out.dquat[4 * i + 2] = (dq[2] - y * dot) * iq;
-        out.dquat[4 * i + 3] = (dq[3] - z * dot) * iq;
-        out.dopacity[i] = g2[5];
+        put(out.dquat + 4 * i, (dq[0] - w * dot) * iq, out.acc);
+        put(out.dquat + 4 * i + 1, (dq[1] - x * dot) * iq, out.acc);
+        put(out.dquat + 4 * i + 2, (dq[2] - y * dot) * iq, out.acc);
+        put(out.dquat + 4 * i + 3, (dq[3] - z * dot) * iq, out.acc);
+        put(out.dopacity + i, g2[5], out.acc);
+    }
+}
+
+constexpr int kL1Threads = 256;
+
+__global__ void __launch_bounds__(kL1Threads)
+l1_loss_grad_kernel(const float4 *__restrict__ img, const float4 *__restrict__ tgt, int64_t n4,
+                    const float *__restrict__ img1, const float *__restrict__ tgt1, int64_t tail,
+                    float weight, float4 *__restrict__ dl, float *__restrict__ dl1,
+                    float *loss_sum) {
+    float acc = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)kL1Threads + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * kL1Threads) {
+        const float4 a = img[i], b = tgt[i];
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+        dl[i] = make_float4(copysignf(d0 != 0.0f ? weight : 0.0f, d0),
+                            copysignf(d1 != 0.0f ? weight : 0.0f, d1),
+                            copysignf(d2 != 0.0f ? weight : 0.0f, d2),
+                            copysignf(d3 != 0.0f ? weight : 0.0f, d3));
+    }
+    if (blockIdx.x == 0 && threadIdx.x < tail) {
+        const float d = img1[threadIdx.x] - tgt1[threadIdx.x];
+        acc += fabsf(d);
+        dl1[threadIdx.x] = copysignf(d != 0.0f ? weight : 0.0f, d);
+    }
+    if (!loss_sum) return;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float s_part[kL1Threads / 32];
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int k = 0; k < kL1Threads / 32; k++) t += s_part[k];
+        atomicAdd(loss_sum, t * weight);
     }
 }
 
 }  // namespace msgs
 
 using namespace msgs;
+
+extern "C" int ms_l1_loss_grad(const float *image, const float *target, int64_t count,
+                               float weight, float *dl_dimage, float *loss_sum, void *stream) {
+    if (count < 0) return fail(MS_ERR_INVALID_ARG, "count must be >= 0");
+    if (count == 0) return MS_OK;
+    if (!image || !target || !dl_dimage) return fail(MS_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned(image, 16) || !aligned(target, 16) || !aligned(dl_dimage, 16))
+        return fail(MS_ERR_INVALID_ARG, "image, target and dl_dimage must be 16-byte aligned");
+    if (loss_sum && !aligned(loss_sum, 4)) return fail(MS_ERR_INVALID_ARG, "loss_sum misaligned");
+    const int64_t n4 = count / 4, tail = count - 4 * n4;
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(ceil_div(n4, kL1Threads), (int64_t)num_sms() * 8));
+    l1_loss_grad_kernel<<<grid, kL1Threads, 0, as_stream(stream)>>>(
+        reinterpret_cast<const float4 *>(image), reinterpret_cast<const float4 *>(target), n4,
+        image + 4 * n4, target + 4 * n4, tail, weight, reinterpret_cast<float4 *>(dl_dimage),
+        dl_dimage + 4 * n4, loss_sum);
+    return cuda_check(cudaGetLastError(), "l1 loss launch");
+}
 
 extern "C" size_t ms_raster_bwd_workspace_bytes(int64_t n) {
     if (n < 0 || n > INT32_MAX) return 0;
@@ -454,8 +514,8 @@ extern "C" size_t ms_raster_bwd_workspace_bytes(int64_t n) {
 extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
                              const ms_proj_t *proj, const ms_bins_t *bins,
                              const float *dl_dimage, const float *final_t,
-                             const uint32_t *n_contrib, const ms_grads_t *grads, void *ws,
-                             size_t ws_bytes, void *stream) {
+                             const uint32_t *n_contrib, const ms_grads_t *grads,
+                             uint32_t flags, void *ws, size_t ws_bytes, void *stream) {
     if (!scene || !cam || !proj || !bins || !grads)
         return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (scene->n < 0 || scene->n > INT32_MAX) return fail(MS_ERR_INVALID_ARG, "scene n out of range");
@@ -471,6 +531,8 @@ extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
     if (scene->sh_degree < -1 || scene->sh_degree > 3)
         return fail(MS_ERR_INVALID_ARG, "sh_degree must be in -1..3");
     if (proj->n < scene->n || !proj->rec) return fail(MS_ERR_INVALID_ARG, "ms_proj_t too small");
+    if (flags & ~MS_BWD_ACCUMULATE) return fail(MS_ERR_INVALID_ARG, "unknown flags");
+    const bool accumulate = (flags & MS_BWD_ACCUMULATE) != 0;
     const size_t need = ms_raster_bwd_workspace_bytes(scene->n);
     if (!ws || ws_bytes < need || !aligned(ws, 16))
         return fail(MS_ERR_INVALID_ARG, "backward workspace missing, too small or misaligned");
@@ -479,7 +541,7 @@ extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
     const int K = scene->sh_degree < 0 ? 1 : (scene->sh_degree + 1) * (scene->sh_degree + 1);
     int rc;
     if ((rc = cuda_check(cudaMemsetAsync(ws, 0, need, st), "bwd workspace memset"))) return rc;
-    if (n > 0) {
+    if (n > 0 && !accumulate) {
         if ((rc = cuda_check(cudaMemsetAsync(grads->dmean, 0, n * 3 * sizeof(float), st), "memset")) ||
             (rc = cuda_check(cudaMemsetAsync(grads->dlog_scale, 0, n * 3 * sizeof(float), st), "memset")) ||
             (rc = cuda_check(cudaMemsetAsync(grads->dquat, 0, n * 4 * sizeof(float), st), "memset")) ||
@@ -523,7 +585,7 @@ extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
         cb.width = (float)cam->width;
         cb.height = (float)cam->height;
         GradsK gk = {grads->dmean, grads->dlog_scale, grads->dquat, grads->dopacity,
-                     grads->dcolor};
+                     grads->dcolor, accumulate};
         int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
         project_bwd_kernel<<<grid, 256, 0, st>>>(sb, cb, static_cast<const float *>(ws), gk);
     }

@@ -74,6 +74,34 @@ def test_argument_errors_need_no_device():
     assert msgs.ms_raster_workspace_bytes(0, 1 << 20) == 0
 
 
+def test_backward_argument_errors_need_no_device():
+    lib = msgs.lib()
+    cam = msgs.camera_struct(inputs.config1_camera())
+    fake = 1 << 20                      # never dereferenced: the checks fail first
+    sc = msgs.ms_scene_t(10, 1, -1, *([fake] * 10))
+    proj = msgs.ms_proj_t(fake, fake, fake, fake, 0, 0, fake, 10)
+    bins = msgs.ms_bins_t(fake, fake, fake, 16)
+    grads = msgs.ms_grads_t(*([fake] * 5))
+    ws = msgs.ms_raster_bwd_workspace_bytes(10)
+    assert ws == 10 * 9 * 4
+    assert msgs.ms_raster_bwd_workspace_bytes(-1) == 0
+
+    def bwd(flags, ws_bytes=ws, g=grads, s=sc):
+        return lib.ms_raster_bwd(ctypes.byref(s), ctypes.byref(cam), ctypes.byref(proj),
+                                 ctypes.byref(bins), fake, fake, fake, ctypes.byref(g), flags,
+                                 fake, ws_bytes, None)
+    assert bwd(2) == msgs.MS_ERR_INVALID_ARG and b"flags" in lib.ms_last_error()
+    assert bwd(msgs.MS_BWD_ACCUMULATE, ws - 4) == msgs.MS_ERR_INVALID_ARG
+    assert bwd(0, g=msgs.ms_grads_t(fake, fake, 0, fake, fake)) == msgs.MS_ERR_INVALID_ARG
+    bad_deg = msgs.ms_scene_t(10, 1, 4, *([fake] * 10))
+    assert bwd(0, s=bad_deg) == msgs.MS_ERR_INVALID_ARG
+    # L1 loss: count 0 is a no-op, negative counts, NULL and misaligned buffers fail
+    assert lib.ms_l1_loss_grad(None, None, 0, 1.0, None, None, None) == msgs.MS_OK
+    assert lib.ms_l1_loss_grad(fake, fake, -1, 1.0, fake, None, None) == msgs.MS_ERR_INVALID_ARG
+    assert lib.ms_l1_loss_grad(fake, None, 8, 1.0, fake, None, None) == msgs.MS_ERR_INVALID_ARG
+    assert lib.ms_l1_loss_grad(fake + 4, fake, 8, 1.0, fake, None, None) == msgs.MS_ERR_INVALID_ARG
+
+
 def test_inputs_module_stands_alone():
     """The shared input module (used by both the oracle side and the CUDA
     side) imports nothing but numpy and the standard library, so neither
