@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--n", type=int, default=N_GAUSS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--profile", default=None, choices=["selective", "all_levels"],
                     help="for profilers: two warm-up sweeps, then one sweep of this mode "
@@ -129,6 +130,110 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------- training step
+
+TRAIN_SCALES = (1, 4, 16, 64)
+
+
+def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
+    """Forward + backward of a multi-scale training batch (Sec. 4.1): four
+    orbit cameras at 1x/4x/16x/64x of 1256x832, selective rendering, L1
+    mean loss per view against seeded U(0,1) targets, gradients of every
+    scene parameter accumulated over the batch.  Timed as one CUDA graph
+    per iteration (prepare, 4 forwards, 4 loss gradients, 4 backwards)."""
+    base = inputs.orbit_cameras(4, seed=2, radius=25.0)
+    cams = [inputs.downscale(c, s) for c, s in zip(base, TRAIN_SCALES)]
+    rng = np.random.default_rng(1)
+    targets = [torch.tensor(rng.uniform(0.0, 1.0, (3, c.height, c.width)).astype(np.float32),
+                            device=dev) for c in cams]
+    probe = msgs.Renderer(sc.n, cams[0].tiles_x * cams[0].tiles_y, 4 * sc.n, device=dev,
+                          with_cover=False, with_mask=False)
+    caps = []
+    for cam in cams:
+        probe.render(ds, cam, "selective")
+        rc, d, _ = msgs.ms_bin_counts(probe.bins)
+        caps.append(int(d * 1.05) + 1024)
+    del probe
+    rs = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, cap, device=dev, with_cover=False,
+                        with_mask=False) for c, cap in zip(cams, caps)]
+    outs = [r.images(c, device=dev) for r, c in zip(rs, cams)]
+    dls = [torch.empty_like(t) for t in targets]
+    grads_t = {k: torch.empty(getattr(ds, k).shape, dtype=torch.float32, device=dev)
+               for k in ("mean", "log_scale", "quat", "opacity", "color")}
+    grads = msgs.ms_grads_t(*(msgs._ptr(grads_t[k]) for k in
+                              ("mean", "log_scale", "quat", "opacity", "color")))
+    bws = msgs.ms_raster_bwd_workspace_bytes(sc.n)
+    bwd_ws = torch.empty(bws, dtype=torch.uint8, device=dev)
+    loss = torch.zeros(1, device=dev)
+    css = [msgs.camera_struct(c) for c in cams]
+
+    def forward():
+        msgs.ms_scene_prepare(ds.struct)
+        loss.zero_()
+        for r, cam, out, tgt, dl in zip(rs, cams, outs, targets, dls):
+            r.render(ds, cam, "selective", out=out)
+            cnt = out[0].numel()
+            msgs.ms_l1_loss_grad(msgs._ptr(out[0]), msgs._ptr(tgt), cnt, 1.0 / cnt,
+                                 msgs._ptr(dl), msgs._ptr(loss))
+
+    def backward():
+        for k, (r, cs, out, dl) in enumerate(zip(rs, css, outs, dls)):
+            msgs.ms_raster_bwd(ds.struct, cs, r.proj, r.bins, msgs._ptr(dl), msgs._ptr(out[1]),
+                               msgs._ptr(out[2]), grads, msgs.MS_BWD_ACCUMULATE if k else 0,
+                               msgs._ptr(bwd_ws), bws)
+
+    forward()
+    backward()
+    for r in rs:
+        r.check()
+    torch.cuda.synchronize()
+    graphs = []
+    for fn in (forward, backward):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        graphs.append(g)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        graphs[0].replay()
+        graphs[1].replay()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    for _ in range(steps):
+        graphs[0].replay()
+        graphs[1].replay()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_step = ev[0].elapsed_time(ev[1]) / 1e3 / steps
+    fwd = bwd = 0.0
+    for _ in range(steps):
+        ev[0].record(stream)
+        graphs[0].replay()
+        ev[1].record(stream)
+        graphs[1].replay()
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        fwd += ev[0].elapsed_time(ev[1])
+        bwd += ev[1].elapsed_time(ev[2])
+    for r in rs:
+        r.check()
+    finite = all(bool(torch.isfinite(t).all()) for t in grads_t.values())
+    launches = 1
+    for cam in cams:
+        tiles = cam.tiles_x * cam.tiles_y
+        launches += 1 + (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2 + 1 + 2
+    return {"metric": "bwd it/s", "value": 1.0 / t_step, "unit": "it/s",
+            "ms_per_step": 1e3 * t_step, "fwd_ms": fwd / steps, "bwd_ms": bwd / steps,
+            "loss": float(loss.item()), "grads_finite": finite,
+            "gpu_launches": launches * steps,
+            "config": {"workload": f"train-multiscale-{sc.n // 1000}k-4level-sh3-4views",
+                       "views": [[c.width, c.height] for c in cams],
+                       "scales": list(TRAIN_SCALES), "mode": "selective",
+                       "loss": "L1 mean per view, targets U(0,1) seed 1",
+                       "launch": "forward and backward each one CUDA graph"}}
 
 
 # ------------------------------------------------------------- oracle arm
@@ -418,6 +523,12 @@ def main():
         tiles = cam.tiles_x * cam.tiles_y
         launches_per_step += 1 + (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2
 
+    train = None
+    if not args.no_train:
+        train = train_step_bench(msgs, torch, ds, sc, dev, max(10, args.steps // 2),
+                                 args.warmup)
+        train["value"] *= world
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f, s, threads, scales = oracle_sweep(oracle_scene(sc), cams, args.cpu_budget_s)
@@ -437,6 +548,7 @@ def main():
                            "ms_per_step": 1e3 * t_all / args.steps},
             "per_scale": per_scale,
             "roofline_all": {"project": roof_project, "raster": roof_raster},
+            "train": train,
         }))
     if world > 1:
         dist.destroy_process_group()
