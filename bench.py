@@ -53,9 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
-    ap.add_argument("--profile", default=None, choices=["selective", "all_levels"],
-                    help="for profilers: two warm-up sweeps, then one sweep of this mode "
-                         "inside the NVTX range 'sweep'; prints no JSON")
+    ap.add_argument("--profile", default=None, choices=["selective", "all_levels", "train"],
+                    help="for profilers: two warm-up sweeps (training steps), then one "
+                         "of this mode inside the NVTX range 'sweep'; prints no JSON")
     return ap.parse_args()
 
 
@@ -137,12 +137,13 @@ class ClockSampler:
 TRAIN_SCALES = (1, 4, 16, 64)
 
 
-def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
+def train_setup(msgs, torch, ds, sc, dev):
     """Forward + backward of a multi-scale training batch (Sec. 4.1): four
     orbit cameras at 1x/4x/16x/64x of 1256x832, selective rendering, L1
     mean loss per view against seeded U(0,1) targets, gradients of every
-    scene parameter accumulated over the batch.  Timed as one CUDA graph
-    per iteration (prepare, 4 forwards, 4 loss gradients, 4 backwards)."""
+    scene parameter accumulated over the batch.  Returns the cameras, the
+    renderers, forward() (prepare, 4 forwards, 4 loss gradients) and
+    backward() (4 backwards), the loss and the gradient buffers."""
     base = inputs.orbit_cameras(4, seed=2, radius=25.0)
     cams = [inputs.downscale(c, s) for c, s in zip(base, TRAIN_SCALES)]
     rng = np.random.default_rng(1)
@@ -180,10 +181,18 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
 
     def backward():
         for k, (r, cs, out, dl) in enumerate(zip(rs, css, outs, dls)):
-            msgs.ms_raster_bwd(ds.struct, cs, r.proj, r.bins, msgs._ptr(dl), msgs._ptr(out[1]),
-                               msgs._ptr(out[2]), grads, msgs.MS_BWD_ACCUMULATE if k else 0,
-                               msgs._ptr(bwd_ws), bws)
+            msgs.ms_raster_bwd(ds.struct, cs, r.proj, r.bins, msgs._ptr(out[0]),
+                               msgs._ptr(out[2]), msgs._ptr(r.rws), r.rws_bytes, msgs._ptr(dl),
+                               grads, msgs.MS_BWD_ACCUMULATE if k else 0, msgs._ptr(bwd_ws),
+                               bws)
 
+    return cams, rs, forward, backward, loss, grads_t
+
+
+def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
+    """The training step timed as two CUDA graphs per iteration (forward,
+    backward) with events on the launching stream."""
+    cams, rs, forward, backward, loss, grads_t = train_setup(msgs, torch, ds, sc, dev)
     forward()
     backward()
     for r in rs:
@@ -329,6 +338,20 @@ def main():
     ds = msgs.DeviceScene(sc, device=dev)
     ds.calibrate(calib)
     max_tiles = cams[0].tiles_x * cams[0].tiles_y
+    if args.profile == "train":
+        _, rs, forward, backward, _, _ = train_setup(msgs, torch, ds, sc, dev)
+        for it in range(3):
+            torch.cuda.synchronize()
+            if it == 2:
+                torch.cuda.nvtx.range_push("sweep")
+            forward()
+            backward()
+            torch.cuda.synchronize()
+            if it == 2:
+                torch.cuda.nvtx.range_pop()
+        for r in rs:
+            r.check()
+        return
     if args.profile:
         cap = 4_000_000 if args.profile == "selective" else 60_000_000
         r = msgs.Renderer(sc.n, max_tiles, cap, device=dev, with_cover=False, with_mask=False)

@@ -295,21 +295,26 @@ typedef struct {
     float *dcolor;
 } ms_grads_t;
 
-/* Workspace bytes ms_raster_bwd needs for n Gaussians (9 floats each). */
+/* Workspace bytes ms_raster_bwd needs for n Gaussians (9 floats each, plus
+ * a counter). */
 size_t ms_raster_bwd_workspace_bytes(int64_t n);
 
 /*
  * Backward of ms_project -> ms_bin -> ms_raster for one frame (the gradient
  * a multi-scale training step propagates, Sec. 4.1 "Multi-Scale
- * Training").  Inputs: the frame's proj and bins as the forward left them,
- * dl_dimage[3][H][W] (dL/d image, planar), and the forward's final_t and
- * n_contrib.  Each tile's list is replayed backwards per pixel from its
- * final transmittance, recomputing every alpha with the forward's exact
- * FP32 operations (so the same Gaussians contribute):
- *   dC/dalpha_k = T_k c_k - R_k / (1 - alpha_k),  dC/dc_k = alpha_k T_k,
- * with R_k the colour behind Gaussian k (including T_final bg), then
- * through alpha = min(0.99, sigma e^power) (no gradient when clamped), the
- * centre and conic, V' = V + 0.3 I, the EWA covariance, the rotation of
+ * Training").  Inputs, all as that frame's forward left them: proj, bins,
+ * the image and n_contrib written by ms_raster, and ms_raster's workspace
+ * `raster_ws` (its tile segmentation and the per-pixel state after each
+ * segment; raster_ws_bytes >= ms_raster_workspace_bytes(tiles,
+ * bins->dup_capacity)); plus dl_dimage[3][H][W] (dL/d image, planar).
+ * Every segment of every tile is walked front to back from the state the
+ * forward reached before it, up to each pixel's last contributor,
+ * recomputing every alpha with the forward's exact FP32 operations (so the
+ * same Gaussians contribute).  With F_k the colour accumulated through
+ * Gaussian k and C the pixel's final colour (background included):
+ *   dC/dalpha_k = T_k c_k - (C - F_k) / (1 - alpha_k),  dC/dc_k = alpha_k T_k,
+ * then through alpha = min(0.99, sigma e^power) (no gradient when clamped),
+ * the centre and conic, V' = V + 0.3 I, the EWA covariance, the rotation of
  * the normalised quaternion, exp(log_scale) and the SH colour (direction
  * term included, zero where the colour was clamped at 0).  Gaussians the
  * frame did not blend get zero.  Selection and coverage are not
@@ -324,9 +329,9 @@ size_t ms_raster_bwd_workspace_bytes(int64_t n);
  */
 #define MS_BWD_ACCUMULATE 1u
 int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
-                  const ms_proj_t *proj, const ms_bins_t *bins,
-                  const float *dl_dimage, const float *final_t,
-                  const uint32_t *n_contrib, const ms_grads_t *grads, uint32_t flags,
+                  const ms_proj_t *proj, const ms_bins_t *bins, const float *image,
+                  const uint32_t *n_contrib, const void *raster_ws, size_t raster_ws_bytes,
+                  const float *dl_dimage, const ms_grads_t *grads, uint32_t flags,
                   void *ws, size_t ws_bytes, void *stream);
 
 /*

@@ -95,8 +95,8 @@ _SIGNATURES = [
     ("ms_raster_bwd_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64]),
     ("ms_raster_bwd", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
                                      ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
-                                     P, P, P, ctypes.POINTER(ms_grads_t), ctypes.c_uint32, P,
-                                     ctypes.c_size_t, P]),
+                                     P, P, P, ctypes.c_size_t, P, ctypes.POINTER(ms_grads_t),
+                                     ctypes.c_uint32, P, ctypes.c_size_t, P]),
     ("ms_l1_loss_grad", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_float, P, P, P]),
     ("ms_raster", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
                                  ctypes.POINTER(ms_camera_t), P, P, P, P, P,
@@ -225,12 +225,14 @@ def ms_raster_bwd_workspace_bytes(n: int) -> int:
 
 
 def ms_raster_bwd(scene: ms_scene_t, cam: ms_camera_t, proj: ms_proj_t, bins: ms_bins_t,
-                  dl_ptr: int, final_t_ptr: int, n_contrib_ptr: int, grads: ms_grads_t,
-                  flags: int, ws_ptr: int, ws_bytes: int, stream=None):
+                  image_ptr: int, n_contrib_ptr: int, raster_ws_ptr: int, raster_ws_bytes: int,
+                  dl_ptr: int, grads: ms_grads_t, flags: int, ws_ptr: int, ws_bytes: int,
+                  stream=None):
     _check(lib().ms_raster_bwd(ctypes.byref(scene), ctypes.byref(cam), ctypes.byref(proj),
-                               ctypes.byref(bins), P(dl_ptr), P(final_t_ptr),
-                               P(n_contrib_ptr), ctypes.byref(grads), int(flags), P(ws_ptr),
-                               ws_bytes, P(_stream(stream))))
+                               ctypes.byref(bins), P(image_ptr), P(n_contrib_ptr),
+                               P(raster_ws_ptr), raster_ws_bytes, P(dl_ptr),
+                               ctypes.byref(grads), int(flags), P(ws_ptr), ws_bytes,
+                               P(_stream(stream))))
 
 
 def ms_l1_loss_grad(image_ptr: int, target_ptr: int, count: int, weight: float, dl_ptr: int,

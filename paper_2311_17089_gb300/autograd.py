@@ -3,8 +3,8 @@
 Marshalling only: the forward is ms_scene_prepare -> ms_project -> ms_bin
 -> ms_raster and the backward is ms_raster_bwd, all CUDA kernels of
 libmsgs.so.  A `Frame` owns one frame's device buffers (projection, tile
-lists, final transmittance, contributor counts), which the backward of that
-frame needs, so every camera of a batch uses its own Frame.
+lists, image, contributor counts, raster workspace), which the backward of
+that frame needs, so every camera of a batch uses its own Frame.
 """
 from __future__ import annotations
 
@@ -78,9 +78,10 @@ class GaussianRender(torch.autograd.Function):
                            level, s_max, s_min, scale, lnop)
         grads = ms_grads_t(_ptr(g["mean"]), _ptr(g["log_scale"]), _ptr(g["quat"]),
                            _ptr(g["opacity"]), _ptr(g["color"]))
-        ms_raster_bwd(sc, camera_struct(frame.cam), r.proj, r.bins,
-                      _ptr(grad_image.contiguous()), _ptr(frame.final_t),
-                      _ptr(frame.n_contrib), grads, 0, _ptr(frame.bwd_ws), frame.bwd_ws_bytes)
+        ms_raster_bwd(sc, camera_struct(frame.cam), r.proj, r.bins, _ptr(frame.image),
+                      _ptr(frame.n_contrib), _ptr(r.rws), r.rws_bytes,
+                      _ptr(grad_image.contiguous()), grads, 0, _ptr(frame.bwd_ws),
+                      frame.bwd_ws_bytes)
         return (g["mean"], g["log_scale"], g["quat"], g["opacity"], g["color"], None, None,
                 None, None, None, None, None)
 

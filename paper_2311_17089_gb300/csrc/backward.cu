@@ -2,17 +2,21 @@
 // (the back-propagation a multi-scale training step runs, Sec. 4.1
 // "Multi-Scale Training").
 //
-// raster_bwd_kernel: one CTA per tile replays the tile's list backwards for
-// every pixel, from its final transmittance and its last contributor
-// (both stored by ms_raster), recomputing each alpha with exactly the
-// forward's FP32 operations, so the same Gaussians contribute.  With R the
-// colour behind Gaussian k (including T_final * bg):
-//   dC/dalpha_k = T_k c_k - R / (1 - alpha_k),  dC/dc_k = alpha_k T_k,
-//   T_k = T_{k+1} / (1 - alpha_k),  R += alpha_k T_k c_k.
+// raster_bwd_kernel: the forward cut every tile's list into segments and
+// left, for each segment, the exact per-pixel state (C, T) after it.  The
+// backward therefore treats segments independently: a CTA takes a segment
+// by ticket, starts each pixel from the state the forward reached before
+// it, and walks the segment front to back up to the pixel's last
+// contributor, recomputing each alpha with exactly the forward's FP32
+// operations (so the same Gaussians contribute).  With F_k the colour
+// accumulated up to and including Gaussian k and C the final pixel colour,
+// the colour behind k is R_k = C - F_k, and
+//   dC/dalpha_k = T_k c_k - R_k / (1 - alpha_k),  dC/dc_k = alpha_k T_k.
 // alpha = sigma e^power (below the 0.99 clamp) gives dsigma and dpower, and
 // power = -(a dx^2 + c dy^2)/2 - b dx dy gives the centre and conic
-// gradients.  Per record, a warp sums its pixels' contributions with
-// shuffles, warps meet in shared memory, and the CTA adds its sums to the
+// gradients.  Per record, a warp reduce-scatters its 32 pixels' nine values
+// (12 shuffles; nine lanes end up owning one full sum each), the owners add
+// them to shared memory, and the CTA adds each record's sums to the
 // per-Gaussian 2D gradient with one atomic per value.
 //
 // project_bwd_kernel: per Gaussian, the chain rule from (centre, conic,
@@ -26,13 +30,13 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "raster_ws.cuh"
 
 namespace msgs {
 
-constexpr int kBwdThreads = 256;
+constexpr int kBwdThreads = kRasterThreads;
 constexpr int kBwdBatch = 256;
 constexpr int kG2 = 9;  // dux, duy, da, db, dc, dsigma, dr, dg, db
-constexpr float kLog2eB = 1.4426950408889634f;
 constexpr float kInvConicA = -1.3862943611198906f;  // 1 / (-log2(e)/2)
 constexpr float kInvConicB = -0.6931471805599453f;  // 1 / (-log2(e))
 
@@ -47,128 +51,199 @@ struct BwdArgs {
     const uint32_t *gidx;
     const float4 *rec;
     uint32_t n_rec;
-    int W, H, tiles_x;
-    float bg0, bg1, bg2;
-    const float *dl;        // [3][H][W]
-    const float *final_t;   // [H][W]
+    int W, H, tiles_x, tiles;
+    const float *image;       // [3][H][W] as the forward wrote it
+    const float *dl;          // [3][H][W]
     const uint32_t *n_contrib;
-    float *g2;              // [n][kG2]
+    const uint32_t *seg_off;  // the forward's segmentation
+    const uint32_t *seg_len;
+    const float4 *pre;        // [max_segs][256] state after each segment
+    uint32_t *ticket;
+    float *g2;                // [n][kG2]
 };
+
+// Sum of v[q] over the 32 lanes of a warp, reduce-scattered: lane l returns
+// the full sum of value q(l) = l < 4 ? l / 2 : l / 4 + 1 when it is an
+// owner (l < 4 ? l even : l % 4 == 0), a partial sum otherwise.  Halving
+// the set of values a lane carries at every step costs 5 + 3 + 2 + 1 + 1
+// shuffles instead of 9 x 5.
+__device__ __forceinline__ float reduce_scatter9(const float v[kG2], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    // xor 16: lanes 0-15 keep values 0-4, lanes 16-31 values 5-8
+    float a[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        const float hi = k < 4 ? v[5 + k] : 0.0f;
+        const float keep = b4 ? hi : v[k], send = b4 ? v[k] : hi;
+        a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    // xor 8: {0,1,2 | 3,4} and {5,6 | 7,8}
+    float b[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float hi = b4 ? (k + 2 < 5 ? a[k + 2] : 0.0f) : (k + 3 < 5 ? a[k + 3] : 0.0f);
+        const float keep = b3 ? hi : a[k], send = b3 ? a[k] : hi;
+        b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    // xor 4: {0,1 | 2}, {3 | 4}, {5 | 6}, {7 | 8}
+    const bool g3 = !b4 && !b3;
+    float c[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const float hi = g3 ? (k + 2 < 3 ? b[k + 2] : 0.0f) : b[k + 1];
+        const float keep = b2 ? hi : b[k], send = b2 ? b[k] : hi;
+        c[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    // xor 2: {0 | 1}; every other group holds one value
+    const bool two = g3 && !b2;
+    const float keep = (two && b1) ? c[1] : c[0];
+    const float send = two ? (b1 ? c[0] : c[1]) : c[0];
+    const float d = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
 
 __global__ void __launch_bounds__(kBwdThreads)
 raster_bwd_kernel(BwdArgs a) {
     __shared__ float4 s_r0[kBwdBatch], s_r1[kBwdBatch];
     __shared__ float2 s_r2[kBwdBatch];
     __shared__ uint32_t s_idx[kBwdBatch];
-    __shared__ float s_acc[kBwdBatch][kG2 + 1];
-    __shared__ uint32_t s_max;
+    __shared__ float s_acc[kBwdBatch][kG2 + 1];  // [kG2] marks a record some pixel took
+    __shared__ uint32_t s_c, s_cnt;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * 16 + (wid & 1) * 8 + (lane & 7);
-    const int py = ty * 16 + (wid >> 1) * 4 + (lane >> 3);
-    const bool inside = px < a.W && py < a.H;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-    const uint32_t start = a.ranges[2 * tile];
-    uint32_t nc = 0;
-    float T = 1.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
-    if (inside) {
-        const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
-        nc = a.n_contrib[p];
-        T = a.final_t[p];
-        d0 = a.dl[p];
-        d1 = a.dl[plane + p];
-        d2 = a.dl[2 * plane + p];
-    }
-    float R0 = T * a.bg0, R1 = T * a.bg1, R2 = T * a.bg2;
-    if (tid == 0) s_max = 0;
+    const bool owner = lane < 4 ? (lane & 1) == 0 : (lane & 3) == 0;
+    const int q_own = lane < 4 ? lane >> 1 : (lane >> 2) + 1;
     for (int i = tid; i < kBwdBatch * (kG2 + 1); i += kBwdThreads) (&s_acc[0][0])[i] = 0.0f;
-    __syncthreads();
-    atomicMax(&s_max, nc);
-    __syncthreads();
-    const uint32_t top = s_max;
-    for (int64_t hi = top; hi > 0; hi -= kBwdBatch) {
-        const uint32_t lo = hi > kBwdBatch ? (uint32_t)hi - kBwdBatch : 0u;
-        const uint32_t cnt = (uint32_t)hi - lo;
-        if ((uint32_t)tid < cnt) {
-            uint32_t g = a.gidx[start + lo + tid];
-            if (g >= a.n_rec) g = 0;  // unreachable unless binning reported an error
-            s_idx[tid] = g;
-            s_r0[tid] = a.rec[3 * (size_t)g];
-            s_r1[tid] = a.rec[3 * (size_t)g + 1];
-            const float4 r2 = a.rec[3 * (size_t)g + 2];
-            s_r2[tid] = make_float2(r2.x, r2.y);
+    const uint32_t total = a.seg_off[a.tiles];
+    const uint32_t L = a.seg_len[0];
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            s_c = atomicAdd(a.ticket, 1u);
+            s_cnt = 0;
         }
         __syncthreads();
-        for (int j = (int)cnt - 1; j >= 0; j--) {
-            const uint32_t pos = lo + (uint32_t)j;  // list position of the record
-            float v[kG2];
+        const uint32_t c = s_c;
+        if (c >= total) break;
+        // the segment: tile t, index k within the tile, list entries [start, start + len)
+        int lo = 0, hi = a.tiles;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.seg_off[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        const int t = lo;
+        const uint32_t k = c - a.seg_off[t];
+        const uint32_t tbeg = a.ranges[2 * t], tend = a.ranges[2 * t + 1];
+        const uint32_t pos0 = k * L;  // tile-relative position of the first entry
+        const uint32_t start = tbeg + pos0;
+        const uint32_t len = tend > start ? min(tend - start, L) : 0u;
+        const int tx = t % a.tiles_x, ty = t / a.tiles_x;
+        const int px = tx * 16 + (wid & 1) * 8 + (lane & 7);
+        const int py = ty * 16 + (wid >> 1) * 4 + (lane >> 3);
+        const bool inside = px < a.W && py < a.H;
+        const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+        uint32_t my_cnt = 0;  // entries of this segment the pixel blended through
+        float T = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
+        float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+        if (inside && len > 0) {
+            const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+            const uint32_t nc = a.n_contrib[p];
+            if (nc > pos0) {
+                my_cnt = min(nc - pos0, len);
+                if (k > 0) {
+                    const float4 st = __ldcg(a.pre + (size_t)(c - 1) * kRasterThreads + tid);
+                    F0 = st.x;
+                    F1 = st.y;
+                    F2 = st.z;
+                    T = st.w;
+                }
+                C0 = a.image[p];
+                C1 = a.image[plane + p];
+                C2 = a.image[2 * plane + p];
+                d0 = a.dl[p];
+                d1 = a.dl[plane + p];
+                d2 = a.dl[2 * plane + p];
+            }
+        }
+        const uint32_t wcnt = __reduce_max_sync(0xffffffffu, my_cnt);
+        if (lane == 0 && wcnt) atomicMax(&s_cnt, wcnt);
+        __syncthreads();
+        const uint32_t cnt_seg = s_cnt;
+        for (uint32_t off = 0; off < cnt_seg; off += kBwdBatch) {
+            const uint32_t nb = min(cnt_seg - off, (uint32_t)kBwdBatch);
+            if ((uint32_t)tid < nb) {
+                uint32_t g = a.gidx[start + off + tid];
+                if (g >= a.n_rec) g = 0;  // unreachable unless binning reported an error
+                s_idx[tid] = g;
+                s_r0[tid] = a.rec[3 * (size_t)g];
+                s_r1[tid] = a.rec[3 * (size_t)g + 1];
+                const float4 r2 = a.rec[3 * (size_t)g + 2];
+                s_r2[tid] = make_float2(r2.x, r2.y);
+            }
+            __syncthreads();
+            const uint32_t jn = wcnt > off ? min(wcnt - off, nb) : 0u;  // warp-uniform
+            for (uint32_t j = 0; j < jn; j++) {
+                float v[kG2];
 #pragma unroll
-            for (int q = 0; q < kG2; q++) v[q] = 0.0f;
-            bool acc = false;
-            if (pos < nc) {
-                const float4 r0 = s_r0[j], r1 = s_r1[j];
-                const float2 r2 = s_r2[j];
-                // the forward's exact FP32 operations
-                const float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
-                const float u = __fmaf_rn(r0.w, dy, __fmul_rn(r0.z, dx));
-                const float pw = __fmaf_rn(__fmul_rn(r1.x, dy), dy, __fmul_rn(dx, u));
-                if (pw <= 0.0f && pw >= r2.y) {
-                    acc = true;
-                    const float e = ex2_approx_b(pw);
-                    const float G = r1.y * e;
-                    const float al = fminf(0.99f, G);
-                    const float om = 1.0f - al;
-                    const float Tk = T / om;
-                    const float dal = d0 * (Tk * r1.z - R0 / om) + d1 * (Tk * r1.w - R1 / om) +
-                                      d2 * (Tk * r2.x - R2 / om);
-                    const float w = al * Tk;
-                    v[6] = w * d0;
-                    v[7] = w * d1;
-                    v[8] = w * d2;
-                    R0 = fmaf(w, r1.z, R0);
-                    R1 = fmaf(w, r1.w, R1);
-                    R2 = fmaf(w, r2.x, R2);
-                    T = Tk;
-                    if (G < 0.99f) {
-                        v[5] = dal * e;
-                        const float dpow = dal * al;
-                        const float ca = r0.z * kInvConicA, cb = r0.w * kInvConicB,
-                                    cc = r1.x * kInvConicA;
-                        v[0] = dpow * (ca * dx + cb * dy);
-                        v[1] = dpow * (cc * dy + cb * dx);
-                        v[2] = dpow * (-0.5f * dx * dx);
-                        v[3] = dpow * (-dx * dy);
-                        v[4] = dpow * (-0.5f * dy * dy);
+                for (int q = 0; q < kG2; q++) v[q] = 0.0f;
+                bool acc = false;
+                if (off + j < my_cnt) {
+                    const float4 r0 = s_r0[j], r1 = s_r1[j];
+                    const float2 r2 = s_r2[j];
+                    // the forward's exact FP32 operations
+                    const float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
+                    const float u = __fmaf_rn(r0.w, dy, __fmul_rn(r0.z, dx));
+                    const float pw = __fmaf_rn(__fmul_rn(r1.x, dy), dy, __fmul_rn(dx, u));
+                    if (pw <= 0.0f && pw >= r2.y) {
+                        acc = true;
+                        const float e = ex2_approx_b(pw);
+                        const float G = r1.y * e;
+                        const float al = fminf(0.99f, G);
+                        const float w = al * T;
+                        F0 = fmaf(w, r1.z, F0);
+                        F1 = fmaf(w, r1.w, F1);
+                        F2 = fmaf(w, r2.x, F2);
+                        const float iom = __fdividef(1.0f, 1.0f - al);
+                        const float dal = d0 * (T * r1.z - (C0 - F0) * iom) +
+                                          d1 * (T * r1.w - (C1 - F1) * iom) +
+                                          d2 * (T * r2.x - (C2 - F2) * iom);
+                        v[6] = w * d0;
+                        v[7] = w * d1;
+                        v[8] = w * d2;
+                        T = T * (1.0f - al);
+                        if (G < 0.99f) {
+                            v[5] = dal * e;
+                            const float dpow = dal * al;
+                            const float ca = r0.z * kInvConicA, cb = r0.w * kInvConicB,
+                                        cc = r1.x * kInvConicA;
+                            v[0] = dpow * (ca * dx + cb * dy);
+                            v[1] = dpow * (cc * dy + cb * dx);
+                            v[2] = dpow * (-0.5f * dx * dx);
+                            v[3] = dpow * (-dx * dy);
+                            v[4] = dpow * (-0.5f * dy * dy);
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, acc)) {
+                    const float sum = reduce_scatter9(v, lane);
+                    if (owner) {
+                        atomicAdd(&s_acc[j][q_own], sum);
+                        if (lane == 0) s_acc[j][kG2] = 1.0f;
                     }
                 }
             }
-            if (__any_sync(0xffffffffu, acc)) {
+            __syncthreads();
+            if ((uint32_t)tid < nb && s_acc[tid][kG2] != 0.0f) {
+                float *dst = a.g2 + (size_t)s_idx[tid] * kG2;
 #pragma unroll
                 for (int q = 0; q < kG2; q++) {
-                    float x = v[q];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                    v[q] = x;
+                    if (s_acc[tid][q] != 0.0f) atomicAdd(dst + q, s_acc[tid][q]);
+                    s_acc[tid][q] = 0.0f;
                 }
-                if (lane == 0) {
-#pragma unroll
-                    for (int q = 0; q < kG2; q++) atomicAdd(&s_acc[j][q], v[q]);
-                    s_acc[j][kG2] = 1.0f;
-                }
+                s_acc[tid][kG2] = 0.0f;
             }
+            __syncthreads();
         }
-        __syncthreads();
-        if ((uint32_t)tid < cnt && s_acc[tid][kG2] != 0.0f) {
-            float *dst = a.g2 + (size_t)s_idx[tid] * kG2;
-#pragma unroll
-            for (int q = 0; q < kG2; q++) {
-                if (s_acc[tid][q] != 0.0f) atomicAdd(dst + q, s_acc[tid][q]);
-                s_acc[tid][q] = 0.0f;
-            }
-            s_acc[tid][kG2] = 0.0f;
-        }
-        __syncthreads();
     }
 }
 
@@ -508,21 +583,35 @@ extern "C" int ms_l1_loss_grad(const float *image, const float *target, int64_t 
 
 extern "C" size_t ms_raster_bwd_workspace_bytes(int64_t n) {
     if (n < 0 || n > INT32_MAX) return 0;
-    return (size_t)(n > 0 ? n : 1) * kG2 * sizeof(float);
+    return al256(4) + (size_t)(n > 0 ? n : 1) * kG2 * sizeof(float);
+}
+
+static int raster_bwd_blocks_per_sm() {
+    static int v = 0;
+    if (v == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, raster_bwd_kernel, kBwdThreads, 0) !=
+                cudaSuccess ||
+            b < 1)
+            b = 1;
+        v = b;
+    }
+    return v;
 }
 
 extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
-                             const ms_proj_t *proj, const ms_bins_t *bins,
-                             const float *dl_dimage, const float *final_t,
-                             const uint32_t *n_contrib, const ms_grads_t *grads,
-                             uint32_t flags, void *ws, size_t ws_bytes, void *stream) {
+                             const ms_proj_t *proj, const ms_bins_t *bins, const float *image,
+                             const uint32_t *n_contrib, const void *raster_ws,
+                             size_t raster_ws_bytes, const float *dl_dimage,
+                             const ms_grads_t *grads, uint32_t flags, void *ws, size_t ws_bytes,
+                             void *stream) {
     if (!scene || !cam || !proj || !bins || !grads)
         return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (scene->n < 0 || scene->n > INT32_MAX) return fail(MS_ERR_INVALID_ARG, "scene n out of range");
     if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
         return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
-    if (!dl_dimage || !final_t || !n_contrib)
-        return fail(MS_ERR_INVALID_ARG, "dl_dimage, final_t and n_contrib are required");
+    if (!dl_dimage || !image || !n_contrib)
+        return fail(MS_ERR_INVALID_ARG, "image, n_contrib and dl_dimage are required");
     if (scene->n > 0 && (!grads->dmean || !grads->dlog_scale || !grads->dquat ||
                          !grads->dopacity || !grads->dcolor))
         return fail(MS_ERR_INVALID_ARG, "ms_grads_t has a NULL buffer");
@@ -531,8 +620,15 @@ extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
     if (scene->sh_degree < -1 || scene->sh_degree > 3)
         return fail(MS_ERR_INVALID_ARG, "sh_degree must be in -1..3");
     if (proj->n < scene->n || !proj->rec) return fail(MS_ERR_INVALID_ARG, "ms_proj_t too small");
+    if (!bins->gauss_idx || !bins->ranges) return fail(MS_ERR_INVALID_ARG, "bins buffers NULL");
     if (flags & ~MS_BWD_ACCUMULATE) return fail(MS_ERR_INVALID_ARG, "unknown flags");
     const bool accumulate = (flags & MS_BWD_ACCUMULATE) != 0;
+    const int tiles_x = (cam->width + 15) / 16, tiles_y = (cam->height + 15) / 16;
+    RasterLayout RL;
+    if (!raster_layout((int64_t)tiles_x * tiles_y, bins->dup_capacity, RL))
+        return fail(MS_ERR_INVALID_ARG, "tiles or dup_capacity out of range");
+    if (!raster_ws || raster_ws_bytes < RL.total || !aligned(raster_ws, 16))
+        return fail(MS_ERR_INVALID_ARG, "forward raster workspace missing or too small");
     const size_t need = ms_raster_bwd_workspace_bytes(scene->n);
     if (!ws || ws_bytes < need || !aligned(ws, 16))
         return fail(MS_ERR_INVALID_ARG, "backward workspace missing, too small or misaligned");
@@ -549,7 +645,8 @@ extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
             (rc = cuda_check(cudaMemsetAsync(grads->dcolor, 0, n * K * 3 * sizeof(float), st), "memset")))
             return rc;
     }
-    const int tiles_x = (cam->width + 15) / 16, tiles_y = (cam->height + 15) / 16;
+    const char *rw = static_cast<const char *>(raster_ws);
+    char *w = static_cast<char *>(ws);
     BwdArgs a;
     a.ranges = bins->ranges;
     a.gidx = bins->gauss_idx;
@@ -558,14 +655,16 @@ extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
     a.W = cam->width;
     a.H = cam->height;
     a.tiles_x = tiles_x;
-    a.bg0 = cam->bg[0];
-    a.bg1 = cam->bg[1];
-    a.bg2 = cam->bg[2];
+    a.tiles = tiles_x * tiles_y;
+    a.image = image;
     a.dl = dl_dimage;
-    a.final_t = final_t;
     a.n_contrib = n_contrib;
-    a.g2 = static_cast<float *>(ws);
-    raster_bwd_kernel<<<tiles_x * tiles_y, kBwdThreads, 0, st>>>(a);
+    a.seg_off = reinterpret_cast<const uint32_t *>(rw + RL.seg_off);
+    a.seg_len = reinterpret_cast<const uint32_t *>(rw + RL.seg_len);
+    a.pre = reinterpret_cast<const float4 *>(rw + RL.pre);
+    a.ticket = reinterpret_cast<uint32_t *>(w);
+    a.g2 = reinterpret_cast<float *>(w + al256(4));
+    raster_bwd_kernel<<<raster_bwd_blocks_per_sm() * num_sms(), kBwdThreads, 0, st>>>(a);
     if (n > 0) {
         SceneB sb;
         sb.n = n;
@@ -587,7 +686,7 @@ extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
         GradsK gk = {grads->dmean, grads->dlog_scale, grads->dquat, grads->dopacity,
                      grads->dcolor, accumulate};
         int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
-        project_bwd_kernel<<<grid, 256, 0, st>>>(sb, cb, static_cast<const float *>(ws), gk);
+        project_bwd_kernel<<<grid, 256, 0, st>>>(sb, cb, a.g2, gk);
     }
     return cuda_check(cudaGetLastError(), "backward launches");
 }

@@ -32,19 +32,16 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "raster_ws.cuh"
 
 namespace msgs {
 
-constexpr int kRasterThreads = 256;
-constexpr int kChunk = 256;                  // records per staged sub-batch
-constexpr uint32_t kMinSegment = 4 * kChunk; // shortest segment a tile is cut into
 constexpr int kRecBytes = 48;                // one raster record
 constexpr int kBufBytes = kChunk * kRecBytes;  // staged records, as copied
 constexpr int kPairs = kChunk / 2;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
-constexpr uint32_t kTermBit = 0x80000000u;
 constexpr uint32_t kAgg = 1u;                // segment flag: local aggregate published
 constexpr uint32_t kPre = 2u;                // segment flag: inclusive prefix published
 
@@ -591,42 +588,6 @@ raster_kernel(RasterArgs a) {
             if (a.n_eval) a.n_eval[p] = s.evals;
         }
     }
-}
-
-struct RasterLayout {
-    size_t ticket, seg_len, flags, tile_done, seg_off, agg, agg2, pre, pre2, total, zero_bytes;
-    int64_t max_segs;
-};
-
-static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-static bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {
-    if (tiles < 1 || tiles > 65536 || cap < 1 || cap > (1ll << 30)) return false;
-    L.max_segs = tiles + ceil_div(cap, kMinSegment);
-    size_t o = 0;
-    L.ticket = o;
-    o = al256(o + 4);
-    L.flags = o;
-    o = al256(o + (size_t)L.max_segs * 4);
-    L.tile_done = o;
-    o = al256(o + (size_t)tiles * 4);
-    L.zero_bytes = o;
-    L.seg_len = o;
-    o = al256(o + 4);
-    L.seg_off = o;
-    o = al256(o + (size_t)(tiles + 1) * 4);
-    const size_t per4 = (size_t)L.max_segs * kRasterThreads * sizeof(float4);
-    const size_t per2 = (size_t)L.max_segs * kRasterThreads * sizeof(uint2);
-    L.agg = o;
-    o = al256(o + per4);
-    L.agg2 = o;
-    o = al256(o + per2);
-    L.pre = o;
-    o = al256(o + per4);
-    L.pre2 = o;
-    o = al256(o + per2);
-    L.total = o;
-    return true;
 }
 
 static int raster_blocks_per_sm() {

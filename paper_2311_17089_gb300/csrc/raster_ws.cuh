@@ -1,0 +1,58 @@
+// Layout of the ms_raster workspace.  The backward reads the forward's
+// segmentation and per-segment prefix states from it, so both sides take
+// the offsets from this one function.
+#pragma once
+
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace msgs {
+
+constexpr int kRasterThreads = 256;          // one thread per pixel of a 16x16 tile
+constexpr int kChunk = 256;                  // records per staged sub-batch
+constexpr uint32_t kMinSegment = 4 * kChunk; // shortest segment a tile is cut into
+constexpr uint32_t kTermBit = 0x80000000u;   // pixel terminated (in the n_eval word)
+
+// Byte offsets inside the workspace.  ticket, flags and tile_done are zeroed
+// by every ms_raster call (zero_bytes); seg_len and seg_off are written by
+// its first kernel; agg/agg2 hold segment-local aggregates and pre/pre2 the
+// inclusive prefix state (C0, C1, C2, T) / (n_contrib, n_eval | term) per
+// segment and pixel, for every segment but a tile's last.
+struct RasterLayout {
+    size_t ticket, seg_len, flags, tile_done, seg_off, agg, agg2, pre, pre2, total, zero_bytes;
+    int64_t max_segs;
+};
+
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {
+    if (tiles < 1 || tiles > 65536 || cap < 1 || cap > (1ll << 30)) return false;
+    L.max_segs = tiles + ceil_div(cap, (int64_t)kMinSegment);
+    size_t o = 0;
+    L.ticket = o;
+    o = al256(o + 4);
+    L.flags = o;
+    o = al256(o + (size_t)L.max_segs * 4);
+    L.tile_done = o;
+    o = al256(o + (size_t)tiles * 4);
+    L.zero_bytes = o;
+    L.seg_len = o;
+    o = al256(o + 4);
+    L.seg_off = o;
+    o = al256(o + (size_t)(tiles + 1) * 4);
+    const size_t per4 = (size_t)L.max_segs * kRasterThreads * 16;
+    const size_t per2 = (size_t)L.max_segs * kRasterThreads * 8;
+    L.agg = o;
+    o = al256(o + per4);
+    L.agg2 = o;
+    o = al256(o + per2);
+    L.pre = o;
+    o = al256(o + per4);
+    L.pre2 = o;
+    o = al256(o + per2);
+    L.total = o;
+    return true;
+}
+
+}  // namespace msgs

@@ -83,18 +83,21 @@ def test_backward_argument_errors_need_no_device():
     bins = msgs.ms_bins_t(fake, fake, fake, 16)
     grads = msgs.ms_grads_t(*([fake] * 5))
     ws = msgs.ms_raster_bwd_workspace_bytes(10)
-    assert ws == 10 * 9 * 4
+    assert ws == 256 + 10 * 9 * 4
     assert msgs.ms_raster_bwd_workspace_bytes(-1) == 0
+    rws = msgs.ms_raster_workspace_bytes(cam.width // 16 * (cam.height // 16), 16)
 
-    def bwd(flags, ws_bytes=ws, g=grads, s=sc):
+    def bwd(flags, ws_bytes=ws, g=grads, s=sc, rws_bytes=rws):
         return lib.ms_raster_bwd(ctypes.byref(s), ctypes.byref(cam), ctypes.byref(proj),
-                                 ctypes.byref(bins), fake, fake, fake, ctypes.byref(g), flags,
-                                 fake, ws_bytes, None)
+                                 ctypes.byref(bins), fake, fake, fake, rws_bytes, fake,
+                                 ctypes.byref(g), flags, fake, ws_bytes, None)
     assert bwd(2) == msgs.MS_ERR_INVALID_ARG and b"flags" in lib.ms_last_error()
     assert bwd(msgs.MS_BWD_ACCUMULATE, ws - 4) == msgs.MS_ERR_INVALID_ARG
     assert bwd(0, g=msgs.ms_grads_t(fake, fake, 0, fake, fake)) == msgs.MS_ERR_INVALID_ARG
     bad_deg = msgs.ms_scene_t(10, 1, 4, *([fake] * 10))
     assert bwd(0, s=bad_deg) == msgs.MS_ERR_INVALID_ARG
+    assert bwd(0, rws_bytes=rws - 16) == msgs.MS_ERR_INVALID_ARG
+    assert b"raster workspace" in lib.ms_last_error()
     # L1 loss: count 0 is a no-op, negative counts, NULL and misaligned buffers fail
     assert lib.ms_l1_loss_grad(None, None, 0, 1.0, None, None, None) == msgs.MS_OK
     assert lib.ms_l1_loss_grad(fake, fake, -1, 1.0, fake, None, None) == msgs.MS_ERR_INVALID_ARG

@@ -150,8 +150,9 @@ def _bwd_raw(sc, cams, flags_seq, ws_list):
         dl = torch.tensor(w, dtype=torch.float32, device="cuda")
         ws = torch.empty(msgs.ms_raster_bwd_workspace_bytes(sc.n), dtype=torch.uint8,
                          device="cuda")
-        msgs.ms_raster_bwd(ds.struct, msgs.camera_struct(cam), r.proj, r.bins, msgs._ptr(dl),
-                           msgs._ptr(ft), msgs._ptr(nc), grads, flags, msgs._ptr(ws), ws.numel())
+        msgs.ms_raster_bwd(ds.struct, msgs.camera_struct(cam), r.proj, r.bins, msgs._ptr(img),
+                           msgs._ptr(nc), msgs._ptr(r.rws), r.rws_bytes, msgs._ptr(dl), grads,
+                           flags, msgs._ptr(ws), ws.numel())
         torch.cuda.synchronize()
     return {k: g[k].cpu().numpy().astype(np.float64) for k in NAMES}
 
