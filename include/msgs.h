@@ -12,6 +12,8 @@
  *   ms_raster         per-pixel front-to-back blend with early termination
  *   ms_raster_bwd     gradient of the image with respect to the scene
  *   ms_l1_loss_grad   L1 image loss and its gradient (training step)
+ *   ms_serve_*        a render server: resident scenes, memory admission,
+ *                     continuous batching of requests over CUDA streams
  *
  * Conventions shared by every call:
  *   - Every pointer inside ms_scene_t, ms_proj_t, ms_bins_t and every
@@ -46,7 +48,8 @@ typedef enum {
     MS_ERR_CAPACITY = 2,    /* more tile duplicates than dup_capacity    */
     MS_ERR_CUDA = 3,        /* a CUDA runtime call failed                */
     MS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up        */
-    MS_ERR_NO_DEVICE = 5    /* no usable sm_103 device                   */
+    MS_ERR_NO_DEVICE = 5,   /* no usable sm_103 device                   */
+    MS_PENDING = 6          /* ms_serve_poll: the request has not finished */
 } ms_status_t;
 
 /* Which Gaussians are rendered (Eq. 6 and the "Filter Small" ablation). */
@@ -346,6 +349,95 @@ int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
  */
 int ms_l1_loss_grad(const float *image, const float *target, int64_t count, float weight,
                     float *dl_dimage, float *loss_sum, void *stream);
+
+/* ------------------------------------------------------------------ serving
+ *
+ * A render server keeps scenes resident on one device and renders camera
+ * requests of any resolution (the 1x..128x multi-scale setting of Sec. 4)
+ * as they arrive.  Admission is by memory: every request's buffers
+ * (projection, tile lists, sort and raster workspaces, image) are carved
+ * from one device arena of mem_budget_bytes allocated at creation; a
+ * request waits in FIFO order until its buffers fit and fewer than
+ * max_inflight requests are on the device.  Admitted requests are spread
+ * over n_streams CUDA streams, so requests that arrive while others run
+ * overlap with them on the GPU (continuous batching).  A request whose
+ * tile duplicates overflow the capacity it was given is rendered again
+ * with the exact count (ms_result_t.retries); the capacity of later
+ * requests of the same scene, mode and tile grid is taken from the largest
+ * count seen.  The paper defines no serving system; this is the runtime
+ * around ms_project -> ms_bin -> ms_raster, whose results it leaves
+ * unchanged: a request renders the same image alone or in a mix.
+ */
+typedef struct ms_server ms_server_t;
+
+typedef struct {
+    int64_t max_gaussians;     /* largest scene ms_serve_add_scene accepts     */
+    int32_t max_width;         /* largest request image                        */
+    int32_t max_height;
+    int32_t max_inflight;      /* requests on the device at once, 1..1024      */
+    int32_t n_streams;         /* CUDA streams, 1..max_inflight                */
+    size_t mem_budget_bytes;   /* device arena for the requests' buffers       */
+    int64_t initial_capacity;  /* tile duplicates assumed for a scene/mode/grid
+                                  not seen yet (0: 2 n, at least 65536)         */
+    int32_t device;            /* CUDA device ordinal                          */
+} ms_serve_cfg_t;
+
+typedef struct {
+    int32_t scene;             /* id from ms_serve_add_scene                   */
+    int32_t mode;              /* ms_mode_t                                    */
+    ms_camera_t cam;           /* width/height <= the configured maxima        */
+    float *image_dev;          /* device [3][H][W] output, caller-owned; NULL:
+                                  rendered into the server's arena             */
+    float *image_host;         /* host [3][H][W] copy of the image (pinned for
+                                  an asynchronous copy), or NULL               */
+} ms_request_t;
+
+typedef struct {
+    int32_t status;            /* MS_OK, MS_PENDING, or the request's error    */
+    int32_t retries;           /* re-renders after a capacity overflow         */
+    int64_t duplicates;        /* tile duplicates of the frame                 */
+    int64_t capacity;          /* duplicate capacity of its last render        */
+    size_t bytes;              /* arena bytes its last render held             */
+    double t_submit;           /* ms_serve_clock() at submission               */
+    double t_start;            /* ... when its first render was enqueued       */
+    double t_done;             /* ... when its image was complete              */
+} ms_result_t;
+
+typedef struct {
+    int64_t submitted, completed, failed, retries;
+    int32_t queued, inflight, peak_inflight, scenes;
+    size_t arena_bytes, arena_used, arena_peak;
+} ms_serve_stats_t;
+
+/* Seconds on the monotonic clock the server stamps results with. */
+double ms_serve_clock(void);
+
+/* Creates a server (allocates the arena and the streams on cfg->device and
+ * starts its scheduler thread).  *out is NULL on failure. */
+int ms_serve_create(const ms_serve_cfg_t *cfg, ms_server_t **out);
+
+/* Registers a resident scene: its device arrays stay caller-owned and must
+ * stay valid and unchanged until ms_serve_destroy; scale and lnop are
+ * (re)computed here with ms_scene_prepare (synchronously). */
+int ms_serve_add_scene(ms_server_t *srv, const ms_scene_t *scene, int32_t *scene_id);
+
+/* Queues a request (copied); returns at once with its ticket.  image_dev
+ * and image_host must stay valid until the request is done. */
+int ms_serve_submit(ms_server_t *srv, const ms_request_t *req, uint64_t *ticket);
+
+/* Non-blocking: res->status is MS_PENDING until the request is done.  A
+ * poll that returns a finished result forgets the ticket. */
+int ms_serve_poll(ms_server_t *srv, uint64_t ticket, ms_result_t *res);
+
+/* Blocks until the request is done or timeout_s passes (then res->status
+ * is MS_PENDING and the ticket stays valid). */
+int ms_serve_wait(ms_server_t *srv, uint64_t ticket, double timeout_s, ms_result_t *res);
+
+int ms_serve_stats(ms_server_t *srv, ms_serve_stats_t *stats);
+
+/* Waits for the requests on the device, drops the queued ones, frees
+ * everything.  srv may be NULL. */
+int ms_serve_destroy(ms_server_t *srv);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmsgs.so")
 
 MS_OK, MS_ERR_INVALID_ARG, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_TIMEOUT = 0, 1, 2, 3, 4
+MS_ERR_NO_DEVICE, MS_PENDING = 5, 6
 MS_SELECTIVE, MS_ALL_LEVELS, MS_FILTER_SMALL = 0, 1, 2
 MODES = {"selective": MS_SELECTIVE, "all_levels": MS_ALL_LEVELS,
          "filter_small": MS_FILTER_SMALL}
@@ -70,6 +71,34 @@ class ms_bins_t(ctypes.Structure):
                 ("dup_capacity", ctypes.c_int64)]
 
 
+class ms_serve_cfg_t(ctypes.Structure):
+    _fields_ = [("max_gaussians", ctypes.c_int64), ("max_width", ctypes.c_int32),
+                ("max_height", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_size_t),
+                ("initial_capacity", ctypes.c_int64), ("device", ctypes.c_int32)]
+
+
+class ms_request_t(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_int32), ("mode", ctypes.c_int32), ("cam", ms_camera_t),
+                ("image_dev", P), ("image_host", P)]
+
+
+class ms_result_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("retries", ctypes.c_int32),
+                ("duplicates", ctypes.c_int64), ("capacity", ctypes.c_int64),
+                ("bytes", ctypes.c_size_t), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ms_serve_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("retries", ctypes.c_int64),
+                ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32),
+                ("peak_inflight", ctypes.c_int32), ("scenes", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
+                ("arena_peak", ctypes.c_size_t)]
+
+
 # (name, restype, argtypes) of every entry point declared in include/msgs.h
 _SIGNATURES = [
     ("ms_last_error", ctypes.c_char_p, []),
@@ -101,6 +130,17 @@ _SIGNATURES = [
     ("ms_raster", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
                                  ctypes.POINTER(ms_camera_t), P, P, P, P, P,
                                  ctypes.c_size_t, P]),
+    ("ms_serve_clock", ctypes.c_double, []),
+    ("ms_serve_create", ctypes.c_int, [ctypes.POINTER(ms_serve_cfg_t), ctypes.POINTER(P)]),
+    ("ms_serve_add_scene", ctypes.c_int, [P, ctypes.POINTER(ms_scene_t),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    ("ms_serve_submit", ctypes.c_int, [P, ctypes.POINTER(ms_request_t),
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+    ("ms_serve_poll", ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(ms_result_t)]),
+    ("ms_serve_wait", ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_double,
+                                     ctypes.POINTER(ms_result_t)]),
+    ("ms_serve_stats", ctypes.c_int, [P, ctypes.POINTER(ms_serve_stats_t)]),
+    ("ms_serve_destroy", ctypes.c_int, [P]),
 ]
 
 _lib = None
@@ -241,6 +281,50 @@ def ms_l1_loss_grad(image_ptr: int, target_ptr: int, count: int, weight: float, 
                                  P(dl_ptr), P(loss_sum_ptr), P(_stream(stream))))
 
 
+def ms_serve_clock() -> float:
+    return float(lib().ms_serve_clock())
+
+
+def ms_serve_create(cfg: ms_serve_cfg_t) -> int:
+    h = P()
+    _check(lib().ms_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def ms_serve_add_scene(srv: int, scene: ms_scene_t) -> int:
+    sid = ctypes.c_int32()
+    _check(lib().ms_serve_add_scene(P(srv), ctypes.byref(scene), ctypes.byref(sid)))
+    return sid.value
+
+
+def ms_serve_submit(srv: int, req: ms_request_t) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().ms_serve_submit(P(srv), ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def ms_serve_poll(srv: int, ticket: int) -> ms_result_t:
+    r = ms_result_t()
+    _check(lib().ms_serve_poll(P(srv), ticket, ctypes.byref(r)))
+    return r
+
+
+def ms_serve_wait(srv: int, ticket: int, timeout_s: float) -> ms_result_t:
+    r = ms_result_t()
+    _check(lib().ms_serve_wait(P(srv), ticket, float(timeout_s), ctypes.byref(r)))
+    return r
+
+
+def ms_serve_stats(srv: int) -> ms_serve_stats_t:
+    st = ms_serve_stats_t()
+    _check(lib().ms_serve_stats(P(srv), ctypes.byref(st)))
+    return st
+
+
+def ms_serve_destroy(srv: int):
+    _check(lib().ms_serve_destroy(P(srv)))
+
+
 # ------------------------------------------------------ buffer helpers
 
 class DeviceScene:
@@ -368,3 +452,47 @@ def render(scene: inputs.Scene, cam: inputs.Camera, mode="selective", dup_capaci
             return img.cpu().numpy(), ft.cpu().numpy(), nc.cpu().numpy()
         cap = d
     raise MsError(MS_ERR_CAPACITY, "duplicate capacity retry failed")
+
+
+class Server:
+    """A render server (ms_serve_*): resident DeviceScenes, requests
+    submitted from any thread, results polled or awaited by ticket."""
+
+    def __init__(self, max_gaussians: int, max_width: int, max_height: int,
+                 mem_budget_bytes: int, max_inflight: int = 64, n_streams: int = 16,
+                 initial_capacity: int = 0, device: int = 0):
+        cfg = ms_serve_cfg_t(max_gaussians, max_width, max_height, max_inflight, n_streams,
+                             mem_budget_bytes, initial_capacity, device)
+        self.handle = ms_serve_create(cfg)
+        self.scenes = []   # keeps the DeviceScenes (their arrays) alive
+
+    def add_scene(self, scene: "DeviceScene") -> int:
+        sid = ms_serve_add_scene(self.handle, scene.struct)
+        self.scenes.append(scene)
+        return sid
+
+    def submit(self, scene_id: int, cam: inputs.Camera, mode="selective", image_dev=None,
+               image_host=None) -> int:
+        req = ms_request_t(scene_id, MODES.get(mode, mode), camera_struct(cam),
+                           _ptr(image_dev), _ptr(image_host))
+        return ms_serve_submit(self.handle, req)
+
+    def poll(self, ticket: int) -> ms_result_t:
+        return ms_serve_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> ms_result_t:
+        return ms_serve_wait(self.handle, ticket, timeout_s)
+
+    def stats(self) -> ms_serve_stats_t:
+        return ms_serve_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            ms_serve_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -39,7 +39,6 @@ namespace msgs {
 constexpr int kRecBytes = 48;                // one raster record
 constexpr int kBufBytes = kChunk * kRecBytes;  // staged records, as copied
 constexpr int kPairs = kChunk / 2;
-constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
 constexpr uint32_t kAgg = 1u;                // segment flag: local aggregate published

@@ -128,3 +128,26 @@ def test_product_does_not_reference_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_serve_argument_errors_need_no_device():
+    lib = msgs.lib()
+    h = ctypes.c_void_p()
+
+    def create(**kw):
+        c = dict(max_gaussians=1000, max_width=256, max_height=256, max_inflight=8, n_streams=2,
+                 mem_budget_bytes=1 << 26, initial_capacity=0, device=0)
+        c.update(kw)
+        cfg = msgs.ms_serve_cfg_t(*c.values())
+        return lib.ms_serve_create(ctypes.byref(cfg), ctypes.byref(h))
+    for bad in (dict(max_gaussians=0), dict(max_width=0), dict(max_inflight=0),
+                dict(n_streams=9), dict(mem_budget_bytes=1000), dict(initial_capacity=-1),
+                dict(device=-1)):
+        rc = create(**bad)
+        assert rc in (msgs.MS_ERR_INVALID_ARG, msgs.MS_ERR_NO_DEVICE), bad
+        assert h.value is None
+    assert lib.ms_serve_destroy(None) == msgs.MS_OK
+    r = msgs.ms_result_t()
+    assert lib.ms_serve_poll(None, 1, ctypes.byref(r)) == msgs.MS_ERR_INVALID_ARG
+    assert lib.ms_serve_submit(None, None, None) == msgs.MS_ERR_INVALID_ARG
+    assert lib.ms_serve_clock() > 0.0
