@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-n", type=int, default=2_000_000)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--profile", default=None, choices=["selective", "all_levels", "train"],
                     help="for profilers: two warm-up sweeps (training steps), then one "
@@ -243,6 +246,110 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
                        "scales": list(TRAIN_SCALES), "mode": "selective",
                        "loss": "L1 mean per view, targets U(0,1) seed 1",
                        "launch": "forward and backward each one CUDA graph"}}
+
+
+# ---------------------------------------------------------------- serving
+
+def sphere_cameras(k, seed, radius=25.0, width=1256, height=832):
+    """k cameras at uniformly random points of a sphere around the origin,
+    looking at it."""
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal((k, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    cams = []
+    for v in d:
+        up = (0.0, -1.0, 0.0) if abs(v[1]) < 0.95 else (0.0, 0.0, 1.0)
+        cams.append(inputs.pinhole(tuple(radius * v), (0.0, 0.0, 0.0), up, width, height, 60.0))
+    return cams
+
+
+def serve_bench(msgs, torch, dev, n_requests, n_gauss, loads=(0.5, 0.7, 0.9)):
+    """Serving loop: two resident scenes of n_gauss Gaussians (the multi-
+    scale generator, seeds 0 and 1, calibrated on the device), requests for
+    random cameras on a radius-25 sphere at a downscale drawn uniformly from
+    1..128x of 1256x832, Poisson arrivals (seed 2) at 0.5/0.7/0.9 of the
+    measured capacity, at most 64 on the device, memory-admitted; every
+    image is copied to pinned host memory.  Latency = completion - submit."""
+    import time as _t
+    dss = []
+    for seed in (0, 1):
+        sc = inputs.multiscale_scene(n=n_gauss, seed=seed)
+        ds = msgs.DeviceScene(sc, device=dev)
+        ds.calibrate(inputs.orbit_cameras(8, seed=1, radius=25.0))
+        dss.append(ds)
+    rng = np.random.default_rng(2)
+    base = sphere_cameras(n_requests, seed=2)
+    reqs = [(int(rng.integers(0, 2)),
+             inputs.downscale(c, int(rng.choice(inputs.SCALES)))) for c in base]
+    ring = 256
+    hosts = [torch.empty((3, 832, 1256), dtype=torch.float32).pin_memory() for _ in range(ring)]
+    budget = 64 << 30
+    out = {}
+    for mode in ("selective", "all_levels"):
+        srv = msgs.Server(max_gaussians=n_gauss, max_width=1256, max_height=832,
+                          mem_budget_bytes=budget, max_inflight=64, n_streams=16,
+                          device=dev.index or 0)
+        ids = [srv.add_scene(ds) for ds in dss]
+
+        def run(arrivals):
+            """Submit reqs at the given offsets (None: all at once); returns
+            the results in order."""
+            tickets, owner = [], [None] * ring
+            t0 = _t.perf_counter()
+            c0 = msgs.ms_serve_clock()
+            for i, (s, cam) in enumerate(reqs):
+                slot = i % ring
+                if owner[slot] is not None:     # ring buffer: wait for its last user
+                    r = srv.wait(owner[slot][0], 120.0)
+                    owner[slot][1].append(r)
+                if arrivals is not None:
+                    delay = t0 + arrivals[i] - _t.perf_counter()
+                    if delay > 0:
+                        _t.sleep(delay)
+                h = hosts[slot].view(-1)[:3 * cam.height * cam.width]
+                res_box = []
+                tickets.append((srv.submit(ids[s], cam, mode, image_host=h), res_box))
+                owner[slot] = tickets[-1]
+            for t, box in tickets:
+                if not box:
+                    box.append(srv.wait(t, 120.0))
+            res = [box[0] for _, box in tickets]
+            bad = [r.status for r in res if r.status != msgs.MS_OK]
+            if bad:
+                raise msgs.MsError(bad[0], "serve request failed")
+            # latency from the scheduled arrival (the submit call may lag it)
+            arr = ([r.t_submit for r in res] if arrivals is None
+                   else [min(r.t_submit, c0 + a) for r, a in zip(res, arrivals)])
+            return res, arr
+
+        def summary(out):
+            res, arr = out
+            lat = np.array([r.t_done - a for r, a in zip(res, arr)]) * 1e3
+            span = max(r.t_done for r in res) - min(arr)
+            return {"fps": len(res) / span, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)),
+                    "mean_ms": float(lat.mean()), "retries": int(sum(r.retries for r in res))}
+
+        run(None)                                   # warm-up: capacity history, caches
+        cap = summary(run(None))                    # closed loop: all requests queued at once
+        loads_out = []
+        for load in loads:
+            rate = load * cap["fps"]
+            gaps = np.random.default_rng(2).exponential(1.0 / rate, len(reqs))
+            res = run(np.cumsum(gaps) - gaps[0])
+            loads_out.append({"load": load, "offered_fps": rate, **summary(res)})
+        st = srv.stats()
+        srv.close()
+        out[mode] = {"capacity": cap, "poisson": loads_out,
+                     "peak_inflight": st.peak_inflight, "arena_peak_gb": st.arena_peak / 1e9}
+    return {"metric": "serve p50/p99 ms", "value": out["selective"]["poisson"][-1]["p99_ms"],
+            "unit": "ms (p99 at 0.9 load, selective)", "higher_is_better": False,
+            "selective": out["selective"], "all_levels": out["all_levels"],
+            "config": {"workload": f"serve-2x{n_gauss // 1000}k-4level-sh3-1256x832-1x..128x",
+                       "scenes": 2, "requests_per_run": len(reqs), "max_inflight": 64,
+                       "streams": 16, "mem_budget_gb": budget / 2 ** 30,
+                       "arrivals": "Poisson, seed 2, rate = load x closed-loop capacity",
+                       "output": "image copied to pinned host memory per request"}}
 
 
 # ------------------------------------------------------------- oracle arm
@@ -552,6 +659,10 @@ def main():
                                  args.warmup)
         train["value"] *= world
 
+    serve = None
+    if not args.no_serve:
+        serve = serve_bench(msgs, torch, dev, args.serve_requests, args.serve_n)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f, s, threads, scales = oracle_sweep(oracle_scene(sc), cams, args.cpu_budget_s)
@@ -572,6 +683,7 @@ def main():
             "per_scale": per_scale,
             "roofline_all": {"project": roof_project, "raster": roof_raster},
             "train": train,
+            "serve": serve,
         }))
     if world > 1:
         dist.destroy_process_group()

@@ -670,7 +670,8 @@ extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_
     a.pre = reinterpret_cast<float4 *>(w + L.pre);
     a.pre2 = reinterpret_cast<uint2 *>(w + L.pre2);
     a.err = reinterpret_cast<unsigned long long *>(bins->counts) + kCntStatus;
-    const int resident = raster_blocks_per_sm() * num_sms();
+    const int resident = (int)std::min<int64_t>((int64_t)raster_blocks_per_sm() * num_sms(),
+                                                kMaxResident);
     segment_offsets_kernel<<<1, 1024, 0, st>>>(bins->ranges, (int)tiles, (uint32_t)resident,
                                                a.seg_off, a.seg_len);
     raster_kernel<<<resident, kRasterThreads, kSmemBytes, st>>>(a);

@@ -5,6 +5,8 @@
 
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace msgs {
@@ -13,6 +15,10 @@ constexpr int kRasterThreads = 256;          // one thread per pixel of a 16x16 
 constexpr int kChunk = 256;                  // records per staged sub-batch
 constexpr uint32_t kMinSegment = 4 * kChunk; // shortest segment a tile is cut into
 constexpr uint32_t kTermBit = 0x80000000u;   // pixel terminated (in the n_eval word)
+// Most CTAs a raster launch runs at once.  The segment length is at least
+// D / resident, so a frame has at most tiles + min(D / kMinSegment,
+// resident) segments; the workspace holds state for that many.
+constexpr int64_t kMaxResident = 4096;
 
 // Byte offsets inside the workspace.  ticket, flags and tile_done are zeroed
 // by every ms_raster call (zero_bytes); seg_len and seg_off are written by
@@ -28,7 +34,7 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 inline bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {
     if (tiles < 1 || tiles > 65536 || cap < 1 || cap > (1ll << 30)) return false;
-    L.max_segs = tiles + ceil_div(cap, (int64_t)kMinSegment);
+    L.max_segs = tiles + std::min(ceil_div(cap, (int64_t)kMinSegment), kMaxResident);
     size_t o = 0;
     L.ticket = o;
     o = al256(o + 4);
