@@ -108,8 +108,11 @@ typedef struct {
  * Output of ms_project; device buffers sized for the scene's n.
  *   rec[n*12]     48-byte raster record of every listed Gaussian (selected
  *                 and touching >= 1 tile): ux, uy, A, B | C, opacity, r, g |
- *                 b, thr, 0, 0, where thr = -log2(e) ln(255 opacity) (so
- *                 alpha >= 1/255 exactly when power log2(e) >= thr) and
+ *                 b, thr, ex, ey, where thr = -log2(e) ln(255 opacity) (so
+ *                 alpha >= 1/255 exactly when power log2(e) >= thr),
+ *                 (ex, ey) = the half extents sqrt(2 ln(255 opacity) V'_xx),
+ *                 sqrt(2 ln(255 opacity) V'_yy) of the alpha >= 1/255 level
+ *                 set (the box the tile rectangle is taken from) and
  *                 (A, B, C) = (k a, 2k b, k c), k =
  *                 -log2(e)/2 as an FP32 constant, each one FP32 product of
  *                 the conic (a, b, c) = inverse dilated covariance, so that

@@ -39,7 +39,7 @@ static CamK make_cam(const ms_camera_t &c) {
 
 struct Foot {
     bool valid;
-    float S, ux, uy, ca, cb, cc;
+    float S, ux, uy, ca, cb, cc, ex, ey;
     uint32_t depth;
     int x0, y0, x1, y1;
     uint32_t ntiles;
@@ -141,6 +141,8 @@ __device__ __forceinline__ void footprint(const float m[3], const float s[3],
     o.cc = fdv(a, detd);
     float ex = fsq(fm(fm(2.0f, L), a));
     float ey = fsq(fm(fm(2.0f, L), cc));
+    o.ex = ex;
+    o.ey = ey;
     float x0 = floorf(fm(fs(ux, ex), 0.0625f)), x1 = floorf(fm(fa(ux, ex), 0.0625f));
     float y0 = floorf(fm(fs(uy, ey), 0.0625f)), y1 = floorf(fm(fa(uy, ey), 0.0625f));
     x0 = fmaxf(x0, 0.0f);
@@ -333,7 +335,7 @@ project_kernel(SceneK sc, CamK cam, int mode, float4 *__restrict__ rec,
                 rec[3 * i + 0] = make_float4(f.ux, f.uy, fm(kConicA, f.ca), fm(kConicB, f.cb));
                 rec[3 * i + 1] = make_float4(fm(kConicA, f.cc), op, col.x, col.y);
                 // alpha >= 1/255 <=> power * log2(e) >= -ln(255 sigma) log2(e)
-                rec[3 * i + 2] = make_float4(col.z, fm(-kLog2e, sc.lnop[i]), 0.0f, 0.0f);
+                rec[3 * i + 2] = make_float4(col.z, fm(-kLog2e, sc.lnop[i]), f.ex, f.ey);
                 rect[i] = make_uint2((uint32_t)f.x0 | ((uint32_t)f.y0 << 16),
                                      (uint32_t)f.x1 | ((uint32_t)f.y1 << 16));
                 depth[i] = f.depth;

@@ -41,6 +41,14 @@ constexpr int kBufBytes = kChunk * kRecBytes;  // staged records, as copied
 constexpr int kPairs = kChunk / 2;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
+#ifndef MS_RASTER_WINDOW
+#define MS_RASTER_WINDOW 16
+#endif
+// Segments of one tile walked at once: segment k starts when segment k - W
+// has published its result (or the tile is done).  Pixels of low-resolution
+// frames terminate long before the end of their tile's list, and every
+// segment started past that point is wasted work.
+constexpr uint32_t kWindow = MS_RASTER_WINDOW;
 constexpr uint32_t kAgg = 1u;                // segment flag: local aggregate published
 constexpr uint32_t kPre = 2u;                // segment flag: inclusive prefix published
 
@@ -192,17 +200,25 @@ struct PixelState {
     bool term;
 };
 
-// A staged sub-batch regrouped in record pairs (2m, 2m+1) with each field
-// of the two records side by side, so one packed FP32x2 instruction
-// evaluates both records' power terms.
-struct PairBuf {
-    float4 q0[kPairs];  // ux0 ux1 uy0 uy1
-    float4 q1[kPairs];  // A0 A1 B0 B1
-    float4 q2[kPairs];  // C0 C1 thr0 thr1
-    float4 q3[kPairs];  // opacity0 opacity1 r0 r1
-    float4 q4[kPairs];  // g0 g1 b0 b1
+// One warp's share of a staged sub-batch: the records whose alpha >= 1/255
+// level set can reach the warp's 8x4 pixel block, in list order, regrouped
+// into pairs (2m, 2m+1) with each field of the two records side by side,
+// so one packed FP32x2 instruction evaluates both records' power terms.
+struct WarpPairs {
+    float4 q0[kPairs];     // ux0 ux1 uy0 uy1
+    float4 q1[kPairs];     // A0 A1 B0 B1
+    float4 q2[kPairs];     // C0 C1 thr0 thr1
+    float4 q3[kPairs];     // opacity0 opacity1 r0 r1
+    float4 q4[kPairs];     // g0 g1 b0 b1
+    uint16_t idx[kChunk];  // index of each record within the sub-batch
 };
-constexpr int kSmemBytes = kBufBytes + (int)sizeof(PairBuf);
+constexpr int kWarps = kRasterThreads / 32;
+constexpr int kSmemBytes = kBufBytes + kWarps * (int)sizeof(WarpPairs);
+// Half extents of a warp's block of pixel centres (8 x 4 pixels) plus a
+// 1-pixel margin that covers FP32 rounding of the alpha test near the edge
+// of the level set.
+constexpr float kBlockHalfX = 3.5f + 1.0f;
+constexpr float kBlockHalfY = 1.5f + 1.0f;
 
 typedef unsigned long long f32x2;  // two FP32 values in one 64-bit register pair
 
@@ -230,35 +246,64 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
     return d;
 }
 
-// Regroup records [0, cnt) of the copied sub-batch into pairs; an odd
-// count is padded with a record that no pixel accepts (thr = +inf).
-__device__ __forceinline__ void regroup(const float4 *__restrict__ aos, uint32_t cnt,
-                                        PairBuf &pb) {
-    const uint32_t i = threadIdx.x;
-    if (i >= ((cnt + 1u) & ~1u)) return;
-    float4 r0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), r1 = r0, r2 = r0;
-    r2.y = __int_as_float(0x7f800000);
-    if (i < cnt) {
-        r0 = aos[3 * i];
-        r1 = aos[3 * i + 1];
-        r2 = aos[3 * i + 2];
+// Compact the records [0, cnt) of the staged sub-batch whose level-set box
+// (centre +- (ex, ey)) can reach the warp's block of pixel centres
+// (centre (cx, cy)) into the warp's pair buffer, keeping list order.  Any
+// other record has alpha < 1/255 at every pixel of the block, so skipping
+// it changes nothing.  An odd count is padded with a record that no pixel
+// accepts (thr = +inf).  Returns the count (warp-uniform).
+__device__ __forceinline__ uint32_t compact(const float4 *__restrict__ aos, uint32_t cnt,
+                                            float cx, float cy, WarpPairs &wp) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t base = 0;
+#pragma unroll
+    for (int k = 0; k < kChunk / 32; k++) {
+        const uint32_t i = (uint32_t)k * 32u + lane;
+        bool rel = false;
+        float4 r0, r2;
+        if (i < cnt) {
+            r0 = aos[3 * i];
+            r2 = aos[3 * i + 2];
+            rel = fabsf(r0.x - cx) <= r2.z + kBlockHalfX && fabsf(r0.y - cy) <= r2.w + kBlockHalfY;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, rel);
+        if (rel) {
+            const float4 r1 = aos[3 * i + 1];
+            const uint32_t p = base + __popc(m & ((1u << lane) - 1u));
+            const uint32_t q = p >> 1, h = p & 1u;
+            float *q0 = reinterpret_cast<float *>(&wp.q0[q]);
+            float *q1 = reinterpret_cast<float *>(&wp.q1[q]);
+            float *q2 = reinterpret_cast<float *>(&wp.q2[q]);
+            float *q3 = reinterpret_cast<float *>(&wp.q3[q]);
+            float *q4 = reinterpret_cast<float *>(&wp.q4[q]);
+            q0[h] = r0.x;
+            q0[2 + h] = r0.y;
+            q1[h] = r0.z;
+            q1[2 + h] = r0.w;
+            q2[h] = r1.x;
+            q2[2 + h] = r2.y;
+            q3[h] = r1.y;
+            q3[2 + h] = r1.z;
+            q4[h] = r1.w;
+            q4[2 + h] = r2.x;
+            wp.idx[p] = (uint16_t)i;
+        }
+        base += __popc(m);
     }
-    const uint32_t m = i >> 1, h = i & 1u;
-    float *q0 = reinterpret_cast<float *>(&pb.q0[m]);
-    float *q1 = reinterpret_cast<float *>(&pb.q1[m]);
-    float *q2 = reinterpret_cast<float *>(&pb.q2[m]);
-    float *q3 = reinterpret_cast<float *>(&pb.q3[m]);
-    float *q4 = reinterpret_cast<float *>(&pb.q4[m]);
-    q0[h] = r0.x;
-    q0[2 + h] = r0.y;
-    q1[h] = r0.z;
-    q1[2 + h] = r0.w;
-    q2[h] = r1.x;
-    q2[2 + h] = r2.y;
-    q3[h] = r1.y;
-    q3[2 + h] = r1.z;
-    q4[h] = r1.w;
-    q4[2 + h] = r2.x;
+    if ((base & 1u) && lane == 0) {
+        const uint32_t q = base >> 1;
+        float *q0 = reinterpret_cast<float *>(&wp.q0[q]);
+        float *q1 = reinterpret_cast<float *>(&wp.q1[q]);
+        float *q2 = reinterpret_cast<float *>(&wp.q2[q]);
+        float *q3 = reinterpret_cast<float *>(&wp.q3[q]);
+        float *q4 = reinterpret_cast<float *>(&wp.q4[q]);
+        q0[1] = q0[3] = q1[1] = q1[3] = q2[1] = 0.0f;
+        q2[3] = __int_as_float(0x7f800000);
+        q3[1] = q3[3] = q4[1] = q4[3] = 0.0f;
+        wp.idx[base] = 0;
+    }
+    __syncwarp();
+    return base;
 }
 
 // One record's contribution once it passed the alpha test: stop before a
@@ -282,18 +327,19 @@ __device__ __forceinline__ bool blend_one(float p, float opacity, float r, float
     return false;
 }
 
-// Blend the regrouped records [0, cnt) into s.  pos0 is the list position
-// of record 0.  power * log2(e) = A dx^2 + B dx dy + C dy^2 is evaluated
-// for both records of a pair at once; a record is skipped when the power
-// is positive or alpha would stay below 1/255 (power * log2(e) < thr).
-__device__ __forceinline__ void blend_pairs(const PairBuf &pb, uint32_t cnt, uint32_t pos0,
-                                            f32x2 fx2, f32x2 fy2, PixelState &s) {
-    const uint32_t np = (cnt + 1) >> 1;
+// Blend the warp's n compacted records of a sub-batch of cnt into s.  pos0
+// is the list position of the sub-batch's first record.  power * log2(e)
+// = A dx^2 + B dx dy + C dy^2 is evaluated for both records of a pair at
+// once; a record is skipped when the power is positive or alpha would stay
+// below 1/255 (power * log2(e) < thr).
+__device__ __forceinline__ void blend_pairs(const WarpPairs &wp, uint32_t n, uint32_t cnt,
+                                            uint32_t pos0, f32x2 fx2, f32x2 fy2, PixelState &s) {
+    const uint32_t np = (n + 1) >> 1;
 #pragma unroll 2
     for (uint32_t m = 0; m < np; m++) {
-        const ulonglong2 v0 = *reinterpret_cast<const ulonglong2 *>(&pb.q0[m]);
-        const ulonglong2 v1 = *reinterpret_cast<const ulonglong2 *>(&pb.q1[m]);
-        const ulonglong2 v2 = *reinterpret_cast<const ulonglong2 *>(&pb.q2[m]);
+        const ulonglong2 v0 = *reinterpret_cast<const ulonglong2 *>(&wp.q0[m]);
+        const ulonglong2 v1 = *reinterpret_cast<const ulonglong2 *>(&wp.q1[m]);
+        const ulonglong2 v2 = *reinterpret_cast<const ulonglong2 *>(&wp.q2[m]);
         const f32x2 dx = sub2(fx2, v0.x), dy = sub2(fy2, v0.y);
         const f32x2 u = fma2(v1.y, dy, mul2(v1.x, dx));
         const f32x2 pw = fma2(mul2(v2.x, dy), dy, mul2(dx, u));
@@ -303,10 +349,10 @@ __device__ __forceinline__ void blend_pairs(const PairBuf &pb, uint32_t cnt, uin
         const bool h0 = p0 <= 0.0f && p0 >= t0;
         const bool h1 = p1 <= 0.0f && p1 >= t1;
         if (!(h0 || h1)) continue;
-        const float4 w3 = pb.q3[m], w4 = pb.q4[m];
-        const uint32_t pos = pos0 + 2 * m;
-        if (h0 && blend_one(p0, w3.x, w3.z, w4.x, w4.z, pos + 1, s)) return;
-        if (h1 && blend_one(p1, w3.y, w3.w, w4.y, w4.w, pos + 2, s)) return;
+        const float4 w3 = wp.q3[m], w4 = wp.q4[m];
+        const uint32_t ix = *reinterpret_cast<const uint32_t *>(&wp.idx[2 * m]);
+        if (h0 && blend_one(p0, w3.x, w3.z, w4.x, w4.z, pos0 + (ix & 0xffffu) + 1, s)) return;
+        if (h1 && blend_one(p1, w3.y, w3.w, w4.y, w4.w, pos0 + (ix >> 16) + 1, s)) return;
     }
     s.evals = pos0 + cnt;
 }
@@ -374,9 +420,9 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
     return *reinterpret_cast<const volatile uint32_t *>(p);
 }
 
-// Walk one segment in sub-batches: while the CTA blends sub-batch j from the
-// regrouped buffer, the bulk copies of sub-batch j+1 land in the copy
-// buffer.  In local mode (`exact` false) the walk stops as soon as the tile
+// Walk one segment in sub-batches: once every warp has compacted sub-batch
+// j into its pair buffer, the bulk copies of sub-batch j+1 land in the copy
+// buffer while the warps blend.  In local mode (`exact` false) the walk stops as soon as the tile
 // is marked done, and returns true (the partial result is then
 // irrelevant).  The CTA stops early once every pixel has terminated.
 // Returns kWalked, kAborted, or kFailed when a copy wait gave up (the CTA
@@ -384,9 +430,9 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
 constexpr int kWalked = 0, kAborted = 1, kFailed = 2;
 __device__ __forceinline__ int run_segment(const RasterArgs &a, const Seg &sg, uint32_t L,
                                             bool exact, bool inside, float fx, float fy,
-                                            PixelState &s, float4 *aos, PairBuf &pb,
-                                            uint64_t *bar, uint32_t &parity,
-                                            uint32_t *s_abort) {
+                                            float cx, float cy, PixelState &s,
+                                            float4 *aos, WarpPairs &wp, uint64_t *bar,
+                                            uint32_t &parity, uint32_t *s_abort) {
     const uint32_t pos0 = sg.k * L;
     if (sg.len == 0) return kWalked;
     const uint32_t nb = (sg.len + kChunk - 1) / kChunk;
@@ -399,13 +445,15 @@ __device__ __forceinline__ int run_segment(const RasterArgs &a, const Seg &sg, u
         const bool ok = wait_batch(a, bar, parity);
         parity ^= 1u;
         if (__syncthreads_or(!ok)) return kFailed;
-        regroup(aos, cnt, pb);
+        // warps whose pixels have all terminated skip their share
+        const bool wlive = __any_sync(0xffffffffu, inside && !s.term);
+        const uint32_t nw = wlive ? compact(aos, cnt, cx, cy, wp) : 0u;
         __syncthreads();
         const bool more = j + 1 < nb;
         if (more)
             issue_batch(a, sg.start + off + kChunk, min(sg.len - off - kChunk, (uint32_t)kChunk),
                         aos, bar);
-        if (inside && !s.term) blend_pairs(pb, cnt, pos0 + off, fx2, fy2, s);
+        if (inside && !s.term) blend_pairs(wp, nw, cnt, pos0 + off, fx2, fy2, s);
         if (threadIdx.x == 0) *s_abort = exact ? 0u : ld_volatile(a.tile_done + sg.t);
         const int done = __syncthreads_count(s.term || !inside);
         abort = *s_abort != 0;
@@ -426,9 +474,10 @@ raster_kernel(RasterArgs a) {
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t s_next;
     __shared__ uint32_t s_flag;
+    __shared__ uint32_t s_wait;
     __shared__ uint32_t s_abort;
     float4 *aos = reinterpret_cast<float4 *>(smem);
-    PairBuf &pb = *reinterpret_cast<PairBuf *>(smem + kBufBytes);
+    WarpPairs &wp = reinterpret_cast<WarpPairs *>(smem + kBufBytes)[threadIdx.x >> 5];
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -445,6 +494,28 @@ raster_kernel(RasterArgs a) {
         const uint32_t c = s_next;
         if (c >= total) break;
         const Seg sg = seg_of(a, c, L);
+        if (sg.k >= kWindow) {
+            // wait for the segment kWindow places earlier in this tile; it
+            // holds an earlier ticket, so its CTA is running
+            if (tid == 0) {
+                uint32_t skip = 0, spins = 0;
+                for (;;) {
+                    if (ld_volatile(a.flags + c - kWindow) != 0) break;
+                    if (ld_volatile(a.tile_done + sg.t)) {
+                        skip = 1;
+                        break;
+                    }
+                    if (++spins > kSpinLimit) {
+                        atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                s_wait = skip;
+            }
+            __syncthreads();
+            if (s_wait) continue;  // an earlier segment finished the tile
+        }
         const uint32_t prev = c - 1;
         bool exact = sg.k == 0;
         if (!exact) {
@@ -462,6 +533,9 @@ raster_kernel(RasterArgs a) {
         const int py = ty * 16 + (wid >> 1) * 4 + (lid >> 3);
         const bool inside = px < a.W && py < a.H;
         const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+        // centre of the warp's block of pixel centres
+        const float cx = (float)(tx * 16 + (wid & 1) * 8) + 4.0f;
+        const float cy = (float)(ty * 16 + (wid >> 1) * 4) + 2.0f;
         PixelState s = {0.0f, 0.0f, 0.0f, 1.0f, 0u, sg.k * L, false};
         bool was_term = false;  // terminated in an earlier segment (already written)
         if (sg.k > 0 && exact) {
@@ -474,8 +548,8 @@ raster_kernel(RasterArgs a) {
         bool active = inside, skip = false, redone = false;
         const bool last_seg = sg.k + 1 == sg.nk;
         for (int pass = 0; pass < 2; pass++) {
-            const int rc = run_segment(a, sg, L, exact || pass == 1, active, fx, fy, s, aos,
-                                       pb, &bar, parity, &s_abort);
+            const int rc = run_segment(a, sg, L, exact || pass == 1, active, fx, fy, cx, cy, s,
+                                       aos, wp, &bar, parity, &s_abort);
             if (rc == kFailed) return;
             if (rc == kAborted) {
                 skip = true;  // an earlier segment finished the tile
@@ -537,7 +611,9 @@ raster_kernel(RasterArgs a) {
                 }
                 const uint32_t j = s_next;
                 in = load_state(a.pre, a.pre2, j);
-                // fold the aggregates after j, four loads in flight at a time
+                // fold the aggregates after j, four loads in flight at a time;
+                // stop once every pixel is known to have terminated before this
+                // segment (the segments it terminated in write it)
                 uint32_t i = j + 1;
                 for (; i + 4 <= c; i += 4) {
                     PixelState x0 = load_state(a.agg, a.agg2, i);
@@ -545,6 +621,10 @@ raster_kernel(RasterArgs a) {
                     PixelState x2 = load_state(a.agg, a.agg2, i + 2);
                     PixelState x3 = load_state(a.agg, a.agg2, i + 3);
                     in = fold(fold(fold(fold(in, x0), x1), x2), x3);
+                    if (__syncthreads_and(in.term || !inside)) {
+                        i = c;
+                        break;
+                    }
                 }
                 for (; i < c; i++) in = fold(in, load_state(a.agg, a.agg2, i));
                 if (in.term) {

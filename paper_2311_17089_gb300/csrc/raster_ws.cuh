@@ -12,8 +12,12 @@
 namespace msgs {
 
 constexpr int kRasterThreads = 256;          // one thread per pixel of a 16x16 tile
-constexpr int kChunk = 256;                  // records per staged sub-batch
-constexpr uint32_t kMinSegment = 4 * kChunk; // shortest segment a tile is cut into
+constexpr int kChunk = 128;                  // records per staged sub-batch
+#ifndef MS_MIN_SEGMENT_CHUNKS
+#define MS_MIN_SEGMENT_CHUNKS 2
+#endif
+// shortest segment a tile is cut into
+constexpr uint32_t kMinSegment = MS_MIN_SEGMENT_CHUNKS * kChunk;
 constexpr uint32_t kTermBit = 0x80000000u;   // pixel terminated (in the n_eval word)
 // Most CTAs a raster launch runs at once.  The segment length is at least
 // D / resident, so a frame has at most tiles + min(D / kMinSegment,

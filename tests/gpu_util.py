@@ -82,6 +82,14 @@ def assert_footprints_equal(g, fp, scene, cam):
                                       np.ascontiguousarray(want, np.float32).view(np.uint32))
     rgb = oracle.colors(scene, cam)[li]
     np.testing.assert_allclose(rec[:, [6, 7, 8]], rgb, rtol=0, atol=2e-6)
+    # the level-set half extents (ex, ey) in the record span the tile rectangle
+    ux, uy, ex, ey = (rec[:, k].astype(np.float32) for k in (0, 1, 10, 11))
+    q = np.float32(0.0625)
+    x0 = np.maximum(np.floor((ux - ex) * q), 0).astype(np.int64)
+    x1 = np.minimum(np.floor((ux + ex) * q), cam.tiles_x - 1).astype(np.int64)
+    y0 = np.maximum(np.floor((uy - ey) * q), 0).astype(np.int64)
+    y1 = np.minimum(np.floor((uy + ey) * q), cam.tiles_y - 1).astype(np.int64)
+    np.testing.assert_array_equal(np.stack([x0, y0, x1, y1], 1), fp["rect"][li])
     return li
 
 
