@@ -75,7 +75,7 @@ def config(n, extra=None):
          "image": [1256, 832], "scales": list(inputs.SCALES),
          "frames_per_step": len(inputs.SCALES), "parallelism": "replicas",
          "l2": "inputs larger than L2 (scene ~250 MB), no flush",
-         "launch": "each 8-frame sweep replayed as one CUDA graph"}
+         "launch": "each 8-frame sweep replayed as one CUDA graph, one stream per frame"}
     if extra:
         c.update(extra)
     return c
@@ -459,48 +459,62 @@ def main():
         for r in rs:
             r.check()
         return
-    if args.profile:
-        cap = 4_000_000 if args.profile == "selective" else 60_000_000
-        r = msgs.Renderer(sc.n, max_tiles, cap, device=dev, with_cover=False, with_mask=False)
-        bufs = [r.images(cam, device=dev) for cam in cams]
-        for it in range(3):
-            if it == 2:
-                torch.cuda.synchronize()
-                torch.cuda.nvtx.range_push("sweep")
-            for cam, out in zip(cams, bufs):
-                r.render(ds, cam, args.profile, out=out)
-            if it == 2:
-                torch.cuda.synchronize()
-                torch.cuda.nvtx.range_pop()
-        r.check()
-        return
-    # size the duplicate capacity from one pass of both modes
-    probe = msgs.Renderer(sc.n, max_tiles, 4 * sc.n, device=dev, with_cover=False,
-                          with_mask=False)
+    # size each frame's duplicate capacity from one pass of both modes
+    probe = msgs.Renderer(sc.n, max_tiles, 60_000_000 if sc.n >= 500_000 else 60 * sc.n,
+                          device=dev, with_cover=False, with_mask=False)
     dmax = {}
     for mode in ("selective", "all_levels"):
         for cam in cams:
             probe.render(ds, cam, mode)
             rc, d, _ = msgs.ms_bin_counts(probe.bins)
+            if rc != msgs.MS_OK:
+                raise msgs.MsError(rc, "probe capacity")
             dmax[(mode, cam.width)] = d
-    cap = int(max(dmax.values()) * 1.05) + 1024
     del probe
-    r = msgs.Renderer(sc.n, max_tiles, cap, device=dev, with_cover=False, with_mask=False)
-    bufs = [r.images(cam, device=dev) for cam in cams]
+    # one renderer (projection, tile lists, workspaces) and one stream per
+    # frame: the frames of a sweep are independent, and the small ones leave
+    # most SMs idle, so they run concurrently
+    rs = [msgs.Renderer(sc.n, cam.tiles_x * cam.tiles_y,
+                        int(max(dmax[("selective", cam.width)],
+                                dmax[("all_levels", cam.width)]) * 1.05) + 1024,
+                        device=dev, with_cover=False, with_mask=False) for cam in cams]
+    bufs = [r.images(cam, device=dev) for r, cam in zip(rs, cams)]
+    streams = [torch.cuda.Stream(device=dev) for _ in cams]
+
+    def step(mode, after=None):
+        main = torch.cuda.current_stream()
+        for r, cam, out, st in zip(rs, cams, bufs, streams):
+            st.wait_stream(main)
+            with torch.cuda.stream(st):
+                r.render(ds, cam, mode, out=out, stream=st)
+                if after is not None:
+                    after(out, st)
+        for st in streams:
+            main.wait_stream(st)
+
+    if args.profile:
+        for it in range(3):
+            torch.cuda.synchronize()
+            if it == 2:
+                torch.cuda.nvtx.range_push("sweep")
+            step(args.profile)
+            torch.cuda.synchronize()
+            if it == 2:
+                torch.cuda.nvtx.range_pop()
+        for r in rs:
+            r.check()
+        return
     neval = [torch.empty((c.height, c.width), dtype=torch.int32, device=dev) for c in cams]
-    def step(mode):
-        for cam, out in zip(cams, bufs):
-            r.render(ds, cam, mode, out=out)
 
     # counts: duplicates, survivors, evaluations per frame
     stats = {}
     for mode in ("selective", "all_levels"):
-        for cam, out, ne in zip(cams, bufs, neval):
+        for r, cam, out, ne in zip(rs, cams, bufs, neval):
             r.render(ds, cam, mode, out=out, n_eval=ne)
-            rc, d, s = msgs.ms_bin_counts(r.bins)
+            rc, d, s_ = msgs.ms_bin_counts(r.bins)
             if rc != msgs.MS_OK:
                 raise msgs.MsError(rc, "capacity")
-            stats[(mode, cam.width)] = dict(D=d, survivors=s,
+            stats[(mode, cam.width)] = dict(D=d, survivors=s_,
                                             P_eval=int(ne.sum(dtype=torch.int64).item()))
 
     # CUDA graphs: one per 8-frame sweep, and one per stage of every frame
@@ -514,14 +528,14 @@ def main():
     g_step = {m: capture(lambda m=m: step(m)) for m in ("selective", "all_levels")}
     g_stage = {}
     for mode in ("selective", "all_levels"):
-        for cam, out in zip(cams, bufs):
+        for r, cam, out in zip(rs, cams, bufs):
             cs = msgs.camera_struct(cam)
             md = msgs.MODES[mode]
             g_stage[(mode, cam.width)] = (
-                capture(lambda cs=cs, md=md: msgs.ms_project(ds.struct, cs, md, r.proj)),
-                capture(lambda cs=cs: msgs.ms_bin(r.proj, sc.n, cs, r.bins, msgs._ptr(r.ws),
-                                                  r.ws_bytes)),
-                capture(lambda cs=cs, out=out: msgs.ms_raster(
+                capture(lambda cs=cs, md=md, r=r: msgs.ms_project(ds.struct, cs, md, r.proj)),
+                capture(lambda cs=cs, r=r: msgs.ms_bin(r.proj, sc.n, cs, r.bins,
+                                                       msgs._ptr(r.ws), r.ws_bytes)),
+                capture(lambda cs=cs, out=out, r=r: msgs.ms_raster(
                     r.proj, r.bins, cs, msgs._ptr(out[0]), msgs._ptr(out[1]),
                     msgs._ptr(out[2]), 0, msgs._ptr(r.rws), r.rws_bytes)))
     torch.cuda.synchronize()
@@ -629,9 +643,8 @@ def main():
             for k, t in host.items():
                 getattr(ds, k).copy_(t, non_blocking=True)
             msgs.ms_scene_prepare(ds.struct)
-            for cam, out, hb in zip(cams, bufs, outs):
-                r.render(ds, cam, "selective", out=out)
-                hb.copy_(out[0], non_blocking=True)
+            hb = iter(outs)
+            step("selective", after=lambda out, st: next(hb).copy_(out[0], non_blocking=True))
 
         for _ in range(args.warmup):
             e2e_step()
