@@ -341,6 +341,40 @@ int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
                   void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * One view of a batched backward: the inputs ms_raster_bwd takes for it.
+ */
+typedef struct {
+    ms_camera_t cam;
+    const ms_proj_t *proj;
+    const ms_bins_t *bins;
+    const float *image;
+    const uint32_t *n_contrib;
+    const void *raster_ws;
+    size_t raster_ws_bytes;
+    const float *dl_dimage;
+} ms_bwd_view_t;
+
+#define MS_MAX_BWD_VIEWS 8
+
+/* Workspace bytes ms_raster_bwd_views needs: n_views x 9 floats per
+ * Gaussian plus a counter; 0 for n_views outside 1..MS_MAX_BWD_VIEWS. */
+size_t ms_raster_bwd_views_workspace_bytes(int64_t n, int32_t n_views);
+
+/*
+ * The backward of a batch of views of one scene (a multi-scale training
+ * batch renders several views at different resolutions, Sec. 4.1): the
+ * same result as ms_raster_bwd for views[0] followed by MS_BWD_ACCUMULATE
+ * calls for the others, in two launches.  One raster pass takes the
+ * segments of every view by ticket, each view's 2D gradients going to its
+ * own part of `ws`; one projection pass then applies, per Gaussian, the
+ * chain rule of every view that blended it and writes the sum once.
+ * `flags` as for ms_raster_bwd.
+ */
+int ms_raster_bwd_views(const ms_scene_t *scene, const ms_bwd_view_t *views, int32_t n_views,
+                        const ms_grads_t *grads, uint32_t flags, void *ws, size_t ws_bytes,
+                        void *stream);
+
+/*
  * L1 photometric loss of a training step (Sec. 4.1 trains with the image
  * loss of the single-scale method; its L1 term):
  *   dl_dimage[i] = weight * sign(image[i] - target[i])   (sign(0) = 0)

@@ -29,6 +29,7 @@ MODES = {"selective": MS_SELECTIVE, "all_levels": MS_ALL_LEVELS,
          "filter_small": MS_FILTER_SMALL}
 MS_STATS_WORDS = 1040
 MS_BWD_ACCUMULATE = 1
+MS_MAX_BWD_VIEWS = 8
 REC_FLOATS = 12
 
 P = ctypes.c_void_p
@@ -69,6 +70,12 @@ class ms_grads_t(ctypes.Structure):
 class ms_bins_t(ctypes.Structure):
     _fields_ = [("gauss_idx", P), ("ranges", P), ("counts", P),
                 ("dup_capacity", ctypes.c_int64)]
+
+
+class ms_bwd_view_t(ctypes.Structure):
+    _fields_ = [("cam", ms_camera_t), ("proj", ctypes.POINTER(ms_proj_t)),
+                ("bins", ctypes.POINTER(ms_bins_t)), ("image", P), ("n_contrib", P),
+                ("raster_ws", P), ("raster_ws_bytes", ctypes.c_size_t), ("dl_dimage", P)]
 
 
 class ms_serve_cfg_t(ctypes.Structure):
@@ -126,6 +133,11 @@ _SIGNATURES = [
                                      ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
                                      P, P, P, ctypes.c_size_t, P, ctypes.POINTER(ms_grads_t),
                                      ctypes.c_uint32, P, ctypes.c_size_t, P]),
+    ("ms_raster_bwd_views_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32]),
+    ("ms_raster_bwd_views", ctypes.c_int, [ctypes.POINTER(ms_scene_t),
+                                           ctypes.POINTER(ms_bwd_view_t), ctypes.c_int32,
+                                           ctypes.POINTER(ms_grads_t), ctypes.c_uint32, P,
+                                           ctypes.c_size_t, P]),
     ("ms_l1_loss_grad", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_float, P, P, P]),
     ("ms_raster", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
                                  ctypes.POINTER(ms_camera_t), P, P, P, P, P,
@@ -273,6 +285,26 @@ def ms_raster_bwd(scene: ms_scene_t, cam: ms_camera_t, proj: ms_proj_t, bins: ms
                                P(raster_ws_ptr), raster_ws_bytes, P(dl_ptr),
                                ctypes.byref(grads), int(flags), P(ws_ptr), ws_bytes,
                                P(_stream(stream))))
+
+
+def ms_raster_bwd_views_workspace_bytes(n: int, n_views: int) -> int:
+    return int(lib().ms_raster_bwd_views_workspace_bytes(n, n_views))
+
+
+def bwd_view(cam: ms_camera_t, proj: ms_proj_t, bins: ms_bins_t, image_ptr: int,
+             n_contrib_ptr: int, raster_ws_ptr: int, raster_ws_bytes: int,
+             dl_ptr: int) -> ms_bwd_view_t:
+    """One view of ms_raster_bwd_views (keeps no reference to proj/bins:
+    the caller keeps them alive)."""
+    return ms_bwd_view_t(cam, ctypes.pointer(proj), ctypes.pointer(bins), P(image_ptr),
+                         P(n_contrib_ptr), P(raster_ws_ptr), raster_ws_bytes, P(dl_ptr))
+
+
+def ms_raster_bwd_views(scene: ms_scene_t, views, grads: ms_grads_t, flags: int, ws_ptr: int,
+                        ws_bytes: int, stream=None):
+    arr = (ms_bwd_view_t * len(views))(*views)
+    _check(lib().ms_raster_bwd_views(ctypes.byref(scene), arr, len(views), ctypes.byref(grads),
+                                     int(flags), P(ws_ptr), ws_bytes, P(_stream(stream))))
 
 
 def ms_l1_loss_grad(image_ptr: int, target_ptr: int, count: int, weight: float, dl_ptr: int,

@@ -46,7 +46,9 @@ __device__ __forceinline__ float ex2_approx_b(float x) {
     return y;
 }
 
-struct BwdArgs {
+constexpr int kMaxViews = MS_MAX_BWD_VIEWS;  // views one batched backward call takes
+
+struct ViewB {                // one view's inputs to raster_bwd_kernel
     const uint32_t *ranges;
     const uint32_t *gidx;
     const float4 *rec;
@@ -58,8 +60,13 @@ struct BwdArgs {
     const uint32_t *seg_off;  // the forward's segmentation
     const uint32_t *seg_len;
     const float4 *pre;        // [max_segs][256] state after each segment
+    float *g2;                // [n][kG2] this view's 2D gradients
+};
+
+struct BwdArgs {
+    ViewB v[kMaxViews];
+    int n_views;
     uint32_t *ticket;
-    float *g2;                // [n][kG2]
 };
 
 // Sum of v[q] over the 32 lanes of a warp, reduce-scattered: lane l returns
@@ -103,27 +110,42 @@ __device__ __forceinline__ float reduce_scatter9(const float v[kG2], int lane) {
 }
 
 __global__ void __launch_bounds__(kBwdThreads)
-raster_bwd_kernel(BwdArgs a) {
+raster_bwd_kernel(const __grid_constant__ BwdArgs args) {
     __shared__ float4 s_r0[kBwdBatch], s_r1[kBwdBatch];
     __shared__ float2 s_r2[kBwdBatch];
     __shared__ uint32_t s_idx[kBwdBatch];
     __shared__ float s_acc[kBwdBatch][kG2 + 1];  // [kG2] marks a record some pixel took
     __shared__ uint32_t s_c, s_cnt;
+    __shared__ uint32_t s_first[kMaxViews + 1];   // first ticket of each view's segments
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool owner = lane < 4 ? (lane & 1) == 0 : (lane & 3) == 0;
     const int q_own = lane < 4 ? lane >> 1 : (lane >> 2) + 1;
     for (int i = tid; i < kBwdBatch * (kG2 + 1); i += kBwdThreads) (&s_acc[0][0])[i] = 0.0f;
-    const uint32_t total = a.seg_off[a.tiles];
-    const uint32_t L = a.seg_len[0];
+    if (tid == 0) {
+        uint32_t run = 0;
+        for (int k = 0; k < args.n_views; k++) {
+            s_first[k] = run;
+            run += args.v[k].seg_off[args.v[k].tiles];
+        }
+        s_first[args.n_views] = run;
+    }
+    __syncthreads();
+    const uint32_t total = s_first[args.n_views];
     for (;;) {
         __syncthreads();
         if (tid == 0) {
-            s_c = atomicAdd(a.ticket, 1u);
+            s_c = atomicAdd(args.ticket, 1u);
             s_cnt = 0;
         }
         __syncthreads();
-        const uint32_t c = s_c;
-        if (c >= total) break;
+        const uint32_t cg = s_c;
+        if (cg >= total) break;
+        // the view whose segments this ticket falls in
+        int view = 0;
+        while (view + 1 < args.n_views && cg >= s_first[view + 1]) view++;
+        const ViewB &a = args.v[view];
+        const uint32_t c = cg - s_first[view];
+        const uint32_t L = a.seg_len[0];
         // the segment: tile t, index k within the tile, list entries [start, start + len)
         int lo = 0, hi = a.tiles;
         while (hi - lo > 1) {
@@ -381,146 +403,178 @@ struct GradsK {
 };
 
 
-__global__ void __launch_bounds__(256)
-project_bwd_kernel(SceneB sc, CamB cam, const float *__restrict__ g2all, GradsK out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sc.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float *g2 = g2all + i * kG2;
-        bool any = false;
-#pragma unroll
-        for (int q = 0; q < kG2; q++) any |= g2[q] != 0.0f;
-        if (!any) continue;
-        const float *W = cam.W;
-        const float m0 = sc.mean[3 * i], m1 = sc.mean[3 * i + 1], m2 = sc.mean[3 * i + 2];
-        const float tx = W[0] * m0 + W[1] * m1 + W[2] * m2 + cam.t[0];
-        const float ty = W[3] * m0 + W[4] * m1 + W[5] * m2 + cam.t[1];
-        const float tz = W[6] * m0 + W[7] * m1 + W[8] * m2 + cam.t[2];
-        const float4 q4 = reinterpret_cast<const float4 *>(sc.quat)[i];
-        const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
-        const float iq = 1.0f / qn;
-        const float w = q4.x * iq, x = q4.y * iq, y = q4.z * iq, z = q4.w * iq;
-        float R[9];
-        R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
-        R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-        R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
-        const float se[3] = {sc.scale[3 * i], sc.scale[3 * i + 1], sc.scale[3 * i + 2]};
-        float M[9], Sg[9];
-        for (int r = 0; r < 3; r++)
-            for (int c = 0; c < 3; c++) M[3 * r + c] = R[3 * r + c] * se[c];
-        for (int r = 0; r < 3; r++)
-            for (int c = 0; c < 3; c++)
-                Sg[3 * r + c] = M[3 * r] * M[3 * c] + M[3 * r + 1] * M[3 * c + 1] +
-                                M[3 * r + 2] * M[3 * c + 2];
-        const float limx = 1.3f * (0.5f * cam.width / cam.fx);
-        const float limy = 1.3f * (0.5f * cam.height / cam.fy);
-        const float xr = tx / tz, yr = ty / tz;
-        const bool clx = fabsf(xr) > limx, cly = fabsf(yr) > limy;
-        const float xc = fminf(limx, fmaxf(-limx, xr)), yc = fminf(limy, fmaxf(-limy, yr));
-        const float J00 = cam.fx / tz, J02 = -cam.fx * xc / tz;
-        const float J11 = cam.fy / tz, J12 = -cam.fy * yc / tz;
-        float T[6];
-        for (int c = 0; c < 3; c++) {
-            T[c] = J00 * W[c] + J02 * W[6 + c];
-            T[3 + c] = J11 * W[3 + c] + J12 * W[6 + c];
-        }
-        // V' and its inverse (the conic)
-        float TS[6];
-        for (int r = 0; r < 2; r++)
-            for (int c = 0; c < 3; c++)
-                TS[3 * r + c] = T[3 * r] * Sg[c] + T[3 * r + 1] * Sg[3 + c] + T[3 * r + 2] * Sg[6 + c];
-        const float va = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + 0.3f;
-        const float vb = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
-        const float vc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + 0.3f;
-        const float idet = 1.0f / (va * vc - vb * vb);
-        const float Qa = vc * idet, Qb = -vb * idet, Qc = va * idet;
-        float dt0 = 0.0f, dt1 = 0.0f, dt2 = 0.0f;
-        // centre
-        dt0 += g2[0] * cam.fx / tz;
-        dt2 += -g2[0] * cam.fx * tx / (tz * tz);
-        dt1 += g2[1] * cam.fy / tz;
-        dt2 += -g2[1] * cam.fy * ty / (tz * tz);
-        // G_V = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]]
-        const float ga = g2[2], gb = 0.5f * g2[3], gc = g2[4];
-        const float A00 = Qa * ga + Qb * gb, A01 = Qa * gb + Qb * gc;
-        const float A10 = Qb * ga + Qc * gb, A11 = Qb * gb + Qc * gc;
-        const float GV0 = -(A00 * Qa + A01 * Qb), GV1 = -(A00 * Qb + A01 * Qc),
-                    GV2 = -(A10 * Qb + A11 * Qc);
-        const float GVm[4] = {GV0, GV1, GV1, GV2};
-        // G_Sigma = T^T G_V T ; G_T = 2 G_V T Sigma
-        float GS[9];
-        for (int r = 0; r < 3; r++)
-            for (int c = 0; c < 3; c++) {
-                float v = 0.0f;
-                for (int p = 0; p < 2; p++)
-                    for (int q = 0; q < 2; q++) v += T[3 * p + r] * GVm[2 * p + q] * T[3 * q + c];
-                GS[3 * r + c] = v;
-            }
-        float GT[6];
-        for (int r = 0; r < 2; r++)
-            for (int c = 0; c < 3; c++)
-                GT[3 * r + c] = 2.0f * (GVm[2 * r] * TS[c] + GVm[2 * r + 1] * TS[3 + c]);
-        // G_J = G_T W^T
-        float GJ[6];
-        for (int r = 0; r < 2; r++)
-            for (int c = 0; c < 3; c++)
-                GJ[3 * r + c] = GT[3 * r] * W[3 * c] + GT[3 * r + 1] * W[3 * c + 1] +
-                                GT[3 * r + 2] * W[3 * c + 2];
-        const float itz2 = 1.0f / (tz * tz);
-        dt2 += GJ[0] * (-cam.fx * itz2) + GJ[4] * (-cam.fy * itz2) + GJ[2] * (cam.fx * xc * itz2) +
-               GJ[5] * (cam.fy * yc * itz2);
-        const float dxc = GJ[2] * (-cam.fx / tz), dyc = GJ[5] * (-cam.fy / tz);
-        if (!clx) {
-            dt0 += dxc / tz;
-            dt2 += -dxc * tx * itz2;
-        }
-        if (!cly) {
-            dt1 += dyc / tz;
-            dt2 += -dyc * ty * itz2;
-        }
-        float dmu[3] = {0.0f, 0.0f, 0.0f};
-        switch (sc.sh_degree) {
-        case 0: color_bwd<0>(i, sc, cam, g2, out.dcolor, out.acc, dmu); break;
-        case 1: color_bwd<1>(i, sc, cam, g2, out.dcolor, out.acc, dmu); break;
-        case 2: color_bwd<2>(i, sc, cam, g2, out.dcolor, out.acc, dmu); break;
-        case 3: color_bwd<3>(i, sc, cam, g2, out.dcolor, out.acc, dmu); break;
-        default:
-            put(out.dcolor + 3 * i, g2[6], out.acc);
-            put(out.dcolor + 3 * i + 1, g2[7], out.acc);
-            put(out.dcolor + 3 * i + 2, g2[8], out.acc);
-        }
+// One view's chain rule for Gaussian i, from its 2D gradient g2: adds the
+// geometry gradients to dm, dls, dqo and dop, and writes (acc false) or
+// adds (acc true) the colour gradient.
+__device__ __forceinline__ void view_chain(const SceneB &sc, const CamB &cam, const float *g2,
+                                           int64_t i, float dm[3], float dls[3], float dqo[4],
+                                           float &dop, float *dcolor, bool acc) {
+    const float *W = cam.W;
+    const float m0 = sc.mean[3 * i], m1 = sc.mean[3 * i + 1], m2 = sc.mean[3 * i + 2];
+    const float tx = W[0] * m0 + W[1] * m1 + W[2] * m2 + cam.t[0];
+    const float ty = W[3] * m0 + W[4] * m1 + W[5] * m2 + cam.t[1];
+    const float tz = W[6] * m0 + W[7] * m1 + W[8] * m2 + cam.t[2];
+    const float4 q4 = reinterpret_cast<const float4 *>(sc.quat)[i];
+    const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float iq = 1.0f / qn;
+    const float w = q4.x * iq, x = q4.y * iq, y = q4.z * iq, z = q4.w * iq;
+    float R[9];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+    const float se[3] = {sc.scale[3 * i], sc.scale[3 * i + 1], sc.scale[3 * i + 2]};
+    float M[9], Sg[9];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) M[3 * r + c] = R[3 * r + c] * se[c];
+    for (int r = 0; r < 3; r++)
         for (int c = 0; c < 3; c++)
-            put(out.dmean + 3 * i + c, W[c] * dt0 + W[3 + c] * dt1 + W[6 + c] * dt2 + dmu[c],
-                out.acc);
-        // Sigma = M M^T: G_M = 2 G_Sigma M;  M = R diag(se)
-        float GM[9];
-        for (int r = 0; r < 3; r++)
-            for (int c = 0; c < 3; c++)
-                GM[3 * r + c] = 2.0f * (GS[3 * r] * M[c] + GS[3 * r + 1] * M[3 + c] +
-                                        GS[3 * r + 2] * M[6 + c]);
-        float GR[9];
+            Sg[3 * r + c] = M[3 * r] * M[3 * c] + M[3 * r + 1] * M[3 * c + 1] +
+                            M[3 * r + 2] * M[3 * c + 2];
+    const float limx = 1.3f * (0.5f * cam.width / cam.fx);
+    const float limy = 1.3f * (0.5f * cam.height / cam.fy);
+    const float xr = tx / tz, yr = ty / tz;
+    const bool clx = fabsf(xr) > limx, cly = fabsf(yr) > limy;
+    const float xc = fminf(limx, fmaxf(-limx, xr)), yc = fminf(limy, fmaxf(-limy, yr));
+    const float J00 = cam.fx / tz, J02 = -cam.fx * xc / tz;
+    const float J11 = cam.fy / tz, J12 = -cam.fy * yc / tz;
+    float T[6];
+    for (int c = 0; c < 3; c++) {
+        T[c] = J00 * W[c] + J02 * W[6 + c];
+        T[3 + c] = J11 * W[3 + c] + J12 * W[6 + c];
+    }
+    // V' and its inverse (the conic)
+    float TS[6];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++)
+            TS[3 * r + c] = T[3 * r] * Sg[c] + T[3 * r + 1] * Sg[3 + c] + T[3 * r + 2] * Sg[6 + c];
+    const float va = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + 0.3f;
+    const float vb = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+    const float vc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + 0.3f;
+    const float idet = 1.0f / (va * vc - vb * vb);
+    const float Qa = vc * idet, Qb = -vb * idet, Qc = va * idet;
+    float dt0 = 0.0f, dt1 = 0.0f, dt2 = 0.0f;
+    // centre
+    dt0 += g2[0] * cam.fx / tz;
+    dt2 += -g2[0] * cam.fx * tx / (tz * tz);
+    dt1 += g2[1] * cam.fy / tz;
+    dt2 += -g2[1] * cam.fy * ty / (tz * tz);
+    // G_V = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]]
+    const float ga = g2[2], gb = 0.5f * g2[3], gc = g2[4];
+    const float A00 = Qa * ga + Qb * gb, A01 = Qa * gb + Qb * gc;
+    const float A10 = Qb * ga + Qc * gb, A11 = Qb * gb + Qc * gc;
+    const float GV0 = -(A00 * Qa + A01 * Qb), GV1 = -(A00 * Qb + A01 * Qc),
+                GV2 = -(A10 * Qb + A11 * Qc);
+    const float GVm[4] = {GV0, GV1, GV1, GV2};
+    // G_Sigma = T^T G_V T ; G_T = 2 G_V T Sigma
+    float GS[9];
+    for (int r = 0; r < 3; r++)
         for (int c = 0; c < 3; c++) {
-            float gs = 0.0f;
-            for (int r = 0; r < 3; r++) {
-                gs += R[3 * r + c] * GM[3 * r + c];
-                GR[3 * r + c] = GM[3 * r + c] * se[c];
-            }
-            put(out.dlog_scale + 3 * i + c, gs * se[c], out.acc);
+            float v = 0.0f;
+            for (int p = 0; p < 2; p++)
+                for (int q = 0; q < 2; q++) v += T[3 * p + r] * GVm[2 * p + q] * T[3 * q + c];
+            GS[3 * r + c] = v;
         }
-        float dq[4];
-        dq[0] = GR[1] * (-2 * z) + GR[2] * (2 * y) + GR[3] * (2 * z) + GR[5] * (-2 * x) +
-                GR[6] * (-2 * y) + GR[7] * (2 * x);
-        dq[1] = GR[1] * (2 * y) + GR[2] * (2 * z) + GR[3] * (2 * y) + GR[4] * (-4 * x) +
-                GR[5] * (-2 * w) + GR[6] * (2 * z) + GR[7] * (2 * w) + GR[8] * (-4 * x);
-        dq[2] = GR[0] * (-4 * y) + GR[1] * (2 * x) + GR[2] * (2 * w) + GR[3] * (2 * x) +
-                GR[5] * (2 * z) + GR[6] * (-2 * w) + GR[7] * (2 * z) + GR[8] * (-4 * y);
-        dq[3] = GR[0] * (-4 * z) + GR[1] * (-2 * w) + GR[2] * (2 * x) + GR[3] * (2 * w) +
-                GR[4] * (-4 * z) + GR[5] * (2 * y) + GR[6] * (2 * x) + GR[7] * (2 * y);
-        const float dot = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
-        put(out.dquat + 4 * i, (dq[0] - w * dot) * iq, out.acc);
-        put(out.dquat + 4 * i + 1, (dq[1] - x * dot) * iq, out.acc);
-        put(out.dquat + 4 * i + 2, (dq[2] - y * dot) * iq, out.acc);
-        put(out.dquat + 4 * i + 3, (dq[3] - z * dot) * iq, out.acc);
-        put(out.dopacity + i, g2[5], out.acc);
+    float GT[6];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++)
+            GT[3 * r + c] = 2.0f * (GVm[2 * r] * TS[c] + GVm[2 * r + 1] * TS[3 + c]);
+    // G_J = G_T W^T
+    float GJ[6];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++)
+            GJ[3 * r + c] = GT[3 * r] * W[3 * c] + GT[3 * r + 1] * W[3 * c + 1] +
+                            GT[3 * r + 2] * W[3 * c + 2];
+    const float itz2 = 1.0f / (tz * tz);
+    dt2 += GJ[0] * (-cam.fx * itz2) + GJ[4] * (-cam.fy * itz2) + GJ[2] * (cam.fx * xc * itz2) +
+           GJ[5] * (cam.fy * yc * itz2);
+    const float dxc = GJ[2] * (-cam.fx / tz), dyc = GJ[5] * (-cam.fy / tz);
+    if (!clx) {
+        dt0 += dxc / tz;
+        dt2 += -dxc * tx * itz2;
+    }
+    if (!cly) {
+        dt1 += dyc / tz;
+        dt2 += -dyc * ty * itz2;
+    }
+    float dmu[3] = {0.0f, 0.0f, 0.0f};
+    switch (sc.sh_degree) {
+    case 0: color_bwd<0>(i, sc, cam, g2, dcolor, acc, dmu); break;
+    case 1: color_bwd<1>(i, sc, cam, g2, dcolor, acc, dmu); break;
+    case 2: color_bwd<2>(i, sc, cam, g2, dcolor, acc, dmu); break;
+    case 3: color_bwd<3>(i, sc, cam, g2, dcolor, acc, dmu); break;
+    default:
+        put(dcolor + 3 * i, g2[6], acc);
+        put(dcolor + 3 * i + 1, g2[7], acc);
+        put(dcolor + 3 * i + 2, g2[8], acc);
+    }
+    for (int c = 0; c < 3; c++) dm[c] += W[c] * dt0 + W[3 + c] * dt1 + W[6 + c] * dt2 + dmu[c];
+    // Sigma = M M^T: G_M = 2 G_Sigma M;  M = R diag(se)
+    float GM[9];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++)
+            GM[3 * r + c] = 2.0f * (GS[3 * r] * M[c] + GS[3 * r + 1] * M[3 + c] +
+                                    GS[3 * r + 2] * M[6 + c]);
+    float GR[9];
+    for (int c = 0; c < 3; c++) {
+        float gs = 0.0f;
+        for (int r = 0; r < 3; r++) {
+            gs += R[3 * r + c] * GM[3 * r + c];
+            GR[3 * r + c] = GM[3 * r + c] * se[c];
+        }
+        dls[c] += gs * se[c];
+    }
+    float dq[4];
+    dq[0] = GR[1] * (-2 * z) + GR[2] * (2 * y) + GR[3] * (2 * z) + GR[5] * (-2 * x) +
+            GR[6] * (-2 * y) + GR[7] * (2 * x);
+    dq[1] = GR[1] * (2 * y) + GR[2] * (2 * z) + GR[3] * (2 * y) + GR[4] * (-4 * x) +
+            GR[5] * (-2 * w) + GR[6] * (2 * z) + GR[7] * (2 * w) + GR[8] * (-4 * x);
+    dq[2] = GR[0] * (-4 * y) + GR[1] * (2 * x) + GR[2] * (2 * w) + GR[3] * (2 * x) +
+            GR[5] * (2 * z) + GR[6] * (-2 * w) + GR[7] * (2 * z) + GR[8] * (-4 * y);
+    dq[3] = GR[0] * (-4 * z) + GR[1] * (-2 * w) + GR[2] * (2 * x) + GR[3] * (2 * w) +
+            GR[4] * (-4 * z) + GR[5] * (2 * y) + GR[6] * (2 * x) + GR[7] * (2 * y);
+    const float dot = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+    dqo[0] += (dq[0] - w * dot) * iq;
+    dqo[1] += (dq[1] - x * dot) * iq;
+    dqo[2] += (dq[2] - y * dot) * iq;
+    dqo[3] += (dq[3] - z * dot) * iq;
+    dop += g2[5];
+}
+
+struct ProjBwdArgs {
+    SceneB sc;
+    CamB cam[kMaxViews];
+    const float *g2[kMaxViews];  // [n][kG2] per view
+    int n_views;
+    GradsK out;
+};
+
+// Per Gaussian: the chain rule of every view that blended it, summed, and
+// written once (or added to the outputs when accumulating).
+__global__ void __launch_bounds__(256)
+project_bwd_kernel(const __grid_constant__ ProjBwdArgs p) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.sc.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float dm[3] = {0.0f, 0.0f, 0.0f}, dls[3] = {0.0f, 0.0f, 0.0f};
+        float dq[4] = {0.0f, 0.0f, 0.0f, 0.0f}, dop = 0.0f;
+        bool touched = false;
+        for (int k = 0; k < p.n_views; k++) {
+            const float *g2 = p.g2[k] + i * kG2;
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < kG2; q++) any |= g2[q] != 0.0f;
+            if (!any) continue;
+            view_chain(p.sc, p.cam[k], g2, i, dm, dls, dq, dop, p.out.dcolor,
+                       p.out.acc || touched);
+            touched = true;
+        }
+        if (!touched) continue;
+        const bool acc = p.out.acc;
+        for (int c = 0; c < 3; c++) {
+            put(p.out.dmean + 3 * i + c, dm[c], acc);
+            put(p.out.dlog_scale + 3 * i + c, dls[c], acc);
+        }
+        for (int c = 0; c < 4; c++) put(p.out.dquat + 4 * i + c, dq[c], acc);
+        put(p.out.dopacity + i, dop, acc);
     }
 }
 
@@ -581,9 +635,13 @@ extern "C" int ms_l1_loss_grad(const float *image, const float *target, int64_t 
     return cuda_check(cudaGetLastError(), "l1 loss launch");
 }
 
+extern "C" size_t ms_raster_bwd_views_workspace_bytes(int64_t n, int32_t n_views) {
+    if (n < 0 || n > INT32_MAX || n_views < 1 || n_views > MS_MAX_BWD_VIEWS) return 0;
+    return al256(4) + (size_t)n_views * al256((size_t)(n > 0 ? n : 1) * kG2 * sizeof(float));
+}
+
 extern "C" size_t ms_raster_bwd_workspace_bytes(int64_t n) {
-    if (n < 0 || n > INT32_MAX) return 0;
-    return al256(4) + (size_t)(n > 0 ? n : 1) * kG2 * sizeof(float);
+    return ms_raster_bwd_views_workspace_bytes(n, 1);
 }
 
 static int raster_bwd_blocks_per_sm() {
@@ -599,19 +657,13 @@ static int raster_bwd_blocks_per_sm() {
     return v;
 }
 
-extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
-                             const ms_proj_t *proj, const ms_bins_t *bins, const float *image,
-                             const uint32_t *n_contrib, const void *raster_ws,
-                             size_t raster_ws_bytes, const float *dl_dimage,
-                             const ms_grads_t *grads, uint32_t flags, void *ws, size_t ws_bytes,
-                             void *stream) {
-    if (!scene || !cam || !proj || !bins || !grads)
-        return fail(MS_ERR_INVALID_ARG, "NULL argument");
+extern "C" int ms_raster_bwd_views(const ms_scene_t *scene, const ms_bwd_view_t *views,
+                                   int32_t n_views, const ms_grads_t *grads, uint32_t flags,
+                                   void *ws, size_t ws_bytes, void *stream) {
+    if (!scene || !views || !grads) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (n_views < 1 || n_views > MS_MAX_BWD_VIEWS)
+        return fail(MS_ERR_INVALID_ARG, "n_views must be 1..MS_MAX_BWD_VIEWS");
     if (scene->n < 0 || scene->n > INT32_MAX) return fail(MS_ERR_INVALID_ARG, "scene n out of range");
-    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
-        return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
-    if (!dl_dimage || !image || !n_contrib)
-        return fail(MS_ERR_INVALID_ARG, "image, n_contrib and dl_dimage are required");
     if (scene->n > 0 && (!grads->dmean || !grads->dlog_scale || !grads->dquat ||
                          !grads->dopacity || !grads->dcolor))
         return fail(MS_ERR_INVALID_ARG, "ms_grads_t has a NULL buffer");
@@ -619,19 +671,65 @@ extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
         return fail(MS_ERR_INVALID_ARG, "scene mean/quat/scale/color is NULL");
     if (scene->sh_degree < -1 || scene->sh_degree > 3)
         return fail(MS_ERR_INVALID_ARG, "sh_degree must be in -1..3");
-    if (proj->n < scene->n || !proj->rec) return fail(MS_ERR_INVALID_ARG, "ms_proj_t too small");
-    if (!bins->gauss_idx || !bins->ranges) return fail(MS_ERR_INVALID_ARG, "bins buffers NULL");
     if (flags & ~MS_BWD_ACCUMULATE) return fail(MS_ERR_INVALID_ARG, "unknown flags");
     const bool accumulate = (flags & MS_BWD_ACCUMULATE) != 0;
-    const int tiles_x = (cam->width + 15) / 16, tiles_y = (cam->height + 15) / 16;
-    RasterLayout RL;
-    if (!raster_layout((int64_t)tiles_x * tiles_y, bins->dup_capacity, RL))
-        return fail(MS_ERR_INVALID_ARG, "tiles or dup_capacity out of range");
-    if (!raster_ws || raster_ws_bytes < RL.total || !aligned(raster_ws, 16))
-        return fail(MS_ERR_INVALID_ARG, "forward raster workspace missing or too small");
-    const size_t need = ms_raster_bwd_workspace_bytes(scene->n);
+    const size_t need = ms_raster_bwd_views_workspace_bytes(scene->n, n_views);
     if (!ws || ws_bytes < need || !aligned(ws, 16))
         return fail(MS_ERR_INVALID_ARG, "backward workspace missing, too small or misaligned");
+    char *w = static_cast<char *>(ws);
+    const size_t g2_bytes = al256((size_t)(scene->n > 0 ? scene->n : 1) * kG2 * sizeof(float));
+    BwdArgs a;
+    ProjBwdArgs pb;
+    a.n_views = n_views;
+    a.ticket = reinterpret_cast<uint32_t *>(w);
+    pb.n_views = n_views;
+    for (int k = 0; k < n_views; k++) {
+        const ms_bwd_view_t &v = views[k];
+        const ms_camera_t *cam = &v.cam;
+        if (!v.proj || !v.bins) return fail(MS_ERR_INVALID_ARG, "view proj or bins is NULL");
+        if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+            return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
+        if (!v.dl_dimage || !v.image || !v.n_contrib)
+            return fail(MS_ERR_INVALID_ARG, "image, n_contrib and dl_dimage are required");
+        if (v.proj->n < scene->n || !v.proj->rec)
+            return fail(MS_ERR_INVALID_ARG, "ms_proj_t too small");
+        if (!v.bins->gauss_idx || !v.bins->ranges)
+            return fail(MS_ERR_INVALID_ARG, "bins buffers NULL");
+        const int tiles_x = (cam->width + 15) / 16, tiles_y = (cam->height + 15) / 16;
+        RasterLayout RL;
+        if (!raster_layout((int64_t)tiles_x * tiles_y, v.bins->dup_capacity, RL))
+            return fail(MS_ERR_INVALID_ARG, "tiles or dup_capacity out of range");
+        if (!v.raster_ws || v.raster_ws_bytes < RL.total || !aligned(v.raster_ws, 16))
+            return fail(MS_ERR_INVALID_ARG, "forward raster workspace missing or too small");
+        const char *rw = static_cast<const char *>(v.raster_ws);
+        ViewB &b = a.v[k];
+        b.ranges = v.bins->ranges;
+        b.gidx = v.bins->gauss_idx;
+        b.rec = reinterpret_cast<const float4 *>(v.proj->rec);
+        b.n_rec = (uint32_t)v.proj->n;
+        b.W = cam->width;
+        b.H = cam->height;
+        b.tiles_x = tiles_x;
+        b.tiles = tiles_x * tiles_y;
+        b.image = v.image;
+        b.dl = v.dl_dimage;
+        b.n_contrib = v.n_contrib;
+        b.seg_off = reinterpret_cast<const uint32_t *>(rw + RL.seg_off);
+        b.seg_len = reinterpret_cast<const uint32_t *>(rw + RL.seg_len);
+        b.pre = reinterpret_cast<const float4 *>(rw + RL.pre);
+        b.g2 = reinterpret_cast<float *>(w + al256(4) + (size_t)k * g2_bytes);
+        CamB &cb = pb.cam[k];
+        for (int q = 0; q < 9; q++) cb.W[q] = cam->R[q];
+        for (int q = 0; q < 3; q++) {
+            cb.t[q] = cam->t[q];
+            cb.campos[q] = cam->campos[q];
+        }
+        cb.fx = cam->fx;
+        cb.fy = cam->fy;
+        cb.width = (float)cam->width;
+        cb.height = (float)cam->height;
+        pb.g2[k] = b.g2;
+    }
     cudaStream_t st = as_stream(stream);
     const int64_t n = scene->n;
     const int K = scene->sh_degree < 0 ? 1 : (scene->sh_degree + 1) * (scene->sh_degree + 1);
@@ -645,48 +743,37 @@ extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
             (rc = cuda_check(cudaMemsetAsync(grads->dcolor, 0, n * K * 3 * sizeof(float), st), "memset")))
             return rc;
     }
-    const char *rw = static_cast<const char *>(raster_ws);
-    char *w = static_cast<char *>(ws);
-    BwdArgs a;
-    a.ranges = bins->ranges;
-    a.gidx = bins->gauss_idx;
-    a.rec = reinterpret_cast<const float4 *>(proj->rec);
-    a.n_rec = (uint32_t)proj->n;
-    a.W = cam->width;
-    a.H = cam->height;
-    a.tiles_x = tiles_x;
-    a.tiles = tiles_x * tiles_y;
-    a.image = image;
-    a.dl = dl_dimage;
-    a.n_contrib = n_contrib;
-    a.seg_off = reinterpret_cast<const uint32_t *>(rw + RL.seg_off);
-    a.seg_len = reinterpret_cast<const uint32_t *>(rw + RL.seg_len);
-    a.pre = reinterpret_cast<const float4 *>(rw + RL.pre);
-    a.ticket = reinterpret_cast<uint32_t *>(w);
-    a.g2 = reinterpret_cast<float *>(w + al256(4));
     raster_bwd_kernel<<<raster_bwd_blocks_per_sm() * num_sms(), kBwdThreads, 0, st>>>(a);
     if (n > 0) {
-        SceneB sb;
-        sb.n = n;
-        sb.sh_degree = scene->sh_degree;
-        sb.mean = scene->mean;
-        sb.quat = scene->quat;
-        sb.color = scene->color;
-        sb.scale = scene->scale;
-        CamB cb;
-        for (int k = 0; k < 9; k++) cb.W[k] = cam->R[k];
-        for (int k = 0; k < 3; k++) {
-            cb.t[k] = cam->t[k];
-            cb.campos[k] = cam->campos[k];
-        }
-        cb.fx = cam->fx;
-        cb.fy = cam->fy;
-        cb.width = (float)cam->width;
-        cb.height = (float)cam->height;
-        GradsK gk = {grads->dmean, grads->dlog_scale, grads->dquat, grads->dopacity,
-                     grads->dcolor, accumulate};
+        pb.sc.n = n;
+        pb.sc.sh_degree = scene->sh_degree;
+        pb.sc.mean = scene->mean;
+        pb.sc.quat = scene->quat;
+        pb.sc.color = scene->color;
+        pb.sc.scale = scene->scale;
+        pb.out = {grads->dmean, grads->dlog_scale, grads->dquat, grads->dopacity, grads->dcolor,
+                  accumulate};
         int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
-        project_bwd_kernel<<<grid, 256, 0, st>>>(sb, cb, a.g2, gk);
+        project_bwd_kernel<<<grid, 256, 0, st>>>(pb);
     }
     return cuda_check(cudaGetLastError(), "backward launches");
+}
+
+extern "C" int ms_raster_bwd(const ms_scene_t *scene, const ms_camera_t *cam,
+                             const ms_proj_t *proj, const ms_bins_t *bins, const float *image,
+                             const uint32_t *n_contrib, const void *raster_ws,
+                             size_t raster_ws_bytes, const float *dl_dimage,
+                             const ms_grads_t *grads, uint32_t flags, void *ws, size_t ws_bytes,
+                             void *stream) {
+    if (!cam) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    ms_bwd_view_t v;
+    v.cam = *cam;
+    v.proj = proj;
+    v.bins = bins;
+    v.image = image;
+    v.n_contrib = n_contrib;
+    v.raster_ws = raster_ws;
+    v.raster_ws_bytes = raster_ws_bytes;
+    v.dl_dimage = dl_dimage;
+    return ms_raster_bwd_views(scene, &v, 1, grads, flags, ws, ws_bytes, stream);
 }

@@ -83,7 +83,11 @@ def test_backward_argument_errors_need_no_device():
     bins = msgs.ms_bins_t(fake, fake, fake, 16)
     grads = msgs.ms_grads_t(*([fake] * 5))
     ws = msgs.ms_raster_bwd_workspace_bytes(10)
-    assert ws == 256 + 10 * 9 * 4
+    assert ws >= 10 * 9 * 4 + 4 and ws % 256 == 0
+    assert msgs.ms_raster_bwd_views_workspace_bytes(10, 1) == ws
+    assert msgs.ms_raster_bwd_views_workspace_bytes(10, 3) > ws
+    assert msgs.ms_raster_bwd_views_workspace_bytes(10, 0) == 0
+    assert msgs.ms_raster_bwd_views_workspace_bytes(10, msgs.MS_MAX_BWD_VIEWS + 1) == 0
     assert msgs.ms_raster_bwd_workspace_bytes(-1) == 0
     rws = msgs.ms_raster_workspace_bytes(cam.width // 16 * (cam.height // 16), 16)
 
@@ -98,6 +102,12 @@ def test_backward_argument_errors_need_no_device():
     assert bwd(0, s=bad_deg) == msgs.MS_ERR_INVALID_ARG
     assert bwd(0, rws_bytes=rws - 16) == msgs.MS_ERR_INVALID_ARG
     assert b"raster workspace" in lib.ms_last_error()
+    v = msgs.bwd_view(cam, proj, bins, fake, fake, fake, rws, fake)
+    arr = (msgs.ms_bwd_view_t * 1)(v)
+    assert lib.ms_raster_bwd_views(ctypes.byref(sc), arr, 0, ctypes.byref(grads), 0, fake, ws,
+                                   None) == msgs.MS_ERR_INVALID_ARG
+    assert lib.ms_raster_bwd_views(ctypes.byref(sc), arr, 1, ctypes.byref(grads), 0, fake,
+                                   ws - 16, None) == msgs.MS_ERR_INVALID_ARG
     # L1 loss: count 0 is a no-op, negative counts, NULL and misaligned buffers fail
     assert lib.ms_l1_loss_grad(None, None, 0, 1.0, None, None, None) == msgs.MS_OK
     assert lib.ms_l1_loss_grad(fake, fake, -1, 1.0, fake, None, None) == msgs.MS_ERR_INVALID_ARG
