@@ -30,11 +30,12 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "f32x2.cuh"
 #include "raster_ws.cuh"
 
 namespace msgs {
 
-constexpr int kBwdThreads = kRasterThreads;
+constexpr int kBwdThreads = 128;  // two pixels per thread
 constexpr int kBwdBatch = 256;
 constexpr int kG2 = 9;  // dux, duy, da, db, dc, dsigma, dr, dg, db
 constexpr float kInvConicA = -1.3862943611198906f;  // 1 / (-log2(e)/2)
@@ -109,6 +110,20 @@ __device__ __forceinline__ float reduce_scatter9(const float v[kG2], int lane) {
     return d + __shfl_xor_sync(0xffffffffu, d, 1);
 }
 
+// Index of tile pixel (x, y) in the forward's thread layout (warp w covers
+// the 8x4 block ((w & 1) * 8, (w >> 1) * 4), lane l its pixel (l & 7, l >> 3)),
+// which is how the forward stores each segment's per-pixel state.
+__device__ __forceinline__ int fwd_index(int x, int y) {
+    return ((y >> 2) * 2 + (x >> 3)) * 32 + (y & 3) * 8 + (x & 7);
+}
+
+// Two pixels of one thread, (x, y) and (x, y + 4): the same dx for every
+// record, so their arithmetic runs as packed FP32x2 pairs.
+struct PixPair {
+    f32x2 T, F0, F1, F2, C0, C1, C2, d0, d1, d2;
+    uint32_t cntA, cntB;  // entries of the segment each pixel blended through
+};
+
 __global__ void __launch_bounds__(kBwdThreads)
 raster_bwd_kernel(const __grid_constant__ BwdArgs args) {
     __shared__ float4 s_r0[kBwdBatch], s_r1[kBwdBatch];
@@ -120,6 +135,12 @@ raster_bwd_kernel(const __grid_constant__ BwdArgs args) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool owner = lane < 4 ? (lane & 1) == 0 : (lane & 3) == 0;
     const int q_own = lane < 4 ? lane >> 1 : (lane >> 2) + 1;
+    // this thread's pixels within a tile: warp w covers the 8x8 block
+    // ((w & 1) * 8, (w >> 1) * 8), lane l the pixels (l & 7, l >> 3) and
+    // (l & 7, (l >> 3) + 4) of it
+    const int lx = (wid & 1) * 8 + (lane & 7);
+    const int lyA = (wid >> 1) * 8 + (lane >> 3), lyB = lyA + 4;
+    const int fA = fwd_index(lx, lyA), fB = fwd_index(lx, lyB);
     for (int i = tid; i < kBwdBatch * (kG2 + 1); i += kBwdThreads) (&s_acc[0][0])[i] = 0.0f;
     if (tid == 0) {
         uint32_t run = 0;
@@ -160,109 +181,150 @@ raster_bwd_kernel(const __grid_constant__ BwdArgs args) {
         const uint32_t start = tbeg + pos0;
         const uint32_t len = tend > start ? min(tend - start, L) : 0u;
         const int tx = t % a.tiles_x, ty = t / a.tiles_x;
-        const int px = tx * 16 + (wid & 1) * 8 + (lane & 7);
-        const int py = ty * 16 + (wid >> 1) * 4 + (lane >> 3);
-        const bool inside = px < a.W && py < a.H;
-        const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-        uint32_t my_cnt = 0;  // entries of this segment the pixel blended through
-        float T = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
-        float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
-        if (inside && len > 0) {
-            const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
-            const uint32_t nc = a.n_contrib[p];
-            if (nc > pos0) {
-                my_cnt = min(nc - pos0, len);
-                if (k > 0) {
-                    const float4 st = __ldcg(a.pre + (size_t)(c - 1) * kRasterThreads + tid);
-                    F0 = st.x;
-                    F1 = st.y;
-                    F2 = st.z;
-                    T = st.w;
+        const int px = tx * 16 + lx;
+        PixPair pp;
+        float st[2][10];  // per pixel: T, F0..2, C0..2, d0..2
+        uint32_t cnt[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int py = ty * 16 + (h ? lyB : lyA);
+            st[h][0] = 1.0f;
+#pragma unroll
+            for (int q = 1; q < 10; q++) st[h][q] = 0.0f;
+            if (px < a.W && py < a.H && len > 0) {
+                const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+                const uint32_t nc = a.n_contrib[p];
+                if (nc > pos0) {
+                    cnt[h] = min(nc - pos0, len);
+                    if (k > 0) {
+                        const float4 s4 =
+                            __ldcg(a.pre + (size_t)(c - 1) * kRasterThreads + (h ? fB : fA));
+                        st[h][0] = s4.w;
+                        st[h][1] = s4.x;
+                        st[h][2] = s4.y;
+                        st[h][3] = s4.z;
+                    }
+                    st[h][4] = a.image[p];
+                    st[h][5] = a.image[plane + p];
+                    st[h][6] = a.image[2 * plane + p];
+                    st[h][7] = a.dl[p];
+                    st[h][8] = a.dl[plane + p];
+                    st[h][9] = a.dl[2 * plane + p];
                 }
-                C0 = a.image[p];
-                C1 = a.image[plane + p];
-                C2 = a.image[2 * plane + p];
-                d0 = a.dl[p];
-                d1 = a.dl[plane + p];
-                d2 = a.dl[2 * plane + p];
             }
         }
-        const uint32_t wcnt = __reduce_max_sync(0xffffffffu, my_cnt);
+        pp.T = pack2(st[0][0], st[1][0]);
+        pp.F0 = pack2(st[0][1], st[1][1]);
+        pp.F1 = pack2(st[0][2], st[1][2]);
+        pp.F2 = pack2(st[0][3], st[1][3]);
+        pp.C0 = pack2(st[0][4], st[1][4]);
+        pp.C1 = pack2(st[0][5], st[1][5]);
+        pp.C2 = pack2(st[0][6], st[1][6]);
+        pp.d0 = pack2(st[0][7], st[1][7]);
+        pp.d1 = pack2(st[0][8], st[1][8]);
+        pp.d2 = pack2(st[0][9], st[1][9]);
+        pp.cntA = cnt[0];
+        pp.cntB = cnt[1];
+        const float fx = (float)px + 0.5f;
+        const f32x2 fy2 = pack2((float)(ty * 16 + lyA) + 0.5f, (float)(ty * 16 + lyB) + 0.5f);
+        const uint32_t wcnt = __reduce_max_sync(0xffffffffu, max(pp.cntA, pp.cntB));
         if (lane == 0 && wcnt) atomicMax(&s_cnt, wcnt);
         __syncthreads();
         const uint32_t cnt_seg = s_cnt;
         for (uint32_t off = 0; off < cnt_seg; off += kBwdBatch) {
             const uint32_t nb = min(cnt_seg - off, (uint32_t)kBwdBatch);
-            if ((uint32_t)tid < nb) {
-                uint32_t g = a.gidx[start + off + tid];
+            for (uint32_t r = tid; r < nb; r += kBwdThreads) {
+                uint32_t g = a.gidx[start + off + r];
                 if (g >= a.n_rec) g = 0;  // unreachable unless binning reported an error
-                s_idx[tid] = g;
-                s_r0[tid] = a.rec[3 * (size_t)g];
-                s_r1[tid] = a.rec[3 * (size_t)g + 1];
+                s_idx[r] = g;
+                s_r0[r] = a.rec[3 * (size_t)g];
+                s_r1[r] = a.rec[3 * (size_t)g + 1];
                 const float4 r2 = a.rec[3 * (size_t)g + 2];
-                s_r2[tid] = make_float2(r2.x, r2.y);
+                s_r2[r] = make_float2(r2.x, r2.y);
             }
             __syncthreads();
             const uint32_t jn = wcnt > off ? min(wcnt - off, nb) : 0u;  // warp-uniform
             for (uint32_t j = 0; j < jn; j++) {
-                float v[kG2];
-#pragma unroll
-                for (int q = 0; q < kG2; q++) v[q] = 0.0f;
-                bool acc = false;
-                if (off + j < my_cnt) {
-                    const float4 r0 = s_r0[j], r1 = s_r1[j];
-                    const float2 r2 = s_r2[j];
-                    // the forward's exact FP32 operations
-                    const float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
-                    const float u = __fmaf_rn(r0.w, dy, __fmul_rn(r0.z, dx));
-                    const float pw = __fmaf_rn(__fmul_rn(r1.x, dy), dy, __fmul_rn(dx, u));
-                    if (pw <= 0.0f && pw >= r2.y) {
-                        acc = true;
-                        const float e = ex2_approx_b(pw);
-                        const float G = r1.y * e;
-                        const float al = fminf(0.99f, G);
-                        const float w = al * T;
-                        F0 = fmaf(w, r1.z, F0);
-                        F1 = fmaf(w, r1.w, F1);
-                        F2 = fmaf(w, r2.x, F2);
-                        const float iom = __fdividef(1.0f, 1.0f - al);
-                        const float dal = d0 * (T * r1.z - (C0 - F0) * iom) +
-                                          d1 * (T * r1.w - (C1 - F1) * iom) +
-                                          d2 * (T * r2.x - (C2 - F2) * iom);
-                        v[6] = w * d0;
-                        v[7] = w * d1;
-                        v[8] = w * d2;
-                        T = T * (1.0f - al);
-                        if (G < 0.99f) {
-                            v[5] = dal * e;
-                            const float dpow = dal * al;
-                            const float ca = r0.z * kInvConicA, cb = r0.w * kInvConicB,
-                                        cc = r1.x * kInvConicA;
-                            v[0] = dpow * (ca * dx + cb * dy);
-                            v[1] = dpow * (cc * dy + cb * dx);
-                            v[2] = dpow * (-0.5f * dx * dx);
-                            v[3] = dpow * (-dx * dy);
-                            v[4] = dpow * (-0.5f * dy * dy);
-                        }
-                    }
-                }
-                if (__any_sync(0xffffffffu, acc)) {
-                    const float sum = reduce_scatter9(v, lane);
-                    if (owner) {
-                        atomicAdd(&s_acc[j][q_own], sum);
-                        if (lane == 0) s_acc[j][kG2] = 1.0f;
-                    }
+                const float4 r0 = s_r0[j], r1 = s_r1[j];
+                const float2 r2 = s_r2[j];
+                // the forward's exact FP32 operations, for both pixels
+                const float dx = __fsub_rn(fx, r0.x);
+                const f32x2 dy = sub2(fy2, splat2(r0.y));
+                const f32x2 u = fma2(splat2(r0.w), dy, splat2(__fmul_rn(r0.z, dx)));
+                const f32x2 pw = fma2(mul2(splat2(r1.x), dy), dy, mul2(splat2(dx), u));
+                float pA, pB;
+                unpack2(pw, pA, pB);
+                const bool accA = off + j < pp.cntA && pA <= 0.0f && pA >= r2.y;
+                const bool accB = off + j < pp.cntB && pB <= 0.0f && pB >= r2.y;
+                if (!__any_sync(0xffffffffu, accA || accB)) continue;
+                // alpha of accepted pixels, 0 for the others (no effect on
+                // T, F or any gradient); gradients through alpha only below
+                // the 0.99 clamp
+                const float eA = ex2_approx_b(accA ? pA : -256.0f);
+                const float eB = ex2_approx_b(accB ? pB : -256.0f);
+                const float GA = r1.y * eA, GB = r1.y * eB;
+                const float alA = accA ? fminf(0.99f, GA) : 0.0f;
+                const float alB = accB ? fminf(0.99f, GB) : 0.0f;
+                const f32x2 al = pack2(alA, alB);
+                const f32x2 mg = pack2(accA && GA < 0.99f ? 1.0f : 0.0f,
+                                       accB && GB < 0.99f ? 1.0f : 0.0f);
+                const f32x2 e = pack2(eA, eB);
+                const f32x2 w = mul2(al, pp.T);
+                const f32x2 cr = splat2(r1.z), cg2 = splat2(r1.w), cb2 = splat2(r2.x);
+                pp.F0 = fma2(w, cr, pp.F0);
+                pp.F1 = fma2(w, cg2, pp.F1);
+                pp.F2 = fma2(w, cb2, pp.F2);
+                const f32x2 om = sub2(splat2(1.0f), al);
+                const f32x2 iom = pack2(__fdividef(1.0f, 1.0f - alA), __fdividef(1.0f, 1.0f - alB));
+                // dC/dalpha = T c - (C - F) / (1 - alpha), summed over channels with dL/dC
+                const f32x2 t0 = fma2(sub2(pp.C0, pp.F0), mul2(splat2(-1.0f), iom),
+                                      mul2(pp.T, cr));
+                const f32x2 t1 = fma2(sub2(pp.C1, pp.F1), mul2(splat2(-1.0f), iom),
+                                      mul2(pp.T, cg2));
+                const f32x2 t2 = fma2(sub2(pp.C2, pp.F2), mul2(splat2(-1.0f), iom),
+                                      mul2(pp.T, cb2));
+                const f32x2 dal = fma2(pp.d2, t2, fma2(pp.d1, t1, mul2(pp.d0, t0)));
+                pp.T = mul2(pp.T, om);
+                const f32x2 hd = mul2(mul2(dal, mg), e);     // dL/dsigma terms
+                const f32x2 dpow = mul2(mul2(dal, mg), al);  // dL/dpower terms
+                const float ca = r0.z * kInvConicA, cb = r0.w * kInvConicB, cc = r1.x * kInvConicA;
+                const f32x2 gx = fma2(splat2(cb), dy, splat2(ca * dx));
+                const f32x2 gy = fma2(splat2(cc), dy, splat2(cb * dx));
+                float v[kG2], lo2, hi2;
+                unpack2(mul2(dpow, gx), lo2, hi2);
+                v[0] = lo2 + hi2;
+                unpack2(mul2(dpow, gy), lo2, hi2);
+                v[1] = lo2 + hi2;
+                unpack2(dpow, lo2, hi2);
+                v[2] = (lo2 + hi2) * (-0.5f * dx * dx);
+                unpack2(mul2(dpow, dy), lo2, hi2);
+                v[3] = -dx * (lo2 + hi2);
+                unpack2(mul2(mul2(dpow, dy), dy), lo2, hi2);
+                v[4] = -0.5f * (lo2 + hi2);
+                unpack2(hd, lo2, hi2);
+                v[5] = lo2 + hi2;
+                unpack2(mul2(w, pp.d0), lo2, hi2);
+                v[6] = lo2 + hi2;
+                unpack2(mul2(w, pp.d1), lo2, hi2);
+                v[7] = lo2 + hi2;
+                unpack2(mul2(w, pp.d2), lo2, hi2);
+                v[8] = lo2 + hi2;
+                const float sum = reduce_scatter9(v, lane);
+                if (owner) {
+                    atomicAdd(&s_acc[j][q_own], sum);
+                    if (lane == 0) s_acc[j][kG2] = 1.0f;
                 }
             }
             __syncthreads();
-            if ((uint32_t)tid < nb && s_acc[tid][kG2] != 0.0f) {
-                float *dst = a.g2 + (size_t)s_idx[tid] * kG2;
+            for (uint32_t r = tid; r < nb; r += kBwdThreads) {
+                if (s_acc[r][kG2] == 0.0f) continue;
+                float *dst = a.g2 + (size_t)s_idx[r] * kG2;
 #pragma unroll
                 for (int q = 0; q < kG2; q++) {
-                    if (s_acc[tid][q] != 0.0f) atomicAdd(dst + q, s_acc[tid][q]);
-                    s_acc[tid][q] = 0.0f;
+                    if (s_acc[r][q] != 0.0f) atomicAdd(dst + q, s_acc[r][q]);
+                    s_acc[r][q] = 0.0f;
                 }
-                s_acc[tid][kG2] = 0.0f;
+                s_acc[r][kG2] = 0.0f;
             }
             __syncthreads();
         }

@@ -32,6 +32,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "f32x2.cuh"
 #include "raster_ws.cuh"
 
 namespace msgs {
@@ -219,32 +220,6 @@ constexpr int kSmemBytes = kBufBytes + kWarps * (int)sizeof(WarpPairs);
 // of the level set.
 constexpr float kBlockHalfX = 3.5f + 1.0f;
 constexpr float kBlockHalfY = 1.5f + 1.0f;
-
-typedef unsigned long long f32x2;  // two FP32 values in one 64-bit register pair
-
-__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
-    f32x2 d;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-    return d;
-}
-__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
 
 // Compact the records [0, cnt) of the staged sub-batch whose level-set box
 // (centre +- (ex, ey)) can reach the warp's block of pixel centres
