@@ -421,10 +421,9 @@ __device__ __forceinline__ void put(float *p, float v, bool acc) { *p = acc ? *p
 // the mean gradient.  Returns the latter in dmu.
 template <int DEG>
 __device__ __forceinline__ void color_bwd(int64_t i, const SceneB &sc, const CamB &cam,
-                                          const float *g2, float *dcolor, bool acc,
+                                          const float *g2, const float *coef, float *dcol,
                                           float dmu[3]) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const float *coef = sc.color + i * K * 3;
     float dx = sc.mean[3 * i] - cam.campos[0], dy = sc.mean[3 * i + 1] - cam.campos[1],
           dz = sc.mean[3 * i + 2] - cam.campos[2];
     const float r = sqrtf(dx * dx + dy * dy + dz * dz), ir = 1.0f / r;
@@ -440,12 +439,11 @@ __device__ __forceinline__ void color_bwd(int64_t i, const SceneB &sc, const Cam
     }
     float dr[3];
     for (int c = 0; c < 3; c++) dr[c] = pre[c] > 0.0f ? g2[6 + c] : 0.0f;
-    float *dst = dcolor + i * K * 3;
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        put(dst + 3 * k, dr[0] * Y[k], acc);
-        put(dst + 3 * k + 1, dr[1] * Y[k], acc);
-        put(dst + 3 * k + 2, dr[2] * Y[k], acc);
+        dcol[3 * k] += dr[0] * Y[k];
+        dcol[3 * k + 1] += dr[1] * Y[k];
+        dcol[3 * k + 2] += dr[2] * Y[k];
     }
     dmu[0] = dmu[1] = dmu[2] = 0.0f;
     if constexpr (DEG >= 1) {
@@ -466,11 +464,12 @@ struct GradsK {
 
 
 // One view's chain rule for Gaussian i, from its 2D gradient g2: adds the
-// geometry gradients to dm, dls, dqo and dop, and writes (acc false) or
-// adds (acc true) the colour gradient.
+// geometry gradients to dm, dls, dqo and dop and the colour gradient to
+// dcol (the Gaussian's row, as is coef).
+template <int DEG>
 __device__ __forceinline__ void view_chain(const SceneB &sc, const CamB &cam, const float *g2,
                                            int64_t i, float dm[3], float dls[3], float dqo[4],
-                                           float &dop, float *dcolor, bool acc) {
+                                           float &dop, const float *coef, float *dcol) {
     const float *W = cam.W;
     const float m0 = sc.mean[3 * i], m1 = sc.mean[3 * i + 1], m2 = sc.mean[3 * i + 2];
     const float tx = W[0] * m0 + W[1] * m1 + W[2] * m2 + cam.t[0];
@@ -559,15 +558,12 @@ __device__ __forceinline__ void view_chain(const SceneB &sc, const CamB &cam, co
         dt2 += -dyc * ty * itz2;
     }
     float dmu[3] = {0.0f, 0.0f, 0.0f};
-    switch (sc.sh_degree) {
-    case 0: color_bwd<0>(i, sc, cam, g2, dcolor, acc, dmu); break;
-    case 1: color_bwd<1>(i, sc, cam, g2, dcolor, acc, dmu); break;
-    case 2: color_bwd<2>(i, sc, cam, g2, dcolor, acc, dmu); break;
-    case 3: color_bwd<3>(i, sc, cam, g2, dcolor, acc, dmu); break;
-    default:
-        put(dcolor + 3 * i, g2[6], acc);
-        put(dcolor + 3 * i + 1, g2[7], acc);
-        put(dcolor + 3 * i + 2, g2[8], acc);
+    if constexpr (DEG >= 0) {
+        color_bwd<DEG>(i, sc, cam, g2, coef, dcol, dmu);
+    } else {  // plain RGB
+        dcol[0] += g2[6];
+        dcol[1] += g2[7];
+        dcol[2] += g2[8];
     }
     for (int c = 0; c < 3; c++) dm[c] += W[c] * dt0 + W[3 + c] * dt1 + W[6 + c] * dt2 + dmu[c];
     // Sigma = M M^T: G_M = 2 G_Sigma M;  M = R diag(se)
@@ -610,34 +606,101 @@ struct ProjBwdArgs {
     GradsK out;
 };
 
-// Per Gaussian: the chain rule of every view that blended it, summed, and
-// written once (or added to the outputs when accumulating).
-__global__ void __launch_bounds__(256)
+constexpr int kProjBwdWarps = 4;
+
+// Colour coefficients per Gaussian and the padded (odd) row stride of their
+// shared-memory copies, so that lanes reading their own rows hit distinct
+// banks.
+template <int DEG>
+struct ColorRows {
+    static constexpr int K = DEG < 0 ? 1 : (DEG + 1) * (DEG + 1);
+    static constexpr int RS = 3 * K;
+    static constexpr int STRIDE = RS | 1;
+    static constexpr int WARP_FLOATS = 2 * 32 * STRIDE;  // coefficient and gradient rows
+};
+
+// A streaming pass over the scene, 32 consecutive Gaussians per warp: the
+// warp stages their colour rows (and, when accumulating, the previous colour
+// gradients) in shared memory with coalesced loads, each lane applies the
+// chain rule of every view that blended its Gaussian, and the warp writes
+// the colour gradient rows back coalesced.  Every output of every Gaussian
+// is written (zero where no view blended it) unless accumulating.
+template <int DEG>
+__global__ void __launch_bounds__(kProjBwdWarps * 32)
 project_bwd_kernel(const __grid_constant__ ProjBwdArgs p) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.sc.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    using CR = ColorRows<DEG>;
+    extern __shared__ float s_rows[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float *s_coef = s_rows + wid * CR::WARP_FLOATS;
+    float *s_dcol = s_coef + 32 * CR::STRIDE;
+    const bool acc = p.out.acc;
+    const int64_t n = p.sc.n;
+    const int64_t warps = (int64_t)gridDim.x * kProjBwdWarps;
+    for (int64_t i0 = ((int64_t)blockIdx.x * kProjBwdWarps + wid) * 32; i0 < n; i0 += warps * 32) {
+        const int64_t i = i0 + lane;
+        const int rows = (int)min((int64_t)32, n - i0);
+        uint32_t vmask = 0;  // views that blended this lane's Gaussian
+        if (i < n) {
+            for (int k = 0; k < p.n_views; k++) {
+                const float *g2 = p.g2[k] + i * kG2;
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < kG2; q++) any |= g2[q] != 0.0f;
+                vmask |= (uint32_t)any << k;
+            }
+        }
+        const bool warp_any = __any_sync(0xffffffffu, vmask != 0);
+        if (!warp_any && acc) continue;
+        const float *gcol = p.sc.color + i0 * CR::RS;
+        float *gdc = p.out.dcolor + i0 * CR::RS;
+        if (warp_any) {
+            for (int e = lane; e < rows * CR::RS; e += 32) {
+                const int r = e / CR::RS, col = e - r * CR::RS;
+                s_coef[r * CR::STRIDE + col] = gcol[e];
+                s_dcol[r * CR::STRIDE + col] = acc ? gdc[e] : 0.0f;
+            }
+        }
+        __syncwarp();
         float dm[3] = {0.0f, 0.0f, 0.0f}, dls[3] = {0.0f, 0.0f, 0.0f};
         float dq[4] = {0.0f, 0.0f, 0.0f, 0.0f}, dop = 0.0f;
-        bool touched = false;
-        for (int k = 0; k < p.n_views; k++) {
-            const float *g2 = p.g2[k] + i * kG2;
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < kG2; q++) any |= g2[q] != 0.0f;
-            if (!any) continue;
-            view_chain(p.sc, p.cam[k], g2, i, dm, dls, dq, dop, p.out.dcolor,
-                       p.out.acc || touched);
-            touched = true;
+        for (int k = 0; k < p.n_views; k++)
+            if (vmask >> k & 1u)
+                view_chain<DEG>(p.sc, p.cam[k], p.g2[k] + i * kG2, i, dm, dls, dq, dop,
+                                s_coef + lane * CR::STRIDE, s_dcol + lane * CR::STRIDE);
+        __syncwarp();
+        for (int e = lane; e < rows * CR::RS; e += 32) {
+            const int r = e / CR::RS;
+            gdc[e] = warp_any ? s_dcol[r * CR::STRIDE + e - r * CR::RS] : 0.0f;
         }
-        if (!touched) continue;
-        const bool acc = p.out.acc;
-        for (int c = 0; c < 3; c++) {
-            put(p.out.dmean + 3 * i + c, dm[c], acc);
-            put(p.out.dlog_scale + 3 * i + c, dls[c], acc);
+        __syncwarp();
+        if (i < n && (vmask != 0 || !acc)) {
+            for (int c = 0; c < 3; c++) {
+                put(p.out.dmean + 3 * i + c, dm[c], acc);
+                put(p.out.dlog_scale + 3 * i + c, dls[c], acc);
+            }
+            for (int c = 0; c < 4; c++) put(p.out.dquat + 4 * i + c, dq[c], acc);
+            put(p.out.dopacity + i, dop, acc);
         }
-        for (int c = 0; c < 4; c++) put(p.out.dquat + 4 * i + c, dq[c], acc);
-        put(p.out.dopacity + i, dop, acc);
     }
+}
+
+template <int DEG>
+static int launch_project_bwd(const ProjBwdArgs &pb, cudaStream_t st) {
+    using CR = ColorRows<DEG>;
+    const int smem = kProjBwdWarps * CR::WARP_FLOATS * (int)sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        int rc = cuda_check(cudaFuncSetAttribute(project_bwd_kernel<DEG>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                            "project_bwd smem attribute");
+        if (rc) return rc;
+        attr = true;
+    }
+    const int64_t warps = ceil_div(pb.sc.n, 32);
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(ceil_div(warps, kProjBwdWarps), (int64_t)num_sms() * 16));
+    project_bwd_kernel<DEG><<<grid, kProjBwdWarps * 32, smem, st>>>(pb);
+    return MS_OK;
 }
 
 constexpr int kL1Threads = 256;
@@ -794,17 +857,8 @@ extern "C" int ms_raster_bwd_views(const ms_scene_t *scene, const ms_bwd_view_t 
     }
     cudaStream_t st = as_stream(stream);
     const int64_t n = scene->n;
-    const int K = scene->sh_degree < 0 ? 1 : (scene->sh_degree + 1) * (scene->sh_degree + 1);
     int rc;
     if ((rc = cuda_check(cudaMemsetAsync(ws, 0, need, st), "bwd workspace memset"))) return rc;
-    if (n > 0 && !accumulate) {
-        if ((rc = cuda_check(cudaMemsetAsync(grads->dmean, 0, n * 3 * sizeof(float), st), "memset")) ||
-            (rc = cuda_check(cudaMemsetAsync(grads->dlog_scale, 0, n * 3 * sizeof(float), st), "memset")) ||
-            (rc = cuda_check(cudaMemsetAsync(grads->dquat, 0, n * 4 * sizeof(float), st), "memset")) ||
-            (rc = cuda_check(cudaMemsetAsync(grads->dopacity, 0, n * sizeof(float), st), "memset")) ||
-            (rc = cuda_check(cudaMemsetAsync(grads->dcolor, 0, n * K * 3 * sizeof(float), st), "memset")))
-            return rc;
-    }
     raster_bwd_kernel<<<raster_bwd_blocks_per_sm() * num_sms(), kBwdThreads, 0, st>>>(a);
     if (n > 0) {
         pb.sc.n = n;
@@ -815,8 +869,14 @@ extern "C" int ms_raster_bwd_views(const ms_scene_t *scene, const ms_bwd_view_t 
         pb.sc.scale = scene->scale;
         pb.out = {grads->dmean, grads->dlog_scale, grads->dquat, grads->dopacity, grads->dcolor,
                   accumulate};
-        int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
-        project_bwd_kernel<<<grid, 256, 0, st>>>(pb);
+        switch (scene->sh_degree) {
+        case 0: rc = launch_project_bwd<0>(pb, st); break;
+        case 1: rc = launch_project_bwd<1>(pb, st); break;
+        case 2: rc = launch_project_bwd<2>(pb, st); break;
+        case 3: rc = launch_project_bwd<3>(pb, st); break;
+        default: rc = launch_project_bwd<-1>(pb, st);
+        }
+        if (rc) return rc;
     }
     return cuda_check(cudaGetLastError(), "backward launches");
 }
