@@ -21,7 +21,7 @@ import sys
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["footprint32.c", "render64.c", "sh64.c", "range.c", "grad64.c"]
+_SOURCES = ["footprint32.c", "render64.c", "sh64.c", "range.c", "grad64.c", "aggregate.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 SELECTIVE, ALL_LEVELS, FILTER_SMALL = 0, 1, 2
@@ -88,6 +88,11 @@ def lib():
         L.or_forward64_full.argtypes = [I64, P, P, P, P, P, I32, P, P, P, P, P, P, P]
         L.or_grad64.argtypes = [I64, P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P]
         L.or_grad64.restype = I64
+        L.or_voxel_key.argtypes = [P, ctypes.c_float, I32]
+        L.or_voxel_key.restype = ctypes.c_uint32
+        L.or_aggregate.argtypes = [I64, P, P, P, P, P, I32, P, P, P, I32, P, I32, ctypes.c_float,
+                                   P, P, P, P, P, P, P, I64]
+        L.or_aggregate.restype = I64
         _lib = L
     return _lib
 
@@ -276,3 +281,32 @@ def grad64(scene, cam, offsets, idx, dl_dimage):
                     _p(np.ascontiguousarray(dl_dimage, np.float64)), _p(g["mean"]),
                     _p(g["log_scale"]), _p(g["quat"]), _p(g["opacity"]), _p(g["color"]))
     return g
+
+
+def voxel_key(mean3, B: float, level_m: int) -> int:
+    m = np.ascontiguousarray(mean3, np.float32)
+    return int(lib().or_voxel_key(_p(m), float(B), int(level_m)))
+
+
+def aggregate(scene, cams, level_m: int, B: float):
+    """AggregateGaussians (Alg. 1) for level l_m: cams are the training
+    cameras already downsampled by 4^(l_m-1).  Returns (new Gaussians as a
+    dict of arrays in voxel-key order, their voxel keys, smallest coverage
+    per input Gaussian)."""
+    n = scene.n
+    scale, lnop = prepare(scene)
+    K = 1 if scene.sh_degree < 0 else (scene.sh_degree + 1) ** 2
+    cam_arr = (_Camera * max(len(cams), 1))(*[camera_struct(c) for c in cams])
+    smin = np.empty(max(n, 1), np.float32)
+    cap = max(n, 1)
+    out = dict(mean=np.zeros((cap, 3), np.float32), log_scale=np.zeros((cap, 3), np.float32),
+               quat=np.zeros((cap, 4), np.float32), opacity=np.zeros(cap, np.float32),
+               color=np.zeros((cap,) + scene.color.shape[1:], np.float32))
+    keys = np.zeros(cap, np.uint32)
+    m = lib().or_aggregate(n, _p(_f32(scene.mean)), _p(_f32(scene.log_scale)),
+                           _p(_f32(scene.quat)), _p(_f32(scene.opacity)), _p(_f32(scene.color)),
+                           scene.sh_degree, _p(np.ascontiguousarray(scene.level, np.uint8)),
+                           _p(scale), _p(lnop), len(cams), cam_arr, level_m, float(B),
+                           _p(smin), _p(out["mean"]), _p(out["log_scale"]), _p(out["quat"]),
+                           _p(out["opacity"]), _p(out["color"]), _p(keys), cap)
+    return {k: v[:m] for k, v in out.items()}, keys[:m], smin[:n]

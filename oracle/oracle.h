@@ -16,6 +16,7 @@
  *   range.c        UpdateRange (Eq. 5), FP64 coverage for pins
  *   grad64.c       FP64 forward with an FP64 projection, and its analytic
  *                  gradient (reverse replay, chain rule to the parameters)
+ *   aggregate.c    AggregateGaussians (Alg. 1) for one coarse level
  *
  * Parity unpinned: nothing here reproduces the paper's PSNR/LPIPS tables
  * (they need the datasets and trained models).
@@ -108,6 +109,22 @@ int64_t or_grad64(int64_t n, const float *mean, const float *log_scale, const fl
                   const or_camera *cam, const int64_t *offsets, const uint32_t *idx,
                   const double *dl_dimage, double *dmean, double *dlog_scale,
                   double *dquat, double *dopacity, double *dcolor);
+
+/* Voxel key of a position for level l_m: per-component normalisation by
+ * the camera extent B, floor(400 / l_m) voxels per axis over [-2, 2],
+ * key = (vz R + vy) R + vx. */
+uint32_t or_voxel_key(const float *mean3, float B, int32_t level_m);
+
+/* AggregateGaussians for level l_m from n Gaussians (scale/lnop from
+ * or_prepare) and n_cams cameras already downsampled by 4^(l_m-1).  Writes
+ * the smallest coverage per Gaussian (+inf if none) to smin and up to
+ * `capacity` new Gaussians in voxel-key order; returns their number. */
+int64_t or_aggregate(int64_t n, const float *mean, const float *log_scale, const float *quat,
+                     const float *opacity, const float *color, int32_t sh_degree,
+                     const uint8_t *level, const float *scale, const float *lnop,
+                     int32_t n_cams, const or_camera *cams, int32_t level_m, float B,
+                     float *smin, float *o_mean, float *o_log_scale, float *o_quat,
+                     float *o_opacity, float *o_color, uint32_t *o_key, int64_t capacity);
 
 #ifdef __cplusplus
 }
