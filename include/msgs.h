@@ -12,6 +12,7 @@
  *   ms_raster         per-pixel front-to-back blend with early termination
  *   ms_raster_bwd     gradient of the image with respect to the scene
  *   ms_l1_loss_grad   L1 image loss and its gradient (training step)
+ *   ms_aggregate      AggregateGaussians: insert a coarse level
  *   ms_serve_*        a render server: resident scenes, memory admission,
  *                     continuous batching of requests over CUDA streams
  *
@@ -386,6 +387,39 @@ int ms_raster_bwd_views(const ms_scene_t *scene, const ms_bwd_view_t *views, int
  */
 int ms_l1_loss_grad(const float *image, const float *target, int64_t count, float weight,
                     float *dl_dimage, float *loss_sum, void *stream);
+
+/* ------------------------------------------------------------- aggregation
+ *
+ * AggregateGaussians (Alg. 1; Sec. 4.1 "Aggregate to Insert Large
+ * Gaussians"; supplementary "Details of Gaussian Aggregation Algorithm")
+ * for one coarse level level_m (2 .. scene->n_levels):
+ *   - every Gaussian of levels < level_m is splatted to every camera in
+ *     cams[n_cams] (host array: the training cameras ALREADY downsampled by
+ *     4^(level_m - 1)); its smallest pixel coverage over the cameras where
+ *     it is valid and touches the image decides: below S_T = 2 px it is
+ *     small;
+ *   - small Gaussians are binned by their position, normalised per
+ *     component (x / B inside [-B, B], sign(x) (2 - B / |x|) outside, with
+ *     B = extent, the half length of the cube spanned by the training
+ *     cameras) on a grid of floor(400 / level_m) voxels per axis over
+ *     [-2, 2]; voxel key = (vz R + vy) R + vx;
+ *   - each voxel gives one new Gaussian of level level_m: the average of its
+ *     members' mean, quat (as stored), log_scale, opacity and color, the
+ *     log_scale then raised by ln(S_T / S_avg), S_avg the members' mean
+ *     smallest coverage; s_max = 0 and s_min = +inf (no range yet).
+ * New Gaussians are written to `out` (device arrays with the scene's
+ * layout and sh_degree; out->n and out->n_levels are ignored) in
+ * voxel-key order, at most `capacity`; n_out is a DEVICE int64[2]:
+ * [0] = number of voxels (may exceed capacity: then only the first
+ * `capacity` are written), [1] = status bits (MS status word, as in
+ * ms_bins_t.counts).  The scene must be prepared (ms_scene_prepare).  The
+ * caller appends the new Gaussians and repeats for the next level.
+ */
+size_t ms_aggregate_workspace_bytes(int64_t n);
+
+int ms_aggregate(const ms_scene_t *scene, const ms_camera_t *cams, int32_t n_cams,
+                 int32_t level_m, float extent, ms_scene_t *out, int64_t capacity,
+                 int64_t *n_out, void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------ serving
  *

@@ -142,6 +142,11 @@ _SIGNATURES = [
     ("ms_raster", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
                                  ctypes.POINTER(ms_camera_t), P, P, P, P, P,
                                  ctypes.c_size_t, P]),
+    ("ms_aggregate_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64]),
+    ("ms_aggregate", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                    ctypes.POINTER(ms_scene_t), ctypes.c_int64, P, P,
+                                    ctypes.c_size_t, P]),
     ("ms_serve_clock", ctypes.c_double, []),
     ("ms_serve_create", ctypes.c_int, [ctypes.POINTER(ms_serve_cfg_t), ctypes.POINTER(P)]),
     ("ms_serve_add_scene", ctypes.c_int, [P, ctypes.POINTER(ms_scene_t),
@@ -311,6 +316,18 @@ def ms_l1_loss_grad(image_ptr: int, target_ptr: int, count: int, weight: float, 
                     loss_sum_ptr: int, stream=None):
     _check(lib().ms_l1_loss_grad(P(image_ptr), P(target_ptr), int(count), float(weight),
                                  P(dl_ptr), P(loss_sum_ptr), P(_stream(stream))))
+
+
+def ms_aggregate_workspace_bytes(n: int) -> int:
+    return int(lib().ms_aggregate_workspace_bytes(n))
+
+
+def ms_aggregate(scene: ms_scene_t, cams, level_m: int, extent: float, out: ms_scene_t,
+                 capacity: int, n_out_ptr: int, ws_ptr: int, ws_bytes: int, stream=None):
+    arr = (ms_camera_t * max(len(cams), 1))(*cams)
+    _check(lib().ms_aggregate(ctypes.byref(scene), arr, len(cams), int(level_m), float(extent),
+                              ctypes.byref(out), int(capacity), P(n_out_ptr), P(ws_ptr),
+                              ws_bytes, P(_stream(stream))))
 
 
 def ms_serve_clock() -> float:
@@ -528,3 +545,36 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def aggregate_level(scene: "DeviceScene", cams, level_m: int, extent: float,
+                    capacity: int | None = None):
+    """ms_aggregate for one coarse level: `cams` are inputs.Camera objects
+    already downsampled by 4^(level_m - 1).  Returns the new Gaussians as a
+    dict of device tensors (mean, log_scale, quat, opacity, color, level,
+    s_max, s_min), in voxel-key order.  Synchronises (reads the count)."""
+    import torch
+    dev = scene.mean.device
+    cap = max(1, scene.n if capacity is None else capacity)
+    ws_bytes = ms_aggregate_workspace_bytes(scene.n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    n_out = torch.zeros(2, dtype=torch.int64, device=dev)
+    for _ in range(2):
+        o = dict(mean=torch.empty((cap, 3), device=dev), log_scale=torch.empty((cap, 3), device=dev),
+                 quat=torch.empty((cap, 4), device=dev), opacity=torch.empty(cap, device=dev),
+                 color=torch.empty((cap,) + tuple(scene.color.shape[1:]), device=dev),
+                 level=torch.empty(cap, dtype=torch.uint8, device=dev),
+                 s_max=torch.empty(cap, device=dev), s_min=torch.empty(cap, device=dev))
+        out = ms_scene_t(cap, scene.n_levels, scene.sh_degree, _ptr(o["mean"]),
+                         _ptr(o["log_scale"]), _ptr(o["quat"]), _ptr(o["opacity"]),
+                         _ptr(o["color"]), _ptr(o["level"]), _ptr(o["s_max"]), _ptr(o["s_min"]),
+                         0, 0)
+        ms_aggregate(scene.struct, [camera_struct(c) for c in cams], level_m, extent, out, cap,
+                     _ptr(n_out), _ptr(ws), ws_bytes)
+        m, status = (int(v) for v in n_out.cpu())
+        if status:
+            raise MsError(MS_ERR_TIMEOUT, f"aggregate sort status {status:#x}")
+        if m <= cap:
+            return {k: v[:m] for k, v in o.items()}
+        cap = m
+    raise MsError(MS_ERR_CAPACITY, "aggregate capacity retry failed")

@@ -23,20 +23,9 @@
 #include <string>
 
 #include "common.cuh"
+#include "sort.cuh"
 
 namespace msgs {
-
-constexpr int kSortThreads = 256;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortIPT = 16;
-constexpr int kPart = kSortThreads * kSortIPT;  // items per partition
-constexpr int kDigits = 256;
-constexpr int kScanWarps = kDigits / 32;
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagPre = 2u << 30;
-constexpr uint32_t kFlagMask = 3u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1;
-constexpr int kLookback = 16;  // predecessors polled per look-back step
 
 constexpr int kDupThreads = 256;
 constexpr int kDupIPT = 4;
@@ -44,22 +33,6 @@ constexpr int kDupPart = kDupThreads * kDupIPT;
 constexpr unsigned long long kDupFlagAgg = 1ull << 62;
 constexpr unsigned long long kDupFlagPre = 2ull << 62;
 constexpr unsigned long long kDupValMask = (1ull << 62) - 1;
-
-struct PassArgs {
-    const uint32_t *keys_in;
-    const uint32_t *vals_in;    // nullptr: value = item index
-    const uint32_t *filter;     // nullptr, or item valid iff filter[i] > 0
-    uint32_t *keys_out;         // nullptr: keys not written
-    uint32_t *vals_out;
-    const uint32_t *n32;        // device item count (u32) or nullptr
-    const unsigned long long *n64;  // device item count (u64) or nullptr
-    uint64_t n_cap;             // count = min(device count, n_cap); or n_cap alone
-    int shift;
-    const uint32_t *hist;       // [256] digit totals of this pass
-    uint32_t *status;           // [partitions][256]
-    uint32_t *ticket;
-    unsigned long long *err;    // status word (bit kStatusTimeout)
-};
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -102,7 +75,6 @@ __device__ __forceinline__ uint64_t pass_count(const PassArgs &a) {
     return n;
 }
 
-constexpr int kSortSmem = (kSortWarps * kDigits + 2 * kPart) * 4;
 
 __global__ void __launch_bounds__(kSortThreads)
 onesweep_pass(PassArgs a) {
