@@ -21,9 +21,14 @@ def _extent(cams):
 
 
 def _fine_scene(n, seed, sh_degree=3):
+    """Level-1 Gaussians only (the input of the first aggregation); plain
+    RGB colour for sh_degree -1."""
     sc = inputs.multiscale_scene(n=n, seed=seed, split=(1.0, 0.0, 0.0, 0.0), box=4.0,
-                                 cluster_sigma=0.8, n_clusters=16, sh_degree=sh_degree)
+                                 cluster_sigma=0.8, n_clusters=16, sh_degree=max(sh_degree, 0))
     sc.n_levels = 4
+    if sh_degree < 0:
+        sc.color = np.random.default_rng(seed).uniform(0, 1, (n, 3)).astype(np.float32)
+        sc.sh_degree = -1
     return sc
 
 
@@ -40,8 +45,6 @@ def _compare(g, o):
 def test_aggregate_level_matches_oracle(level_m, deg):
     require_cuda()
     sc = _fine_scene(30_000, seed=level_m, sh_degree=deg)
-    if deg < 0:
-        sc.color = np.random.default_rng(0).uniform(0, 1, (sc.n, 3)).astype(np.float32)
     base = inputs.orbit_cameras(6, seed=level_m, radius=10.0, width=512, height=384)
     cams = [inputs.downscale(c, 4 ** (level_m - 1)) for c in base]
     B = _extent(base)

@@ -130,7 +130,7 @@ def test_training_step_reduces_l1_loss():
         loss = (img - target).abs().mean()
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(loss.item())
     assert losses[-1] < 0.5 * losses[0], losses
 
 
