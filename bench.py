@@ -260,6 +260,52 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
                                  "call over the views) each one CUDA graph"}}
 
 
+# ------------------------------------------------------------ aggregation
+
+def aggregate_bench(msgs, torch, ds, sc, dev, reps=10):
+    """AggregateGaussians (Alg. 1) for level 2 on the resident scene: every
+    level-1 Gaussian splatted to the 8 calibration cameras at 4x, small ones
+    binned into 200^3 voxels and pooled.  Timed with events on one stream
+    (one CUDA graph per call)."""
+    base = inputs.orbit_cameras(8, seed=1, radius=25.0)
+    cams = [msgs.camera_struct(inputs.downscale(c, 4)) for c in base]
+    extent = float(max(np.abs(np.asarray(c.campos, np.float32)).max() for c in base))
+    cap = sc.n
+    ws_b = msgs.ms_aggregate_workspace_bytes(sc.n)
+    ws = torch.empty(ws_b, dtype=torch.uint8, device=dev)
+    n_out = torch.zeros(2, dtype=torch.int64, device=dev)
+    o = [torch.empty((cap, 3), device=dev), torch.empty((cap, 3), device=dev),
+         torch.empty((cap, 4), device=dev), torch.empty(cap, device=dev),
+         torch.empty((cap,) + tuple(ds.color.shape[1:]), device=dev),
+         torch.empty(cap, dtype=torch.uint8, device=dev), torch.empty(cap, device=dev),
+         torch.empty(cap, device=dev)]
+    out = msgs.ms_scene_t(cap, ds.n_levels, ds.sh_degree, *(msgs._ptr(t) for t in o), 0, 0)
+
+    def call():
+        msgs.ms_aggregate(ds.struct, cams, 2, extent, out, cap, msgs._ptr(n_out),
+                          msgs._ptr(ws), ws_b)
+    call()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        call()
+    for _ in range(2):
+        g.replay()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    m, status = (int(v) for v in n_out.cpu())
+    return {"ms_per_call": e0.elapsed_time(e1) / reps, "new_gaussians": m,
+            "inputs": int((sc.level < 2).sum()), "status": status,
+            "config": {"level_m": 2, "cameras": 8, "downscale": 4, "voxels_per_axis": 200,
+                       "extent": extent}}
+
+
 # ---------------------------------------------------------------- serving
 
 def sphere_cameras(k, seed, radius=25.0, width=1256, height=832):
@@ -684,6 +730,8 @@ def main():
                                  args.warmup)
         train["value"] *= world
 
+    aggregate = aggregate_bench(msgs, torch, ds, sc, dev)
+
     serve = None
     if not args.no_serve:
         serve = serve_bench(msgs, torch, dev, args.serve_requests, args.serve_n)
@@ -708,6 +756,7 @@ def main():
             "per_scale": per_scale,
             "roofline_all": {"project": roof_project, "raster": roof_raster},
             "train": train,
+            "aggregate": aggregate,
             "serve": serve,
         }))
     if world > 1:
