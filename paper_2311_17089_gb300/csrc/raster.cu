@@ -214,7 +214,7 @@ struct WarpPairs {
     uint16_t idx[kChunk];  // index of each record within the sub-batch
 };
 constexpr int kWarps = kRasterThreads / 32;
-constexpr int kSmemBytes = kBufBytes + kWarps * (int)sizeof(WarpPairs);
+constexpr int kSmemBytes = 2 * kBufBytes + kWarps * (int)sizeof(WarpPairs);
 // Half extents of a warp's block of pixel centres (8 x 4 pixels) plus a
 // 1-pixel margin that covers FP32 rounding of the alpha test near the edge
 // of the level set.
@@ -332,12 +332,14 @@ __device__ __forceinline__ void blend_pairs(const WarpPairs &wp, uint32_t n, uin
     s.evals = pos0 + cnt;
 }
 
-// All threads: arm the mbarrier with the sub-batch's byte count, then each
-// thread issues a bulk copy of its gathered record.
+// Thread 0 arms the buffer's mbarrier with the sub-batch's byte count and
+// every thread issues the bulk copies of its gathered records.  The phase
+// cannot complete before the arming arrival, so no barrier is needed
+// between the two; the caller guarantees that every warp is done reading
+// the buffer.
 __device__ __forceinline__ void issue_batch(const RasterArgs &a, uint32_t first, uint32_t cnt,
                                             float4 *buf, uint64_t *bar) {
     if (threadIdx.x == 0) mbar_expect_tx(bar, cnt * kRecBytes);
-    __syncthreads();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     for (uint32_t i = threadIdx.x; i < cnt; i += kRasterThreads) {
         uint32_t g = a.gidx[first + i];
@@ -395,47 +397,50 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
     return *reinterpret_cast<const volatile uint32_t *>(p);
 }
 
-// Walk one segment in sub-batches: once every warp has compacted sub-batch
-// j into its pair buffer, the bulk copies of sub-batch j+1 land in the copy
-// buffer while the warps blend.  In local mode (`exact` false) the walk stops as soon as the tile
-// is marked done, and returns true (the partial result is then
-// irrelevant).  The CTA stops early once every pixel has terminated.
-// Returns kWalked, kAborted, or kFailed when a copy wait gave up (the CTA
-// must then stop).
+// Walk one segment in sub-batches through two staging buffers: while the
+// warps compact and blend sub-batch j from one buffer, the bulk copies of
+// sub-batch j + 1 land in the other.  One CTA barrier per sub-batch (the
+// termination count) also guarantees that every warp has compacted
+// sub-batch j before sub-batch j + 2 is copied over it.  In local mode
+// (`exact` false) the walk stops as soon as the tile is marked done.  The
+// CTA stops early once every pixel has terminated.  Returns kWalked,
+// kAborted, or kFailed when a copy wait gave up (the CTA must then stop).
 constexpr int kWalked = 0, kAborted = 1, kFailed = 2;
 __device__ __forceinline__ int run_segment(const RasterArgs &a, const Seg &sg, uint32_t L,
                                             bool exact, bool inside, float fx, float fy,
                                             float cx, float cy, PixelState &s,
                                             float4 *aos, WarpPairs &wp, uint64_t *bar,
-                                            uint32_t &parity, uint32_t *s_abort) {
+                                            uint32_t &par, uint32_t *s_abort,
+                                            uint32_t *s_fail) {
     const uint32_t pos0 = sg.k * L;
     if (sg.len == 0) return kWalked;
     const uint32_t nb = (sg.len + kChunk - 1) / kChunk;
     const f32x2 fx2 = pack2(fx, fx), fy2 = pack2(fy, fy);
-    issue_batch(a, sg.start, min(sg.len, (uint32_t)kChunk), aos, bar);
+    issue_batch(a, sg.start, min(sg.len, (uint32_t)kChunk), aos, &bar[0]);
     bool abort = false;
     for (uint32_t j = 0; j < nb; j++) {
-        const uint32_t off = j * kChunk;
+        const uint32_t b = j & 1u, off = j * kChunk;
         const uint32_t cnt = min(sg.len - off, (uint32_t)kChunk);
-        const bool ok = wait_batch(a, bar, parity);
-        parity ^= 1u;
-        if (__syncthreads_or(!ok)) return kFailed;
-        // warps whose pixels have all terminated skip their share
-        const bool wlive = __any_sync(0xffffffffu, inside && !s.term);
-        const uint32_t nw = wlive ? compact(aos, cnt, cx, cy, wp) : 0u;
-        __syncthreads();
+        const bool ok = wait_batch(a, &bar[b], (par >> b) & 1u);
+        par ^= 1u << b;
         const bool more = j + 1 < nb;
         if (more)
             issue_batch(a, sg.start + off + kChunk, min(sg.len - off - kChunk, (uint32_t)kChunk),
-                        aos, bar);
-        if (inside && !s.term) blend_pairs(wp, nw, cnt, pos0 + off, fx2, fy2, s);
+                        aos + (b ^ 1u) * 3 * kChunk, &bar[b ^ 1u]);
+        // warps whose pixels have all terminated skip their share
+        const bool wok = __all_sync(0xffffffffu, ok);
+        if (!ok) *s_fail = 1u;
+        const bool wlive = wok && __any_sync(0xffffffffu, inside && !s.term);
+        const uint32_t nw = wlive ? compact(aos + b * 3 * kChunk, cnt, cx, cy, wp) : 0u;
+        if (wlive && inside && !s.term) blend_pairs(wp, nw, cnt, pos0 + off, fx2, fy2, s);
         if (threadIdx.x == 0) *s_abort = exact ? 0u : ld_volatile(a.tile_done + sg.t);
         const int done = __syncthreads_count(s.term || !inside);
+        if (*s_fail) return kFailed;
         abort = *s_abort != 0;
         if (done == kRasterThreads || abort) {
             if (more) {  // drain the copies already issued
-                wait_batch(a, bar, parity);
-                parity ^= 1u;
+                wait_batch(a, &bar[b ^ 1u], (par >> (b ^ 1u)) & 1u);
+                par ^= 1u << (b ^ 1u);
             }
             break;
         }
@@ -446,22 +451,25 @@ __device__ __forceinline__ int run_segment(const RasterArgs &a, const Seg &sg, u
 __global__ void __launch_bounds__(kRasterThreads)
 raster_kernel(RasterArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t s_next;
+    __shared__ uint32_t s_fail;
     __shared__ uint32_t s_flag;
     __shared__ uint32_t s_wait;
     __shared__ uint32_t s_abort;
     float4 *aos = reinterpret_cast<float4 *>(smem);
-    WarpPairs &wp = reinterpret_cast<WarpPairs *>(smem + kBufBytes)[threadIdx.x >> 5];
+    WarpPairs &wp = reinterpret_cast<WarpPairs *>(smem + 2 * kBufBytes)[threadIdx.x >> 5];
     const int tid = threadIdx.x;
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const uint32_t total = a.seg_off[a.tiles];
     const uint32_t L = a.seg_len[0];
-    uint32_t parity = 0u;
+    uint32_t parity = 0u;  // phase parity of bar[0] (bit 0) and bar[1] (bit 1)
     for (;;) {
         __syncthreads();
         if (tid == 0) s_next = atomicAdd(a.ticket, 1u);
@@ -524,7 +532,7 @@ raster_kernel(RasterArgs a) {
         const bool last_seg = sg.k + 1 == sg.nk;
         for (int pass = 0; pass < 2; pass++) {
             const int rc = run_segment(a, sg, L, exact || pass == 1, active, fx, fy, cx, cy, s,
-                                       aos, wp, &bar, parity, &s_abort);
+                                       aos, wp, bar, parity, &s_abort, &s_fail);
             if (rc == kFailed) return;
             if (rc == kAborted) {
                 skip = true;  // an earlier segment finished the tile
