@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-near-far", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-n", type=int, default=2_000_000)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
@@ -258,6 +259,76 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
                        "loss": "L1 mean per view, targets U(0,1) seed 1",
                        "launch": "forward (one stream per view) and backward (one batched "
                                  "call over the views) each one CUDA graph"}}
+
+
+# ------------------------------------------------------------- near / far
+
+def near_far_bench(msgs, torch, dev, n=3_000_000, scales=(1, 8, 64)):
+    """The near/far stress workload: 3M Gaussians (dense unit ball, sparse
+    shell of radius 50), 32 orbit cameras at radii 2 .. 60 (calibrated on
+    the device), rendered selectively at each scale of 1256x832.  Per scale:
+    frames/s over the 32 cameras (one stream, one graph per camera), the
+    tile-list skew (longest list / mean non-empty list) and the
+    early-termination rate (pixels that stopped before the end of their
+    tile's list)."""
+    sc = inputs.near_far_scene(n=n, seed=0)
+    cams = inputs.orbit_cameras(32, seed=3, radius=np.geomspace(2.0, 60.0, 32))
+    ds = msgs.DeviceScene(sc, device=dev)
+    ds.calibrate(cams)
+    out = {}
+    for s in scales:
+        fr = [inputs.downscale(c, s) for c in cams]
+        probe = msgs.Renderer(n, fr[0].tiles_x * fr[0].tiles_y, 16 * n, device=dev,
+                              with_cover=False, with_mask=False)
+        dmax = 0
+        for cam in fr:  # the exact count is reported even when it overflows
+            probe.render(ds, cam, "selective")
+            dmax = max(dmax, msgs.ms_bin_counts(probe.bins)[1])
+        del probe
+        r = msgs.Renderer(n, fr[0].tiles_x * fr[0].tiles_y, int(dmax * 1.02) + 1024, device=dev,
+                          with_cover=False, with_mask=False)
+        bufs = r.images(fr[0], device=dev)
+        ne = torch.empty((fr[0].height, fr[0].width), dtype=torch.int32, device=dev)
+        skews, terms, ds_ = [], [], []
+        for cam in fr:
+            r.render(ds, cam, "selective", out=bufs, n_eval=ne)
+            d, _ = r.check()
+            tiles = cam.tiles_x * cam.tiles_y
+            rg = r.ranges[:2 * tiles].view(-1, 2).to(torch.int64)
+            ln = (rg[:, 1] - rg[:, 0]).clamp(min=0)
+            nz = ln[ln > 0]
+            skews.append(float(nz.max() / nz.float().mean()) if len(nz) else 0.0)
+            # the list length of each pixel's tile, against the positions walked
+            ty = torch.arange(cam.height, device=dev) // 16
+            tx = torch.arange(cam.width, device=dev) // 16
+            plen = ln[(ty[:, None] * cam.tiles_x + tx[None, :])]
+            terms.append(float((ne.to(torch.int64) < plen).float().mean()))
+            ds_.append(d)
+        graphs = []
+        for cam in fr:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                r.render(ds, cam, "selective", out=bufs)
+            graphs.append(g)
+        for g in graphs:
+            g.replay()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for g in graphs:
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        r.check()
+        out[f"{fr[0].width}x{fr[0].height}"] = {
+            "fps": len(fr) * 1e3 / e0.elapsed_time(e1),
+            "tile_list_skew_mean": float(np.mean(skews)), "tile_list_skew_max": float(np.max(skews)),
+            "early_termination_rate": float(np.mean(terms)), "D_mean": float(np.mean(ds_))}
+        del r, graphs
+    return {"config": {"workload": f"near-far-{n // 1000}k-4level-sh3-32cams-r2..60",
+                       "mode": "selective", "cameras": 32, "scales": list(scales)},
+            "per_scale": out}
 
 
 # ------------------------------------------------------------ aggregation
@@ -731,6 +802,7 @@ def main():
         train["value"] *= world
 
     aggregate = aggregate_bench(msgs, torch, ds, sc, dev)
+    near_far = None if args.no_near_far else near_far_bench(msgs, torch, dev)
 
     serve = None
     if not args.no_serve:
@@ -757,6 +829,7 @@ def main():
             "roofline_all": {"project": roof_project, "raster": roof_raster},
             "train": train,
             "aggregate": aggregate,
+            "near_far": near_far,
             "serve": serve,
         }))
     if world > 1:

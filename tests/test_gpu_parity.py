@@ -123,6 +123,32 @@ def test_full_size_multiscale_sampled(cuda):
             assert_image_close(g, o, tiles=tiles, cam=cam)
 
 
+def test_full_size_near_far_sampled(cuda):
+    """3M Gaussians: a dense unit ball and a sparse shell of radius 50
+    (the near/far stress workload), cameras on an orbit at radii from 2
+    to 60, at 8x and 64x of 1256x832: every footprint and tile list
+    bit-exact; the image on sampled tiles plus the longest list's tile."""
+    sc = inputs.near_far_scene(n=3_000_000, seed=0)
+    radii = np.geomspace(2.0, 60.0, 32)
+    cams = inputs.orbit_cameras(32, seed=3, radius=radii)
+    sc = calibrated(sc, cams[::8])
+    rng = np.random.default_rng(1)
+    ds = msgs.DeviceScene(sc)
+    for k in (0, 15, 31):
+        for s in (8, 64):
+            cam = inputs.downscale(cams[k], s)
+            g = gpu_frame(sc, cam, "selective", ds=ds)
+            fp = oracle.footprints(sc, cam, "selective")
+            assert_footprints_equal(g, fp, sc, cam)
+            off, idx = oracle.tile_lists(fp, cam)
+            assert_lists_equal(g, off, idx)
+            ntiles = cam.tiles_x * cam.tiles_y
+            tiles = sorted(set(rng.choice(ntiles, min(12, ntiles), replace=False).tolist()
+                               + [int(np.argmax(np.diff(off)))]))
+            o = oracle.render(sc, cam, "selective", tiles=tiles)
+            assert_image_close(g, o, tiles=tiles, cam=cam)
+
+
 # ------------------------------------------------------------- edge cases
 
 def test_empty_scene(cuda):
