@@ -40,6 +40,7 @@ N_GAUSS = 1_000_000
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 OPS_PER_EVAL = 16          # FP32 operations per pixel-Gaussian evaluation
+RASTER_DRAM_BYTES_PER_LAUNCH = 26.33e6   # raster_kernel, selective sweep, measured
 
 
 def parse():
@@ -754,7 +755,13 @@ def main():
     if dominant == "bin":
         roof = dict(roof_project)
         roof["note"] = "binning dominates; project roofline shown"
-    roof = dict(roof, traffic=None, stage_ms_per_step=stage_ms)
+    # DRAM bytes per launch of the dominant kernel: dram__bytes_read.sum +
+    # dram__bytes_write.sum of one ncu capture of this sweep's eight raster
+    # launches, averaged (to be taken again whenever the kernel changes)
+    traffic = RASTER_DRAM_BYTES_PER_LAUNCH if roof is roof_raster else None
+    roof = dict(roof, traffic=traffic, stage_ms_per_step=stage_ms,
+                traffic_source="ncu capture, mean over the sweep's raster launches"
+                if traffic else None)
 
     # end to end through the public API with host buffers
     e2e = None
