@@ -267,3 +267,24 @@ def test_long_lists_split_across_ctas(cuda, wh, n, op):
     else:
         assert (o["n_contrib"] == n).all()
     assert_image_close(g, o, max_flagged=0.15)
+
+
+def test_one_long_list_among_many_tiles_and_overflow(cuda):
+    """A 320-tile frame where one tile lists ~30k Gaussians among many short
+    lists: lists bit-exact and image within tolerance; a capacity far below
+    D reports the exact D and the retry matches."""
+    rng = np.random.default_rng(21)
+    n = 30_000
+    sc = inputs.single_level_scene(n=n, seed=21)
+    # most Gaussians packed around one point (one tile), the rest spread out
+    sc.mean[: n - 2000] = (rng.normal(0.0, 0.01, (n - 2000, 3)) + [0.05, 0.05, 0.0]).astype(np.float32)
+    sc.log_scale[: n - 2000] = rng.normal(-4.0, 0.3, (n - 2000, 3)).astype(np.float32)
+    cam = inputs.config1_camera(320, 256)
+    fp = oracle.footprints(sc, cam, "all_levels")
+    off, idx = oracle.tile_lists(fp, cam)
+    assert cam.tiles_x * cam.tiles_y >= 200 and np.diff(off).max() > 3 * 8192
+    g = gpu_frame(sc, cam, "all_levels", cap=1000)   # overflows first, then retries
+    assert g["D"] == len(idx)
+    assert_lists_equal(g, off, idx)
+    o = oracle.render(sc, cam, "all_levels")
+    assert_image_close(g, o, cam=cam, max_flagged=0.05)
