@@ -601,19 +601,20 @@ def main():
                 raise msgs.MsError(rc, "probe capacity")
             dmax[(mode, cam.width)] = d
     del probe
-    # one renderer (projection, tile lists, workspaces) and one stream per
-    # frame: the frames of a sweep are independent, and the small ones leave
-    # most SMs idle, so they run concurrently
-    rs = [msgs.Renderer(sc.n, cam.tiles_x * cam.tiles_y,
-                        int(max(dmax[("selective", cam.width)],
-                                dmax[("all_levels", cam.width)]) * 1.05) + 1024,
-                        device=dev, with_cover=False, with_mask=False) for cam in cams]
-    bufs = [r.images(cam, device=dev) for r, cam in zip(rs, cams)]
+    # one renderer (projection, tile lists, workspaces) per frame and mode,
+    # sized by that frame's duplicate count, and one stream per frame: the
+    # frames of a sweep are independent, and the small ones leave most SMs
+    # idle, so they run concurrently
+    rs_mode = {m: [msgs.Renderer(sc.n, cam.tiles_x * cam.tiles_y,
+                                 int(dmax[(m, cam.width)] * 1.05) + 1024, device=dev,
+                                 with_cover=False, with_mask=False) for cam in cams]
+               for m in ("selective", "all_levels")}
+    bufs = [rs_mode["selective"][k].images(cam, device=dev) for k, cam in enumerate(cams)]
     streams = [torch.cuda.Stream(device=dev) for _ in cams]
 
     def step(mode, after=None):
         main = torch.cuda.current_stream()
-        for r, cam, out, st in zip(rs, cams, bufs, streams):
+        for r, cam, out, st in zip(rs_mode[mode], cams, bufs, streams):
             st.wait_stream(main)
             with torch.cuda.stream(st):
                 r.render(ds, cam, mode, out=out, stream=st)
@@ -631,7 +632,7 @@ def main():
             torch.cuda.synchronize()
             if it == 2:
                 torch.cuda.nvtx.range_pop()
-        for r in rs:
+        for r in rs_mode[args.profile]:
             r.check()
         return
     neval = [torch.empty((c.height, c.width), dtype=torch.int32, device=dev) for c in cams]
@@ -639,7 +640,7 @@ def main():
     # counts: duplicates, survivors, evaluations per frame
     stats = {}
     for mode in ("selective", "all_levels"):
-        for r, cam, out, ne in zip(rs, cams, bufs, neval):
+        for r, cam, out, ne in zip(rs_mode[mode], cams, bufs, neval):
             r.render(ds, cam, mode, out=out, n_eval=ne)
             rc, d, s_ = msgs.ms_bin_counts(r.bins)
             if rc != msgs.MS_OK:
@@ -658,7 +659,7 @@ def main():
     g_step = {m: capture(lambda m=m: step(m)) for m in ("selective", "all_levels")}
     g_stage = {}
     for mode in ("selective", "all_levels"):
-        for r, cam, out in zip(rs, cams, bufs):
+        for r, cam, out in zip(rs_mode[mode], cams, bufs):
             cs = msgs.camera_struct(cam)
             md = msgs.MODES[mode]
             g_stage[(mode, cam.width)] = (

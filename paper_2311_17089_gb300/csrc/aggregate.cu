@@ -227,7 +227,7 @@ static bool agg_layout(int64_t n, AggLayout &L) {
     if (n < 0 || n > INT32_MAX) return false;
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    L.parts = ceil_div((int64_t)nn, kPart);
+    L.parts = sort_parts((uint64_t)nn);
     L.hblocks = ceil_div((int64_t)nn, kAggThreads);
     size_t o = 0;
     L.smin = o;
@@ -317,20 +317,10 @@ extern "C" int ms_aggregate(const ms_scene_t *scene, const ms_camera_t *cams, in
         agg_cover_kernel<<<grid, kAggThreads, 0, st>>>(sk, make_cam(cams[c]), level_m, smin);
     agg_key_kernel<<<grid, kAggThreads, 0, st>>>(sk, level_m, extent, smin, flag, keys, hist,
                                                  n_small);
-    static bool attr = false;
-    if (!attr) {
-        if ((rc = cuda_check(cudaFuncSetAttribute(onesweep_pass,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  kSortSmem),
-                             "sort smem attribute")))
-            return rc;
-        attr = true;
-    }
     uint32_t *bufs_k[2] = {reinterpret_cast<uint32_t *>(w + L.ka),
                            reinterpret_cast<uint32_t *>(w + L.kb)};
     uint32_t *bufs_v[2] = {reinterpret_cast<uint32_t *>(w + L.va),
                            reinterpret_cast<uint32_t *>(w + L.vb)};
-    const int sgrid = (int)std::min<int64_t>(L.parts, (int64_t)num_sms() * 2);
     for (int p = 0; p < kAggPasses; p++) {
         PassArgs a;
         a.keys_in = p == 0 ? keys : bufs_k[(p - 1) & 1];
@@ -346,7 +336,7 @@ extern "C" int ms_aggregate(const ms_scene_t *scene, const ms_camera_t *cams, in
         a.status = reinterpret_cast<uint32_t *>(w + L.status) + (size_t)p * L.parts * 256;
         a.ticket = reinterpret_cast<uint32_t *>(w + L.tickets) + p;
         a.err = reinterpret_cast<unsigned long long *>(w + L.err);
-        onesweep_pass<<<sgrid, kSortThreads, kSortSmem, st>>>(a);
+        if ((rc = launch_onesweep(a, (uint64_t)n, st))) return rc;
     }
     const uint32_t *skeys = bufs_k[(kAggPasses - 1) & 1];
     const uint32_t *sidx = bufs_v[(kAggPasses - 1) & 1];

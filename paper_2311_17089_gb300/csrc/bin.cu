@@ -76,8 +76,10 @@ __device__ __forceinline__ uint64_t pass_count(const PassArgs &a) {
 }
 
 
+template <int IPT>
 __global__ void __launch_bounds__(kSortThreads)
 onesweep_pass(PassArgs a) {
+    constexpr int kPart = SortCfg<IPT>::kPart;
     extern __shared__ __align__(16) uint32_t sort_smem[];
     uint32_t(*s_whist)[kDigits] = reinterpret_cast<uint32_t(*)[kDigits]>(sort_smem);
     uint32_t *s_keys = sort_smem + kSortWarps * kDigits;
@@ -106,23 +108,23 @@ onesweep_pass(PassArgs a) {
         if (p >= parts) break;
         // ---- load every item first (all loads in flight together), then
         // rank (warp-striped, rounds in item order)
-        uint32_t key[kSortIPT], val[kSortIPT], rank[kSortIPT];
-        bool ok[kSortIPT];
-        const uint64_t wbase = (uint64_t)p * kPart + (uint64_t)warp * 32 * kSortIPT;
+        uint32_t key[IPT], val[IPT], rank[IPT];
+        bool ok[IPT];
+        const uint64_t wbase = (uint64_t)p * kPart + (uint64_t)warp * 32 * IPT;
 #pragma unroll
-        for (int r = 0; r < kSortIPT; r++) {
+        for (int r = 0; r < IPT; r++) {
             const uint64_t i = wbase + (uint64_t)r * 32 + lane;
             ok[r] = i < n;
             if (a.filter && ok[r]) ok[r] = __ldg(a.filter + i) > 0;
         }
 #pragma unroll
-        for (int r = 0; r < kSortIPT; r++) {
+        for (int r = 0; r < IPT; r++) {
             const uint64_t i = wbase + (uint64_t)r * 32 + lane;
             key[r] = ok[r] ? a.keys_in[i] : 0u;
             val[r] = ok[r] ? (a.vals_in ? a.vals_in[i] : (uint32_t)i) : 0u;
         }
 #pragma unroll
-        for (int r = 0; r < kSortIPT; r++) {
+        for (int r = 0; r < IPT; r++) {
             const bool valid = ok[r];
             const uint32_t d = (key[r] >> a.shift) & 255u;
             const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u);
@@ -195,7 +197,7 @@ onesweep_pass(PassArgs a) {
         __syncthreads();
         // ---- stage digit-sorted in shared memory
 #pragma unroll
-        for (int r = 0; r < kSortIPT; r++) {
+        for (int r = 0; r < IPT; r++) {
             if (rank[r] == 0xffffffffu) continue;
             uint32_t dd = rank[r] >> 16;
             uint32_t pos = s_excl[dd] + s_whist[warp][dd] + (rank[r] & 0xffffu);
@@ -241,6 +243,7 @@ struct DupArgs {
     const unsigned long long *dup;  // duplicates D (device)
     uint32_t *tstatus;           // tile-pass look-back words, zeroed here
     uint64_t tstride;            // words per tile pass in tstatus
+    uint32_t tpart;              // partition size of the tile passes
 };
 
 __global__ void __launch_bounds__(kDupThreads)
@@ -259,7 +262,7 @@ duplicate_kernel(DupArgs a) {
     {
         // clear the look-back words the tile passes will use (only as many
         // partitions as D needs; the passes start after this kernel ends)
-        const uint64_t words = ((umin64(*a.dup, a.cap) + kPart - 1) / kPart) * 256;
+        const uint64_t words = ((umin64(*a.dup, a.cap) + a.tpart - 1) / a.tpart) * 256;
         for (uint64_t w = blockIdx.x * (uint64_t)kDupThreads + tid; w < words;
              w += (uint64_t)gridDim.x * kDupThreads) {
             a.tstatus[w] = 0u;
@@ -402,6 +405,30 @@ __global__ void finish_counts_kernel(const uint32_t *__restrict__ stats,
     if (d > cap) atomicOr(counts + kCntStatus, (unsigned long long)kStatusOverflow);
 }
 
+// ------------------------------------------------------------ launcher
+
+template <int IPT>
+static int launch_pass(const PassArgs &a, uint64_t bound, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        int rc = cuda_check(cudaFuncSetAttribute(onesweep_pass<IPT>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 SortCfg<IPT>::kSmem),
+                            "radix smem attribute");
+        if (rc) return rc;
+        attr = true;
+    }
+    const int64_t parts = (int64_t)((bound + SortCfg<IPT>::kPart - 1) / SortCfg<IPT>::kPart);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(parts, (int64_t)num_sms() * 2));
+    onesweep_pass<IPT><<<grid, kSortThreads, SortCfg<IPT>::kSmem, st>>>(a);
+    return MS_OK;
+}
+
+int launch_onesweep(const PassArgs &a, uint64_t bound, cudaStream_t st) {
+    return bound <= kSmallPassItems ? launch_pass<kSmallIPT>(a, bound, st)
+                                    : launch_pass<kLargeIPT>(a, bound, st);
+}
+
 // ------------------------------------------------------------ workspace
 
 struct BinLayout {
@@ -418,8 +445,8 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static bool layout(int64_t n, int64_t cap, BinLayout &L) {
     if (n < 0 || n > INT32_MAX || cap < 1 || cap > (1ll << 30)) return false;
     int64_t nn = n > 0 ? n : 1;
-    L.dparts = ceil_div(nn, kPart);
-    L.tparts = ceil_div(cap, kPart);
+    L.dparts = sort_parts((uint64_t)nn);
+    L.tparts = sort_parts((uint64_t)cap);
     L.dupparts = ceil_div(nn, kDupPart);
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -476,15 +503,6 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     cudaStream_t st = as_stream(stream);
     char *w = static_cast<char *>(ws);
     int rc;
-    static bool attr_set = false;
-    if (!attr_set) {
-        if ((rc = cuda_check(cudaFuncSetAttribute(onesweep_pass,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  kSortSmem),
-                             "radix smem attribute")))
-            return rc;
-        attr_set = true;
-    }
     if ((rc = cuda_check(cudaMemsetAsync(w + L.zero_begin, 0, L.total - L.zero_begin, st),
                          "workspace memset")))
         return rc;
@@ -497,7 +515,6 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(w + off); };
     uint32_t *tickets = U32(L.tickets);
     unsigned long long *err = reinterpret_cast<unsigned long long *>(out->counts) + kCntStatus;
-    const int per_sm = 2;
     const int sms = num_sms();
 
     finish_counts_kernel<<<1, 1, 0, st>>>(proj->stats, reinterpret_cast<unsigned long long *>(out->counts),
@@ -508,7 +525,6 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
         reinterpret_cast<const unsigned long long *>(proj->stats + kStatDup);
     uint32_t *dk[2] = {U32(L.dkeys_a), U32(L.dkeys_b)};
     uint32_t *dv[2] = {U32(L.dvals_a), U32(L.dvals_b)};
-    int dgrid = (int)std::min<int64_t>(L.dparts, (int64_t)sms * per_sm);
     for (int pass = 0; pass < 4; pass++) {
         PassArgs a;
         a.keys_in = pass == 0 ? proj->depth : dk[(pass - 1) & 1];
@@ -524,7 +540,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
         a.status = U32(L.dstatus) + (size_t)pass * L.dparts * 256;
         a.ticket = tickets + pass;
         a.err = err;
-        onesweep_pass<<<dgrid, kSortThreads, kSortSmem, st>>>(a);
+        if ((rc = launch_onesweep(a, (uint64_t)n, st))) return rc;
     }
     // after 4 passes (out: a, b, a, b) the depth-ordered indices are in dv[1]
     // ---- duplicate into (tile, index) entries
@@ -546,11 +562,11 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     da.dup = dup64;
     da.tstatus = U32(L.tstatus);
     da.tstride = (uint64_t)L.tparts * 256;
+    da.tpart = (uint32_t)sort_part((uint64_t)out->dup_capacity);
     int dupgrid = (int)std::min<int64_t>(L.dupparts, (int64_t)sms * 4);
     duplicate_kernel<<<dupgrid, kDupThreads, 0, st>>>(da);
     // ---- stable sort by tile id
     const int tpasses = tiles <= 256 ? 1 : 2;
-    int tgrid = (int)std::min<int64_t>(L.tparts, (int64_t)sms * per_sm);
     uint32_t *final_keys = U32(L.tkeys_b);
     for (int pass = 0; pass < tpasses; pass++) {
         PassArgs a;
@@ -569,7 +585,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
         a.status = U32(L.tstatus) + (size_t)pass * L.tparts * 256;
         a.ticket = tickets + 5 + pass;
         a.err = err;
-        onesweep_pass<<<tgrid, kSortThreads, kSortSmem, st>>>(a);
+        if ((rc = launch_onesweep(a, (uint64_t)out->dup_capacity, st))) return rc;
     }
     ranges_kernel<<<sms * 4, 256, 0, st>>>(final_keys, dup64, (uint64_t)out->dup_capacity,
                                            (uint32_t)tiles, out->ranges);

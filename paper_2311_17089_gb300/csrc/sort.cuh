@@ -3,14 +3,19 @@
 // small Gaussians.  Defined in bin.cu.
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace msgs {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortIPT = 16;
-constexpr int kPart = kSortThreads * kSortIPT;  // items per partition
+// Items per thread of a partition: passes over at most kSmallPassItems
+// items use small partitions (more CTAs, shorter per-partition latency),
+// larger passes bigger ones.
+constexpr int kSmallIPT = 8;
+constexpr int kLargeIPT = 16;
+constexpr uint64_t kSmallPassItems = 2ull << 20;
 constexpr int kDigits = 256;
 constexpr int kScanWarps = kDigits / 32;
 constexpr uint32_t kFlagAgg = 1u << 30;
@@ -19,7 +24,19 @@ constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr int kLookback = 16;  // predecessors polled per look-back step
 
-constexpr int kSortSmem = (kSortWarps * kDigits + 2 * kPart) * 4;
+template <int IPT>
+struct SortCfg {
+    static constexpr int kPart = kSortThreads * IPT;  // items per partition
+    static constexpr int kSmem = (kSortWarps * kDigits + 2 * kPart) * 4;
+};
+
+// Partition size of a pass over at most `bound` items.
+inline uint64_t sort_part(uint64_t bound) {
+    return bound <= kSmallPassItems ? SortCfg<kSmallIPT>::kPart : SortCfg<kLargeIPT>::kPart;
+}
+inline int64_t sort_parts(uint64_t bound) {
+    return (int64_t)((bound + sort_part(bound) - 1) / sort_part(bound));
+}
 
 struct PassArgs {
     const uint32_t *keys_in;
@@ -41,7 +58,9 @@ struct PassArgs {
 // filter[i] > 0 when a filter is given, compacted in index order) are
 // scattered stably by digit (key >> shift) & 255 into keys_out/vals_out.
 // hist holds the digit totals of the items taken; status must hold
-// ceil(count / kPart) x 256 zeroed words and ticket one zeroed word.
-__global__ void onesweep_pass(PassArgs a);
+// sort_parts(bound) x 256 zeroed words and ticket one zeroed word, `bound`
+// being an upper bound of count known on the host (it picks the partition
+// size and the grid).  Defined in bin.cu.
+int launch_onesweep(const PassArgs &a, uint64_t bound, cudaStream_t st);
 
 }  // namespace msgs
