@@ -99,14 +99,150 @@ __device__ __forceinline__ float3 gaussian_color(const float *__restrict__ color
 
 // ------------------------------------------------------------- kernels
 
-__global__ void prepare_kernel(int64_t n, const float *__restrict__ log_scale,
-                               const float *__restrict__ opacity,
-                               float *__restrict__ scale, float *__restrict__ lnop) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+// ---------------------------------------------------------------- prepare
+//
+// scale = exp(log_scale) and lnop = ln(255 opacity), each the float nearest
+// to the exact value (the definition rounds an FP64 evaluation to FP32).
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so both are
+// evaluated in float-float arithmetic (an unevaluated sum of two floats,
+// about 46 correct bits): range reduction by ln 2, a 1/32 (exp) or 1/64
+// (ln) table step, then a Taylor series of the remainder.  The result is
+// rounded to float; when the float-float value lies within its error bound
+// of a rounding midpoint, an FP64 evaluation decides (a few values in 10^5).
+
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff ff_fast(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {  // accurate sum
+    ff s = ff_two_sum(a.h, b.h);
+    const ff t = ff_two_sum(a.l, b.l);
+    s = ff_fast(s.h, __fadd_rn(s.l, t.h));
+    return ff_fast(s.h, __fadd_rn(s.l, t.l));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return ff_fast(p, e);
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+    const float p = __fmul_rn(a.h, b);
+    return ff_fast(p, __fmaf_rn(a.l, b, __fmaf_rn(a.h, b, -p)));
+}
+
+// v.h is the float nearest to v.h + v.l + d for every |d| <= err.
+__device__ __forceinline__ bool ff_rounds_to_hi(ff v, float err) {
+    const float ah = fabsf(v.h);
+    const float up = __fsub_rn(__int_as_float(__float_as_int(ah) + 1), ah);
+    const float dn = __fsub_rn(ah, __int_as_float(__float_as_int(ah) - 1));
+    const float l = v.h < 0.0f ? -v.l : v.l;
+    return l < __fsub_rn(__fmul_rn(0.5f, up), err) && l > __fsub_rn(err, __fmul_rn(0.5f, dn));
+}
+
+// ln 2 = kLn2A + kLn2B + kLn2C (kLn2A has 12 significant bits, so k kLn2A
+// is exact for |k| < 2^12); 1/6, 1/24, 1/3 as float-float
+constexpr float kLn2A = 0x1.62ep-1f, kLn2B = 0x1.0bfbe8p-15f, kLn2C = 0x1.cf79acp-40f;
+constexpr float kR6h = 0x1.555556p-3f, kR6l = -0x1.555556p-28f;
+constexpr float kR24h = 0x1.555556p-5f, kR24l = -0x1.555556p-30f;
+constexpr float kR3h = 0x1.555556p-2f, kR3l = -0x1.555556p-27f;
+constexpr float kFFErr = 0x1p-42f;  // relative error bound of the float-float results
+constexpr int kExpTab = 25;         // exp(j/32), j = -12 .. 12
+constexpr int kLnTab = 49;          // ln(3/4 + j/64), j = 0 .. 48
+
+__device__ __forceinline__ float exp_rn(float x, const ff *texp) {
+    if (!(fabsf(x) < 80.0f)) return (float)exp((double)x);
+    const float k = rintf(__fmul_rn(x, 1.44269504f));  // |k| <= 116
+    ff r = ff_two_sum(x, -__fmul_rn(k, kLn2A));
+    const ff kb = ff_two_prod(k, kLn2B);
+    r = ff_add(r, {-kb.h, -kb.l});
+    r = ff_add(r, {-__fmul_rn(k, kLn2C), 0.0f});
+    const float j = rintf(__fmul_rn(r.h, 32.0f));     // |j| <= 12
+    r = ff_add(r, {-__fmul_rn(j, 0.03125f), 0.0f});   // |r| <= 1/64
+    // exp(r) = 1 + r(1 + r(1/2 + r(1/6 + r(1/24 + r q)))), q the float tail
+    const float q = __fmaf_rn(r.h, __fmaf_rn(r.h, 1.0f / 5040.0f, 1.0f / 720.0f), 1.0f / 120.0f);
+    ff p = ff_add({kR24h, kR24l}, ff_mulf(r, q));
+    p = ff_add({kR6h, kR6l}, ff_mul(r, p));
+    p = ff_add({0.5f, 0.0f}, ff_mul(r, p));
+    p = ff_add({1.0f, 0.0f}, ff_mul(r, p));
+    p = ff_add({1.0f, 0.0f}, ff_mul(r, p));
+    ff e = ff_mul(texp[(int)j + 12], p);
+    const int ki = (int)k;
+    e.h = ldexpf(e.h, ki);
+    e.l = ldexpf(e.l, ki);
+    if (ff_rounds_to_hi(e, __fmul_rn(kFFErr, fabsf(e.h)))) return e.h;
+    return (float)exp((double)x);
+}
+
+__device__ __forceinline__ float lnop_rn(float sigma, const ff *tln) {
+    if (!(sigma > 1e-30f) || !(sigma < 1e30f)) return (float)log(255.0 * (double)sigma);
+    const ff y = ff_two_prod(255.0f, sigma);  // exact
+    // y = 2^ex m, m in [3/4, 3/2)
+    const int bits = __float_as_int(y.h);
+    int ex = ((bits >> 23) & 0xff) - 127;
+    float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+    if (m >= 1.5f) {
+        m = __fmul_rn(m, 0.5f);
+        ex += 1;
+    }
+    const float ml = ldexpf(y.l, -ex);
+    const float j = rintf(__fmul_rn(__fsub_rn(m, 0.75f), 64.0f));  // 0 .. 48
+    const float c = __fmaf_rn(j, 0.015625f, 0.75f);                // exact
+    // t = (m + ml - c) / c, |t| <= 1/96
+    const ff num = ff_two_sum(__fsub_rn(m, c), ml);
+    const float t0 = __fdiv_rn(num.h, c);
+    const float rem = __fadd_rn(__fmaf_rn(-t0, c, num.h), num.l);
+    const ff t = ff_fast(t0, __fdiv_rn(rem, c));
+    // ln(1 + t) = t (1 + t(-1/2 + t(1/3 + t(-1/4 + t q)))), q the float tail
+    const float q = __fmaf_rn(t.h, __fmaf_rn(t.h, __fmaf_rn(t.h, -0.125f, 1.0f / 7.0f), -1.0f / 6.0f), 0.2f);
+    ff p = ff_add({-0.25f, 0.0f}, ff_mulf(t, q));
+    p = ff_add({kR3h, kR3l}, ff_mul(t, p));
+    p = ff_add({-0.5f, 0.0f}, ff_mul(t, p));
+    p = ff_add({1.0f, 0.0f}, ff_mul(t, p));
+    const ff lg = ff_mul(t, p);
+    const float exf = (float)ex;
+    const ff eb = ff_two_prod(exf, kLn2B);
+    ff a = ff_add({__fmul_rn(exf, kLn2A), 0.0f}, eb);
+    a = ff_add(a, {__fmul_rn(exf, kLn2C), 0.0f});
+    const ff tl = tln[(int)j];
+    const ff sum = ff_add(ff_add(a, tl), lg);
+    const float err = __fmul_rn(kFFErr, __fadd_rn(__fadd_rn(fabsf(a.h), fabsf(tl.h)), fabsf(lg.h)));
+    if (ff_rounds_to_hi(sum, err)) return sum.h;
+    return (float)log(255.0 * (double)sigma);
+}
+
+__global__ void __launch_bounds__(256)
+prepare_kernel(int64_t n, const float *__restrict__ log_scale, const float *__restrict__ opacity,
+               float *__restrict__ scale, float *__restrict__ lnop) {
+    __shared__ ff s_exp[kExpTab], s_ln[kLnTab];
+    const int t = threadIdx.x;
+    if (t < kExpTab) {
+        const double v = exp((double)(t - 12) / 32.0);
+        const float h = (float)v;
+        s_exp[t] = {h, (float)(v - (double)h)};
+    } else if (t >= 64 && t < 64 + kLnTab) {
+        const double v = log(0.75 + (double)(t - 64) / 64.0);
+        const float h = (float)v;
+        s_ln[t - 64] = {h, (float)(v - (double)h)};
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + t; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        for (int k = 0; k < 3; k++)
-            scale[3 * i + k] = (float)exp((double)log_scale[3 * i + k]);
-        lnop[i] = (float)log(255.0 * (double)opacity[i]);
+        for (int k = 0; k < 3; k++) scale[3 * i + k] = exp_rn(log_scale[3 * i + k], s_exp);
+        lnop[i] = lnop_rn(opacity[i], s_ln);
     }
 }
 

@@ -288,3 +288,42 @@ def test_one_long_list_among_many_tiles_and_overflow(cuda):
     assert_lists_equal(g, off, idx)
     o = oracle.render(sc, cam, "all_levels")
     assert_image_close(g, o, cam=cam, max_flagged=0.05)
+
+
+def test_scene_prepare_bit_exact_many_values(cuda):
+    """exp(log_scale) and ln(255 opacity) rounded to float, on 4M values
+    across the float range the scenes use and its edges (the device
+    evaluates them in float-float with an FP64 decision near midpoints)."""
+    import torch
+    rng = np.random.default_rng(17)
+    m = 4_000_000
+    ls = np.concatenate([rng.uniform(-12.0, 6.0, m // 2), rng.normal(-3.5, 2.0, m // 4),
+                         rng.uniform(-79.9, 79.9, m // 4)]).astype(np.float32)
+    op = np.concatenate([rng.uniform(0.0, 1.0, m // 2), 1.0 / (1.0 + np.exp(-rng.normal(0, 3, m // 4))),
+                         10.0 ** rng.uniform(-30, 0, m // 4)]).astype(np.float32)
+    tiny = np.float32(1.0 / 255.0)
+    edges_ls = np.array([0.0, -0.0, 1e-30, -1e-30, 79.99, -79.99, 80.0, -80.0, 88.0, -87.0,
+                         100.0, np.inf, -np.inf, np.nan], np.float32)
+    edges_op = np.array([1.0, 0.5, tiny, np.nextafter(tiny, np.float32(1)),
+                         np.nextafter(tiny, np.float32(0)), 1e-6, 1e-30, 1e-35, 0.0, -0.5,
+                         np.inf, np.nan, 3.0, 1e31], np.float32)
+    ls = np.concatenate([ls, edges_ls])
+    op = np.concatenate([op, edges_op])
+    n = len(ls) // 3 * 3
+    sc = inputs.single_level_scene(n=n // 3, seed=0)
+    sc.log_scale = ls[:n].reshape(-1, 3)
+    sc.opacity = op[: n // 3]
+    want_scale, want_lnop = oracle.prepare(sc)
+    dev = torch.device("cuda")
+    lsd = torch.tensor(sc.log_scale, device=dev)
+    opd = torch.tensor(sc.opacity, device=dev)
+    scale = torch.empty_like(lsd)
+    lnop = torch.empty_like(opd)
+    st = msgs.ms_scene_t(sc.n, 1, -1, 1, msgs._ptr(lsd), 1, msgs._ptr(opd), 1, 1, 1, 1,
+                         msgs._ptr(scale), msgs._ptr(lnop))
+    msgs.ms_scene_prepare(st)
+    torch.cuda.synchronize()
+    for got, want in ((scale.cpu().numpy(), want_scale), (lnop.cpu().numpy(), want_lnop)):
+        nan = np.isnan(want)          # NaN payloads may differ; positions may not
+        np.testing.assert_array_equal(np.isnan(got), nan)
+        np.testing.assert_array_equal(got[~nan].view(np.uint32), want[~nan].view(np.uint32))
