@@ -403,6 +403,7 @@ __global__ void finish_counts_kernel(const uint32_t *__restrict__ stats,
     counts[kCntDup] = d;
     counts[kCntSurvivors] = stats[kStatSurvivors];
     if (d > cap) atomicOr(counts + kCntStatus, (unsigned long long)kStatusOverflow);
+    if (stats[kStatStatus]) atomicOr(counts + kCntStatus, (unsigned long long)stats[kStatStatus]);
 }
 
 // ------------------------------------------------------------ launcher

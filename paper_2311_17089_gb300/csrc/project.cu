@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "footprint.cuh"
+#include "tma.cuh"
 
 namespace msgs {
 
@@ -252,30 +253,94 @@ constexpr float kConicA = -0.72134752044448170f;   // -log2(e) / 2
 constexpr float kConicB = -1.4426950408889634f;    // -log2(e)
 constexpr float kLog2e = 1.4426950408889634f;
 
-// K1: one thread per Gaussian (grid-stride), writes the footprint outputs,
-// the raster record of listed Gaussians, and accumulates the survivor
-// count, the duplicate count and the four depth-digit histograms that the
-// binning stage's radix sort needs.
+// The per-Gaussian geometry of one chunk of kProjThreads Gaussians, staged
+// in shared memory by bulk copies (7 arrays, 13,568 bytes).
+struct ProjStage {
+    float mean[3 * kProjThreads];
+    float scale[3 * kProjThreads];
+    float4 quat[kProjThreads];
+    float lnop[kProjThreads];
+    float smax[kProjThreads];
+    float smin[kProjThreads];
+    uint8_t level[kProjThreads];
+};
+constexpr uint32_t kProjStageBytes = (3 + 3 + 4 + 3) * 4 * kProjThreads + kProjThreads;
+static_assert(sizeof(ProjStage) == kProjStageBytes, "stage layout");
+
+// Threads 0..6 of warp 0 issue the bulk copies of chunk c (every array
+// offset is a multiple of 256 elements, so 16-byte aligned when the arrays
+// are).
+__device__ __forceinline__ void issue_chunk(const SceneK &sc, int64_t c, ProjStage &st,
+                                            uint64_t *bar) {
+    if (threadIdx.x >= 7) return;
+    const int64_t i0 = c * kProjThreads;
+    if (threadIdx.x == 0) mbar_expect_tx(bar, kProjStageBytes);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    switch (threadIdx.x) {
+    case 0: bulk_copy_g2s(st.mean, sc.mean + 3 * i0, 12 * kProjThreads, bar); break;
+    case 1: bulk_copy_g2s(st.scale, sc.scale + 3 * i0, 12 * kProjThreads, bar); break;
+    case 2: bulk_copy_g2s(st.quat, sc.quat + 4 * i0, 16 * kProjThreads, bar); break;
+    case 3: bulk_copy_g2s(st.lnop, sc.lnop + i0, 4 * kProjThreads, bar); break;
+    case 4: bulk_copy_g2s(st.smax, sc.s_max + i0, 4 * kProjThreads, bar); break;
+    case 5: bulk_copy_g2s(st.smin, sc.s_min + i0, 4 * kProjThreads, bar); break;
+    default: bulk_copy_g2s(st.level, sc.level + i0, kProjThreads, bar); break;
+    }
+}
+
+// K1: one thread per Gaussian, chunks of kProjThreads Gaussians per CTA
+// (grid-stride).  While a chunk is processed, the geometry of the CTA's
+// next chunk streams into the other stage buffer (full chunks of 16-byte
+// aligned arrays; the ragged last chunk, or unaligned arrays, read global
+// memory directly).  Writes the footprint outputs, the raster record of
+// listed Gaussians, and accumulates the survivor count, the duplicate count
+// and the four depth-digit histograms that the binning stage's radix sort
+// needs.
 __global__ void __launch_bounds__(kProjThreads, kProjBlocksPerSM)
-project_kernel(SceneK sc, CamK cam, int mode, float4 *__restrict__ rec,
+project_kernel(SceneK sc, CamK cam, int mode, bool staged_ok, float4 *__restrict__ rec,
                uint2 *__restrict__ rect, uint32_t *__restrict__ n_tiles,
                uint32_t *__restrict__ depth, float *__restrict__ cover,
                uint32_t *__restrict__ mask, uint32_t *__restrict__ stats) {
     __shared__ uint32_t s_hist[4][256];
     __shared__ uint32_t s_surv;
     __shared__ unsigned long long s_dup;
+    __shared__ __align__(128) ProjStage s_st[2];
+    __shared__ __align__(8) uint64_t s_bar[2];
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     if (threadIdx.x == 0) {
         s_surv = 0;
         s_dup = 0;
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     uint32_t my_surv = 0;
     unsigned long long my_dup = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nchunks = (sc.n + kProjThreads - 1) / kProjThreads;
+    auto full = [&](int64_t c) { return staged_ok && (c + 1) * kProjThreads <= sc.n; };
+    if ((int64_t)blockIdx.x < nchunks && full(blockIdx.x)) issue_chunk(sc, blockIdx.x, s_st[0], &s_bar[0]);
+    uint32_t par = 0;
+    int it = 0;
     // all threads of a warp iterate together so warp ballots stay full
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < sc.n; base += stride) {
-        int64_t i = base + threadIdx.x;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x, it++) {
+        const int b = it & 1;
+        const int64_t cn = c + gridDim.x;
+        if (cn < nchunks && full(cn)) issue_chunk(sc, cn, s_st[b ^ 1], &s_bar[b ^ 1]);
+        bool staged = full(c);
+        if (staged) {
+            bool ok = false;
+            for (uint32_t spins = 0; spins < kSpinLimit && !ok; spins++)
+                ok = mbar_try_wait(&s_bar[b], (par >> b) & 1u);
+            par ^= 1u << b;
+            if (!ok) {  // copies still out: this chunk reads global memory
+                staged = false;
+                atomicOr(stats + kStatStatus, (uint32_t)kStatusTimeout);
+            }
+        }
+        const ProjStage &st = s_st[b];
+        const int64_t base = c * kProjThreads;
+        const int t = threadIdx.x;
+        int64_t i = base + t;
         bool in = i < sc.n;
         Foot f;
         f.valid = false;
@@ -283,13 +348,36 @@ project_kernel(SceneK sc, CamK cam, int mode, float4 *__restrict__ rec,
         f.S = -1.0f;
         bool sel = false;
         if (in) {
-            float m[3] = {sc.mean[3 * i], sc.mean[3 * i + 1], sc.mean[3 * i + 2]};
-            float s[3] = {sc.scale[3 * i], sc.scale[3 * i + 1], sc.scale[3 * i + 2]};
-            float4 q = reinterpret_cast<const float4 *>(sc.quat)[i];
-            footprint(m, s, q, sc.lnop[i], cam, f);
-            if (f.valid)
-                sel = select_pred(f.S, sc.level[i], sc.n_levels, sc.s_max[i],
-                                  sc.s_min[i], mode);
+            float m[3], sv[3], lnop_i, smax_i, smin_i;
+            float4 q;
+            int level_i;
+            if (staged) {
+                m[0] = st.mean[3 * t];
+                m[1] = st.mean[3 * t + 1];
+                m[2] = st.mean[3 * t + 2];
+                sv[0] = st.scale[3 * t];
+                sv[1] = st.scale[3 * t + 1];
+                sv[2] = st.scale[3 * t + 2];
+                q = st.quat[t];
+                lnop_i = st.lnop[t];
+                smax_i = st.smax[t];
+                smin_i = st.smin[t];
+                level_i = st.level[t];
+            } else {
+                m[0] = sc.mean[3 * i];
+                m[1] = sc.mean[3 * i + 1];
+                m[2] = sc.mean[3 * i + 2];
+                sv[0] = sc.scale[3 * i];
+                sv[1] = sc.scale[3 * i + 1];
+                sv[2] = sc.scale[3 * i + 2];
+                q = reinterpret_cast<const float4 *>(sc.quat)[i];
+                lnop_i = sc.lnop[i];
+                smax_i = sc.s_max[i];
+                smin_i = sc.s_min[i];
+                level_i = sc.level[i];
+            }
+            footprint(m, sv, q, lnop_i, cam, f);
+            if (f.valid) sel = select_pred(f.S, level_i, sc.n_levels, smax_i, smin_i, mode);
             bool listed = sel && f.ntiles > 0;
             n_tiles[i] = listed ? f.ntiles : 0u;
             if (cover) cover[i] = f.S;
@@ -301,7 +389,7 @@ project_kernel(SceneK sc, CamK cam, int mode, float4 *__restrict__ rec,
                 rec[3 * i + 0] = make_float4(f.ux, f.uy, fm(kConicA, f.ca), fm(kConicB, f.cb));
                 rec[3 * i + 1] = make_float4(fm(kConicA, f.cc), op, col.x, col.y);
                 // alpha >= 1/255 <=> power * log2(e) >= -ln(255 sigma) log2(e)
-                rec[3 * i + 2] = make_float4(col.z, fm(-kLog2e, sc.lnop[i]), f.ex, f.ey);
+                rec[3 * i + 2] = make_float4(col.z, fm(-kLog2e, lnop_i), f.ex, f.ey);
                 rect[i] = make_uint2((uint32_t)f.x0 | ((uint32_t)f.y0 << 16),
                                      (uint32_t)f.x1 | ((uint32_t)f.y1 << 16));
                 depth[i] = f.depth;
@@ -317,6 +405,7 @@ project_kernel(SceneK sc, CamK cam, int mode, float4 *__restrict__ rec,
             uint32_t bits = __ballot_sync(0xffffffffu, in && sel);
             if ((threadIdx.x & 31) == 0 && in) mask[i >> 5] = bits;
         }
+        __syncthreads();  // the buffer is refilled by the next iteration but one
     }
     // block reduction of the counters
     for (int o = 16; o > 0; o >>= 1) {
@@ -408,8 +497,14 @@ extern "C" int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
                          "stats memset")))
         return rc;
     if (scene->n == 0) return MS_OK;
+    // bulk staging needs every geometry array 16-byte aligned
+    const bool staged_ok = aligned(scene->mean, 16) && aligned(scene->scale, 16) &&
+                           aligned(scene->quat, 16) && aligned(scene->lnop, 16) &&
+                           aligned(scene->s_max, 16) && aligned(scene->s_min, 16) &&
+                           aligned(scene->level, 16);
     project_kernel<<<grid_for(scene->n, kProjThreads, kProjBlocksPerSM), kProjThreads, 0, st>>>(
-        make_scene(*scene), make_cam(*cam), (int)mode, reinterpret_cast<float4 *>(out->rec),
+        make_scene(*scene), make_cam(*cam), (int)mode, staged_ok,
+        reinterpret_cast<float4 *>(out->rec),
         reinterpret_cast<uint2 *>(out->rect), out->n_tiles, out->depth, out->cover, out->mask,
         out->stats);
     return cuda_check(cudaGetLastError(), "project_kernel launch");

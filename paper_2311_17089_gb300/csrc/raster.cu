@@ -33,6 +33,7 @@
 
 #include "common.cuh"
 #include "f32x2.cuh"
+#include "tma.cuh"
 #include "raster_ws.cuh"
 
 namespace msgs {
@@ -57,42 +58,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
-                                              uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
 }
 
 struct RasterArgs {
@@ -404,14 +369,14 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
 // sub-batch j before sub-batch j + 2 is copied over it.  In local mode
 // (`exact` false) the walk stops as soon as the tile is marked done.  The
 // CTA stops early once every pixel has terminated.  Returns kWalked,
-// kAborted, or kFailed when a copy wait gave up (the CTA must then stop).
-constexpr int kWalked = 0, kAborted = 1, kFailed = 2;
+// kAborted.  A copy wait that gives up sets the status word and ends the
+// waiting warps' pixels; the walk stays in step across the CTA.
+constexpr int kWalked = 0, kAborted = 1;
 __device__ __forceinline__ int run_segment(const RasterArgs &a, const Seg &sg, uint32_t L,
                                             bool exact, bool inside, float fx, float fy,
                                             float cx, float cy, PixelState &s,
                                             float4 *aos, WarpPairs &wp, uint64_t *bar,
-                                            uint32_t &par, uint32_t *s_abort,
-                                            uint32_t *s_fail) {
+                                            uint32_t &par, uint32_t *s_abort) {
     const uint32_t pos0 = sg.k * L;
     if (sg.len == 0) return kWalked;
     const uint32_t nb = (sg.len + kChunk - 1) / kChunk;
@@ -427,16 +392,20 @@ __device__ __forceinline__ int run_segment(const RasterArgs &a, const Seg &sg, u
         if (more)
             issue_batch(a, sg.start + off + kChunk, min(sg.len - off - kChunk, (uint32_t)kChunk),
                         aos + (b ^ 1u) * 3 * kChunk, &bar[b ^ 1u]);
-        // warps whose pixels have all terminated skip their share
+        // a copy wait that gave up has set the status word: the warp's pixels
+        // stop here (their result is reported wrong), the walk goes on in
+        // step with the other warps
         const bool wok = __all_sync(0xffffffffu, ok);
-        if (!ok) *s_fail = 1u;
+        if (!wok) s.term = true;
+        // warps whose pixels have all terminated skip their share
         const bool wlive = wok && __any_sync(0xffffffffu, inside && !s.term);
         const uint32_t nw = wlive ? compact(aos + b * 3 * kChunk, cnt, cx, cy, wp) : 0u;
         if (wlive && inside && !s.term) blend_pairs(wp, nw, cnt, pos0 + off, fx2, fy2, s);
-        if (threadIdx.x == 0) *s_abort = exact ? 0u : ld_volatile(a.tile_done + sg.t);
+        // two slots: a warp may still be reading sub-batch j's value while
+        // thread 0 writes sub-batch j + 1's (one barrier per sub-batch)
+        if (threadIdx.x == 0) s_abort[b] = exact ? 0u : ld_volatile(a.tile_done + sg.t);
         const int done = __syncthreads_count(s.term || !inside);
-        if (*s_fail) return kFailed;
-        abort = *s_abort != 0;
+        abort = s_abort[b] != 0;
         if (done == kRasterThreads || abort) {
             if (more) {  // drain the copies already issued
                 wait_batch(a, &bar[b ^ 1u], (par >> (b ^ 1u)) & 1u);
@@ -448,22 +417,20 @@ __device__ __forceinline__ int run_segment(const RasterArgs &a, const Seg &sg, u
     return abort ? kAborted : kWalked;
 }
 
-__global__ void __launch_bounds__(kRasterThreads)
+__global__ void __launch_bounds__(kRasterThreads, 4)  // 64 registers: 4 CTAs per SM
 raster_kernel(RasterArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t s_next;
-    __shared__ uint32_t s_fail;
     __shared__ uint32_t s_flag;
     __shared__ uint32_t s_wait;
-    __shared__ uint32_t s_abort;
+    __shared__ uint32_t s_abort[2];
     float4 *aos = reinterpret_cast<float4 *>(smem);
     WarpPairs &wp = reinterpret_cast<WarpPairs *>(smem + 2 * kBufBytes)[threadIdx.x >> 5];
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
-        s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -532,8 +499,7 @@ raster_kernel(RasterArgs a) {
         const bool last_seg = sg.k + 1 == sg.nk;
         for (int pass = 0; pass < 2; pass++) {
             const int rc = run_segment(a, sg, L, exact || pass == 1, active, fx, fy, cx, cy, s,
-                                       aos, wp, bar, parity, &s_abort, &s_fail);
-            if (rc == kFailed) return;
+                                       aos, wp, bar, parity, s_abort);
             if (rc == kAborted) {
                 skip = true;  // an earlier segment finished the tile
                 break;
