@@ -124,11 +124,12 @@ struct PixPair {
     uint32_t cntA, cntB;  // entries of the segment each pixel blended through
 };
 
-__global__ void __launch_bounds__(kBwdThreads)
+__global__ void __launch_bounds__(kBwdThreads, 8)  // 64 registers: 8 CTAs per SM
 raster_bwd_kernel(const __grid_constant__ BwdArgs args) {
     __shared__ float4 s_r0[kBwdBatch], s_r1[kBwdBatch];
-    __shared__ float2 s_r2[kBwdBatch];
+    __shared__ float4 s_r2[kBwdBatch];             // b, thr, ex, ey
     __shared__ uint32_t s_idx[kBwdBatch];
+    __shared__ uint16_t s_list[kBwdThreads / 32][kBwdBatch];  // per warp: records in reach
     __shared__ float s_acc[kBwdBatch][kG2 + 1];  // [kG2] marks a record some pixel took
     __shared__ uint32_t s_c, s_cnt;
     __shared__ uint32_t s_first[kMaxViews + 1];   // first ticket of each view's segments
@@ -227,6 +228,9 @@ raster_bwd_kernel(const __grid_constant__ BwdArgs args) {
         pp.cntB = cnt[1];
         const float fx = (float)px + 0.5f;
         const f32x2 fy2 = pack2((float)(ty * 16 + lyA) + 0.5f, (float)(ty * 16 + lyB) + 0.5f);
+        // centre of the warp's 8x8 block of pixel centres
+        const float bcx = (float)(tx * 16 + (wid & 1) * 8) + 4.0f;
+        const float bcy = (float)(ty * 16 + (wid >> 1) * 8) + 4.0f;
         const uint32_t wcnt = __reduce_max_sync(0xffffffffu, max(pp.cntA, pp.cntB));
         if (lane == 0 && wcnt) atomicMax(&s_cnt, wcnt);
         __syncthreads();
@@ -239,14 +243,30 @@ raster_bwd_kernel(const __grid_constant__ BwdArgs args) {
                 s_idx[r] = g;
                 s_r0[r] = a.rec[3 * (size_t)g];
                 s_r1[r] = a.rec[3 * (size_t)g + 1];
-                const float4 r2 = a.rec[3 * (size_t)g + 2];
-                s_r2[r] = make_float2(r2.x, r2.y);
+                s_r2[r] = a.rec[3 * (size_t)g + 2];
             }
             __syncthreads();
             const uint32_t jn = wcnt > off ? min(wcnt - off, nb) : 0u;  // warp-uniform
-            for (uint32_t j = 0; j < jn; j++) {
+            // the records whose level-set box (plus 1 px) reaches the warp's
+            // 8x8 block of pixel centres, in list order; any other record has
+            // alpha < 1/255 at all of the warp's pixels
+            uint32_t nl = 0;
+            for (uint32_t j0 = 0; j0 < jn; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                bool rel = false;
+                if (j < jn) {
+                    const float4 r0 = s_r0[j], r2 = s_r2[j];
+                    rel = fabsf(r0.x - bcx) <= r2.z + 4.5f && fabsf(r0.y - bcy) <= r2.w + 4.5f;
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, rel);
+                if (rel) s_list[wid][nl + __popc(m & ((1u << lane) - 1u))] = (uint16_t)j;
+                nl += __popc(m);
+            }
+            __syncwarp();
+            for (uint32_t li = 0; li < nl; li++) {
+                const uint32_t j = s_list[wid][li];
                 const float4 r0 = s_r0[j], r1 = s_r1[j];
-                const float2 r2 = s_r2[j];
+                const float4 r2 = s_r2[j];
                 // the forward's exact FP32 operations, for both pixels
                 const float dx = __fsub_rn(fx, r0.x);
                 const f32x2 dy = sub2(fy2, splat2(r0.y));
