@@ -60,6 +60,18 @@ typedef enum {
     MS_FILTER_SMALL = 2  /* second clause of Eq. 6 only, no exemption      */
 } ms_mode_t;
 
+/* How ms_raster_ex spreads a frame's blend over the GPU (the result is the
+ * same blend either way, up to FP32 rounding). */
+typedef enum {
+    MS_RASTER_AUTO = 0,  /* TILE when the frame has at least as many tiles as
+                            CTAs of the tile kernel fit on the GPU, else LIST */
+    MS_RASTER_TILE = 1,  /* one thread per pixel; long lists split into
+                            segments merged exactly across CTAs             */
+    MS_RASTER_LIST = 2   /* one warp per pixel; lanes take consecutive list
+                            entries, a product scan of (1 - alpha) decides
+                            termination                                     */
+} ms_raster_strategy_t;
+
 /*
  * A scene of n 3D Gaussians (Sec. 3.1: centre, covariance from scale and
  * rotation, opacity, colour; Sec. 4.1: level and coverage range).
@@ -267,26 +279,37 @@ int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed,
 size_t ms_raster_workspace_bytes(int64_t tiles, int64_t dup_capacity);
 
 /*
- * Front-to-back blend (Sec. 3.1, Eq. 3): 256-thread CTAs, one thread per
- * pixel of a 16x16 tile, sampled at the pixel centre.  Lists longer than
- * 512 entries are split across CTAs and merged exactly (the result of one
- * sequential walk, up to FP32 rounding).  For each Gaussian of
- * the tile's list in order: power = -(a dx^2 + c dy^2)/2 - b dx dy; skip if
- * power > 0; alpha = min(0.99, sigma e^power); skip if alpha < 1/255; stop
- * before a Gaussian that would bring T below 1e-4; C += alpha T rgb,
- * T *= 1 - alpha.  Writes image[3][H][W] (planar, C + T bg), final_t[H][W]
- * and n_contrib[H][W] (1 + list position of the last blended Gaussian, 0 if
- * none).  n_eval[H][W] receives the number of list entries the pixel
- * evaluated up to and including the one that ended it (the algorithmic
- * work, for measurement).  final_t, n_contrib and n_eval may be NULL.
- * `ws` (16-B aligned) of ms_raster_workspace_bytes(tiles, dup_capacity)
- * bytes is scratch owned by the call until the stream passes it.  A
- * bounded wait that gives up sets status bit 2 in bins->counts.
+ * Front-to-back blend (Sec. 3.1, Eq. 3), sampled at pixel centres.  For
+ * each Gaussian of the tile's list in order: power = -(a dx^2 + c dy^2)/2
+ * - b dx dy; skip if power > 0; alpha = min(0.99, sigma e^power); skip if
+ * alpha < 1/255; stop before a Gaussian that would bring T below 1e-4;
+ * C += alpha T rgb, T *= 1 - alpha.  Writes image[3][H][W] (planar,
+ * C + T bg), final_t[H][W] and n_contrib[H][W] (1 + list position of the
+ * last blended Gaussian, 0 if none).  n_eval[H][W] receives the number of
+ * list entries the pixel evaluated up to and including the one that ended
+ * it (the algorithmic work, for measurement).  final_t, n_contrib and
+ * n_eval may be NULL.  `ws` (16-B aligned) of
+ * ms_raster_workspace_bytes(tiles, dup_capacity) bytes is scratch owned by
+ * the call until the stream passes it; it also keeps the per-segment state
+ * ms_raster_bwd starts from.  A bounded wait that gives up sets status
+ * bit 2 in bins->counts.  ms_raster uses MS_RASTER_AUTO.
  */
 int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins,
               const ms_camera_t *cam, float *image, float *final_t,
               uint32_t *n_contrib, uint32_t *n_eval, void *ws,
               size_t ws_bytes, void *stream);
+
+/*
+ * ms_raster with the blend's parallelisation chosen by `strategy`
+ * (ms_raster_strategy_t; MS_ERR_INVALID_ARG for any other value).  Both
+ * strategies compute the blend above (Sec. 3.1, Eq. 3) from the same tile
+ * lists with the same FP32 alpha; they differ only in the rounding of the
+ * transmittance products.
+ */
+int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
+                 const ms_camera_t *cam, float *image, float *final_t,
+                 uint32_t *n_contrib, uint32_t *n_eval, void *ws,
+                 size_t ws_bytes, int strategy, void *stream);
 
 /*
  * Gradients of a loss with respect to the scene parameters, outputs of

@@ -27,6 +27,8 @@ MS_ERR_NO_DEVICE, MS_PENDING = 5, 6
 MS_SELECTIVE, MS_ALL_LEVELS, MS_FILTER_SMALL = 0, 1, 2
 MODES = {"selective": MS_SELECTIVE, "all_levels": MS_ALL_LEVELS,
          "filter_small": MS_FILTER_SMALL}
+MS_RASTER_AUTO, MS_RASTER_TILE, MS_RASTER_LIST = 0, 1, 2
+STRATEGIES = {"auto": MS_RASTER_AUTO, "tile": MS_RASTER_TILE, "list": MS_RASTER_LIST}
 MS_STATS_WORDS = 1040
 MS_BWD_ACCUMULATE = 1
 MS_MAX_BWD_VIEWS = 8
@@ -142,6 +144,9 @@ _SIGNATURES = [
     ("ms_raster", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
                                  ctypes.POINTER(ms_camera_t), P, P, P, P, P,
                                  ctypes.c_size_t, P]),
+    ("ms_raster_ex", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
+                                    ctypes.POINTER(ms_camera_t), P, P, P, P, P,
+                                    ctypes.c_size_t, ctypes.c_int, P]),
     ("ms_aggregate_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64]),
     ("ms_aggregate", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
@@ -275,6 +280,14 @@ def ms_raster(proj: ms_proj_t, bins: ms_bins_t, cam: ms_camera_t, image_ptr: int
     _check(lib().ms_raster(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam),
                            P(image_ptr), P(final_t_ptr), P(n_contrib_ptr), P(n_eval_ptr),
                            P(ws_ptr), ws_bytes, P(_stream(stream))))
+
+
+def ms_raster_ex(proj: ms_proj_t, bins: ms_bins_t, cam: ms_camera_t, image_ptr: int,
+                 final_t_ptr: int, n_contrib_ptr: int, n_eval_ptr: int, ws_ptr: int,
+                 ws_bytes: int, strategy: int, stream=None):
+    _check(lib().ms_raster_ex(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam),
+                              P(image_ptr), P(final_t_ptr), P(n_contrib_ptr), P(n_eval_ptr),
+                              P(ws_ptr), ws_bytes, int(strategy), P(_stream(stream))))
 
 
 def ms_raster_bwd_workspace_bytes(n: int) -> int:
@@ -463,10 +476,11 @@ class Renderer:
                 torch.empty((H, W), dtype=torch.int32, device=device))
 
     def render(self, scene: DeviceScene, cam: inputs.Camera, mode="selective", out=None,
-               stream=None, n_eval=None):
+               stream=None, n_eval=None, strategy="auto"):
         """Enqueue project -> bin -> raster.  Returns (image, final_t,
         n_contrib) device tensors; call `check()` after to learn D and
-        whether the capacity sufficed."""
+        whether the capacity sufficed.  `strategy` picks the raster kernel
+        ("auto", "tile" or "list", see ms_raster_ex)."""
         if cam.tiles_x * cam.tiles_y > self.max_tiles:
             raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
         cs = camera_struct(cam)
@@ -474,8 +488,9 @@ class Renderer:
         ms_project(scene.struct, cs, m, self.proj, stream)
         ms_bin(self.proj, scene.n, cs, self.bins, _ptr(self.ws), self.ws_bytes, stream)
         image, final_t, n_contrib = out if out is not None else self.images(cam)
-        ms_raster(self.proj, self.bins, cs, _ptr(image), _ptr(final_t), _ptr(n_contrib),
-                  _ptr(n_eval), _ptr(self.rws), self.rws_bytes, stream)
+        ms_raster_ex(self.proj, self.bins, cs, _ptr(image), _ptr(final_t), _ptr(n_contrib),
+                     _ptr(n_eval), _ptr(self.rws), self.rws_bytes,
+                     STRATEGIES.get(strategy, strategy), stream)
         return image, final_t, n_contrib
 
     def check(self, stream=None):

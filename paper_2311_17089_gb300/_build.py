@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmsgs.so")
-SOURCES = ["api.cu", "project.cu", "bin.cu", "raster.cu", "backward.cu", "serve.cu", "aggregate.cu"]
+SOURCES = ["api.cu", "project.cu", "bin.cu", "raster.cu", "raster_list.cu", "backward.cu",
+           "serve.cu", "aggregate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-Wall", "-I", INCLUDE, "-I", CSRC]

@@ -10,18 +10,22 @@ from __future__ import annotations
 
 import torch
 
-from . import (MODES, MsError, MS_OK, MS_MAX_BWD_VIEWS, Renderer, _ptr, bwd_view,
-               camera_struct, ms_bin, ms_bin_counts, ms_grads_t, ms_project, ms_raster,
+from . import (MODES, STRATEGIES, MsError, MS_OK, MS_MAX_BWD_VIEWS, Renderer, _ptr, bwd_view,
+               camera_struct, ms_bin, ms_bin_counts, ms_grads_t, ms_project, ms_raster_ex,
                ms_raster_bwd, ms_raster_bwd_views, ms_raster_bwd_views_workspace_bytes,
                ms_raster_bwd_workspace_bytes, ms_scene_prepare, ms_scene_t)
 from . import inputs
 
 
 class Frame:
-    """Buffers for rendering and differentiating one view."""
+    """Buffers for rendering and differentiating one view.  `strategy`
+    picks the forward's raster kernel ("auto", "tile" or "list",
+    ms_raster_ex); the backward reads either one's segment states."""
 
-    def __init__(self, n: int, cam: inputs.Camera, dup_capacity: int, device="cuda"):
+    def __init__(self, n: int, cam: inputs.Camera, dup_capacity: int, device="cuda",
+                 strategy="auto"):
         self.cam = cam
+        self.strategy = STRATEGIES.get(strategy, strategy)
         self.renderer = Renderer(n, cam.tiles_x * cam.tiles_y, dup_capacity, device=device,
                                  with_cover=False, with_mask=False)
         self.image, self.final_t, self.n_contrib = self.renderer.images(cam, device=device)
@@ -57,8 +61,8 @@ class GaussianRender(torch.autograd.Function):
         cs = camera_struct(frame.cam)
         ms_project(sc, cs, MODES.get(mode, mode), r.proj)
         ms_bin(r.proj, n, cs, r.bins, _ptr(r.ws), r.ws_bytes)
-        ms_raster(r.proj, r.bins, cs, _ptr(frame.image), _ptr(frame.final_t),
-                  _ptr(frame.n_contrib), 0, _ptr(r.rws), r.rws_bytes)
+        ms_raster_ex(r.proj, r.bins, cs, _ptr(frame.image), _ptr(frame.final_t),
+                     _ptr(frame.n_contrib), 0, _ptr(r.rws), r.rws_bytes, frame.strategy)
         ctx.frame = frame
         ctx.meta = (n, n_levels, sh_degree)
         ctx.save_for_backward(mean, log_scale, quat, opacity, color, level, s_max, s_min,
@@ -111,8 +115,8 @@ class GaussianRenderViews(torch.autograd.Function):
             cs = camera_struct(frame.cam)
             ms_project(sc, cs, MODES.get(mode, mode), r.proj)
             ms_bin(r.proj, n, cs, r.bins, _ptr(r.ws), r.ws_bytes)
-            ms_raster(r.proj, r.bins, cs, _ptr(frame.image), _ptr(frame.final_t),
-                      _ptr(frame.n_contrib), 0, _ptr(r.rws), r.rws_bytes)
+            ms_raster_ex(r.proj, r.bins, cs, _ptr(frame.image), _ptr(frame.final_t),
+                         _ptr(frame.n_contrib), 0, _ptr(r.rws), r.rws_bytes, frame.strategy)
             outs.append(frame.image.clone())
         ctx.frames = frames
         ctx.meta = (n, n_levels, sh_degree)

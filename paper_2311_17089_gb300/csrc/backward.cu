@@ -110,13 +110,6 @@ __device__ __forceinline__ float reduce_scatter9(const float v[kG2], int lane) {
     return d + __shfl_xor_sync(0xffffffffu, d, 1);
 }
 
-// Index of tile pixel (x, y) in the forward's thread layout (warp w covers
-// the 8x4 block ((w & 1) * 8, (w >> 1) * 4), lane l its pixel (l & 7, l >> 3)),
-// which is how the forward stores each segment's per-pixel state.
-__device__ __forceinline__ int fwd_index(int x, int y) {
-    return ((y >> 2) * 2 + (x >> 3)) * 32 + (y & 3) * 8 + (x & 7);
-}
-
 // Two pixels of one thread, (x, y) and (x, y + 4): the same dx for every
 // record, so their arithmetic runs as packed FP32x2 pairs.
 struct PixPair {

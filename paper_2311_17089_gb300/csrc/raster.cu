@@ -35,6 +35,7 @@
 #include "f32x2.cuh"
 #include "tma.cuh"
 #include "raster_ws.cuh"
+#include "raster_list.cuh"
 
 namespace msgs {
 
@@ -641,9 +642,12 @@ extern "C" size_t ms_raster_workspace_bytes(int64_t tiles, int64_t dup_capacity)
     return L.total;
 }
 
-extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_camera_t *cam,
-                         float *image, float *final_t, uint32_t *n_contrib, uint32_t *n_eval,
-                         void *ws, size_t ws_bytes, void *stream) {
+extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
+                            const ms_camera_t *cam, float *image, float *final_t,
+                            uint32_t *n_contrib, uint32_t *n_eval, void *ws, size_t ws_bytes,
+                            int strategy, void *stream) {
+    if (strategy != MS_RASTER_AUTO && strategy != MS_RASTER_TILE && strategy != MS_RASTER_LIST)
+        return fail(MS_ERR_INVALID_ARG, "unknown raster strategy");
     if (!proj || !bins || !cam || !image) return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
         return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
@@ -671,7 +675,14 @@ extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_
             return rc;
         attr_set = true;
     }
-    if ((rc = cuda_check(cudaMemsetAsync(w, 0, L.zero_bytes, st), "raster workspace memset")))
+    const int resident = (int)std::min<int64_t>((int64_t)raster_blocks_per_sm() * num_sms(),
+                                                kMaxResident);
+    // a frame with fewer tiles than resident CTAs cannot fill the GPU one
+    // tile per CTA: blend it list-parallel instead
+    const bool list = strategy == MS_RASTER_LIST ||
+                      (strategy == MS_RASTER_AUTO && tiles < (int64_t)resident);
+    if (!list &&
+        (rc = cuda_check(cudaMemsetAsync(w, 0, L.zero_bytes, st), "raster workspace memset")))
         return rc;
     RasterArgs a;
     a.ranges = bins->ranges;
@@ -699,10 +710,39 @@ extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_
     a.pre = reinterpret_cast<float4 *>(w + L.pre);
     a.pre2 = reinterpret_cast<uint2 *>(w + L.pre2);
     a.err = reinterpret_cast<unsigned long long *>(bins->counts) + kCntStatus;
-    const int resident = (int)std::min<int64_t>((int64_t)raster_blocks_per_sm() * num_sms(),
-                                                kMaxResident);
+    // the segmentation is the same for both kernels: the backward walks it
     segment_offsets_kernel<<<1, 1024, 0, st>>>(bins->ranges, (int)tiles, (uint32_t)resident,
                                                a.seg_off, a.seg_len);
+    if (list) {
+        ListArgs la;
+        la.ranges = a.ranges;
+        la.gidx = a.gidx;
+        la.rec = a.rec;
+        la.n_rec = a.n_rec;
+        la.W = a.W;
+        la.H = a.H;
+        la.tiles_x = a.tiles_x;
+        la.tiles = a.tiles;
+        la.bg0 = a.bg0;
+        la.bg1 = a.bg1;
+        la.bg2 = a.bg2;
+        la.image = a.image;
+        la.final_t = a.final_t;
+        la.n_contrib = a.n_contrib;
+        la.n_eval = a.n_eval;
+        la.seg_off = a.seg_off;
+        la.seg_len = a.seg_len;
+        la.pre = a.pre;
+        if ((rc = cuda_check(cudaGetLastError(), "segment offsets launch"))) return rc;
+        return cuda_check(launch_raster_list(la, st), "raster list launch");
+    }
     raster_kernel<<<resident, kRasterThreads, kSmemBytes, st>>>(a);
     return cuda_check(cudaGetLastError(), "raster launches");
+}
+
+extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_camera_t *cam,
+                         float *image, float *final_t, uint32_t *n_contrib, uint32_t *n_eval,
+                         void *ws, size_t ws_bytes, void *stream) {
+    return ms_raster_ex(proj, bins, cam, image, final_t, n_contrib, n_eval, ws, ws_bytes,
+                        MS_RASTER_AUTO, stream);
 }

@@ -34,6 +34,15 @@ struct RasterLayout {
     int64_t max_segs;
 };
 
+// Slot of tile pixel (x, y) (0..15 each) in a segment's per-pixel state
+// arrays: the tile kernel's thread layout, where warp w covers the 8x4 block
+// ((w & 1) * 8, (w >> 1) * 4) and lane l its pixel (l & 7, l >> 3).  Both
+// forward kernels store prefix states in this order and the backward reads
+// them in it.
+__host__ __device__ __forceinline__ int fwd_index(int x, int y) {
+    return ((y >> 2) * 2 + (x >> 3)) * 32 + (y & 3) * 8 + (x & 7);
+}
+
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 inline bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {

@@ -21,17 +21,17 @@ def calibrated(scene, cams):
     return oracle.calibrate(scene.copy(), cams)
 
 
-def gpu_frame(scene, cam, mode="selective", cap=None, ds=None):
-    """Run ms_project -> ms_bin -> ms_raster; return host copies."""
+def gpu_frame(scene, cam, mode="selective", cap=None, ds=None, strategy="auto"):
+    """Run ms_project -> ms_bin -> ms_raster_ex(strategy); return host copies."""
     torch = require_cuda()
     ds = ds or msgs.DeviceScene(scene)
     cap = cap or max(4096, 16 * scene.n)
     r = msgs.Renderer(scene.n, cam.tiles_x * cam.tiles_y, cap)
-    img, ft, nc = r.render(ds, cam, mode)
+    img, ft, nc = r.render(ds, cam, mode, strategy=strategy)
     rc, d, surv = msgs.ms_bin_counts(r.bins)
     if rc == msgs.MS_ERR_CAPACITY:
         r = msgs.Renderer(scene.n, cam.tiles_x * cam.tiles_y, max(d, 1))
-        img, ft, nc = r.render(ds, cam, mode)
+        img, ft, nc = r.render(ds, cam, mode, strategy=strategy)
         rc, d, surv = msgs.ms_bin_counts(r.bins)
     assert rc == msgs.MS_OK, rc
     torch.cuda.synchronize()

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 NAMES = ("mean", "log_scale", "quat", "opacity", "color")
 
 
-def gpu_grads(sc, cam, w, mode="all_levels"):
+def gpu_grads(sc, cam, w, mode="all_levels", strategy="auto"):
     torch = require_cuda()
     dev = torch.device("cuda")
     params = {k: torch.tensor(np.ascontiguousarray(getattr(sc, k), np.float32), device=dev,
@@ -22,7 +22,7 @@ def gpu_grads(sc, cam, w, mode="all_levels"):
     level = torch.tensor(sc.level, device=dev)
     smax = torch.tensor(sc.s_max, device=dev)
     smin = torch.tensor(sc.s_min, device=dev)
-    frame = ag.Frame(sc.n, cam, max(4096, 64 * sc.n), device=dev)
+    frame = ag.Frame(sc.n, cam, max(4096, 64 * sc.n), device=dev, strategy=strategy)
     img = ag.render(params, level, smax, smin, sc.n_levels, sc.sh_degree, frame, mode)
     ag.check_frame(frame)
     loss = (img * torch.tensor(w, dtype=torch.float32, device=dev)).sum()
@@ -43,16 +43,46 @@ def compare(gg, go, rel=1e-3, floor=1e-4):
         assert not bad.any(), (k, int(bad.sum()), float((err / scale).max()))
 
 
+@pytest.mark.parametrize("strategy", ["tile", "list"])
 @pytest.mark.parametrize("seed,deg,n,size", [(0, -1, 64, 64), (1, 3, 64, 64), (2, 1, 400, 96),
                                               (3, 3, 3000, 160)])
-def test_backward_matches_oracle_gradient(seed, deg, n, size):
+def test_backward_matches_oracle_gradient(seed, deg, n, size, strategy):
+    """The backward after either raster kernel's forward."""
     sc = inputs.tiny_scene(n=n, seed=seed, sh_degree=deg, extent=0.8 if n > 100 else 0.6)
     cam = inputs.config1_camera(size, size)
     cam.bg[:] = [0.2, 0.3, 0.1]
     w = np.random.default_rng(seed).standard_normal((3, size, size))
-    gg, _ = gpu_grads(sc, cam, w)
+    gg, _ = gpu_grads(sc, cam, w, strategy=strategy)
     fp = oracle.footprints(sc, cam, "all_levels")
     off, idx = oracle.tile_lists(fp, cam)
+    go = oracle.grad64(sc, cam, off, idx, w)
+    compare(gg, go)
+
+
+@pytest.mark.parametrize("strategy", ["tile", "list"])
+def test_backward_long_lists_many_segments(strategy):
+    """Thousands of faint, wide Gaussians on a 48x32 frame (6 tiles): every
+    tile's list spans several segments, so the backward starts most
+    segments from the prefix state the forward stored at its start (the
+    list kernel stores it at each segment boundary a pixel passes, the tile
+    kernel when it publishes the segment).  Pixels terminate in later
+    segments (opacity ~0.01)."""
+    rng = np.random.default_rng(11)
+    n = 4000
+    mean = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.4, 0.4, n),
+                     rng.uniform(-1.0, 1.0, n)], 1).astype(np.float32)
+    log_scale = rng.normal(np.log(6.0), 0.05, (n, 3)).astype(np.float32)
+    quat = rng.standard_normal((n, 4)).astype(np.float32)
+    opacity = rng.uniform(0.008, 0.014, n).astype(np.float32)
+    color = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    sc = inputs.Scene(mean, log_scale, quat, opacity, color, np.ones(n, np.uint8), 1, -1,
+                      np.zeros(n, np.float32), np.full(n, np.inf, np.float32))
+    cam = inputs.config1_camera(48, 32)
+    fp = oracle.footprints(sc, cam, "all_levels")
+    off, idx = oracle.tile_lists(fp, cam)
+    assert np.diff(off).min() > 4 * 256    # several 256-entry segments per tile
+    w = rng.standard_normal((3, 32, 48))
+    gg, _ = gpu_grads(sc, cam, w, strategy=strategy)
     go = oracle.grad64(sc, cam, off, idx, w)
     compare(gg, go)
 

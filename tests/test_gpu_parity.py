@@ -36,12 +36,17 @@ def test_scene_prepare_matches_oracle(cuda):
     np.testing.assert_array_equal(ds.lnop.cpu().numpy(), lnop)
 
 
+STRATEGIES = ["tile", "list"]
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
 @pytest.mark.parametrize("mode", ["all_levels", "selective"])
-def test_single_level_config_full_parity(cuda, mode):
-    """10k single-level Gaussians, 256x256 (16x16 tiles)."""
+def test_single_level_config_full_parity(cuda, mode, strategy):
+    """10k single-level Gaussians, 256x256 (16x16 tiles), with either
+    raster kernel."""
     sc = inputs.single_level_scene()
     cam = inputs.config1_camera()
-    g = gpu_frame(sc, cam, mode)
+    g = gpu_frame(sc, cam, mode, strategy=strategy)
     o = oracle.render(sc, cam, mode)
     assert_footprints_equal(g, o["fp"], sc, cam)
     assert_lists_equal(g, o["offsets"], o["idx"])
@@ -49,14 +54,15 @@ def test_single_level_config_full_parity(cuda, mode):
     assert flagged < 0.01 * cam.width * cam.height
 
 
+@pytest.mark.parametrize("strategy", STRATEGIES)
 @pytest.mark.parametrize("scale", [1, 2, 4, 8, 16, 32, 64, 128])
 @pytest.mark.parametrize("mode", ["selective", "all_levels", "filter_small"])
-def test_multiscale_all_scales(cuda, ms_scene_50k, mode, scale):
+def test_multiscale_all_scales(cuda, ms_scene_50k, mode, scale, strategy):
     """50k-Gaussian 4-level scene at every evaluation scale of 1256x832
-    (ragged right-hand tiles at most scales)."""
+    (ragged right-hand tiles at most scales), with either raster kernel."""
     sc = ms_scene_50k
     cam = inputs.downscale(inputs.config2_camera(), scale)
-    g = gpu_frame(sc, cam, mode)
+    g = gpu_frame(sc, cam, mode, strategy=strategy)
     o = oracle.render(sc, cam, mode)
     assert_footprints_equal(g, o["fp"], sc, cam)
     assert_lists_equal(g, o["offsets"], o["idx"])
@@ -151,11 +157,12 @@ def test_full_size_near_far_sampled(cuda):
 
 # ------------------------------------------------------------- edge cases
 
-def test_empty_scene(cuda):
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_empty_scene(cuda, strategy):
     sc = inputs.single_level_scene(n=0)
     cam = inputs.config1_camera(40, 24)
     cam.bg[:] = [0.25, 0.5, 1.0]
-    g = gpu_frame(sc, cam, "selective")
+    g = gpu_frame(sc, cam, "selective", strategy=strategy)
     assert g["D"] == 0
     np.testing.assert_array_equal(g["image"], np.broadcast_to(cam.bg[:, None, None], (3, 24, 40)))
     assert np.all(g["final_t"] == 1.0) and np.all(g["n_contrib"] == 0)
@@ -171,12 +178,13 @@ def test_everything_culled(cuda):
     assert np.all(g["image"] == 0.0)
 
 
+@pytest.mark.parametrize("strategy", STRATEGIES)
 @pytest.mark.parametrize("wh", [(1, 1), (33, 17), (16, 16), (17, 1), (300, 7)])
-def test_ragged_sizes(cuda, wh):
+def test_ragged_sizes(cuda, wh, strategy):
     sc = inputs.single_level_scene(n=3000, seed=4)
     cam = inputs.config1_camera(*wh)
     cam.bg[:] = [0.1, 0.2, 0.3]
-    g = gpu_frame(sc, cam, "all_levels")
+    g = gpu_frame(sc, cam, "all_levels", strategy=strategy)
     o = oracle.render(sc, cam, "all_levels")
     assert_footprints_equal(g, o["fp"], sc, cam)
     assert_lists_equal(g, o["offsets"], o["idx"])
@@ -239,15 +247,18 @@ def test_capacity_overflow_reported_then_retry(cuda):
     assert_lists_equal(g, o["offsets"], o["idx"])
 
 
+@pytest.mark.parametrize("strategy", STRATEGIES)
 @pytest.mark.parametrize("wh,n,op", [((16, 16), 6000, (0.008, 0.014)),
                                      ((48, 32), 9000, (0.008, 0.014)),
                                      ((16, 16), 1500, (0.0050, 0.0058))])
-def test_long_lists_split_across_ctas(cuda, wh, n, op):
-    """Thousands of faint, wide Gaussians on few tiles: lists are split into
-    512-entry chunks blended by different CTAs.  With opacity ~0.01 every
-    pixel's T falls about 1% per Gaussian and it terminates inside a later
-    chunk; with opacity ~0.005 over 1500 entries no pixel terminates.  The
-    merge must reproduce the sequential blend."""
+def test_long_lists_split_across_ctas(cuda, wh, n, op, strategy):
+    """Thousands of faint, wide Gaussians on few tiles.  The tile kernel
+    splits the lists into segments blended by different CTAs; the list
+    kernel walks each pixel's whole list across the lanes of one warp.
+    With opacity ~0.01 every pixel's T falls about 1% per Gaussian and it
+    terminates inside a later segment; with opacity ~0.005 over 1500
+    entries no pixel terminates.  Both must reproduce the sequential
+    blend."""
     rng = np.random.default_rng(n)
     mean = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.4, 0.4, n),
                      rng.uniform(-1.0, 1.0, n)], 1).astype(np.float32)
@@ -258,7 +269,7 @@ def test_long_lists_split_across_ctas(cuda, wh, n, op):
     sc = inputs.Scene(mean, log_scale, quat, opacity, color, np.ones(n, np.uint8), 1, -1,
                       np.zeros(n, np.float32), np.full(n, np.inf, np.float32))
     cam = inputs.config1_camera(*wh)
-    g = gpu_frame(sc, cam, "all_levels")
+    g = gpu_frame(sc, cam, "all_levels", strategy=strategy)
     o = oracle.render(sc, cam, "all_levels")
     assert_lists_equal(g, o["offsets"], o["idx"])
     assert np.diff(o["offsets"]).max() > 1024
