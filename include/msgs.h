@@ -64,7 +64,7 @@ typedef enum {
  * same blend either way, up to FP32 rounding). */
 typedef enum {
     MS_RASTER_AUTO = 0,  /* TILE when the frame has at least as many tiles as
-                            CTAs of the tile kernel fit on the GPU, else LIST */
+                            the GPU has SMs, else LIST                       */
     MS_RASTER_TILE = 1,  /* one thread per pixel; long lists split into
                             segments merged exactly across CTAs             */
     MS_RASTER_LIST = 2   /* one warp per pixel; lanes take consecutive list
