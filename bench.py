@@ -747,18 +747,33 @@ def main():
     roof_project = {"bound": "hbm", "kernel": "project_kernel",
                     "achieved": proj_bytes / proj_s / 1e9, "peak": hbm_peak, "unit": "GB/s"}
     roof_project["frac"] = roof_project["achieved"] / roof_project["peak"]
-    roof_raster = {"bound": "alu", "kernel": "raster_kernel",
+    roof_raster = {"bound": "alu", "kernel": "raster_kernel (tile) + raster_list_kernel",
                    "achieved": OPS_PER_EVAL * evals / raster_s / 1e12, "peak": alu_peak,
                    "unit": "Tops/s"}
     roof_raster["frac"] = roof_raster["achieved"] / roof_raster["peak"]
+    # the same split by kernel: ms_raster blends frames with at least as many
+    # tiles as SMs with the tile kernel, the others with the list kernel
+    by_kernel = {}
+    for cam in cams:
+        name = ("raster_kernel" if cam.tiles_x * cam.tiles_y >= torch.cuda.get_device_properties(
+            dev).multi_processor_count else "raster_list_kernel")
+        e = by_kernel.setdefault(name, {"frames": [], "P_eval": 0, "ms": 0.0})
+        e["frames"].append(f"{cam.width}x{cam.height}")
+        e["P_eval"] += stats[("selective", cam.width)]["P_eval"]
+        e["ms"] += per_scale["selective"][f"{cam.width}x{cam.height}"]["raster_ms"]
+    for e in by_kernel.values():
+        e["achieved"] = OPS_PER_EVAL * e["P_eval"] / (e["ms"] / 1e3) / 1e12
+        e["frac"] = e["achieved"] / alu_peak
+    roof_raster["by_kernel"] = by_kernel
     dominant = max(stage_ms, key=stage_ms.get)
     roof = roof_raster if dominant == "raster" else roof_project
     if dominant == "bin":
         roof = dict(roof_project)
         roof["note"] = "binning dominates; project roofline shown"
-    # DRAM bytes per launch of the dominant kernel: dram__bytes_read.sum +
+    # DRAM bytes per launch of the dominant stage: dram__bytes_read.sum +
     # dram__bytes_write.sum of one ncu capture of this sweep's eight raster
-    # launches, averaged (to be taken again whenever the kernel changes)
+    # launches (both kernels), averaged (to be taken again whenever a raster
+    # kernel changes)
     traffic = RASTER_DRAM_BYTES_PER_LAUNCH if roof is roof_raster else None
     roof = dict(roof, traffic=traffic, stage_ms_per_step=stage_ms,
                 traffic_source="ncu capture, mean over the sweep's raster launches"
