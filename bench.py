@@ -40,7 +40,7 @@ N_GAUSS = 1_000_000
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 OPS_PER_EVAL = 16          # FP32 operations per pixel-Gaussian evaluation
-RASTER_DRAM_BYTES_PER_LAUNCH = 26.30e6   # raster_kernel, selective sweep, measured
+RASTER_DRAM_BYTES_PER_LAUNCH = 23.35e6   # both raster kernels, selective sweep, measured
 
 
 def parse():
