@@ -72,6 +72,19 @@ def test_argument_errors_need_no_device():
     assert lib.ms_raster(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam), None, None, None, None, None, 0, None) == msgs.MS_ERR_INVALID_ARG
     assert msgs.ms_raster_workspace_bytes(4108, 1 << 20) > 0
     assert msgs.ms_raster_workspace_bytes(0, 1 << 20) == 0
+    # ms_raster_ex: an unknown strategy is rejected before anything else
+    fake = 1 << 20
+    fproj = msgs.ms_proj_t(fake, fake, fake, fake, 0, 0, fake, 10)
+    fbins = msgs.ms_bins_t(fake, fake, fake, 16)
+    for strategy in (-1, 3, 1000):
+        assert lib.ms_raster_ex(ctypes.byref(fproj), ctypes.byref(fbins), ctypes.byref(cam), fake,
+                                None, None, None, fake, 1 << 30, strategy,
+                                None) == msgs.MS_ERR_INVALID_ARG
+        assert b"strategy" in lib.ms_last_error()
+    for strategy in msgs.STRATEGIES.values():  # then the usual argument checks
+        assert lib.ms_raster_ex(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam), None,
+                                None, None, None, None, 0, strategy,
+                                None) == msgs.MS_ERR_INVALID_ARG
 
 
 def test_backward_argument_errors_need_no_device():
