@@ -87,6 +87,22 @@ def test_backward_long_lists_many_segments(strategy):
     compare(gg, go)
 
 
+@pytest.mark.parametrize("strategy", ["tile", "list"])
+def test_backward_deep_lists(strategy):
+    """The backward on 7.5k-8.3k-entry lists where half of the pixels
+    terminate early and the other half blend far down the list."""
+    from test_gpu_parity import deep_lists_scene
+    sc = deep_lists_scene(seed=32)
+    cam = inputs.config1_camera(48, 32)
+    w = np.random.default_rng(33).standard_normal((3, 32, 48))
+    gg, _ = gpu_grads(sc, cam, w, strategy=strategy)
+    fp = oracle.footprints(sc, cam, "all_levels")
+    off, idx = oracle.tile_lists(fp, cam)
+    assert np.diff(off).min() > 4096
+    go = oracle.grad64(sc, cam, off, idx, w)
+    compare(gg, go)
+
+
 def test_backward_multiscale_selective():
     sc = inputs.multiscale_scene(n=20_000, seed=2, box=2.0, cluster_sigma=0.5, n_clusters=16)
     cam = inputs.config2_camera(256, 192, distance=6.0)

@@ -280,6 +280,49 @@ def test_long_lists_split_across_ctas(cuda, wh, n, op, strategy):
     assert_image_close(g, o, max_flagged=0.15)
 
 
+def deep_lists_scene(seed=31):
+    """A 48x32 frame whose tile lists hold more than 4096 entries: 40k
+    faint Gaussians about 2 px wide spread over the whole view (each pixel
+    sees a few percent of its tile's list, so most pixels never terminate
+    and blend entries past 4096), and 400 large, fairly opaque ones in
+    front of the left half (those pixels terminate within the first few
+    dozen entries)."""
+    rng = np.random.default_rng(seed)
+    nf, nb = 400, 40_000
+    n = nf + nb
+    mean = np.empty((n, 3), np.float32)
+    mean[:nf] = np.stack([rng.uniform(-0.75, 0.0, nf), rng.uniform(-0.5, 0.5, nf),
+                          rng.uniform(-1.8, -1.6, nf)], 1)
+    mean[nf:] = np.stack([rng.uniform(-1.8, 1.8, nb), rng.uniform(-1.2, 1.2, nb),
+                          rng.uniform(-0.3, 0.3, nb)], 1)
+    log_scale = np.empty((n, 3), np.float32)
+    log_scale[:nf] = rng.normal(np.log(0.08), 0.1, (nf, 3))
+    log_scale[nf:] = rng.normal(np.log(0.03), 0.1, (nb, 3))
+    quat = rng.standard_normal((n, 4)).astype(np.float32)
+    opacity = np.concatenate([rng.uniform(0.5, 0.9, nf), rng.uniform(0.01, 0.03, nb)]).astype(np.float32)
+    color = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    return inputs.Scene(mean, log_scale, quat, opacity, color, np.ones(n, np.uint8), 1, -1,
+                        np.zeros(n, np.float32), np.full(n, np.inf, np.float32))
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_long_lists_early_and_deep_pixels(cuda, strategy):
+    """Six tiles whose lists hold 7.5k-8.3k entries: about half of the
+    pixels terminate within the first few dozen entries, the other half
+    blend entries past 4096 and mostly never terminate (the list kernel's
+    slowest case: one warp walks such a pixel's whole list)."""
+    sc = deep_lists_scene()
+    cam = inputs.config1_camera(48, 32)
+    o = oracle.render(sc, cam, "all_levels")
+    assert np.diff(o["offsets"]).min() > 4096 + 1024
+    early = (o["final_t"] < 1e-3) & (o["n_contrib"] < 2048)
+    deep = o["n_contrib"] > 4096 + 512
+    assert early.mean() > 0.2 and deep.mean() > 0.2, (early.mean(), deep.mean())
+    g = gpu_frame(sc, cam, "all_levels", strategy=strategy)
+    assert_lists_equal(g, o["offsets"], o["idx"])
+    assert_image_close(g, o, max_flagged=0.1)
+
+
 def test_one_long_list_among_many_tiles_and_overflow(cuda):
     """A 320-tile frame where one tile lists ~30k Gaussians among many short
     lists: lists bit-exact and image within tolerance; a capacity far below
