@@ -612,12 +612,12 @@ def main():
     bufs = [rs_mode["selective"][k].images(cam, device=dev) for k, cam in enumerate(cams)]
     streams = [torch.cuda.Stream(device=dev) for _ in cams]
 
-    def step(mode, after=None):
+    def step(mode, after=None, scene=None):
         main = torch.cuda.current_stream()
         for r, cam, out, st in zip(rs_mode[mode], cams, bufs, streams):
             st.wait_stream(main)
             with torch.cuda.stream(st):
-                r.render(ds, cam, mode, out=out, stream=st)
+                r.render(scene or ds, cam, mode, out=out, stream=st)
                 if after is not None:
                     after(out, st)
         for st in streams:
@@ -791,25 +791,50 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in host.values())
         d2h = sum(t.numel() * t.element_size() for t in outs)
 
-        def e2e_step():
-            for k, t in host.items():
-                getattr(ds, k).copy_(t, non_blocking=True)
-            msgs.ms_scene_prepare(ds.struct)
-            hb = iter(outs)
-            step("selective", after=lambda out, st: next(hb).copy_(out[0], non_blocking=True))
+        # every step uploads the whole scene and reads back all 8 images;
+        # two scene buffers let step i + 1's upload and prepare run on a copy
+        # stream while step i renders from the other buffer
+        scenes = [ds, msgs.DeviceScene(sc, device=dev, prepare=False)]
+        up = torch.cuda.Stream(device=dev)
+        ready = [torch.cuda.Event(), torch.cuda.Event()]
+        freed = [torch.cuda.Event(), torch.cuda.Event()]
 
-        for _ in range(args.warmup):
-            e2e_step()
+        def upload(i):
+            d = scenes[i % 2]
+            up.wait_event(freed[i % 2])  # the step that last rendered from it is done
+            with torch.cuda.stream(up):
+                for k, t in host.items():
+                    getattr(d, k).copy_(t, non_blocking=True)
+                msgs.ms_scene_prepare(d.struct, stream=up)
+            ready[i % 2].record(up)
+
+        def render(i):
+            main = torch.cuda.current_stream()
+            main.wait_event(ready[i % 2])
+            hb = iter(outs)
+            step("selective", after=lambda out, st: next(hb).copy_(out[0], non_blocking=True),
+                 scene=scenes[i % 2])
+            freed[i % 2].record(main)
+
+        def e2e_run(k):
+            upload(0)
+            for i in range(k):
+                if i + 1 < k:
+                    upload(i + 1)
+                render(i)
+
+        e2e_run(args.warmup)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
+        e2e_run(args.steps)
         torch.cuda.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
         barrier()
         e2e = {"value": world * frames * args.steps / t_e2e, "unit": "frames/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "pipeline": "scene upload + prepare of step i+1 on a copy stream during "
+                           "step i's render (two scene buffers); images read back per frame"}
 
     # kernels of libmsgs per frame: project; finish_counts, 4 depth passes,
     # duplicate, 1-2 tile passes, ranges; chunk offsets, raster
