@@ -382,17 +382,42 @@ duplicate_kernel(DupArgs a) {
     }
 }
 
-// [start, end) of every tile's run in the tile-sorted keys.
+// [start, end) of every tile's run in the tile-sorted keys.  Each thread
+// takes 8 consecutive keys (two 16-byte loads when the keys are 16-byte
+// aligned) and the key on either side, all loaded before any is compared,
+// so a thread has several loads in flight instead of one per key.
+constexpr uint32_t kNoTile = 0xffffffffu;
 __global__ void ranges_kernel(const uint32_t *__restrict__ keys,
                               const unsigned long long *__restrict__ dup, uint64_t cap,
                               uint32_t tiles, uint32_t *__restrict__ ranges) {
     const uint64_t n = umin64(*dup, cap);
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t k = keys[i];
-        if (k >= tiles) continue;
-        if (i == 0 || keys[i - 1] != k) ranges[2 * (uint64_t)k] = (uint32_t)i;
-        if (i + 1 == n || keys[i + 1] != k) ranges[2 * (uint64_t)k + 1] = (uint32_t)(i + 1);
+    const uint64_t chunks = (n + 7) / 8;
+    const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+    for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < chunks;
+         c += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t base = c * 8;
+        uint32_t k[8];
+        if (vec && base + 8 <= n) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(keys + base));
+            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(keys + base) + 1);
+            k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+            k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++) k[j] = base + j < n ? __ldg(keys + base + j) : kNoTile;
+        }
+        const uint32_t prev = base > 0 ? __ldg(keys + base - 1) : kNoTile;
+        const uint32_t next = base + 8 < n ? __ldg(keys + base + 8) : kNoTile;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const uint32_t kk = k[j];
+            if (kk >= tiles) continue;  // also the positions past n
+            const uint32_t left = j == 0 ? prev : k[j - 1];
+            const uint32_t right = j == 7 ? next : k[j + 1];
+            const uint32_t i = (uint32_t)(base + j);
+            if (left != kk) ranges[2 * (uint64_t)kk] = i;
+            if (right != kk) ranges[2 * (uint64_t)kk + 1] = i + 1;
+        }
     }
 }
 
