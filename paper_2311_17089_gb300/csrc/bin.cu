@@ -30,6 +30,8 @@ namespace msgs {
 constexpr int kDupThreads = 256;
 constexpr int kDupIPT = 4;
 constexpr int kDupPart = kDupThreads * kDupIPT;
+constexpr int kDupRun = 8;                      // entries one thread emits per window
+constexpr int kDupWin = kDupThreads * kDupRun;  // entries staged per window
 constexpr unsigned long long kDupFlagAgg = 1ull << 62;
 constexpr unsigned long long kDupFlagPre = 2ull << 62;
 constexpr unsigned long long kDupValMask = (1ull << 62) - 1;
@@ -252,6 +254,7 @@ duplicate_kernel(DupArgs a) {
     __shared__ uint32_t s_idx[kDupPart];
     __shared__ uint2 s_rect[kDupPart];
     __shared__ uint32_t s_hist[2][256];
+    __shared__ uint2 s_emit[kDupWin];
     __shared__ uint32_t s_warp[kSortWarps];
     __shared__ uint32_t s_part;
     __shared__ unsigned long long s_prefix;
@@ -349,30 +352,75 @@ duplicate_kernel(DupArgs a) {
         }
         __syncthreads();
         const uint64_t base = s_prefix;
-        for (uint32_t k = tid; k < total; k += kDupThreads) {
-            // last item whose offset is <= k
-            int lo = 0, hi = kDupPart;  // invariant s_off[lo] <= k < s_off[hi]
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (s_off[mid] <= k) lo = mid;
-                else hi = mid;
+        // emission in windows of kDupWin entries: each thread builds a run of
+        // kDupRun consecutive entries (one search for the run's first item,
+        // then it steps through the items' tile rectangles), the window is
+        // staged in shared memory and written out coalesced
+        for (uint32_t w0 = 0; w0 < total; w0 += kDupWin) {
+            const uint32_t k0 = w0 + (uint32_t)tid * kDupRun;
+            if (k0 < total) {
+                // last item whose offset is <= k0
+                int lo = 0, hi = kDupPart;  // invariant s_off[lo] <= k0 < s_off[hi]
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (s_off[mid] <= k0) lo = mid;
+                    else hi = mid;
+                }
+                uint2 rc = s_rect[lo];
+                uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16;
+                uint32_t w = (rc.y & 0xffffu) - x0 + 1;
+                const uint32_t m = k0 - s_off[lo];
+                uint32_t xx = m % w, yy = m / w;
+                uint32_t hb = 0xffffffffu, hc = 0;  // run of equal high bytes
+#pragma unroll 4
+                for (int r = 0; r < kDupRun; r++) {
+                    const uint32_t k = k0 + r;
+                    if (k >= total) break;
+                    while (k >= s_off[lo + 1]) {  // next item with tiles
+                        lo++;
+                        rc = s_rect[lo];
+                        x0 = rc.x & 0xffffu;
+                        y0 = rc.x >> 16;
+                        w = (rc.y & 0xffffu) - x0 + 1;
+                        xx = 0;
+                        yy = 0;
+                    }
+                    uint32_t tile = (y0 + yy) * (uint32_t)a.tiles_x + x0 + xx;
+                    if (++xx == w) {
+                        xx = 0;
+                        yy++;
+                    }
+                    if (tile >= a.tiles) {
+                        atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                        tile = 0xffffffffu;  // not written
+                    } else if (base + k < a.cap) {  // the entries the tile passes sort
+                        atomicAdd(&s_hist[0][tile & 255u], 1u);
+                        const uint32_t h = (tile >> 8) & 255u;
+                        if (h != hb) {
+                            if (hc) atomicAdd(&s_hist[1][hb], hc);
+                            hb = h;
+                            hc = 0;
+                        }
+                        hc++;
+                    }
+                    s_emit[tid * kDupRun + r] = make_uint2(tile, s_idx[lo]);
+                }
+                if (hc) atomicAdd(&s_hist[1][hb], hc);
             }
-            uint32_t m = k - s_off[lo];
-            uint2 rc = s_rect[lo];
-            uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
-            uint32_t w = x1 - x0 + 1;
-            uint32_t tile = (y0 + m / w) * (uint32_t)a.tiles_x + x0 + m % w;
-            uint64_t g = base + k;
-            if (tile >= a.tiles) {
-                atomicOr(a.err, (unsigned long long)kStatusTimeout);
-            } else if (g < a.cap) {
-                a.keys_out[g] = tile;
-                a.vals_out[g] = s_idx[lo];
-                atomicAdd(&s_hist[0][tile & 255u], 1u);
-                atomicAdd(&s_hist[1][(tile >> 8) & 255u], 1u);
-            } else {
-                atomicOr(a.err, (unsigned long long)kStatusOverflow);
+            __syncthreads();
+            const uint32_t cnt = min(total - w0, (uint32_t)kDupWin);
+            for (uint32_t j = tid; j < cnt; j += kDupThreads) {
+                const uint2 e = s_emit[j];
+                const uint64_t g = base + w0 + j;
+                if (e.x == 0xffffffffu) continue;  // reported above
+                if (g < a.cap) {
+                    a.keys_out[g] = e.x;
+                    a.vals_out[g] = e.y;
+                } else {
+                    atomicOr(a.err, (unsigned long long)kStatusOverflow);
+                }
             }
+            __syncthreads();
         }
     }
     __syncthreads();
