@@ -10,6 +10,7 @@
  *   ms_update_range   UpdateRange of the coverage bounds
  *   ms_bin            16x16 tile binning with a stable (tile, depth) order
  *   ms_raster         per-pixel front-to-back blend with early termination
+ *   ms_raster_ex      the same with the blend's parallelisation chosen
  *   ms_raster_bwd     gradient of the image with respect to the scene
  *   ms_l1_loss_grad   L1 image loss and its gradient (training step)
  *   ms_aggregate      AggregateGaussians: insert a coarse level
