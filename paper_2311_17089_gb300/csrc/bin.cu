@@ -493,7 +493,8 @@ static int launch_pass(const PassArgs &a, uint64_t bound, cudaStream_t st) {
         attr = true;
     }
     const int64_t parts = (int64_t)((bound + SortCfg<IPT>::kPart - 1) / SortCfg<IPT>::kPart);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(parts, (int64_t)num_sms() * 2));
+    const int per_sm = bound <= kSmallPassItems ? kSmallPassCtasPerSm : kLargePassCtasPerSm;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(parts, (int64_t)num_sms() * per_sm));
     onesweep_pass<IPT><<<grid, kSortThreads, SortCfg<IPT>::kSmem, st>>>(a);
     return MS_OK;
 }

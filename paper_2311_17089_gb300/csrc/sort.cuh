@@ -10,12 +10,15 @@ namespace msgs {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-// Items per thread of a partition: passes over at most kSmallPassItems
-// items use small partitions (more CTAs, shorter per-partition latency),
-// larger passes bigger ones.
+// Items per thread of a partition (2048-item partitions).  Passes over at
+// most kSmallPassItems items run 2 CTAs per SM, so that the frames rendered
+// at once share the GPU; larger passes 4, for more loads in flight (their
+// 16-item, 2-CTA variant was 1-4% slower on the large passes).
 constexpr int kSmallIPT = 8;
-constexpr int kLargeIPT = 16;
+constexpr int kLargeIPT = 8;
 constexpr uint64_t kSmallPassItems = 2ull << 20;
+constexpr int kSmallPassCtasPerSm = 2;
+constexpr int kLargePassCtasPerSm = 4;
 constexpr int kDigits = 256;
 constexpr int kScanWarps = kDigits / 32;
 constexpr uint32_t kFlagAgg = 1u << 30;
