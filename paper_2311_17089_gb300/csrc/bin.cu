@@ -9,7 +9,7 @@
 // over D entries).  Stability gives every tile's list in (depth, index)
 // order, exactly the order of a (tile, depth, index) sort.
 //
-// Onesweep pass (single-pass LSD radix step): each CTA takes a 4096-item
+// Onesweep pass (single-pass LSD radix step): each CTA takes a 2048-item
 // partition by atomic ticket, ranks its items stably per 8-bit digit with
 // warp match, publishes its per-digit counts and obtains the counts of all
 // earlier partitions by decoupled look-back, then scatters through shared
