@@ -89,13 +89,16 @@ onesweep_pass(PassArgs a) {
     __shared__ uint32_t s_base[kDigits];
     __shared__ uint32_t s_excl[kDigits];
     __shared__ uint32_t s_prefix[kDigits];
+    __shared__ uint32_t s_gofs[kDigits];
     __shared__ uint32_t s_warp[kScanWarps];
     __shared__ uint32_t s_part;
     __shared__ uint32_t s_total;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t n = pass_count(a);
-    const uint64_t parts = (n + kPart - 1) / kPart;
+    // a pass holds fewer than 2^31 items (capacity <= 2^30, scenes < 2^31),
+    // so item indices and scatter positions are 32-bit
+    const uint32_t n = (uint32_t)pass_count(a);
+    const uint32_t parts = (n + kPart - 1) / kPart;
     {
         uint32_t tot;
         uint32_t b = block_excl_scan256(tid < kDigits ? a.hist[tid] : 0u, s_warp, tot);
@@ -112,16 +115,16 @@ onesweep_pass(PassArgs a) {
         // rank (warp-striped, rounds in item order)
         uint32_t key[IPT], val[IPT], rank[IPT];
         bool ok[IPT];
-        const uint64_t wbase = (uint64_t)p * kPart + (uint64_t)warp * 32 * IPT;
+        const uint32_t wbase = p * (uint32_t)kPart + (uint32_t)warp * 32u * IPT;
 #pragma unroll
         for (int r = 0; r < IPT; r++) {
-            const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+            const uint32_t i = wbase + (uint32_t)r * 32u + lane;
             ok[r] = i < n;
             if (a.filter && ok[r]) ok[r] = __ldg(a.filter + i) > 0;
         }
 #pragma unroll
         for (int r = 0; r < IPT; r++) {
-            const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+            const uint32_t i = wbase + (uint32_t)r * 32u + lane;
             key[r] = ok[r] ? a.keys_in[i] : 0u;
             val[r] = ok[r] ? (a.vals_in ? a.vals_in[i] : (uint32_t)i) : 0u;
         }
@@ -194,7 +197,12 @@ onesweep_pass(PassArgs a) {
         }
         uint32_t tot;
         const uint32_t ex = block_excl_scan256(local, s_warp, tot);
-        if (tid < kDigits) s_excl[d] = ex;
+        if (tid < kDigits) {
+            s_excl[d] = ex;
+            // output position of the partition's j-th staged item of digit d
+            // is s_gofs[d] + j (modulo 2^32)
+            s_gofs[d] = s_base[d] + s_prefix[d] - ex;
+        }
         if (tid == 0) s_total = tot;
         __syncthreads();
         // ---- stage digit-sorted in shared memory
@@ -210,9 +218,8 @@ onesweep_pass(PassArgs a) {
         // ---- coalesced scatter
         const uint32_t total = s_total;
         for (uint32_t j = tid; j < total; j += kSortThreads) {
-            uint32_t k = s_keys[j];
-            uint32_t dd = (k >> a.shift) & 255u;
-            uint64_t g = (uint64_t)s_base[dd] + s_prefix[dd] + (j - s_excl[dd]);
+            const uint32_t k = s_keys[j];
+            const uint32_t g = s_gofs[(k >> a.shift) & 255u] + j;
             if (g >= n) {  // only reachable after a wait gave up
                 atomicOr(a.err, (unsigned long long)kStatusTimeout);
                 continue;
