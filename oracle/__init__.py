@@ -79,7 +79,7 @@ def lib():
         L.or_tile_lists.restype = I64
         L.or_sh_basis64.argtypes = [I32, P, P]
         L.or_colors64.argtypes = [I64, P, P, I32, P, P]
-        L.or_render64.argtypes = [I64, P, P, P, P, P, P, P, I32, D, D, P, P, P, P]
+        L.or_render64.argtypes = [I64, P, P, P, P, P, P, P, I32, D, D, P, P, P, P, P]
         L.or_render64.restype = I64
         L.or_render64_brute.argtypes = [I64, P, P, P, P, D, P, P, P]
         L.or_render64_brute.restype = I64
@@ -178,6 +178,7 @@ def render(scene, cam, mode="selective", tiles=None, prepared=None,
     image = np.full((3, H, W), np.nan)
     final_t = np.full((H, W), np.nan)
     n_contrib = np.zeros((H, W), np.uint32)
+    n_eval = np.zeros((H, W), np.int64)
     flags = np.zeros((H, W), np.uint8)
     cs = camera_struct(cam)
     sel = None
@@ -188,9 +189,9 @@ def render(scene, cam, mode="selective", tiles=None, prepared=None,
         _p(offsets), _p(idx if len(idx) else np.zeros(1, np.uint32)),
         _p(sel) if sel is not None else None,
         0 if sel is None else len(sel), alpha_flag_rel, t_flag_rel,
-        _p(image), _p(final_t), _p(n_contrib), _p(flags))
+        _p(image), _p(final_t), _p(n_contrib), _p(flags), _p(n_eval))
     return dict(image=image, final_t=final_t, n_contrib=n_contrib,
-                flags=flags, evals=int(evals), fp=fp, offsets=offsets,
+                flags=flags, evals=int(evals), n_eval=n_eval, fp=fp, offsets=offsets,
                 idx=idx, rgb=rgb)
 
 

@@ -80,7 +80,7 @@ int64_t or_render64(int64_t n, const or_fp *fp, const float *opacity,
                     const int32_t *tile_sel, int32_t n_tile_sel,
                     double alpha_flag_rel, double t_flag_rel,
                     double *image, double *final_t, uint32_t *n_contrib,
-                    uint8_t *flags);
+                    uint8_t *flags, int64_t *n_eval);
 
 int64_t or_render64_brute(int64_t n, const or_fp *fp, const float *opacity,
                           const double *rgb, const or_camera *cam,

@@ -143,13 +143,17 @@ static void blend_pixel(const uint32_t *list, int64_t len, const or_fp *fp,
     }
 }
 
+/* Per-tile FP64 blend over the lists of step 1.  n_eval (may be NULL)
+ * receives, per pixel, the list entries evaluated up to and including the
+ * one that ended the pixel (the whole list if none did); the return value is
+ * their sum over the rendered pixels. */
 int64_t or_render64(int64_t n, const or_fp *fp, const float *opacity,
                     const double *rgb, const or_camera *cam,
                     const int64_t *offsets, const uint32_t *idx,
                     const int32_t *tile_sel, int32_t n_tile_sel,
                     double alpha_flag_rel, double t_flag_rel,
                     double *image, double *final_t, uint32_t *n_contrib,
-                    uint8_t *flags)
+                    uint8_t *flags, int64_t *n_eval)
 {
     (void)n;
     int W = cam->width, H = cam->height;
@@ -175,6 +179,8 @@ int64_t or_render64(int64_t n, const or_fp *fp, const float *opacity,
                 final_t[p] = st.T;
                 n_contrib[p] = st.n_contrib;
                 flags[p] = st.flags;
+                if (n_eval)
+                    n_eval[p] = st.evals;
                 evals += st.evals;
             }
     }

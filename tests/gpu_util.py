@@ -27,11 +27,12 @@ def gpu_frame(scene, cam, mode="selective", cap=None, ds=None, strategy="auto"):
     ds = ds or msgs.DeviceScene(scene)
     cap = cap or max(4096, 16 * scene.n)
     r = msgs.Renderer(scene.n, cam.tiles_x * cam.tiles_y, cap)
-    img, ft, nc = r.render(ds, cam, mode, strategy=strategy)
+    ne = torch.empty((cam.height, cam.width), dtype=torch.int32, device=ds.mean.device)
+    img, ft, nc = r.render(ds, cam, mode, strategy=strategy, n_eval=ne)
     rc, d, surv = msgs.ms_bin_counts(r.bins)
     if rc == msgs.MS_ERR_CAPACITY:
         r = msgs.Renderer(scene.n, cam.tiles_x * cam.tiles_y, max(d, 1))
-        img, ft, nc = r.render(ds, cam, mode, strategy=strategy)
+        img, ft, nc = r.render(ds, cam, mode, strategy=strategy, n_eval=ne)
         rc, d, surv = msgs.ms_bin_counts(r.bins)
     assert rc == msgs.MS_OK, rc
     torch.cuda.synchronize()
@@ -40,6 +41,7 @@ def gpu_frame(scene, cam, mode="selective", cap=None, ds=None, strategy="auto"):
     out = dict(
         image=img.cpu().numpy(), final_t=ft.cpu().numpy(),
         n_contrib=nc.cpu().numpy().view(np.uint32),
+        n_eval=ne.cpu().numpy().view(np.uint32),
         n_tiles=r.n_tiles.cpu().numpy().view(np.uint32)[:scene.n],
         depth=r.depth.cpu().numpy().view(np.uint32)[:scene.n],
         rect=r.rect.cpu().numpy().view(np.uint32).reshape(n, 2)[:scene.n],
@@ -105,7 +107,7 @@ def assert_lists_equal(g, offsets, idx):
 
 
 def assert_image_close(g, o, tiles=None, cam=None, atol=IMAGE_ATOL, max_flagged=0.02):
-    """Colour, final T and contributor count on pixels where no evaluation
+    """Colour, final T, contributor and evaluation counts on pixels where no evaluation
     sat on a threshold (flag bit 0: alpha near 1/255; bit 1: T (1 - alpha)
     near 1e-4).  A flip at either threshold changes the pixel by up to
     alpha T, not bounded by atol, so flagged pixels are only counted."""
@@ -123,4 +125,6 @@ def assert_image_close(g, o, tiles=None, cam=None, atol=IMAGE_ATOL, max_flagged=
     terr = np.abs(g["final_t"] - o["final_t"])[ok]
     assert terr.size == 0 or terr.max() <= atol, terr.max()
     np.testing.assert_array_equal(g["n_contrib"][ok], o["n_contrib"][ok])
+    # the evaluation count behind the benchmark's roofline (P_eval)
+    np.testing.assert_array_equal(g["n_eval"][ok].astype(np.int64), o["n_eval"][ok])
     return float(err.max()) if err.size else 0.0, int(region.sum() - ok.sum())

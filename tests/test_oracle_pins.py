@@ -293,6 +293,39 @@ def test_white_scene_telescopes(orc):
     assert np.any(r["final_t"] < 1e-3)
 
 
+def test_evaluation_counts(orc):
+    """The per-pixel evaluation count (the work the raster roofline counts):
+    every entry of the tile's list up to and including the one that ended
+    the pixel, else the whole list.  The ending entry is a Gaussian with
+    alpha >= 1/255 at the pixel that would bring the final T below 1e-4
+    (Eq. 3, stop before it), it comes after the last blended entry, and the
+    counts sum to the returned total."""
+    cam = inputs.config1_camera(128, 96)
+    sc = inputs.single_level_scene(n=12000, seed=5)
+    r = orc.render(sc, cam, "all_levels")
+    ne, nc, ft = r["n_eval"], r["n_contrib"].astype(np.int64), r["final_t"]
+    off, idx, fp = r["offsets"], r["idx"], r["fp"]
+    assert ne.sum() == r["evals"]
+    lens = np.diff(off)
+    ended = 0
+    for y in range(cam.height):
+        for x in range(cam.width):
+            t = (y // 16) * cam.tiles_x + x // 16
+            n = int(ne[y, x])
+            assert nc[y, x] < n <= lens[t] or nc[y, x] == n == lens[t]
+            if n == lens[t]:
+                continue
+            g = idx[off[t] + n - 1]
+            dx, dy = x + 0.5 - float(fp["ux"][g]), y + 0.5 - float(fp["uy"][g])
+            a, b, c = (float(v) for v in fp["conic"][g])
+            power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+            alpha = min(0.99, float(sc.opacity[g]) * math.exp(power))
+            assert power <= 0.0 and alpha >= 1.0 / 255.0
+            assert ft[y, x] * (1.0 - alpha) < 1e-4
+            ended += 1
+    assert ended > 200
+
+
 def test_brute_force_equals_tiled(orc):
     """Per-pixel blending of every selected Gaussian in one global depth
     order, with no tiles, equals the tiled render bit for bit wherever no
