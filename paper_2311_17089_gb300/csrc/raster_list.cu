@@ -158,57 +158,64 @@ __global__ void __launch_bounds__(256) raster_list_kernel(ListArgs a) {
                 cr[q] = r1.z;  // slots past the list's end hold zeros
                 cg[q] = r1.w;
                 cb[q] = r2.x;
-                float v = __fsub_rn(1.0f, al[q]);
+            }
+            // a sub-batch no lane accepts (common for pixels far down a list
+            // in a sparse region) leaves T and the colour unchanged
+            if (__any_sync(kFull, accm != 0u)) {
 #pragma unroll
-                for (uint32_t o = 1; o < 32u; o <<= 1) {
-                    const float y = __shfl_up_sync(kFull, v, o);
-                    if (lane >= o) v = __fmul_rn(v, y);
+                for (int q = 0; q < kListSteps; q++) {
+                    float v = __fsub_rn(1.0f, al[q]);
+#pragma unroll
+                    for (uint32_t o = 1; o < 32u; o <<= 1) {
+                        const float y = __shfl_up_sync(kFull, v, o);
+                        if (lane >= o) v = __fmul_rn(v, y);
+                    }
+                    inc[q] = v;
+                    tot[q] = __shfl_sync(kFull, v, 31);
                 }
-                inc[q] = v;
-                tot[q] = __shfl_sync(kFull, v, 31);
-            }
-            // phase 2: T before each step, T after every entry, and the
-            // first step with an accepted entry that would bring T below
-            // 1e-4 (T is monotone, so later steps cannot end it sooner)
-            float tin[kListSteps], ta[kListSteps];
-            uint32_t tm[kListSteps];
-            tin[0] = T;
+                // phase 2: T before each step, T after every entry, and the
+                // first step with an accepted entry that would bring T below
+                // 1e-4 (T is monotone, so later steps cannot end it sooner)
+                float tin[kListSteps], ta[kListSteps];
+                uint32_t tm[kListSteps];
+                tin[0] = T;
 #pragma unroll
-            for (int q = 1; q < kListSteps; q++) tin[q] = __fmul_rn(tin[q - 1], tot[q - 1]);
+                for (int q = 1; q < kListSteps; q++) tin[q] = __fmul_rn(tin[q - 1], tot[q - 1]);
 #pragma unroll
-            for (int q = 0; q < kListSteps; q++) {
-                ta[q] = __fmul_rn(tin[q], inc[q]);
-                tm[q] = __ballot_sync(kFull, ((accm >> q) & 1u) && ta[q] < kListTStop);
-            }
-            int qt = kListSteps;
+                for (int q = 0; q < kListSteps; q++) {
+                    ta[q] = __fmul_rn(tin[q], inc[q]);
+                    tm[q] = __ballot_sync(kFull, ((accm >> q) & 1u) && ta[q] < kListTStop);
+                }
+                int qt = kListSteps;
 #pragma unroll
-            for (int q = kListSteps - 1; q >= 0; q--)
-                if (tm[q]) qt = q;
-            uint32_t kt = 32u;
+                for (int q = kListSteps - 1; q >= 0; q--)
+                    if (tm[q]) qt = q;
+                uint32_t kt = 32u;
 #pragma unroll
-            for (int q = 0; q < kListSteps; q++)
-                if (q == qt) kt = (uint32_t)__ffs(tm[q]) - 1u;
-            // blend the entries before the end: alpha_k T_{k-1} rgb_k
-            float tend = 0.0f;
+                for (int q = 0; q < kListSteps; q++)
+                    if (q == qt) kt = (uint32_t)__ffs(tm[q]) - 1u;
+                // blend the entries before the end: alpha_k T_{k-1} rgb_k
+                float tend = 0.0f;
 #pragma unroll
-            for (int q = 0; q < kListSteps; q++) {
-                if (q > qt) break;
-                float tb = __shfl_up_sync(kFull, ta[q], 1);  // T before this lane's entry
-                if (lane == 0) tb = tin[q];
-                const bool bl = ((accm >> q) & 1u) && (q < qt || lane < kt);
-                const float wgt = bl ? __fmul_rn(al[q], tb) : 0.0f;
-                c0 = __fmaf_rn(wgt, cr[q], c0);
-                c1 = __fmaf_rn(wgt, cg[q], c1);
-                c2 = __fmaf_rn(wgt, cb[q], c2);
-                if (bl) last = base + (uint32_t)q * 32u + lane + 1u;
-                if (q == qt) tend = tb;
-            }
-            if (qt < kListSteps) {
-                T = __shfl_sync(kFull, tend, kt);  // T before the entry that ends the pixel
-                evals = base + (uint32_t)qt * 32u + kt + 1u;
-                live = false;
-            } else {
-                T = __fmul_rn(tin[kListSteps - 1], tot[kListSteps - 1]);
+                for (int q = 0; q < kListSteps; q++) {
+                    if (q > qt) break;
+                    float tb = __shfl_up_sync(kFull, ta[q], 1);  // T before this lane's entry
+                    if (lane == 0) tb = tin[q];
+                    const bool bl = ((accm >> q) & 1u) && (q < qt || lane < kt);
+                    const float wgt = bl ? __fmul_rn(al[q], tb) : 0.0f;
+                    c0 = __fmaf_rn(wgt, cr[q], c0);
+                    c1 = __fmaf_rn(wgt, cg[q], c1);
+                    c2 = __fmaf_rn(wgt, cb[q], c2);
+                    if (bl) last = base + (uint32_t)q * 32u + lane + 1u;
+                    if (q == qt) tend = tb;
+                }
+                if (qt < kListSteps) {
+                    T = __shfl_sync(kFull, tend, kt);  // T before the entry that ends the pixel
+                    evals = base + (uint32_t)qt * 32u + kt + 1u;
+                    live = false;
+                } else {
+                    T = __fmul_rn(tin[kListSteps - 1], tot[kListSteps - 1]);
+                }
             }
             // segment boundaries fall on sub-batch ends (L is a multiple of
             // the sub-batch): the state after segment (base + batch) / L - 1,
