@@ -610,7 +610,10 @@ def main():
                                  with_cover=False, with_mask=False) for cam in cams]
                for m in ("selective", "all_levels")}
     bufs = [rs_mode["selective"][k].images(cam, device=dev) for k, cam in enumerate(cams)]
-    streams = [torch.cuda.Stream(device=dev) for _ in cams]
+    # the three finest frames (the tile kernel's) have the longest chains:
+    # their streams get the higher priority
+    streams = [torch.cuda.Stream(device=dev, priority=(-1 if k < 3 else 0))
+               for k, _ in enumerate(cams)]
 
     def step(mode, after=None, scene=None):
         main = torch.cuda.current_stream()
