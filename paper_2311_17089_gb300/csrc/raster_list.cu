@@ -15,6 +15,10 @@
 //   - The first accepted entry whose T_k falls below 1e-4 ends the pixel
 //     (it is not blended); the entries before it add alpha_k T_{k-1} rgb_k
 //     into per-lane partial colours, summed across the warp at the end.
+//   - A warp takes its entries in sub-batches of four such steps; one vote
+//     per sub-batch skips the scans and the blend of a sub-batch in which
+//     no lane accepts its entry (a pixel far down a list in a sparse
+//     region sees many).
 // The result is the sequential blend up to FP32 rounding of the products.
 // Nothing is speculative: a CTA walks its tile's list only until all of its
 // pixels have terminated.  At every boundary of the frame's segmentation
