@@ -83,6 +83,27 @@ def config(n, extra=None):
     return c
 
 
+# ---------------------------------------------------------- replicas
+
+def reduce_max(x: float, world: int, device) -> float:
+    """The largest of the ranks' values (the job's time is its slowest
+    rank's); every rank gets it.  `device`: a CUDA device under NCCL, the
+    CPU under gloo."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput of N replicas: every rank renders the same
+    number of units, the time is the slowest rank's (reduce_max)."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -565,11 +586,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, dev)
 
     sc, cams, calib = workload(args.n)
     ds = msgs.DeviceScene(sc, device=dev)
@@ -700,8 +717,8 @@ def main():
     t_all = timed("all_levels", args.steps)
 
     frames = len(cams)
-    value = world * frames * args.steps / t_sel
-    value_all = world * frames * args.steps / t_all
+    value = job_rate(frames * args.steps, world, t_sel)
+    value_all = job_rate(frames * args.steps, world, t_all)
 
     # per-scale and per-stage timing (events on the launching stream)
     per_scale = {"selective": {}, "all_levels": {}}
@@ -834,7 +851,7 @@ def main():
         torch.cuda.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
         barrier()
-        e2e = {"value": world * frames * args.steps / t_e2e, "unit": "frames/s",
+        e2e = {"value": job_rate(frames * args.steps, world, t_e2e), "unit": "frames/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "pipeline": "scene upload + prepare of step i+1 on a copy stream during "
                            "step i's render (two scene buffers); images read back per frame"}
