@@ -643,7 +643,10 @@ __global__ void __launch_bounds__(kProjBwdWarps * 32)
 project_bwd_kernel(const __grid_constant__ ProjBwdArgs p) {
     using CR = ColorRows<DEG>;
     extern __shared__ float s_rows[];
+    __shared__ CamB s_cam[kMaxViews];  // lanes on different views read them at once
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < p.n_views; k += blockDim.x) s_cam[k] = p.cam[k];
+    __syncthreads();
     float *s_coef = s_rows + wid * CR::WARP_FLOATS;
     float *s_dcol = s_coef + 32 * CR::STRIDE;
     const bool acc = p.out.acc;
@@ -676,10 +679,18 @@ project_bwd_kernel(const __grid_constant__ ProjBwdArgs p) {
         __syncwarp();
         float dm[3] = {0.0f, 0.0f, 0.0f}, dls[3] = {0.0f, 0.0f, 0.0f};
         float dq[4] = {0.0f, 0.0f, 0.0f, 0.0f}, dop = 0.0f;
-        for (int k = 0; k < p.n_views; k++)
-            if (vmask >> k & 1u)
-                view_chain<DEG>(p.sc, p.cam[k], p.g2[k] + i * kG2, i, dm, dls, dq, dop,
+        // each lane walks its own views in ascending order (the order of the
+        // sums is the same for every lane), so a round is idle only for lanes
+        // with fewer views, not for every view another lane needs
+        uint32_t m = vmask;
+        while (__any_sync(0xffffffffu, m != 0u)) {
+            if (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1u;
+                view_chain<DEG>(p.sc, s_cam[k], p.g2[k] + i * kG2, i, dm, dls, dq, dop,
                                 s_coef + lane * CR::STRIDE, s_dcol + lane * CR::STRIDE);
+            }
+        }
         __syncwarp();
         for (int e = lane; e < rows * CR::RS; e += 32) {
             const int r = e / CR::RS;
