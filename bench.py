@@ -492,7 +492,8 @@ def serve_bench(msgs, torch, dev, n_requests, n_gauss, loads=(0.5, 0.7, 0.9)):
         st = srv.stats()
         srv.close()
         out[mode] = {"capacity": cap, "poisson": loads_out,
-                     "peak_inflight": st.peak_inflight, "arena_peak_gb": st.arena_peak / 1e9}
+                     "peak_inflight": st.peak_inflight, "arena_peak_gb": st.arena_peak / 1e9,
+                     "issue_us_per_render": st.issue_seconds / max(st.renders, 1) * 1e6}
     return {"metric": "serve p50/p99 ms", "value": out["selective"]["poisson"][-1]["p99_ms"],
             "unit": "ms (p99 at 0.9 load, selective)", "higher_is_better": False,
             "selective": out["selective"], "all_levels": out["all_levels"],

@@ -502,6 +502,9 @@ typedef struct {
     int64_t submitted, completed, failed, retries;
     int32_t queued, inflight, peak_inflight, scenes;
     size_t arena_bytes, arena_used, arena_peak;
+    int64_t renders;           /* renders enqueued (requests plus re-renders)  */
+    double issue_seconds;      /* scheduler time spent enqueuing them: the
+                                  host cost of the launches and copies         */
 } ms_serve_stats_t;
 
 /* Seconds on the monotonic clock the server stamps results with. */

@@ -105,7 +105,8 @@ class ms_serve_stats_t(ctypes.Structure):
                 ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32),
                 ("peak_inflight", ctypes.c_int32), ("scenes", ctypes.c_int32),
                 ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
-                ("arena_peak", ctypes.c_size_t)]
+                ("arena_peak", ctypes.c_size_t), ("renders", ctypes.c_int64),
+                ("issue_seconds", ctypes.c_double)]
 
 
 # (name, restype, argtypes) of every entry point declared in include/msgs.h

@@ -169,7 +169,8 @@ struct ms_server {
     std::unordered_map<uint64_t, msgs::Request *> reqs;
     uint64_t next_ticket = 1;
     int inflight = 0, peak_inflight = 0, next_stream = 0;
-    int64_t submitted = 0, completed = 0, failed = 0, retries = 0;
+    int64_t submitted = 0, completed = 0, failed = 0, retries = 0, renders = 0;
+    double issue_s = 0;
     bool stop = false;
     std::thread sched;
 };
@@ -323,8 +324,12 @@ void scheduler(ms_server *s) {
             cudaStream_t st = s->streams[s->next_stream];
             s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
             lk.unlock();
+            const double t_issue = now_s();
             const int rc = launch(s, q, st);
+            const double t_issued = now_s();
             lk.lock();
+            s->renders++;
+            s->issue_s += t_issued - t_issue;
             if (rc != MS_OK) {
                 // whatever was enqueued before the failure may still run:
                 // keep the range until the stream has drained
@@ -500,6 +505,8 @@ extern "C" int ms_serve_stats(ms_server_t *s, ms_serve_stats_t *st) {
     st->arena_bytes = s->arena.size();
     st->arena_used = s->arena.used();
     st->arena_peak = s->arena.peak();
+    st->renders = s->renders;
+    st->issue_seconds = s->issue_s;
     return MS_OK;
 }
 

@@ -91,6 +91,7 @@ def test_host_output_and_memory_admission(scenes):
         st = srv.stats()
     assert all(r.status == msgs.MS_OK for r in results)
     assert st.arena_peak <= st.arena_bytes <= budget
+    assert st.renders == st.completed + st.retries and st.issue_seconds > 0
     assert results[0].bytes == one
     assert st.peak_inflight * min(r.bytes for r in results) <= budget
     assert st.peak_inflight < len(hosts)
