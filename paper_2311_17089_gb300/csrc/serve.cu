@@ -24,6 +24,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "arena.h"
 #include "common.cuh"
 #include "raster_ws.cuh"
 
@@ -38,54 +39,6 @@ double now_s() {
     using clk = std::chrono::steady_clock;
     return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
 }
-
-// First-fit allocator over [0, size): free ranges keyed by offset, merged
-// with their neighbours on release.
-class Arena {
-  public:
-    void init(size_t size) {
-        size_ = size;
-        free_.clear();
-        if (size) free_[0] = size;
-        used_ = peak_ = 0;
-    }
-    bool alloc(size_t bytes, size_t &off) {
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < bytes) continue;
-            off = it->first;
-            const size_t rest = it->second - bytes;
-            free_.erase(it);
-            if (rest) free_[off + bytes] = rest;
-            used_ += bytes;
-            peak_ = std::max(peak_, used_);
-            return true;
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        used_ -= bytes;
-        auto next = free_.lower_bound(off);
-        if (next != free_.end() && off + bytes == next->first) {
-            bytes += next->second;
-            next = free_.erase(next);
-        }
-        if (next != free_.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == off) {
-                prev->second += bytes;
-                return;
-            }
-        }
-        free_[off] = bytes;
-    }
-    size_t size() const { return size_; }
-    size_t used() const { return used_; }
-    size_t peak() const { return peak_; }
-
-  private:
-    size_t size_ = 0, used_ = 0, peak_ = 0;
-    std::map<size_t, size_t> free_;
-};
 
 struct Layout {  // byte offsets of one request's buffers inside its range
     size_t rec, rect, n_tiles, depth, stats, gidx, ranges, counts, bin_ws, bin_ws_bytes, rws,
