@@ -202,15 +202,17 @@ def train_setup(msgs, torch, ds, sc, dev):
     bwd_ws = torch.empty(bwd_bytes, dtype=torch.uint8, device=dev)
 
     def forward():
-        # the views are independent: each renders and takes its loss on its
-        # own stream
+        # one projection pass for the four views; then each view bins,
+        # blends and takes its loss on its own stream
         msgs.ms_scene_prepare(ds.struct)
         loss.zero_()
         main = torch.cuda.current_stream()
+        msgs.ms_project_views(ds.struct, css, msgs.MODES["selective"], [r.proj for r in rs],
+                              main)
         for r, cam, out, tgt, dl, st in zip(rs, cams, outs, targets, dls, streams):
             st.wait_stream(main)
             with torch.cuda.stream(st):
-                r.render(ds, cam, "selective", out=out, stream=st)
+                r.bin_raster(ds, cam, out=out, stream=st)
                 cnt = out[0].numel()
                 msgs.ms_l1_loss_grad(msgs._ptr(out[0]), msgs._ptr(tgt), cnt, 1.0 / cnt,
                                      msgs._ptr(dl), msgs._ptr(loss), stream=st)
@@ -266,10 +268,10 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
     for r in rs:
         r.check()
     finite = all(bool(torch.isfinite(t).all()) for t in grads_t.values())
-    launches = 1
+    launches = 2                                    # prepare; one projection for the views
     for cam in cams:
         tiles = cam.tiles_x * cam.tiles_y
-        launches += 1 + (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2 + 1
+        launches += (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2 + 1
     launches += 2                                   # batched backward: raster, projection
     return {"metric": "bwd it/s", "value": 1.0 / t_step, "unit": "it/s",
             "ms_per_step": 1e3 * t_step, "fwd_ms": fwd / steps, "bwd_ms": bwd / steps,
@@ -633,12 +635,25 @@ def main():
     streams = [torch.cuda.Stream(device=dev, priority=(-1 if k < 3 else 0))
                for k, _ in enumerate(cams)]
 
-    def step(mode, after=None, scene=None):
+    css = [msgs.camera_struct(cam) for cam in cams]
+
+    def step(mode, after=None, scene=None, views=True):
+        # views: one projection pass for the eight frames (they share the
+        # camera centre, so a Gaussian listed at several scales is coloured
+        # once), then each frame's binning and blend on its own stream;
+        # otherwise each frame projects on its own stream
         main = torch.cuda.current_stream()
+        d = scene or ds
+        if views:
+            msgs.ms_project_views(d.struct, css, msgs.MODES[mode],
+                                  [r.proj for r in rs_mode[mode]], main)
         for r, cam, out, st in zip(rs_mode[mode], cams, bufs, streams):
             st.wait_stream(main)
             with torch.cuda.stream(st):
-                r.render(scene or ds, cam, mode, out=out, stream=st)
+                if views:
+                    r.bin_raster(d, cam, out=out, stream=st)
+                else:
+                    r.render(d, cam, mode, out=out, stream=st)
                 if after is not None:
                     after(out, st)
         for st in streams:
@@ -678,6 +693,14 @@ def main():
         return g
 
     g_step = {m: capture(lambda m=m: step(m)) for m in ("selective", "all_levels")}
+    g_views = capture(lambda: msgs.ms_project_views(ds.struct, css, msgs.MODES["selective"],
+                                                    [r.proj for r in rs_mode["selective"]]))
+    # Gaussians listed in at least one frame: each reads its SH row once
+    listed_any = torch.zeros(sc.n, dtype=torch.bool, device=dev)
+    g_views.replay()
+    for r in rs_mode["selective"]:
+        listed_any |= r.n_tiles[:sc.n] != 0
+    n_listed_any = int(listed_any.sum().item())
     g_stage = {}
     for mode in ("selective", "all_levels"):
         for r, cam, out in zip(rs_mode[mode], cams, bufs):
@@ -743,8 +766,16 @@ def main():
                 "fps": 1e3 / sum(ms), "project_ms": ms[0], "bin_ms": ms[1],
                 "raster_ms": ms[2], **stats[(mode, cam.width)]}
             if mode == "selective":
-                for k, name in enumerate(("project", "bin", "raster")):
+                for k, name in (1, "bin"), (2, "raster"):
                     stage_ms[name] += ms[k]
+    # the sweep projects its eight frames in one launch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        g_views.replay()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    stage_ms["project"] = ev[0].elapsed_time(ev[1]) / reps
     clk = clocks.stop()
 
     # roofline of the dominant stage of the selective step
@@ -756,16 +787,19 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     n = sc.n
-    proj_bytes = 0
+    # one pass: the geometry (53 B) once; per frame the tile count (4 B) of
+    # every Gaussian and the 48-B record of each survivor; the SH row and
+    # opacity (196 B) once per Gaussian listed in any frame
+    proj_bytes = 53 * n + 196 * n_listed_any
     evals = 0
     for cam in cams:
         s = stats[("selective", cam.width)]
-        proj_bytes += 57 * n + (192 + 4 + 48) * s["survivors"]
+        proj_bytes += 4 * n + 48 * s["survivors"]
         evals += s["P_eval"]
     proj_s = stage_ms["project"] / 1e3
     raster_s = stage_ms["raster"] / 1e3
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2070.0e6 / 1e12   # T ops/s at max clock
-    roof_project = {"bound": "hbm", "kernel": "project_kernel",
+    roof_project = {"bound": "hbm", "kernel": f"project_kernel ({len(cams)} views, one launch)",
                     "achieved": proj_bytes / proj_s / 1e9, "peak": hbm_peak, "unit": "GB/s"}
     roof_project["frac"] = roof_project["achieved"] / roof_project["peak"]
     roof_raster = {"bound": "alu", "kernel": "raster_kernel (tile) + raster_list_kernel",
@@ -833,8 +867,12 @@ def main():
             main = torch.cuda.current_stream()
             main.wait_event(ready[i % 2])
             hb = iter(outs)
+            # per-frame projections: with the next scene's upload sharing the
+            # host link, frames that finish staggered overlap their
+            # read-backs with it better than frames released together by one
+            # projection pass (1.47-1.50 vs 1.51 ms per step)
             step("selective", after=lambda out, st: next(hb).copy_(out[0], non_blocking=True),
-                 scene=scenes[i % 2])
+                 scene=scenes[i % 2], views=False)
             freed[i % 2].record(main)
 
         def e2e_run(k):
@@ -857,12 +895,13 @@ def main():
                "pipeline": "scene upload + prepare of step i+1 on a copy stream during "
                            "step i's render (two scene buffers); images read back per frame"}
 
-    # kernels of libmsgs per frame: project; finish_counts, 4 depth passes,
-    # duplicate, 1-2 tile passes, ranges; chunk offsets, raster
-    launches_per_step = 0
+    # kernels of libmsgs per step: one projection for every frame; per frame
+    # finish_counts, 4 depth passes, duplicate, 1-2 tile passes, ranges;
+    # chunk offsets, raster
+    launches_per_step = 1
     for cam in cams:
         tiles = cam.tiles_x * cam.tiles_y
-        launches_per_step += 1 + (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2
+        launches_per_step += (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2
 
     train = None
     if not args.no_train:

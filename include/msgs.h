@@ -6,6 +6,7 @@
  *
  *   ms_scene_prepare  per-scene activations (exp(log_scale), ln(255 sigma))
  *   ms_project        EWA splat, pixel coverage, selection, SH colour
+ *   ms_project_views  the same for up to MS_MAX_PROJ_VIEWS cameras in one pass
  *   ms_select         re-run the selection predicate on stored coverage
  *   ms_update_range   UpdateRange of the coverage bounds
  *   ms_bin            16x16 tile binning with a stable (tile, depth) order
@@ -204,6 +205,21 @@ int ms_scene_prepare(const ms_scene_t *scene, void *stream);
  */
 int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
                ms_mode_t mode, const ms_proj_t *out, void *stream);
+
+#define MS_MAX_PROJ_VIEWS 8
+
+/*
+ * ms_project for n_views cameras at once (1..MS_MAX_PROJ_VIEWS): outs[v]
+ * receives, bit for bit, what ms_project(scene, &cams[v], mode, &outs[v])
+ * writes.  One pass over the scene reads each Gaussian's geometry once and
+ * forms its 3D covariance once; the camera-dependent steps run per view,
+ * and views whose cameras share a centre (campos) share the listed
+ * Gaussians' SH colour (the multi-scale setting of Sec. 4: one pose at
+ * several resolutions).  cams and outs are host arrays of n_views entries;
+ * the outs[v] must not overlap one another.
+ */
+int ms_project_views(const ms_scene_t *scene, const ms_camera_t *cams, int32_t n_views,
+                     ms_mode_t mode, const ms_proj_t *outs, void *stream);
 
 /*
  * Selection predicate alone (Eq. 6, Sec. 4.1 exemptions) on a coverage

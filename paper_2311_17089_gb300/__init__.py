@@ -116,6 +116,9 @@ _SIGNATURES = [
     ("ms_scene_prepare", ctypes.c_int, [ctypes.POINTER(ms_scene_t), P]),
     ("ms_project", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
                                   ctypes.c_int, ctypes.POINTER(ms_proj_t), P]),
+    ("ms_project_views", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
+                                        ctypes.c_int32, ctypes.c_int, ctypes.POINTER(ms_proj_t),
+                                        P]),
     ("ms_select", ctypes.c_int, [ctypes.POINTER(ms_scene_t), P, ctypes.c_int, P, P]),
     ("ms_update_range", ctypes.c_int, [ctypes.POINTER(ms_scene_t),
                                        ctypes.POINTER(ms_camera_t), ctypes.c_int32, P]),
@@ -231,6 +234,21 @@ def ms_scene_prepare(scene: ms_scene_t, stream=None):
 def ms_project(scene: ms_scene_t, cam: ms_camera_t, mode: int, out: ms_proj_t, stream=None):
     _check(lib().ms_project(ctypes.byref(scene), ctypes.byref(cam), int(mode),
                             ctypes.byref(out), P(_stream(stream))))
+
+
+MS_MAX_PROJ_VIEWS = 8
+
+
+def ms_project_views(scene: ms_scene_t, cams, mode: int, outs, stream=None):
+    """ms_project for len(cams) <= MS_MAX_PROJ_VIEWS cameras in one pass;
+    outs[v] (an ms_proj_t) receives view v's outputs."""
+    n = len(cams)
+    if len(outs) != n:
+        raise MsError(MS_ERR_INVALID_ARG, "one ms_proj_t per camera")
+    ca = (ms_camera_t * max(n, 1))(*cams)
+    oa = (ms_proj_t * max(n, 1))(*outs)
+    _check(lib().ms_project_views(ctypes.byref(scene), ca, n, int(mode), oa,
+                                  P(_stream(stream))))
 
 
 def ms_select(scene: ms_scene_t, cover_ptr: int, mode: int, mask_ptr: int, stream=None):
@@ -484,9 +502,16 @@ class Renderer:
         ("auto", "tile" or "list", see ms_raster_ex)."""
         if cam.tiles_x * cam.tiles_y > self.max_tiles:
             raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
+        ms_project(scene.struct, camera_struct(cam), MODES.get(mode, mode), self.proj, stream)
+        return self.bin_raster(scene, cam, out, stream, n_eval, strategy)
+
+    def bin_raster(self, scene: DeviceScene, cam: inputs.Camera, out=None, stream=None,
+                   n_eval=None, strategy="auto"):
+        """Enqueue bin -> raster of this renderer's projection (left by
+        ms_project or ms_project_views for `cam`)."""
+        if cam.tiles_x * cam.tiles_y > self.max_tiles:
+            raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
         cs = camera_struct(cam)
-        m = MODES.get(mode, mode)
-        ms_project(scene.struct, cs, m, self.proj, stream)
         ms_bin(self.proj, scene.n, cs, self.bins, _ptr(self.ws), self.ws_bytes, stream)
         image, final_t, n_contrib = out if out is not None else self.images(cam)
         ms_raster_ex(self.proj, self.bins, cs, _ptr(image), _ptr(final_t), _ptr(n_contrib),
@@ -499,6 +524,41 @@ class Renderer:
         if rc == MS_ERR_CAPACITY:
             raise MsError(rc, f"tile duplicates {d} exceed capacity {self.dup_capacity}")
         return d, s
+
+
+def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=None,
+                 streams=None, strategy="auto"):
+    """Several frames of one scene: one ms_project_views pass for every
+    (up to MS_MAX_PROJ_VIEWS) cameras on the current stream, then each
+    frame's bin -> raster on its own stream (streams[v], or the current
+    stream), which the current stream waits for.  renderers[v] holds frame
+    v's buffers.  Returns the (image, final_t, n_contrib) of every frame."""
+    import torch
+    n = len(cams)
+    if len(renderers) != n or (outs is not None and len(outs) != n):
+        raise MsError(MS_ERR_INVALID_ARG, "one renderer (and output) per camera")
+    for r, cam in zip(renderers, cams):
+        if cam.tiles_x * cam.tiles_y > r.max_tiles:
+            raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
+    main = torch.cuda.current_stream()
+    m = MODES.get(mode, mode)
+    for v0 in range(0, n, MS_MAX_PROJ_VIEWS):
+        sl = slice(v0, min(n, v0 + MS_MAX_PROJ_VIEWS))
+        ms_project_views(scene.struct, [camera_struct(c) for c in cams[sl]], m,
+                         [r.proj for r in renderers[sl]], main)
+    res = []
+    for v, (r, cam) in enumerate(zip(renderers, cams)):
+        st = streams[v] if streams is not None else main
+        if st is not main:
+            st.wait_stream(main)
+        with torch.cuda.stream(st):
+            res.append(r.bin_raster(scene, cam, None if outs is None else outs[v], st,
+                                    strategy=strategy))
+    if streams is not None:
+        for st in streams:
+            if st is not main:
+                main.wait_stream(st)
+    return res
 
 
 def render(scene: inputs.Scene, cam: inputs.Camera, mode="selective", dup_capacity=None):

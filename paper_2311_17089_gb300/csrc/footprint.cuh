@@ -47,25 +47,17 @@ struct Foot {
 
 __device__ __forceinline__ bool fin(float v) { return isfinite(v); }
 
-// FP32 footprint (Sec. 3.1 EWA splat, Eq. 4 dilation by 0.3 px^2,
-// Sec. 4.1 pixel coverage, Sec. 3.1 16x16 tiles).
-__device__ __forceinline__ void footprint(const float m[3], const float s[3],
-                                          float4 q, float L, const CamK &c,
-                                          Foot &o) {
-    o.valid = false;
-    o.S = -1.0f;
-    o.ntiles = 0;
-    o.x0 = o.y0 = 0;
-    o.x1 = o.y1 = -1;
-    const float *W = c.W;
-    float tx = fa(fa(fa(fm(W[0], m[0]), fm(W[1], m[1])), fm(W[2], m[2])), c.t[0]);
-    float ty = fa(fa(fa(fm(W[3], m[0]), fm(W[4], m[1])), fm(W[5], m[2])), c.t[1]);
-    float tz = fa(fa(fa(fm(W[6], m[0]), fm(W[7], m[1])), fm(W[8], m[2])), c.t[2]);
-    o.depth = __float_as_uint(tz);
+// The view-independent part of the footprint (Sec. 3.1): the 3D covariance
+// Sigma = R S S^T R^T of the Gaussian, R from the normalised quaternion q,
+// as its six distinct entries (xx, xy, xz, yy, yz, zz).  False when q has
+// no finite positive norm (the Gaussian is then invalid in every view).
+__device__ __forceinline__ bool cov3d(const float s[3], float4 q, float S6[6]) {
     float n2 = fa(fa(fa(fm(q.x, q.x), fm(q.y, q.y)), fm(q.z, q.z)), fm(q.w, q.w));
-    if (!(L > 0.0f) || !fin(L) || !(tz > c.near_plane) || !fin(tz) ||
-        !(n2 > 0.0f) || !fin(n2))
-        return;
+    if (!(n2 > 0.0f) || !fin(n2)) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) S6[k] = 0.0f;
+        return false;
+    }
     float rn = fdv(1.0f, fsq(n2));
     float w = fm(q.x, rn), x = fm(q.y, rn), y = fm(q.z, rn), z = fm(q.w, rn);
     float xx = fm(x, x), yy = fm(y, y), zz = fm(z, z);
@@ -86,16 +78,33 @@ __device__ __forceinline__ void footprint(const float m[3], const float s[3],
     for (int r = 0; r < 3; r++)
 #pragma unroll
         for (int k = 0; k < 3; k++) M[3 * r + k] = fm(R[3 * r + k], s[k]);
-    float S3[9];
+    int j = 0;
 #pragma unroll
     for (int r = 0; r < 3; r++)
 #pragma unroll
-        for (int k = r; k < 3; k++) {
-            float v = fa(fa(fm(M[3 * r], M[3 * k]), fm(M[3 * r + 1], M[3 * k + 1])),
+        for (int k = r; k < 3; k++)
+            S6[j++] = fa(fa(fm(M[3 * r], M[3 * k]), fm(M[3 * r + 1], M[3 * k + 1])),
                          fm(M[3 * r + 2], M[3 * k + 2]));
-            S3[3 * r + k] = v;
-            S3[3 * k + r] = v;
-        }
+    return true;
+}
+
+// FP32 footprint in one camera (Sec. 3.1 EWA splat, Eq. 4 dilation by
+// 0.3 px^2, Sec. 4.1 pixel coverage, Sec. 3.1 16x16 tiles) from the mean,
+// the 3D covariance of cov3d (cov_ok its result) and L = ln(255 sigma).
+__device__ __forceinline__ void footprint_cov(const float m[3], const float S6[6], bool cov_ok,
+                                              float L, const CamK &c, Foot &o) {
+    o.valid = false;
+    o.S = -1.0f;
+    o.ntiles = 0;
+    o.x0 = o.y0 = 0;
+    o.x1 = o.y1 = -1;
+    const float *W = c.W;
+    float tx = fa(fa(fa(fm(W[0], m[0]), fm(W[1], m[1])), fm(W[2], m[2])), c.t[0]);
+    float ty = fa(fa(fa(fm(W[3], m[0]), fm(W[4], m[1])), fm(W[5], m[2])), c.t[1]);
+    float tz = fa(fa(fa(fm(W[6], m[0]), fm(W[7], m[1])), fm(W[8], m[2])), c.t[2]);
+    o.depth = __float_as_uint(tz);
+    if (!(L > 0.0f) || !fin(L) || !(tz > c.near_plane) || !fin(tz) || !cov_ok) return;
+    const float S3[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
     float limx = fm(1.3f, fdv(fm(0.5f, (float)c.width), c.fx));
     float limy = fm(1.3f, fdv(fm(0.5f, (float)c.height), c.fy));
     float xr = fdv(tx, tz), yr = fdv(ty, tz);
@@ -156,6 +165,14 @@ __device__ __forceinline__ void footprint(const float m[3], const float s[3],
         o.y1 = (int)y1;
         o.ntiles = (uint32_t)((o.x1 - o.x0 + 1) * (o.y1 - o.y0 + 1));
     }
+}
+
+// The footprint of one Gaussian in one camera.
+__device__ __forceinline__ void footprint(const float m[3], const float s[3], float4 q,
+                                          float L, const CamK &c, Foot &o) {
+    float S6[6];
+    const bool ok = cov3d(s, q, S6);
+    footprint_cov(m, S6, ok, L, c, o);
 }
 
 struct SceneK {

@@ -8,6 +8,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cstring>
+
 #include "common.cuh"
 #include "footprint.cuh"
 #include "tma.cuh"
@@ -287,35 +289,83 @@ __device__ __forceinline__ void issue_chunk(const SceneK &sc, int64_t c, ProjSta
     }
 }
 
+// The outputs of one view (the buffers of its ms_proj_t).
+struct ProjOut {
+    float4 *rec;
+    uint2 *rect;
+    uint32_t *n_tiles, *depth;
+    float *cover;
+    uint32_t *mask, *stats;
+};
+
+// The cameras and outputs of one launch.  color_src[v] is the first view
+// whose camera centre equals view v's (bitwise), so views that share a
+// centre share the SH colour of a Gaussian listed in both.
+template <int MAXV>
+struct ProjViews {
+    int n_views;
+    int color_src[MAXV];
+    CamK cam[MAXV];
+    ProjOut out[MAXV];
+};
+
+// Depth-digit histograms in shared memory hold two 16-bit counts per word
+// (digits 2k and 2k + 1 of word k).  A CTA adds at most one count per pass
+// and view for each Gaussian, so flushing them to global memory at least
+// every kHistFlushChunks chunks keeps every count below 2^16.
+constexpr int kHistFlushChunks = 255;
+static_assert(kHistFlushChunks * kProjThreads < 65536, "16-bit digit counts");
+
+template <int MAXV>
+__device__ __forceinline__ void flush_hist(uint32_t (*s_hist)[4][128], const ProjViews<MAXV> &pv) {
+    for (int k = threadIdx.x; k < pv.n_views * 512; k += blockDim.x) {
+        const int v = k >> 9, w = k & 511;
+        uint32_t &word = (&s_hist[v][0][0])[w];
+        const uint32_t x = word;
+        if (x) {
+            const int pass = w >> 7, d = (w & 127) * 2;
+            uint32_t *g = pv.out[v].stats + kStatHist + 256 * pass + d;
+            if (x & 0xffffu) atomicAdd(g, x & 0xffffu);
+            if (x >> 16) atomicAdd(g + 1, x >> 16);
+            word = 0;
+        }
+    }
+}
+
 // K1: one thread per Gaussian, chunks of kProjThreads Gaussians per CTA
 // (grid-stride).  While a chunk is processed, the geometry of the CTA's
 // next chunk streams into the other stage buffer (full chunks of 16-byte
 // aligned arrays; the ragged last chunk, or unaligned arrays, read global
-// memory directly).  Writes the footprint outputs, the raster record of
-// listed Gaussians, and accumulates the survivor count, the duplicate count
-// and the four depth-digit histograms that the binning stage's radix sort
-// needs.
-__global__ void __launch_bounds__(kProjThreads, kProjBlocksPerSM)
-project_kernel(SceneK sc, CamK cam, int mode, bool staged_ok, float4 *__restrict__ rec,
-               uint2 *__restrict__ rect, uint32_t *__restrict__ n_tiles,
-               uint32_t *__restrict__ depth, float *__restrict__ cover,
-               uint32_t *__restrict__ mask, uint32_t *__restrict__ stats) {
-    __shared__ uint32_t s_hist[4][256];
-    __shared__ uint32_t s_surv;
-    __shared__ unsigned long long s_dup;
+// memory directly).  The 3D covariance of a Gaussian is formed once; then,
+// view by view, its footprint, selection and (for listed Gaussians) record
+// are written to that view's outputs, with the survivor count, the
+// duplicate count and the four depth-digit histograms that the binning
+// stage's radix sort needs.
+// CTAs per SM: one view fits 64 registers; the view loop keeps the
+// Gaussian's geometry and covariance live across views and gets 80.
+template <int MAXV>
+constexpr int proj_blocks_per_sm() { return MAXV == 1 ? kProjBlocksPerSM : 3; }
+
+template <int MAXV>
+__global__ void __launch_bounds__(kProjThreads, proj_blocks_per_sm<MAXV>())
+project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, bool staged_ok) {
+    __shared__ uint32_t s_hist[MAXV][4][128];
+    __shared__ uint32_t s_surv[MAXV];
+    __shared__ unsigned long long s_dup[MAXV];
     __shared__ __align__(128) ProjStage s_st[2];
     __shared__ __align__(8) uint64_t s_bar[2];
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < MAXV * 512; i += blockDim.x) (&s_hist[0][0][0])[i] = 0;
+    if (threadIdx.x < MAXV) {
+        s_surv[threadIdx.x] = 0;
+        s_dup[threadIdx.x] = 0;
+    }
     if (threadIdx.x == 0) {
-        s_surv = 0;
-        s_dup = 0;
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    uint32_t my_surv = 0;
-    unsigned long long my_dup = 0;
+    const int nv = MAXV == 1 ? 1 : pv.n_views;
     const int64_t nchunks = (sc.n + kProjThreads - 1) / kProjThreads;
     auto full = [&](int64_t c) { return staged_ok && (c + 1) * kProjThreads <= sc.n; };
     if ((int64_t)blockIdx.x < nchunks && full(blockIdx.x)) issue_chunk(sc, blockIdx.x, s_st[0], &s_bar[0]);
@@ -334,23 +384,21 @@ project_kernel(SceneK sc, CamK cam, int mode, bool staged_ok, float4 *__restrict
             par ^= 1u << b;
             if (!ok) {  // copies still out: this chunk reads global memory
                 staged = false;
-                atomicOr(stats + kStatStatus, (uint32_t)kStatusTimeout);
+                for (int v = 0; v < pv.n_views; v++)
+                    atomicOr(pv.out[v].stats + kStatStatus, (uint32_t)kStatusTimeout);
             }
         }
         const ProjStage &st = s_st[b];
         const int64_t base = c * kProjThreads;
         const int t = threadIdx.x;
-        int64_t i = base + t;
-        bool in = i < sc.n;
-        Foot f;
-        f.valid = false;
-        f.ntiles = 0;
-        f.S = -1.0f;
-        bool sel = false;
+        const int64_t i = base + t;
+        const bool in = i < sc.n;
+        float m[3] = {0.0f, 0.0f, 0.0f}, S6[6], lnop_i = 0.0f, smax_i = 0.0f, smin_i = 0.0f;
+        int level_i = 0;
+        bool cov_ok = false;
         if (in) {
-            float m[3], sv[3], lnop_i, smax_i, smin_i;
+            float sv[3];
             float4 q;
-            int level_i;
             if (staged) {
                 m[0] = st.mean[3 * t];
                 m[1] = st.mean[3 * t + 1];
@@ -376,55 +424,73 @@ project_kernel(SceneK sc, CamK cam, int mode, bool staged_ok, float4 *__restrict
                 smin_i = sc.s_min[i];
                 level_i = sc.level[i];
             }
-            footprint(m, sv, q, lnop_i, cam, f);
-            if (f.valid) sel = select_pred(f.S, level_i, sc.n_levels, smax_i, smin_i, mode);
-            bool listed = sel && f.ntiles > 0;
-            n_tiles[i] = listed ? f.ntiles : 0u;
-            if (cover) cover[i] = f.S;
-            if (listed) {
-                float op = sc.opacity[i];
-                float3 col = gaussian_color(sc.color, sc.sh_degree, i, m[0] - cam.campos[0],
-                                            m[1] - cam.campos[1], m[2] - cam.campos[2]);
-                // conic pre-scaled so power * log2(e) = A dx^2 + B dx dy + C dy^2
-                rec[3 * i + 0] = make_float4(f.ux, f.uy, fm(kConicA, f.ca), fm(kConicB, f.cb));
-                rec[3 * i + 1] = make_float4(fm(kConicA, f.cc), op, col.x, col.y);
-                // alpha >= 1/255 <=> power * log2(e) >= -ln(255 sigma) log2(e)
-                rec[3 * i + 2] = make_float4(col.z, fm(-kLog2e, lnop_i), f.ex, f.ey);
-                rect[i] = make_uint2((uint32_t)f.x0 | ((uint32_t)f.y0 << 16),
-                                     (uint32_t)f.x1 | ((uint32_t)f.y1 << 16));
-                depth[i] = f.depth;
-                my_surv++;
-                my_dup += f.ntiles;
-                atomicAdd(&s_hist[0][f.depth & 255], 1u);
-                atomicAdd(&s_hist[1][(f.depth >> 8) & 255], 1u);
-                atomicAdd(&s_hist[2][(f.depth >> 16) & 255], 1u);
-                atomicAdd(&s_hist[3][f.depth >> 24], 1u);
+            cov_ok = cov3d(sv, q, S6);
+        }
+        float3 col = make_float3(0.0f, 0.0f, 0.0f);
+        float op = 0.0f;
+        int col_src = -1;  // view whose camera centre col was evaluated towards
+        for (int v = 0; v < nv; v++) {
+            const CamK &cam = pv.cam[v];
+            const ProjOut &o = pv.out[v];
+            bool sel = false, listed = false;
+            uint32_t ntiles = 0;
+            if (in) {
+                Foot f;
+                footprint_cov(m, S6, cov_ok, lnop_i, cam, f);
+                if (f.valid) sel = select_pred(f.S, level_i, sc.n_levels, smax_i, smin_i, mode);
+                listed = sel && f.ntiles > 0;
+                ntiles = listed ? f.ntiles : 0u;
+                o.n_tiles[i] = ntiles;
+                if (o.cover) o.cover[i] = f.S;
+                if (listed) {
+                    const int src = pv.color_src[v];
+                    if (src != col_src) {
+                        if (col_src < 0) op = sc.opacity[i];
+                        col = gaussian_color(sc.color, sc.sh_degree, i, m[0] - cam.campos[0],
+                                             m[1] - cam.campos[1], m[2] - cam.campos[2]);
+                        col_src = src;
+                    }
+                    // conic pre-scaled so power * log2(e) = A dx^2 + B dx dy + C dy^2
+                    o.rec[3 * i + 0] = make_float4(f.ux, f.uy, fm(kConicA, f.ca), fm(kConicB, f.cb));
+                    o.rec[3 * i + 1] = make_float4(fm(kConicA, f.cc), op, col.x, col.y);
+                    // alpha >= 1/255 <=> power * log2(e) >= -ln(255 sigma) log2(e)
+                    o.rec[3 * i + 2] = make_float4(col.z, fm(-kLog2e, lnop_i), f.ex, f.ey);
+                    o.rect[i] = make_uint2((uint32_t)f.x0 | ((uint32_t)f.y0 << 16),
+                                           (uint32_t)f.x1 | ((uint32_t)f.y1 << 16));
+                    o.depth[i] = f.depth;
+                    uint32_t(*h)[128] = s_hist[MAXV == 1 ? 0 : v];
+#pragma unroll
+                    for (int p = 0; p < 4; p++) {
+                        const uint32_t d = (f.depth >> (8 * p)) & 255u;
+                        atomicAdd(&h[p][d >> 1], 1u << (16 * (d & 1u)));
+                    }
+                }
+            }
+            if (o.mask) {
+                const uint32_t bits = __ballot_sync(0xffffffffu, in && sel);
+                if ((threadIdx.x & 31) == 0 && in) o.mask[i >> 5] = bits;
+            }
+            // ntiles <= 2^22 per Gaussian, so a warp's sum fits 32 bits
+            const uint32_t ws = __reduce_add_sync(0xffffffffu, listed ? 1u : 0u);
+            const uint32_t wd = __reduce_add_sync(0xffffffffu, ntiles);
+            if ((threadIdx.x & 31) == 0 && ws) {
+                atomicAdd(&s_surv[MAXV == 1 ? 0 : v], ws);
+                atomicAdd(&s_dup[MAXV == 1 ? 0 : v], (unsigned long long)wd);
             }
         }
-        if (mask) {
-            uint32_t bits = __ballot_sync(0xffffffffu, in && sel);
-            if ((threadIdx.x & 31) == 0 && in) mask[i >> 5] = bits;
-        }
         __syncthreads();  // the buffer is refilled by the next iteration but one
+        if ((it + 1) % kHistFlushChunks == 0) {
+            flush_hist<MAXV>(s_hist, pv);
+            __syncthreads();
+        }
     }
-    // block reduction of the counters
-    for (int o = 16; o > 0; o >>= 1) {
-        my_surv += __shfl_xor_sync(0xffffffffu, my_surv, o);
-        my_dup += __shfl_xor_sync(0xffffffffu, my_dup, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (my_surv) atomicAdd(&s_surv, my_surv);
-        if (my_dup) atomicAdd(&s_dup, my_dup);
-    }
+    flush_hist<MAXV>(s_hist, pv);
     __syncthreads();
-    for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
-        uint32_t v = (&s_hist[0][0])[k];
-        if (v) atomicAdd(&stats[kStatHist + k], v);
-    }
-    if (threadIdx.x == 0) {
-        if (s_surv) atomicAdd(&stats[kStatSurvivors], s_surv);
-        if (s_dup)
-            atomicAdd(reinterpret_cast<unsigned long long *>(stats + kStatDup), s_dup);
+    if (threadIdx.x < nv) {
+        const int v = threadIdx.x;
+        uint32_t *stats = pv.out[v].stats;
+        if (s_surv[v]) atomicAdd(&stats[kStatSurvivors], s_surv[v]);
+        if (s_dup[v]) atomicAdd(reinterpret_cast<unsigned long long *>(stats + kStatDup), s_dup[v]);
     }
 }
 
@@ -480,34 +546,77 @@ extern "C" int ms_scene_prepare(const ms_scene_t *scene, void *stream) {
     return cuda_check(cudaGetLastError(), "prepare_kernel launch");
 }
 
-extern "C" int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
-                          ms_mode_t mode, const ms_proj_t *out, void *stream) {
-    int rc = check_scene(scene, true);
-    if (rc) return rc;
-    if ((rc = check_cam(cam))) return rc;
-    if (mode != MS_SELECTIVE && mode != MS_ALL_LEVELS && mode != MS_FILTER_SMALL)
-        return fail(MS_ERR_INVALID_ARG, "unknown mode");
+namespace msgs {
+namespace {
+
+int check_proj_out(const ms_scene_t *scene, const ms_proj_t *out) {
     if (!out || !out->rec || !out->rect || !out->n_tiles || !out->depth || !out->stats)
         return fail(MS_ERR_INVALID_ARG, "ms_proj_t has a NULL required buffer");
     if (out->n < scene->n) return fail(MS_ERR_INVALID_ARG, "ms_proj_t holds fewer Gaussians than the scene");
     if (!aligned(out->rec, 16) || !aligned(out->rect, 8) || !aligned(out->stats, 16))
         return fail(MS_ERR_INVALID_ARG, "rec must be 16-B, rect 8-B, stats 16-B aligned");
-    cudaStream_t st = as_stream(stream);
-    if ((rc = cuda_check(cudaMemsetAsync(out->stats, 0, MS_STATS_WORDS * sizeof(uint32_t), st),
-                         "stats memset")))
-        return rc;
-    if (scene->n == 0) return MS_OK;
+    return MS_OK;
+}
+
+template <int MAXV>
+int launch_project(const ms_scene_t *scene, const ms_camera_t *cams, int nv, ms_mode_t mode,
+                   const ms_proj_t *outs, cudaStream_t st) {
+    ProjViews<MAXV> pv;
+    pv.n_views = nv;
+    for (int v = 0; v < MAXV; v++) {
+        const int u = v < nv ? v : 0;
+        pv.cam[v] = make_cam(cams[u]);
+        const ms_proj_t &o = outs[u];
+        pv.out[v] = ProjOut{reinterpret_cast<float4 *>(o.rec), reinterpret_cast<uint2 *>(o.rect),
+                            o.n_tiles, o.depth, o.cover, o.mask, o.stats};
+        pv.color_src[v] = v;
+        for (int w = 0; w < v && v < nv; w++)
+            if (std::memcmp(cams[w].campos, cams[v].campos, sizeof(cams[v].campos)) == 0) {
+                pv.color_src[v] = w;
+                break;
+            }
+    }
     // bulk staging needs every geometry array 16-byte aligned
     const bool staged_ok = aligned(scene->mean, 16) && aligned(scene->scale, 16) &&
                            aligned(scene->quat, 16) && aligned(scene->lnop, 16) &&
                            aligned(scene->s_max, 16) && aligned(scene->s_min, 16) &&
                            aligned(scene->level, 16);
-    project_kernel<<<grid_for(scene->n, kProjThreads, kProjBlocksPerSM), kProjThreads, 0, st>>>(
-        make_scene(*scene), make_cam(*cam), (int)mode, staged_ok,
-        reinterpret_cast<float4 *>(out->rec),
-        reinterpret_cast<uint2 *>(out->rect), out->n_tiles, out->depth, out->cover, out->mask,
-        out->stats);
+    project_kernel<MAXV><<<grid_for(scene->n, kProjThreads, proj_blocks_per_sm<MAXV>()),
+                           kProjThreads, 0, st>>>(
+        make_scene(*scene), pv, (int)mode, staged_ok);
     return cuda_check(cudaGetLastError(), "project_kernel launch");
+}
+
+}  // namespace
+}  // namespace msgs
+
+extern "C" int ms_project_views(const ms_scene_t *scene, const ms_camera_t *cams,
+                                int32_t n_views, ms_mode_t mode, const ms_proj_t *outs,
+                                void *stream) {
+    int rc = check_scene(scene, true);
+    if (rc) return rc;
+    if (n_views < 1 || n_views > MS_MAX_PROJ_VIEWS)
+        return fail(MS_ERR_INVALID_ARG, "n_views must be 1..MS_MAX_PROJ_VIEWS");
+    if (!cams || !outs) return fail(MS_ERR_INVALID_ARG, "cams/outs is NULL");
+    if (mode != MS_SELECTIVE && mode != MS_ALL_LEVELS && mode != MS_FILTER_SMALL)
+        return fail(MS_ERR_INVALID_ARG, "unknown mode");
+    for (int v = 0; v < n_views; v++) {
+        if ((rc = check_cam(&cams[v]))) return rc;
+        if ((rc = check_proj_out(scene, &outs[v]))) return rc;
+    }
+    cudaStream_t st = as_stream(stream);
+    for (int v = 0; v < n_views; v++)
+        if ((rc = cuda_check(cudaMemsetAsync(outs[v].stats, 0, MS_STATS_WORDS * sizeof(uint32_t), st),
+                             "stats memset")))
+            return rc;
+    if (scene->n == 0) return MS_OK;
+    if (n_views == 1) return launch_project<1>(scene, cams, 1, mode, outs, st);
+    return launch_project<MS_MAX_PROJ_VIEWS>(scene, cams, n_views, mode, outs, st);
+}
+
+extern "C" int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
+                          ms_mode_t mode, const ms_proj_t *out, void *stream) {
+    return ms_project_views(scene, cam, 1, mode, out, stream);
 }
 
 extern "C" int ms_select(const ms_scene_t *scene, const float *cover, ms_mode_t mode,

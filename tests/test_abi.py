@@ -61,6 +61,20 @@ def test_argument_errors_need_no_device():
     assert lib.ms_scene_prepare(ctypes.byref(sc), None) == msgs.MS_ERR_INVALID_ARG
     sc.n = 10
     assert lib.ms_project(ctypes.byref(sc), ctypes.byref(cam), 0, ctypes.byref(proj), None) == msgs.MS_ERR_INVALID_ARG
+    # ms_project_views: the view count and the arrays are checked first
+    empty = msgs.ms_scene_t()
+    cams2 = (msgs.ms_camera_t * 2)(cam, cam)
+    projs2 = (msgs.ms_proj_t * 2)(proj, proj)
+    for n_views in (0, -1, msgs.MS_MAX_PROJ_VIEWS + 1):
+        assert lib.ms_project_views(ctypes.byref(empty), cams2, n_views, 0, projs2,
+                                    None) == msgs.MS_ERR_INVALID_ARG
+        assert b"n_views" in lib.ms_last_error()
+    assert lib.ms_project_views(ctypes.byref(empty), None, 1, 0, projs2, None) == msgs.MS_ERR_INVALID_ARG
+    assert lib.ms_project_views(ctypes.byref(empty), cams2, 1, 0, None, None) == msgs.MS_ERR_INVALID_ARG
+    assert lib.ms_project_views(ctypes.byref(empty), cams2, 2, 7, projs2, None) == msgs.MS_ERR_INVALID_ARG
+    assert lib.ms_project_views(ctypes.byref(empty), cams2, 2, 0, projs2,
+                                None) == msgs.MS_ERR_INVALID_ARG  # NULL output buffers
+    assert b"NULL" in lib.ms_last_error()
     # bad camera
     bad = msgs.camera_struct(inputs.config1_camera())
     bad.width = 0

@@ -1,0 +1,169 @@
+"""ms_project_views: several cameras projected in one pass must write, for
+every view, exactly what ms_project writes for that camera alone (the
+bit-exact footprint contract), whatever the number of views, the mode, the
+mix of camera centres (views with a shared centre share the SH colour) and
+the invalid Gaussians; and the footprints of a view match the oracle's.
+Frames rendered by render_views equal frames rendered one by one."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2311_17089_gb300 as msgs
+from paper_2311_17089_gb300 import inputs
+
+from gpu_util import assert_footprints_equal, calibrated, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+BUFFERS = ("rec", "rect", "n_tiles", "depth", "cover", "mask", "stats")
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    return require_cuda()
+
+
+@pytest.fixture(scope="module")
+def ms_scene_50k():
+    sc = inputs.multiscale_scene(n=50_000, seed=0)
+    return calibrated(sc, inputs.orbit_cameras(8, seed=1, radius=25.0))
+
+
+def degenerate_scene():
+    """A ragged count (not a multiple of the 256-Gaussian chunk) with
+    invalid Gaussians of every kind."""
+    sc = inputs.single_level_scene(n=3001, seed=6)
+    sc.quat[0:10] = 0.0
+    sc.mean[10:20, 0] = np.nan
+    sc.log_scale[20:30] = -30.0
+    sc.log_scale[30:35] = 30.0
+    sc.opacity[35:45] = 1.0 / 255.0
+    sc.mean[50:60, 2] = -3.0
+    return sc
+
+
+def renderers(sc, cams):
+    rs = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, 16 * sc.n + 4096) for c in cams]
+    for r in rs:  # unlisted entries are not written: start from zeros on both sides
+        for b in BUFFERS:
+            getattr(r, b).zero_()
+    return rs
+
+
+def project_both(torch, sc, cams, mode):
+    ds = msgs.DeviceScene(sc)
+    alone, joint = renderers(sc, cams), renderers(sc, cams)
+    m = msgs.MODES[mode]
+    for r, c in zip(alone, cams):
+        msgs.ms_project(ds.struct, msgs.camera_struct(c), m, r.proj)
+    msgs.ms_project_views(ds.struct, [msgs.camera_struct(c) for c in cams], m,
+                          [r.proj for r in joint])
+    torch.cuda.synchronize()
+    return alone, joint
+
+
+def assert_views_equal(alone, joint):
+    for v, (a, j) in enumerate(zip(alone, joint)):
+        for b in BUFFERS:
+            assert getattr(a, b).equal(getattr(j, b)), (v, b)
+
+
+def shared_centre_cams():
+    return [inputs.downscale(inputs.config2_camera(), s) for s in inputs.SCALES]
+
+
+def mixed_cams():
+    """Centres A, B, A, C, B, A: a Gaussian's colour is evaluated again
+    whenever the centre changes and reused when it repeats."""
+    a, b, c = inputs.orbit_cameras(3, seed=4, radius=25.0, width=400, height=300)
+    return [a, b, inputs.downscale(a, 2), c, inputs.downscale(b, 4), inputs.downscale(a, 8)]
+
+
+@pytest.mark.parametrize("mode", ["selective", "all_levels", "filter_small"])
+def test_eight_views_shared_centre_equal_single_views(cuda, ms_scene_50k, mode):
+    alone, joint = project_both(cuda, ms_scene_50k, shared_centre_cams(), mode)
+    assert_views_equal(alone, joint)
+    assert all(int(r.n_tiles.count_nonzero()) > 0 for r in joint)
+
+
+@pytest.mark.parametrize("n_views", [1, 2, 3, 6])
+def test_mixed_centres_any_view_count(cuda, ms_scene_50k, n_views):
+    cams = mixed_cams()[:n_views]
+    alone, joint = project_both(cuda, ms_scene_50k, cams, "selective")
+    assert_views_equal(alone, joint)
+
+
+def test_invalid_gaussians_and_ragged_chunk(cuda):
+    sc = degenerate_scene()
+    cams = [inputs.config1_camera(96, 80), inputs.config1_camera(48, 40),
+            inputs.config1_camera(400, 300)]
+    alone, joint = project_both(cuda, sc, cams, "all_levels")
+    assert_views_equal(alone, joint)
+    assert int(joint[0].n_tiles[:20].count_nonzero()) == 0
+
+
+def test_views_match_oracle_footprints(cuda, ms_scene_50k):
+    sc = ms_scene_50k
+    cams = mixed_cams()
+    _, joint = project_both(cuda, sc, cams, "selective")
+    n = sc.n
+    for r, cam in zip(joint, cams):
+        g = dict(n_tiles=r.n_tiles.cpu().numpy().view(np.uint32)[:n],
+                 depth=r.depth.cpu().numpy().view(np.uint32)[:n],
+                 rect=r.rect.cpu().numpy().view(np.uint32).reshape(-1, 2)[:n],
+                 cover=r.cover.cpu().numpy()[:n], mask=r.mask.cpu().numpy().view(np.uint32),
+                 rec=r.rec.cpu().numpy().reshape(-1, 12)[:n])
+        assert_footprints_equal(g, oracle.footprints(sc, cam, "selective"), sc, cam)
+
+
+def test_render_views_equals_frames_rendered_alone(cuda, ms_scene_50k):
+    torch = cuda
+    sc = ms_scene_50k
+    cams = shared_centre_cams() + mixed_cams()[:3]  # 11 frames: two projection passes
+    ds = msgs.DeviceScene(sc)
+    alone = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, 16 * sc.n) for c in cams]
+    joint = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, 16 * sc.n) for c in cams]
+    want = [r.render(ds, c, "selective") for r, c in zip(alone, cams)]
+    streams = [torch.cuda.Stream() for _ in cams]
+    got = msgs.render_views(ds, joint, cams, "selective", streams=streams)
+    torch.cuda.synchronize()
+    for r in alone + joint:
+        r.check()
+    for v, (w, g) in enumerate(zip(want, got)):
+        for a, b in zip(w, g):
+            assert a.equal(b), v
+
+
+def test_histogram_flush_on_a_30M_scene(cuda):
+    """30M Gaussians: with two views (456 CTAs of 256 threads) every CTA
+    processes more than 255 chunks, so its 16-bit digit counts are flushed
+    mid-launch; one view (608 CTAs) never flushes early.  Counters,
+    histograms and footprints still agree bit for bit."""
+    torch = cuda
+    sc = inputs.single_level_scene(n=30_000_000, seed=9)
+    ds = msgs.DeviceScene(sc)
+    n = sc.n
+    cams = [inputs.config1_camera(96, 80), inputs.config1_camera(40, 24)]
+
+    def proj():
+        t = dict(rec=torch.zeros(n * 12, dtype=torch.float32, device="cuda"),
+                 rect=torch.zeros(n * 2, dtype=torch.int32, device="cuda"),
+                 n_tiles=torch.zeros(n, dtype=torch.int32, device="cuda"),
+                 depth=torch.zeros(n, dtype=torch.int32, device="cuda"),
+                 stats=torch.zeros(msgs.MS_STATS_WORDS, dtype=torch.int32, device="cuda"))
+        p = msgs.ms_proj_t(msgs._ptr(t["rec"]), msgs._ptr(t["rect"]), msgs._ptr(t["n_tiles"]),
+                           msgs._ptr(t["depth"]), 0, 0, msgs._ptr(t["stats"]), n)
+        return t, p
+
+    m = msgs.MODES["all_levels"]
+    joint = [proj() for _ in cams]
+    msgs.ms_project_views(ds.struct, [msgs.camera_struct(c) for c in cams], m,
+                          [p for _, p in joint])
+    for (tj, _), cam in zip(joint, cams):
+        ta, pa = proj()
+        msgs.ms_project(ds.struct, msgs.camera_struct(cam), m, pa)
+        torch.cuda.synchronize()
+        assert int(ta["stats"][0]) > 65536  # survivors: more than one 16-bit count
+        for k in ta:
+            assert ta[k].equal(tj[k]), k
+        del ta, pa
