@@ -40,6 +40,8 @@ N_GAUSS = 1_000_000
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 OPS_PER_EVAL = 16          # FP32 operations per pixel-Gaussian evaluation
+MUFU_LANES_PER_SM = 16     # ex2 results per SM per clock (one ex2 per evaluation)
+PAPER_LEVEL_MIX = (0.95, 0.035, 0.01, 0.005)   # coarse levels under 5% of the Gaussians
 RASTER_DRAM_BYTES_PER_LAUNCH = 23.35e6   # both raster kernels, selective sweep, measured
 
 
@@ -55,6 +57,7 @@ def parse():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-near-far", action="store_true")
+    ap.add_argument("--no-level-mix", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-n", type=int, default=2_000_000)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
@@ -283,6 +286,84 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
                        "loss": "L1 mean per view, targets U(0,1) seed 1",
                        "launch": "forward (one stream per view) and backward (one batched "
                                  "call over the views) each one CUDA graph"}}
+
+
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: the
+    implementer and part codes)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    fields = {}
+    for line in info:
+        k, _, v = line.partition(":")
+        fields.setdefault(k.strip(), v.strip())
+    if "model name" in fields:
+        return fields["model name"]
+    return " ".join(f"{k} {fields[k]}" for k in ("CPU implementer", "CPU part") if k in fields) \
+        or "unknown"
+
+
+# ---------------------------------------------------------- level mix
+
+def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_MIX):
+    """The sweep on a scene whose coarse levels hold under 5% of the
+    Gaussians (the paper's setting; the main workload puts 30% there):
+    the same generator, cameras and calibration with split 95/3.5/1/0.5%.
+    One 8-frame sweep (one multi-view projection, then each frame's bin and
+    raster on its own stream) replayed from a CUDA graph; selective and
+    all-levels frames/s."""
+    sc = inputs.multiscale_scene(n=n, seed=0, split=split)
+    ds = msgs.DeviceScene(sc, device=dev)
+    ds.calibrate(calib)
+    max_tiles = cams[0].tiles_x * cams[0].tiles_y
+    probe = msgs.Renderer(n, max_tiles, 60 * n, device=dev, with_cover=False, with_mask=False)
+    out = {"config": {"workload": f"multiscale-{n // 1000}k-levelmix-"
+                                  + "/".join(f"{100 * f:g}" for f in split) + "-sweep8",
+                      "split": list(split)}}
+    css = [msgs.camera_struct(c) for c in cams]
+    streams = [torch.cuda.Stream(device=dev, priority=(-1 if k < 3 else 0))
+               for k in range(len(cams))]
+    for mode in ("selective", "all_levels"):
+        caps = []
+        for cam in cams:
+            probe.render(ds, cam, mode)
+            caps.append(msgs.ms_bin_counts(probe.bins)[1])
+        rs = [msgs.Renderer(n, c.tiles_x * c.tiles_y, int(d * 1.05) + 1024, device=dev,
+                            with_cover=False, with_mask=False) for c, d in zip(cams, caps)]
+        bufs = [r.images(c, device=dev) for r, c in zip(rs, cams)]
+
+        def sweep():
+            main = torch.cuda.current_stream()
+            msgs.ms_project_views(ds.struct, css, msgs.MODES[mode], [r.proj for r in rs], main)
+            for r, cam, o, st in zip(rs, cams, bufs, streams):
+                st.wait_stream(main)
+                with torch.cuda.stream(st):
+                    r.bin_raster(ds, cam, out=o, stream=st)
+            for st in streams:
+                main.wait_stream(st)
+
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            sweep()
+        for _ in range(3):
+            g.replay()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for r in rs:
+            r.check()
+        out[mode] = {"fps": len(cams) * steps * 1e3 / e0.elapsed_time(e1),
+                     "D": [int(d) for d in caps]}
+        del rs, bufs, g
+    out["selective_over_all_levels"] = out["selective"]["fps"] / out["all_levels"]["fps"]
+    return out
 
 
 # ------------------------------------------------------------- near / far
@@ -557,7 +638,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config(args.n),
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads,
-                         "kind": "oracle",
+                         "kind": "oracle", "cpu_model": cpu_model(),
                          "sample": f"selective frames at widths {scales} per step "
                                    f"(coarse to fine until {budget:.1f} s)"},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
@@ -806,6 +887,11 @@ def main():
                    "achieved": OPS_PER_EVAL * evals / raster_s / 1e12, "peak": alu_peak,
                    "unit": "Tops/s"}
     roof_raster["frac"] = roof_raster["achieved"] / roof_raster["peak"]
+    # the co-bound: one ex2 per evaluation on the MUFU unit
+    mufu_peak = SM_COUNT * MUFU_LANES_PER_SM * 2070.0e6 / 1e12
+    roof_raster["co_bound"] = {"bound": "mufu", "achieved": evals / raster_s / 1e12,
+                               "peak": mufu_peak, "unit": "T ex2/s",
+                               "frac": evals / raster_s / 1e12 / mufu_peak}
     # the same split by kernel: ms_raster blends frames with at least as many
     # tiles as SMs with the tile kernel, the others with the list kernel
     by_kernel = {}
@@ -910,6 +996,8 @@ def main():
         train["value"] *= world
 
     aggregate = aggregate_bench(msgs, torch, ds, sc, dev)
+    level_mix = None if args.no_level_mix else level_mix_bench(
+        msgs, torch, dev, sc.n, cams, calib, max(20, args.steps // 2))
     near_far = None if args.no_near_far else near_far_bench(msgs, torch, dev)
 
     serve = None
@@ -920,6 +1008,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f, s, threads, scales = oracle_sweep(oracle_scene(sc), cams, args.cpu_budget_s)
         cpu = {"value": f / s, "unit": "frames/s", "cores": threads, "kind": "oracle",
+               "cpu_model": cpu_model(),
                "sample": f"{f} selective frames of the same scene at widths {scales}"}
 
     if rank == 0:
@@ -937,6 +1026,7 @@ def main():
             "roofline_all": {"project": roof_project, "raster": roof_raster},
             "train": train,
             "aggregate": aggregate,
+            "level_mix": level_mix,
             "near_far": near_far,
             "serve": serve,
         }))
