@@ -215,8 +215,12 @@ int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
  * forms its 3D covariance once; the camera-dependent steps run per view,
  * and views whose cameras share a centre (campos) share the listed
  * Gaussians' SH colour (the multi-scale setting of Sec. 4: one pose at
- * several resolutions).  cams and outs are host arrays of n_views entries;
- * the outs[v] must not overlap one another.
+ * several resolutions).  cams and outs are host arrays of n_views entries
+ * (read during the call only); the device buffers of the outs[v] are the
+ * caller's and must not overlap one another.  Errors: MS_ERR_INVALID_ARG
+ * for n_views outside 1..MS_MAX_PROJ_VIEWS, NULL cams/outs, or any camera
+ * or output that ms_project would reject, all found before any work is
+ * enqueued.
  */
 int ms_project_views(const ms_scene_t *scene, const ms_camera_t *cams, int32_t n_views,
                      ms_mode_t mode, const ms_proj_t *outs, void *stream);
