@@ -5,7 +5,8 @@ Argument marshalling only: every step of the rendering path runs in the
 CUDA kernels of libmsgs.so.  PyTorch provides device memory and streams.
 The functions `ms_*` mirror the C entry points one to one and raise
 `MsError` on a non-zero status.  `DeviceScene` and `Renderer` hold the
-torch-allocated buffers a frame needs and chain the calls.
+torch-allocated buffers a frame needs and chain the calls; `render_views`
+renders several frames of one scene from one `ms_project_views` pass.
 
 There is no CPU fallback: if libmsgs.so cannot be built or loaded, or no
 CUDA device is present, the calls raise.

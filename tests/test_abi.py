@@ -101,6 +101,16 @@ def test_argument_errors_need_no_device():
                                 None) == msgs.MS_ERR_INVALID_ARG
 
 
+def test_multi_view_helpers_check_lengths_first():
+    """The view helpers reject mismatched lists before touching a device."""
+    cam = msgs.camera_struct(inputs.config1_camera())
+    with pytest.raises(msgs.MsError):
+        msgs.ms_project_views(msgs.ms_scene_t(), [cam, cam], msgs.MS_SELECTIVE,
+                              [msgs.ms_proj_t()])
+    with pytest.raises(msgs.MsError):
+        msgs.render_views(None, [object()], [], "selective")
+
+
 def test_backward_argument_errors_need_no_device():
     lib = msgs.lib()
     cam = msgs.camera_struct(inputs.config1_camera())
