@@ -536,8 +536,9 @@ def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=Non
     v's buffers.  Returns the (image, final_t, n_contrib) of every frame."""
     import torch
     n = len(cams)
-    if len(renderers) != n or (outs is not None and len(outs) != n):
-        raise MsError(MS_ERR_INVALID_ARG, "one renderer (and output) per camera")
+    if (len(renderers) != n or (outs is not None and len(outs) != n)
+            or (streams is not None and len(streams) != n)):
+        raise MsError(MS_ERR_INVALID_ARG, "one renderer (and output and stream) per camera")
     for r, cam in zip(renderers, cams):
         if cam.tiles_x * cam.tiles_y > r.max_tiles:
             raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")

@@ -109,6 +109,8 @@ def test_multi_view_helpers_check_lengths_first():
                               [msgs.ms_proj_t()])
     with pytest.raises(msgs.MsError):
         msgs.render_views(None, [object()], [], "selective")
+    with pytest.raises(msgs.MsError):
+        msgs.render_views(None, [object()], [object()], "selective", streams=[])
 
 
 def test_backward_argument_errors_need_no_device():
