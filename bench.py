@@ -43,6 +43,7 @@ OPS_PER_EVAL = 16          # FP32 operations per pixel-Gaussian evaluation
 MUFU_LANES_PER_SM = 16     # ex2 results per SM per clock (one ex2 per evaluation)
 PAPER_LEVEL_MIX = (0.95, 0.035, 0.01, 0.005)   # coarse levels under 5% of the Gaussians
 RASTER_DRAM_BYTES_PER_LAUNCH = 23.35e6   # both raster kernels, selective sweep, measured
+PROJECT_VIEWS_DRAM_BYTES_PER_LAUNCH = 516.8e6   # project_kernel<8> of the selective sweep, measured
 
 
 def parse():
@@ -883,6 +884,9 @@ def main():
     roof_project = {"bound": "hbm", "kernel": f"project_kernel ({len(cams)} views, one launch)",
                     "achieved": proj_bytes / proj_s / 1e9, "peak": hbm_peak, "unit": "GB/s"}
     roof_project["frac"] = roof_project["achieved"] / roof_project["peak"]
+    # DRAM bytes of one ncu capture of the sweep's projection launch (to be
+    # taken again whenever the projection kernel changes)
+    roof_project["traffic"] = PROJECT_VIEWS_DRAM_BYTES_PER_LAUNCH
     roof_raster = {"bound": "alu", "kernel": "raster_kernel (tile) + raster_list_kernel",
                    "achieved": OPS_PER_EVAL * evals / raster_s / 1e12, "peak": alu_peak,
                    "unit": "Tops/s"}
@@ -915,9 +919,11 @@ def main():
     # dram__bytes_write.sum of one ncu capture of this sweep's eight raster
     # launches (both kernels), averaged (to be taken again whenever a raster
     # kernel changes)
-    traffic = RASTER_DRAM_BYTES_PER_LAUNCH if roof is roof_raster else None
+    traffic = RASTER_DRAM_BYTES_PER_LAUNCH if roof is roof_raster else roof.get("traffic")
     roof = dict(roof, traffic=traffic, stage_ms_per_step=stage_ms,
-                traffic_source="ncu capture, mean over the sweep's raster launches"
+                traffic_source=("ncu capture, mean over the sweep's raster launches"
+                                if roof is roof_raster else
+                                "ncu capture of the sweep's projection launch")
                 if traffic else None)
 
     # end to end through the public API with host buffers
