@@ -28,10 +28,13 @@ SELECTIVE, ALL_LEVELS, FILTER_SMALL = 0, 1, 2
 MODES = {"selective": SELECTIVE, "all_levels": ALL_LEVELS,
          "filter_small": FILTER_SMALL}
 
-# Relative margins around the blend's two thresholds inside which a
-# single-precision evaluation may decide differently (flags, render64.c).
-ALPHA_FLAG_REL = 1e-4
-T_FLAG_REL = 1e-4
+# Smallest relative margins around the blend's two thresholds inside which
+# a single-precision evaluation may decide differently (flags, render64.c);
+# each decision's margin is the larger of this floor and the bound of the
+# single-precision error of the quantities it compares.
+ALPHA_FLAG_REL = 1e-5
+T_FLAG_REL = 1e-5
+MAX_ALTERNATIVES = 256
 
 FP_DTYPE = np.dtype([
     ("valid", np.uint8), ("selected", np.uint8), ("cover", np.float32),
@@ -83,6 +86,8 @@ def lib():
         L.or_render64.restype = I64
         L.or_render64_brute.argtypes = [I64, P, P, P, P, D, P, P, P]
         L.or_render64_brute.restype = I64
+        L.or_pixel_alternatives.argtypes = [P, P, P, P, I64, D, D, D, D, I32, P]
+        L.or_pixel_alternatives.restype = I32
         L.or_update_range.argtypes = [I64, P, P, P, P, P, I32, I32, P, P, P]
         L.or_coverage64.argtypes = [I64, P, P, P, P, P, P, P, P, P]
         L.or_forward64_full.argtypes = [I64, P, P, P, P, P, I32, P, P, P, P, P, P, P]
@@ -192,7 +197,30 @@ def render(scene, cam, mode="selective", tiles=None, prepared=None,
         _p(image), _p(final_t), _p(n_contrib), _p(flags), _p(n_eval))
     return dict(image=image, final_t=final_t, n_contrib=n_contrib,
                 flags=flags, evals=int(evals), n_eval=n_eval, fp=fp, offsets=offsets,
-                idx=idx, rgb=rgb)
+                idx=idx, rgb=rgb, opacity=_f32(scene.opacity), cam=cam,
+                alpha_flag_rel=alpha_flag_rel, t_flag_rel=t_flag_rel)
+
+
+def pixel_alternatives(o, x: int, y: int, max_alts: int = MAX_ALTERNATIVES):
+    """Every result pixel (x, y) of the render `o` (from render()) may take
+    when its flagged decisions go either way: an array of rows (C0, C1, C2
+    including T bg, T, n_contrib, n_eval), or None if there are more than
+    max_alts.  The exact (FP64) decisions give one of the rows."""
+    cam = o["cam"]
+    t = (y // 16) * cam.tiles_x + x // 16
+    off, idx = o["offsets"], o["idx"]
+    lst = np.ascontiguousarray(idx[off[t]:off[t + 1]], np.uint32)
+    out = np.zeros((max_alts, 6))
+    k = lib().or_pixel_alternatives(
+        _p(o["fp"]), _p(o["opacity"]), _p(o["rgb"]),
+        _p(lst if len(lst) else np.zeros(1, np.uint32)), len(lst), x + 0.5, y + 0.5,
+        o["alpha_flag_rel"], o["t_flag_rel"], max_alts, _p(out))
+    if k < 0:
+        return None
+    out = out[:k]
+    bg = np.asarray(cam.bg, np.float64)
+    out[:, :3] += out[:, 3:4] * bg[None, :]
+    return out
 
 
 def render_brute(scene, cam, mode="selective", prepared=None,

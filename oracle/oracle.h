@@ -87,6 +87,15 @@ int64_t or_render64_brute(int64_t n, const or_fp *fp, const float *opacity,
                           double alpha_flag_rel, double *image,
                           double *final_t, uint8_t *flags);
 
+/* Every result one pixel (centre px, py) may correctly take when the
+ * decisions that render64.c flags are taken either way: up to max_alts rows
+ * of (C0, C1, C2, T, n_contrib, n_eval) in out.  Returns the number of
+ * rows, or -1 if there are more than max_alts. */
+int32_t or_pixel_alternatives(const or_fp *fp, const float *opacity, const double *rgb,
+                              const uint32_t *list, int64_t len, double px, double py,
+                              double alpha_flag_rel, double t_flag_rel, int32_t max_alts,
+                              double *out);
+
 void or_update_range(int64_t n, const float *mean, const float *scale,
                      const float *quat, const float *lnop,
                      const uint8_t *level, int32_t n_levels,

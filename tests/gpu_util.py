@@ -1,5 +1,7 @@
 """Shared helpers of the GPU parity tests: run the CUDA path through the
 C-ABI binding and compare with the oracle on the same seeded inputs."""
+import os
+
 import numpy as np
 
 import oracle
@@ -106,11 +108,31 @@ def assert_lists_equal(g, offsets, idx):
     np.testing.assert_array_equal(g["ranges"][ne, 0], offsets[:-1][ne])
 
 
-def assert_image_close(g, o, tiles=None, cam=None, atol=IMAGE_ATOL, max_flagged=0.02):
-    """Colour, final T, contributor and evaluation counts on pixels where no evaluation
-    sat on a threshold (flag bit 0: alpha near 1/255; bit 1: T (1 - alpha)
-    near 1e-4).  A flip at either threshold changes the pixel by up to
-    alpha T, not bounded by atol, so flagged pixels are only counted."""
+FLAG_LOG = []   # (test case, pixels compared, flagged pixels) of every image check
+
+
+def _matches_alternative(alts, col, t, nc, ne, atol):
+    """True when the GPU's pixel equals one of the oracle's alternatives:
+    colour and T within atol, contributor and evaluation counts exact."""
+    if alts is None:
+        return False
+    for row in alts:
+        if (np.all(np.abs(col - row[:3]) <= atol) and abs(t - row[3]) <= atol
+                and int(nc) == int(row[4]) and int(ne) == int(row[5])):
+            return True
+    return False
+
+
+def assert_image_close(g, o, tiles=None, cam=None, atol=IMAGE_ATOL, label=None):
+    """Every pixel of the region against the oracle.  Where no decision sat
+    within single-precision reach of a threshold (flag bit 0: alpha near
+    1/255; bit 1: T (1 - alpha) near 1e-4), colour and final T must be within
+    atol and the contributor and evaluation counts exact.  A flagged pixel
+    may correctly take either branch of each flagged decision (a flip moves
+    it by up to alpha T, beyond atol), so it must equal, to the same
+    tolerance, one of the results the oracle reaches by taking those
+    decisions each way (oracle.pixel_alternatives).  Returns (max colour
+    error on unflagged pixels, number of flagged pixels)."""
     flags = o["flags"]
     region = np.ones_like(flags, bool)
     if tiles is not None:
@@ -119,7 +141,6 @@ def assert_image_close(g, o, tiles=None, cam=None, atol=IMAGE_ATOL, max_flagged=
             tx, ty = t % cam.tiles_x, t // cam.tiles_x
             region[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16] = True
     ok = region & (flags == 0)
-    assert ok.sum() >= (1 - max_flagged) * region.sum(), (ok.sum(), region.sum())
     err = np.abs(g["image"] - o["image"])[:, ok]
     assert err.size == 0 or err.max() <= atol, err.max()
     terr = np.abs(g["final_t"] - o["final_t"])[ok]
@@ -127,4 +148,14 @@ def assert_image_close(g, o, tiles=None, cam=None, atol=IMAGE_ATOL, max_flagged=
     np.testing.assert_array_equal(g["n_contrib"][ok], o["n_contrib"][ok])
     # the evaluation count behind the benchmark's roofline (P_eval)
     np.testing.assert_array_equal(g["n_eval"][ok].astype(np.int64), o["n_eval"][ok])
-    return float(err.max()) if err.size else 0.0, int(region.sum() - ok.sum())
+    flagged = np.argwhere(region & (flags != 0))
+    bad = []
+    for y, x in flagged:
+        alts = oracle.pixel_alternatives(o, int(x), int(y))
+        if not _matches_alternative(alts, g["image"][:, y, x], g["final_t"][y, x],
+                                    g["n_contrib"][y, x], g["n_eval"][y, x], atol):
+            bad.append((int(x), int(y), None if alts is None else len(alts)))
+    assert not bad, f"flagged pixels matching no alternative: {bad[:8]} ({len(bad)})"
+    case = label or os.environ.get("PYTEST_CURRENT_TEST", "image").split(" ")[0]
+    FLAG_LOG.append((case, int(region.sum()), len(flagged)))
+    return float(err.max()) if err.size else 0.0, len(flagged)

@@ -31,16 +31,25 @@ def gpu_grads(sc, cam, w, mode="all_levels", strategy="auto"):
     return {k: params[k].grad.detach().cpu().numpy().astype(np.float64) for k in NAMES}, img
 
 
+GRAD_LOG = []   # (test case, parameter, entries, entries within rel only through the floor)
+
+
 def compare(gg, go, rel=1e-3, floor=1e-4):
     """Each entry within rel of the oracle's value plus a floor relative to
-    the largest entry of that parameter (entries of Gaussians that only
-    touch threshold pixels)."""
+    the largest entry of that parameter.  The floor covers entries that are
+    small sums of larger terms (FP32 accumulation over many pixels cancels)
+    and Gaussians that touch pixels whose threshold decisions the FP32 path
+    and the FP64 oracle take differently; the entries that pass only
+    through it are counted (GRAD_LOG, printed at the end of the run)."""
+    import os
+    case = os.environ.get("PYTEST_CURRENT_TEST", "grad").split(" ")[0]
     for k in NAMES:
         a, b = gg[k].reshape(-1), go[k].reshape(-1)
         scale = max(np.abs(b).max(), 1e-30)
         err = np.abs(a - b)
         bad = err > rel * np.abs(b) + floor * scale
         assert not bad.any(), (k, int(bad.sum()), float((err / scale).max()))
+        GRAD_LOG.append((case, k, int(a.size), int((err > rel * np.abs(b)).sum())))
 
 
 @pytest.mark.parametrize("strategy", ["tile", "list"])

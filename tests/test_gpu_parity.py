@@ -277,7 +277,7 @@ def test_long_lists_split_across_ctas(cuda, wh, n, op, strategy):
         assert (o["n_contrib"] > 600).all() and (o["final_t"] < 1.1e-2).all()
     else:
         assert (o["n_contrib"] == n).all()
-    assert_image_close(g, o, max_flagged=0.15)
+    assert_image_close(g, o)
 
 
 def deep_lists_scene(seed=31):
@@ -320,7 +320,7 @@ def test_long_lists_early_and_deep_pixels(cuda, strategy):
     assert early.mean() > 0.2 and deep.mean() > 0.2, (early.mean(), deep.mean())
     g = gpu_frame(sc, cam, "all_levels", strategy=strategy)
     assert_lists_equal(g, o["offsets"], o["idx"])
-    assert_image_close(g, o, max_flagged=0.1)
+    assert_image_close(g, o)
 
 
 def test_one_long_list_among_many_tiles_and_overflow(cuda):
@@ -341,7 +341,7 @@ def test_one_long_list_among_many_tiles_and_overflow(cuda):
     assert g["D"] == len(idx)
     assert_lists_equal(g, off, idx)
     o = oracle.render(sc, cam, "all_levels")
-    assert_image_close(g, o, cam=cam, max_flagged=0.05)
+    assert_image_close(g, o, cam=cam)
 
 
 def test_scene_prepare_bit_exact_many_values(cuda):

@@ -464,3 +464,112 @@ def test_sh_colour_is_view_dependent_and_dc_offset(orc):
     rgb = orc.colors(sc, cam)
     want = np.maximum(0.0, 0.5 / math.sqrt(math.pi) * sc.color[:, 0, :].astype(np.float64) + 0.5)
     np.testing.assert_allclose(rgb, want, rtol=1e-12)
+
+
+def _cartesian_sh(k, d):
+    """Textbook real spherical harmonics in Cartesian form (unit vector d =
+    (x, y, z), no Condon-Shortley phase, k = l^2 + l + m) for the
+    coefficients the colour pins use."""
+    x, y, z = d
+    c1 = math.sqrt(3.0 / (4.0 * math.pi))
+    c33 = 0.25 * math.sqrt(35.0 / (2.0 * math.pi))
+    c30 = 0.25 * math.sqrt(7.0 / math.pi)
+    c31 = 0.25 * math.sqrt(21.0 / (2.0 * math.pi))
+    table = {
+        1: c1 * y,                                   # l = 1, m = -1
+        2: c1 * z,                                   # l = 1, m = 0
+        3: c1 * x,                                   # l = 1, m = 1
+        9: c33 * y * (3 * x * x - y * y),            # l = 3, m = -3
+        12: c30 * z * (5 * z * z - 3),               # l = 3, m = 0
+        13: c31 * x * (5 * z * z - 1),               # l = 3, m = 1
+        15: c33 * x * (x * x - 3 * y * y),           # l = 3, m = 3
+    }
+    return table[k]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 9, 12, 13, 15])
+def test_sh_colour_single_coefficient_direction_and_layout(orc, k):
+    """A lone SH coefficient f at index k of channel c gives colour
+    max(0, 0.5 + f Y_k(d)) in channel c and 0.5 in the others, with d the
+    unit direction from the camera centre to the mean.  Placing the mean on
+    the other side of the camera flips d and so the sign of Y_k for the odd
+    degrees 1 and 3: a colour taken along campos - mean, or a coefficient
+    read as [k][i][c] or [i][c][k], fails."""
+    cam = inputs.config1_camera(64, 64)
+    campos = np.asarray(cam.campos, np.float64)
+    for deg in (1, 3):
+        if k >= (deg + 1) ** 2:
+            continue
+        K = (deg + 1) ** 2
+        for ch in range(3):
+            for sign in (1.0, -1.0):
+                off = sign * np.array([0.9, -0.4, 0.6])
+                pos = (campos + off).astype(np.float32)[None]
+                sc = one_gaussian(pos, [-3.0] * 3)
+                sc.sh_degree = deg
+                sc.color = np.zeros((1, K, 3), np.float32)
+                f = np.float32(0.37)
+                sc.color[0, k, ch] = f
+                rgb = orc.colors(sc, cam)[0]
+                d = pos[0].astype(np.float64) - campos
+                d /= np.linalg.norm(d)
+                want = np.full(3, 0.5)
+                want[ch] = max(0.0, 0.5 + float(f) * _cartesian_sh(k, d))
+                np.testing.assert_allclose(rgb, want, rtol=0, atol=1e-7)
+                # the odd degrees change sign with the direction
+                assert abs(_cartesian_sh(k, d)) > 0.01
+
+
+def test_forward64_full_isotropic_closed_form(orc):
+    """The FP64 forward that the gradient differentiates (FP64 projection,
+    fixed tile lists): one isotropic Gaussian on the optical axis at depth
+    3 renders rgb min(0.99, sigma exp(-r^2 / (2 (s_px^2 + 0.3)))) where that
+    is >= 1/255, with s_px = f e^s / 3 and r the distance to the image
+    centre; with SH degree 0 the colour is 0.5 + f_0 / (2 sqrt(pi))."""
+    cam = inputs.config1_camera(64, 64)
+    for ls, op, dc in [(-3.0, 0.8, (0.2, -0.5, 0.9)), (-4.5, 0.95, (1.0, 0.0, 0.5)),
+                       (-2.0, 0.3, (0.7, 0.7, -1.5))]:
+        sc = one_gaussian([[0, 0, 0]], [ls] * 3, opacity=op)
+        sc.sh_degree = 0
+        sc.color = np.asarray(dc, np.float32).reshape(1, 1, 3)
+        fp = orc.footprints(sc, cam, "all_levels")
+        off, idx = orc.tile_lists(fp, cam)
+        r = orc.forward64(sc, cam, off, idx)
+        s_px = cam.fx * math.exp(ls) / 3.0
+        ys, xs = np.mgrid[0:64, 0:64] + 0.5
+        r2 = (xs - 32.0) ** 2 + (ys - 32.0) ** 2
+        g = op * np.exp(-r2 / (2 * (s_px ** 2 + 0.3)))
+        alpha = np.where(g >= 1 / 255, np.minimum(0.99, g), 0.0)
+        rgb = np.maximum(0.0, 0.5 + np.asarray(dc, np.float64) / (2 * math.sqrt(math.pi)))
+        want = alpha[None] * rgb[:, None, None]
+        near = np.abs(g - 1 / 255) < 1e-6
+        # the camera pose and the inputs are FP32 values: about 1e-8 relative
+        np.testing.assert_allclose(r["image"][:, ~near], want[:, ~near], rtol=0, atol=1e-7)
+        np.testing.assert_allclose(r["final_t"][~near], 1 - alpha[~near], rtol=0, atol=1e-7)
+        assert (alpha > 0).sum() >= 12
+
+
+@pytest.mark.parametrize("seed,deg,nl,mode", [(0, -1, 1, "all_levels"), (1, 3, 4, "selective"),
+                                              (2, 1, 2, "all_levels"), (5, 3, 1, "all_levels")])
+def test_forward64_full_matches_footprint_render(orc, seed, deg, nl, mode):
+    """The FP64 forward (FP64 projection of every splat) and the renderer
+    whose splats come from the FP32 footprint produce the same image: they
+    differ only by the rounding of the splat parameters to FP32, far below
+    the 2e-4 tolerance, and on pixels whose decisions sit away from the
+    thresholds they take the same contributors.  A Jacobian or colour slip
+    in the FP64 projection that its own finite differences cannot see (it
+    is shared by the forward and the gradient) fails here."""
+    sc = inputs.tiny_scene(n=64, seed=seed, sh_degree=deg, n_levels=nl)
+    cam = inputs.config1_camera(64, 64)
+    cam.bg[:] = [0.1, 0.2, 0.3]
+    if nl > 1:
+        orc.calibrate(sc, inputs.orbit_cameras(4, seed=seed, radius=3.0, width=64, height=64))
+    t = orc.render(sc, cam, mode)
+    f = orc.forward64(sc, cam, t["offsets"], t["idx"])
+    ok = t["flags"] == 0
+    assert ok.mean() > 0.97
+    # both images include the background T bg
+    np.testing.assert_allclose(f["image"][:, ok], t["image"][:, ok], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(f["final_t"][ok], t["final_t"][ok], rtol=0, atol=1e-5)
+    np.testing.assert_array_equal(f["n_contrib"][ok], t["n_contrib"][ok])
+    assert np.abs(t["image"] - t["final_t"][None] * 0.2).max() > 0.05   # something is drawn
