@@ -37,10 +37,9 @@ from paper_2311_17089_gb300 import inputs  # noqa: E402
 METRIC = ("frames/s at 1x-128x downscale, selective vs all-levels; "
           "serve p50/p99 ms; bwd it/s")
 N_GAUSS = 1_000_000
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128    # nominal, for the derived peak shown beside the measured one
 OPS_PER_EVAL = 16          # FP32 operations per pixel-Gaussian evaluation
-MUFU_LANES_PER_SM = 16     # ex2 results per SM per clock (one ex2 per evaluation)
+MUFU_LANES_PER_SM = 16     # nominal ex2 results per SM per clock (one ex2 per evaluation)
 PAPER_LEVEL_MIX = (0.95, 0.035, 0.01, 0.005)   # coarse levels under 5% of the Gaussians
 RASTER_DRAM_BYTES_PER_LAUNCH = 23.35e6   # both raster kernels, selective sweep, measured
 PROJECT_VIEWS_DRAM_BYTES_PER_LAUNCH = 516.8e6   # project_kernel<8> of the selective sweep, measured
@@ -160,6 +159,47 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------- measured peaks
+
+def alu_peaks(msgs, torch, dev, reps=3):
+    """FP32 and MUFU throughput measured on this GPU by the library's probe
+    kernels (scalar FFMA, packed FFMA2, ex2), each launch timed with CUDA
+    events on its stream and the SM clock sampled meanwhile.  The FP32 peak
+    is the faster of the scalar and packed forms, in FP32 operations/s (an
+    FMA counts as one operation, as in the blend's operation count)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    iters = {msgs.MS_PROBE_FFMA: 4000, msgs.MS_PROBE_FFMA2: 2000, msgs.MS_PROBE_EX2: 500}
+    res = {}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    for kind, name in ((msgs.MS_PROBE_FFMA, "ffma"), (msgs.MS_PROBE_FFMA2, "ffma2"),
+                       (msgs.MS_PROBE_EX2, "ex2")):
+        msgs.ms_alu_probe(kind, blocks, iters[kind], msgs._ptr(out))
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(4):
+                msgs.ms_alu_probe(kind, blocks, iters[kind], msgs._ptr(out))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dt = e0.elapsed_time(e1) / 1e3
+            rate = 4 * msgs.ms_alu_probe_ops(kind, blocks, iters[kind]) / dt / 1e12
+            best = rate if best is None else max(best, rate)
+        res[name] = best
+    clk = clocks.stop()
+    res["unit"] = "T ops/s (ex2: T ex2/s)"
+    res["sm_count"] = sms
+    res["clocks"] = clk
+    res["fp32_peak"] = max(res["ffma"], res["ffma2"])
+    return res
 
 
 # ---------------------------------------------------------- training step
@@ -365,6 +405,52 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
         del rs, bufs, g
     out["selective_over_all_levels"] = out["selective"]["fps"] / out["all_levels"]["fps"]
     return out
+
+
+# --------------------------------------------------------- single level
+
+def single_level_bench(msgs, torch, dev, steps):
+    """The single-level configuration: 10k Gaussians (means U[-1,1]^3,
+    log-scales N(-3.5, 0.5), opacity sigmoid(N(0,1)), plain RGB), one camera
+    at distance 3, fov 60 deg, 256x256, black background.  One frame =
+    ms_project -> ms_bin -> ms_raster replayed from a CUDA graph; frames/s
+    with the raster stage's ALU rate (its evaluations counted exactly)."""
+    sc = inputs.single_level_scene(n=10_000, seed=0)
+    cam = inputs.config1_camera()
+    ds = msgs.DeviceScene(sc, device=dev)
+    r = msgs.Renderer(sc.n, cam.tiles_x * cam.tiles_y, 64 * sc.n, device=dev)
+    out = r.images(cam, device=dev)
+    ne = torch.empty((cam.height, cam.width), dtype=torch.int32, device=dev)
+    r.render(ds, cam, "selective", out=out, n_eval=ne)
+    d, surv = r.check()
+    p_eval = int(ne.sum(dtype=torch.int64).item())
+    cs = msgs.camera_struct(cam)
+    stream = torch.cuda.current_stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        r.render(ds, cam, "selective", out=out)
+    g_r = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_r):
+        msgs.ms_raster(r.proj, r.bins, cs, msgs._ptr(out[0]), msgs._ptr(out[1]),
+                       msgs._ptr(out[2]), 0, msgs._ptr(r.rws), r.rws_bytes)
+    res = {"config": {"workload": "single-level-10k-rgb-256x256", "gaussians": sc.n,
+                      "image": [cam.width, cam.height],
+                      "launch": "project + bin + raster as one CUDA graph"}}
+    for name, graph in (("frame", g), ("raster", g_r)):
+        for _ in range(3):
+            graph.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[f"{name}_ms"] = e0.elapsed_time(e1) / steps
+    r.check()
+    res.update(fps=1e3 / res["frame_ms"], D=int(d), survivors=int(surv), P_eval=p_eval,
+               raster_tops=OPS_PER_EVAL * p_eval / (res["raster_ms"] / 1e3) / 1e12)
+    return res
 
 
 # ------------------------------------------------------------- near / far
@@ -880,7 +966,12 @@ def main():
         evals += s["P_eval"]
     proj_s = stage_ms["project"] / 1e3
     raster_s = stage_ms["raster"] / 1e3
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2070.0e6 / 1e12   # T ops/s at max clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks_alu = alu_peaks(msgs, torch, dev)
+    alu_peak = peaks_alu["fp32_peak"]
+    mufu_peak = peaks_alu["ex2"]
+    # the unit-count figure at the maximum clock, for context
+    alu_nominal = sms * FP32_LANES_PER_SM * 2070.0e6 / 1e12
     roof_project = {"bound": "hbm", "kernel": f"project_kernel ({len(cams)} views, one launch)",
                     "achieved": proj_bytes / proj_s / 1e9, "peak": hbm_peak, "unit": "GB/s"}
     roof_project["frac"] = roof_project["achieved"] / roof_project["peak"]
@@ -889,10 +980,12 @@ def main():
     roof_project["traffic"] = PROJECT_VIEWS_DRAM_BYTES_PER_LAUNCH
     roof_raster = {"bound": "alu", "kernel": "raster_kernel (tile) + raster_list_kernel",
                    "achieved": OPS_PER_EVAL * evals / raster_s / 1e12, "peak": alu_peak,
-                   "unit": "Tops/s"}
+                   "unit": "Tops/s",
+                   "peak_source": "measured: the faster of the scalar FFMA and packed FFMA2 "
+                                  "probes (bench leg alu_peaks), one FMA = one operation",
+                   "peak_nominal": alu_nominal}
     roof_raster["frac"] = roof_raster["achieved"] / roof_raster["peak"]
     # the co-bound: one ex2 per evaluation on the MUFU unit
-    mufu_peak = SM_COUNT * MUFU_LANES_PER_SM * 2070.0e6 / 1e12
     roof_raster["co_bound"] = {"bound": "mufu", "achieved": evals / raster_s / 1e12,
                                "peak": mufu_peak, "unit": "T ex2/s",
                                "frac": evals / raster_s / 1e12 / mufu_peak}
@@ -900,8 +993,7 @@ def main():
     # tiles as SMs with the tile kernel, the others with the list kernel
     by_kernel = {}
     for cam in cams:
-        name = ("raster_kernel" if cam.tiles_x * cam.tiles_y >= torch.cuda.get_device_properties(
-            dev).multi_processor_count else "raster_list_kernel")
+        name = ("raster_kernel" if cam.tiles_x * cam.tiles_y >= sms else "raster_list_kernel")
         e = by_kernel.setdefault(name, {"frames": [], "P_eval": 0, "ms": 0.0})
         e["frames"].append(f"{cam.width}x{cam.height}")
         e["P_eval"] += stats[("selective", cam.width)]["P_eval"]
@@ -910,6 +1002,19 @@ def main():
         e["achieved"] = OPS_PER_EVAL * e["P_eval"] / (e["ms"] / 1e3) / 1e12
         e["frac"] = e["achieved"] / alu_peak
     roof_raster["by_kernel"] = by_kernel
+    # binning (compaction + duplication, sort, ranges): the algorithmic bytes
+    # of each frame, read the survivors' tile counts and records (44 B), write
+    # D (tile, depth, index) entries (12 B), one sorting read + write of them
+    # (24 B), and the ranges read of the sorted keys (8 B)
+    bin_bytes = 0
+    for cam in cams:
+        st_ = stats[("selective", cam.width)]
+        bin_bytes += 44 * st_["survivors"] + 44 * st_["D"]
+    roof_bin = {"bound": "hbm", "kernel": "binning (finish counts, 4 depth passes, duplicate, "
+                                          "1-2 tile passes, ranges), 8 frames each timed alone",
+                "achieved": bin_bytes / (stage_ms["bin"] / 1e3) / 1e9, "peak": hbm_peak,
+                "unit": "GB/s", "bytes_per_step": bin_bytes}
+    roof_bin["frac"] = roof_bin["achieved"] / hbm_peak
     dominant = max(stage_ms, key=stage_ms.get)
     roof = roof_raster if dominant == "raster" else roof_project
     if dominant == "bin":
@@ -1002,6 +1107,8 @@ def main():
         train["value"] *= world
 
     aggregate = aggregate_bench(msgs, torch, ds, sc, dev)
+    single_level = single_level_bench(msgs, torch, dev, max(50, args.steps))
+    single_level["raster_frac"] = single_level["raster_tops"] / alu_peak
     level_mix = None if args.no_level_mix else level_mix_bench(
         msgs, torch, dev, sc.n, cams, calib, max(20, args.steps // 2))
     near_far = None if args.no_near_far else near_far_bench(msgs, torch, dev)
@@ -1029,9 +1136,11 @@ def main():
             "all_levels": {"value": value_all, "unit": "frames/s",
                            "ms_per_step": 1e3 * t_all / args.steps},
             "per_scale": per_scale,
-            "roofline_all": {"project": roof_project, "raster": roof_raster},
+            "roofline_all": {"project": roof_project, "bin": roof_bin, "raster": roof_raster},
+            "alu_peaks": peaks_alu,
             "train": train,
             "aggregate": aggregate,
+            "single_level": single_level,
             "level_mix": level_mix,
             "near_far": near_far,
             "serve": serve,

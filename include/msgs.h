@@ -274,8 +274,12 @@ int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
  *     is enqueued.  For example, n = 262144 Gaussians with dup_capacity =
  *     524288 fits; larger scenes must use ms_bin with their own workspace.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current.  Make that first
- *     call before any stream capture on the device.
+ *     (cudaGetSymbolAddress) with that device current, and later calls on
+ *     that device reuse it; first calls from several host threads at once
+ *     are safe.  Make that first call before any stream capture on the
+ *     device.  The address belongs to the device's primary context: after
+ *     cudaDeviceReset the library must be unloaded and loaded again before
+ *     this entry point is used on that device.
  *   - All calls share the one array.  Each call clears the parts that must
  *     start at zero, so nothing carries over between calls that run one
  *     after the other.  Calls that overlap on the GPU (different streams
@@ -556,6 +560,23 @@ int ms_serve_stats(ms_server_t *srv, ms_serve_stats_t *stats);
 /* Waits for the requests on the device, drops the queued ones, frees
  * everything.  srv may be NULL. */
 int ms_serve_destroy(ms_server_t *srv);
+
+/*
+ * Measurement probes (the paper has no counterpart): the throughput of the
+ * units the blend's roofline is stated against.  ms_alu_probe enqueues one
+ * launch of `blocks` CTAs of 256 threads, each thread running 8 independent
+ * chains of `iters` x 16 operations of one kind:
+ *   MS_PROBE_FFMA   scalar fma.rn.f32            (1 FP32 operation each)
+ *   MS_PROBE_FFMA2  packed fma.rn.f32x2          (2 FP32 operations each)
+ *   MS_PROBE_EX2    ex2.approx.ftz.f32 on MUFU   (1 ex2 each)
+ * and writes one float per thread to out[blocks * 256] (device memory owned
+ * by the caller).  ms_alu_probe_ops returns the operations one such launch
+ * performs (0 on invalid arguments); the caller times the launch with CUDA
+ * events on `stream` and divides.  Errors: MS_ERR_INVALID_ARG, MS_ERR_CUDA.
+ */
+enum { MS_PROBE_FFMA = 0, MS_PROBE_FFMA2 = 1, MS_PROBE_EX2 = 2 };
+int ms_alu_probe(int kind, int blocks, int iters, float *out, void *stream);
+double ms_alu_probe_ops(int kind, int blocks, int iters);
 
 #ifdef __cplusplus
 }

@@ -168,6 +168,8 @@ _SIGNATURES = [
                                      ctypes.POINTER(ms_result_t)]),
     ("ms_serve_stats", ctypes.c_int, [P, ctypes.POINTER(ms_serve_stats_t)]),
     ("ms_serve_destroy", ctypes.c_int, [P]),
+    ("ms_alu_probe", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]),
+    ("ms_alu_probe_ops", ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
 ]
 
 _lib = None
@@ -277,6 +279,19 @@ def ms_bin_noalloc(proj: ms_proj_t, n: int, cam: ms_camera_t, out: ms_bins_t, st
     workspace, for callers that cannot allocate device memory."""
     _check(lib().ms_bin_noalloc(ctypes.byref(proj), int(n), ctypes.byref(cam),
                                 ctypes.byref(out), P(_stream(stream))))
+
+
+MS_PROBE_FFMA, MS_PROBE_FFMA2, MS_PROBE_EX2 = 0, 1, 2
+
+
+def ms_alu_probe(kind: int, blocks: int, iters: int, out_ptr: int, stream=None):
+    """One throughput-probe launch (FFMA, packed FFMA2 or MUFU ex2)."""
+    _check(lib().ms_alu_probe(int(kind), int(blocks), int(iters), P(out_ptr),
+                              P(_stream(stream))))
+
+
+def ms_alu_probe_ops(kind: int, blocks: int, iters: int) -> float:
+    return float(lib().ms_alu_probe_ops(int(kind), int(blocks), int(iters)))
 
 
 def ms_bin_counts(bins: ms_bins_t, stream=None):

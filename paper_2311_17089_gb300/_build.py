@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmsgs.so")
 SOURCES = ["api.cu", "project.cu", "bin.cu", "raster.cu", "raster_list.cu", "backward.cu",
-           "serve.cu", "aggregate.cu"]
+           "serve.cu", "aggregate.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-Wall", "-I", INCLUDE, "-I", CSRC]

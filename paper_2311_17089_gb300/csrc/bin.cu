@@ -17,6 +17,8 @@
 // polled with relaxed accesses (no fences; many polls in flight at once).  Every wait on another CTA is bounded; a wait that gives up sets
 // a status bit and the CTA carries on, so a kernel can never hang.
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdint.h>
 
 #include <algorithm>
@@ -711,7 +713,9 @@ static __device__ __align__(256) unsigned char g_bin_scratch[kStaticScratchBytes
 
 extern "C" int ms_bin_noalloc(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
                               const ms_bins_t *out, void *stream) {
-    static void *addr[64] = {nullptr};
+    // one cached device address per device; host threads making a first
+    // call at once store the same value, so an atomic is all that is needed
+    static std::atomic<void *> addr[64];
     if (!cam || !out) return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
         return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
@@ -727,13 +731,13 @@ extern "C" int ms_bin_noalloc(const ms_proj_t *proj, int64_t n, const ms_camera_
     int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
     if (rc) return rc;
     if (dev < 0 || dev >= 64) return fail(MS_ERR_INVALID_ARG, "device index beyond 63");
-    if (!addr[dev]) {
+    void *p = addr[dev].load(std::memory_order_acquire);
+    if (!p) {
         // first call on this device: the array's device address (the host
         // symbol is only a stand-in and must never reach a kernel)
-        void *p = nullptr;
         if ((rc = cuda_check(cudaGetSymbolAddress(&p, g_bin_scratch), "cudaGetSymbolAddress")))
             return rc;
-        addr[dev] = p;
+        addr[dev].store(p, std::memory_order_release);
     }
-    return ms_bin(proj, n, cam, out, addr[dev], kStaticScratchBytes, stream);
+    return ms_bin(proj, n, cam, out, p, kStaticScratchBytes, stream);
 }
