@@ -993,7 +993,8 @@ def main():
     # tiles as SMs with the tile kernel, the others with the list kernel
     by_kernel = {}
     for cam in cams:
-        name = ("raster_kernel" if cam.tiles_x * cam.tiles_y >= sms else "raster_list_kernel")
+        nt = cam.tiles_x * cam.tiles_y
+        name = "raster_kernel" if nt >= sms else "raster_list_kernel"
         e = by_kernel.setdefault(name, {"frames": [], "P_eval": 0, "ms": 0.0})
         e["frames"].append(f"{cam.width}x{cam.height}")
         e["P_eval"] += stats[("selective", cam.width)]["P_eval"]

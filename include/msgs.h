@@ -69,9 +69,12 @@ typedef enum {
                             the GPU has SMs, else LIST                       */
     MS_RASTER_TILE = 1,  /* one thread per pixel; long lists split into
                             segments merged exactly across CTAs             */
-    MS_RASTER_LIST = 2   /* one warp per pixel; lanes take consecutive list
+    MS_RASTER_LIST = 2,  /* one warp per pixel; lanes take consecutive list
                             entries, a product scan of (1 - alpha) decides
                             termination                                     */
+    MS_RASTER_GROUP8 = 3,  /* G = 8, 16 or 32 lanes per pixel, 4 consecutive */
+    MS_RASTER_GROUP16 = 4, /* list entries per lane, one product scan over   */
+    MS_RASTER_GROUP32 = 5  /* the group's lanes per 4 G entries              */
 } ms_raster_strategy_t;
 
 /*

@@ -29,7 +29,10 @@ MS_SELECTIVE, MS_ALL_LEVELS, MS_FILTER_SMALL = 0, 1, 2
 MODES = {"selective": MS_SELECTIVE, "all_levels": MS_ALL_LEVELS,
          "filter_small": MS_FILTER_SMALL}
 MS_RASTER_AUTO, MS_RASTER_TILE, MS_RASTER_LIST = 0, 1, 2
-STRATEGIES = {"auto": MS_RASTER_AUTO, "tile": MS_RASTER_TILE, "list": MS_RASTER_LIST}
+MS_RASTER_GROUP8, MS_RASTER_GROUP16, MS_RASTER_GROUP32 = 3, 4, 5
+STRATEGIES = {"auto": MS_RASTER_AUTO, "tile": MS_RASTER_TILE, "list": MS_RASTER_LIST,
+              "group8": MS_RASTER_GROUP8, "group16": MS_RASTER_GROUP16,
+              "group32": MS_RASTER_GROUP32}
 MS_STATS_WORDS = 1040
 MS_BWD_ACCUMULATE = 1
 MS_MAX_BWD_VIEWS = 8

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmsgs.so")
-SOURCES = ["api.cu", "project.cu", "bin.cu", "raster.cu", "raster_list.cu", "backward.cu",
+SOURCES = ["api.cu", "project.cu", "bin.cu", "raster.cu", "raster_list.cu", "raster_group.cu", "backward.cu",
            "serve.cu", "aggregate.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

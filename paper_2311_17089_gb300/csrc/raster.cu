@@ -646,7 +646,7 @@ extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
                             const ms_camera_t *cam, float *image, float *final_t,
                             uint32_t *n_contrib, uint32_t *n_eval, void *ws, size_t ws_bytes,
                             int strategy, void *stream) {
-    if (strategy != MS_RASTER_AUTO && strategy != MS_RASTER_TILE && strategy != MS_RASTER_LIST)
+    if (strategy < MS_RASTER_AUTO || strategy > MS_RASTER_GROUP32)
         return fail(MS_ERR_INVALID_ARG, "unknown raster strategy");
     if (!proj || !bins || !cam || !image) return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
@@ -681,9 +681,18 @@ extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
     // tile kernel then splits every list into many segments, most of them
     // blended speculatively, and the list-parallel kernel is faster (it
     // costs about twice the instructions per evaluation, but none is
-    // speculative; measured crossover between 70 and 260 tiles on GB300)
-    const bool list = strategy == MS_RASTER_LIST ||
-                      (strategy == MS_RASTER_AUTO && tiles < (int64_t)num_sms());
+    // speculative; measured crossover between 70 and 260 tiles on GB300).
+    // The group kernels are chosen only explicitly: the 8-lane one blends a
+    // 314x208 frame alone faster than the tile kernel (176 against 200 us on
+    // GB300) but costs more SM time, and the concurrent 8-frame sweep was
+    // slower with it (1.236 against 1.222 ms).
+    const int64_t sms = num_sms();
+    const int group = strategy == MS_RASTER_GROUP8    ? 8
+                      : strategy == MS_RASTER_GROUP16 ? 16
+                      : strategy == MS_RASTER_GROUP32 ? 32
+                                                      : 0;
+    const bool list = group > 0 || strategy == MS_RASTER_LIST ||
+                      (strategy == MS_RASTER_AUTO && tiles < sms);
     if (!list &&
         (rc = cuda_check(cudaMemsetAsync(w, 0, L.zero_bytes, st), "raster workspace memset")))
         return rc;
@@ -737,6 +746,7 @@ extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
         la.seg_len = a.seg_len;
         la.pre = a.pre;
         if ((rc = cuda_check(cudaGetLastError(), "segment offsets launch"))) return rc;
+        if (group > 0) return cuda_check(launch_raster_group(la, group, st), "raster group launch");
         return cuda_check(launch_raster_list(la, st), "raster list launch");
     }
     raster_kernel<<<resident, kRasterThreads, kSmemBytes, st>>>(a);

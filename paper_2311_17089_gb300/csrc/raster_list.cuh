@@ -32,4 +32,8 @@ constexpr int kListCtasPerTile = 256 / kListPixelsPerCta;
 // workspace zeroing needed).
 cudaError_t launch_raster_list(const ListArgs &a, cudaStream_t st);
 
+// Enqueue the group blend (raster_group.cu): each pixel's list walked by a
+// group of `group` lanes (8, 16 or 32), 4 consecutive entries per lane.
+cudaError_t launch_raster_group(const ListArgs &a, int group, cudaStream_t st);
+
 }  // namespace msgs

@@ -36,7 +36,7 @@ def test_scene_prepare_matches_oracle(cuda):
     np.testing.assert_array_equal(ds.lnop.cpu().numpy(), lnop)
 
 
-STRATEGIES = ["tile", "list"]
+STRATEGIES = ["tile", "list", "group8", "group16", "group32"]
 
 
 @pytest.mark.parametrize("strategy", STRATEGIES)
