@@ -606,10 +606,14 @@ def serve_bench(msgs, torch, dev, n_requests, n_gauss, loads=(0.5, 0.7, 0.9)):
     hosts = [torch.empty((3, 832, 1256), dtype=torch.float32).pin_memory() for _ in range(ring)]
     budget = 64 << 30
     out = {}
-    for mode in ("selective", "all_levels"):
+    base_rate = {}
+    for mode, mb in (("selective", 1), ("selective", 0), ("all_levels", 1), ("all_levels", 0)):
+        # max_batch_views 1: every request projected by itself (the unbatched
+        # reference); 0: requests of one scene and mode admitted together
+        # share one projection pass of up to 8 cameras
         srv = msgs.Server(max_gaussians=n_gauss, max_width=1256, max_height=832,
                           mem_budget_bytes=budget, max_inflight=64, n_streams=16,
-                          device=dev.index or 0)
+                          device=dev.index or 0, max_batch_views=mb)
         ids = [srv.add_scene(ds) for ds in dss]
 
         def run(arrivals):
@@ -652,25 +656,48 @@ def serve_bench(msgs, torch, dev, n_requests, n_gauss, loads=(0.5, 0.7, 0.9)):
                     "mean_ms": float(lat.mean()), "retries": int(sum(r.retries for r in res))}
 
         run(None)                                   # warm-up: capacity history, caches
+        st0 = srv.stats()
         cap = summary(run(None))                    # closed loop: all requests queued at once
+        st1 = srv.stats()
+        passes = st1.proj_passes - st0.proj_passes
+        renders = st1.renders - st0.renders
+        proj_ms = (st1.proj_seconds - st0.proj_seconds) * 1e3
+        # projection GPU time (CUDA events around each pass, which shares the
+        # GPU with the other requests' work) against the GPU time one request
+        # takes at capacity (the closed loop's wall time per request)
+        cap.update(proj_passes=passes, views_per_pass=renders / max(passes, 1),
+                   proj_ms_per_request=proj_ms / max(renders, 1),
+                   proj_share=(proj_ms / max(renders, 1)) / (1e3 / cap["fps"]))
+        # Poisson arrivals at fractions of the unbatched server's capacity, so
+        # both servers see the same offered rates
+        if mb == 1:
+            base_rate[mode] = cap["fps"]
         loads_out = []
         for load in loads:
-            rate = load * cap["fps"]
+            rate = load * base_rate[mode]
             gaps = np.random.default_rng(2).exponential(1.0 / rate, len(reqs))
             res = run(np.cumsum(gaps) - gaps[0])
             loads_out.append({"load": load, "offered_fps": rate, **summary(res)})
         st = srv.stats()
         srv.close()
-        out[mode] = {"capacity": cap, "poisson": loads_out,
-                     "peak_inflight": st.peak_inflight, "arena_peak_gb": st.arena_peak / 1e9,
-                     "issue_us_per_render": st.issue_seconds / max(st.renders, 1) * 1e6}
+        out[mode + ("_unbatched" if mb == 1 else "")] = {
+            "capacity": cap, "poisson": loads_out, "peak_inflight": st.peak_inflight,
+            "arena_peak_gb": st.arena_peak / 1e9,
+            "issue_us_per_render": st.issue_seconds / max(st.renders, 1) * 1e6}
     return {"metric": "serve p50/p99 ms", "value": out["selective"]["poisson"][-1]["p99_ms"],
-            "unit": "ms (p99 at 0.9 load, selective)", "higher_is_better": False,
+            "unit": "ms (p99 at 0.9 of the unbatched capacity, selective)",
+            "higher_is_better": False,
             "selective": out["selective"], "all_levels": out["all_levels"],
+            "selective_unbatched": out["selective_unbatched"],
+            "all_levels_unbatched": out["all_levels_unbatched"],
             "config": {"workload": f"serve-2x{n_gauss // 1000}k-4level-sh3-1256x832-1x..128x",
                        "scenes": 2, "requests_per_run": len(reqs), "max_inflight": 64,
                        "streams": 16, "mem_budget_gb": budget / 2 ** 30,
-                       "arrivals": "Poisson, seed 2, rate = load x closed-loop capacity",
+                       "projection": "requests of one scene and mode admitted together share "
+                                     "one ms_project_views pass (up to 8 cameras); "
+                                     "selective_unbatched: one ms_project per request",
+                       "arrivals": "Poisson, seed 2, rate = load x closed-loop capacity of "
+                                   "the unbatched server (the same rates for both)",
                        "output": "image copied to pinned host memory per request"}}
 
 

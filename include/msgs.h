@@ -52,7 +52,9 @@ typedef enum {
     MS_ERR_CUDA = 3,        /* a CUDA runtime call failed                */
     MS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up        */
     MS_ERR_NO_DEVICE = 5,   /* no usable sm_103 device                   */
-    MS_PENDING = 6          /* ms_serve_poll: the request has not finished */
+    MS_PENDING = 6,         /* ms_serve_poll: the request has not finished */
+    MS_ERR_OOM = 7          /* serving: a request's buffers can never fit the
+                               arena, or the arena could not be allocated   */
 } ms_status_t;
 
 /* Which Gaussians are rendered (Eq. 6 and the "Filter Small" ablation). */
@@ -482,7 +484,14 @@ int ms_aggregate(const ms_scene_t *scene, const ms_camera_t *cams, int32_t n_cam
  * request waits in FIFO order until its buffers fit and fewer than
  * max_inflight requests are on the device.  Admitted requests are spread
  * over n_streams CUDA streams, so requests that arrive while others run
- * overlap with them on the GPU (continuous batching).  A request whose
+ * overlap with them on the GPU (continuous batching).  Requests for the
+ * same scene and mode admitted together (the queue's head and later queued
+ * requests that match it, up to max_batch_views) share one ms_project_views
+ * pass: the scene's geometry is read once for all of them; each then bins
+ * and blends on its own stream.  While requests are in flight, a head with
+ * matching company waits until enough of max_inflight is free for the
+ * batch.  A request that can never fit the arena
+ * finishes with MS_ERR_OOM.  A request whose
  * tile duplicates overflow the capacity it was given is rendered again
  * with the exact count (ms_result_t.retries); the capacity of later
  * requests of the same scene, mode and tile grid is taken from the largest
@@ -502,6 +511,11 @@ typedef struct {
     int64_t initial_capacity;  /* tile duplicates assumed for a scene/mode/grid
                                   not seen yet (0: 2 n, at least 65536)         */
     int32_t device;            /* CUDA device ordinal                          */
+    int32_t max_batch_views;   /* requests of one scene and mode admitted
+                                  together share one projection pass
+                                  (ms_project_views) of up to this many
+                                  cameras, 1..MS_MAX_PROJ_VIEWS (0: the
+                                  maximum; 1: one ms_project per request)    */
 } ms_serve_cfg_t;
 
 typedef struct {
@@ -532,6 +546,10 @@ typedef struct {
     int64_t renders;           /* renders enqueued (requests plus re-renders)  */
     double issue_seconds;      /* scheduler time spent enqueuing them: the
                                   host cost of the launches and copies         */
+    int64_t proj_passes;       /* projection passes (one per admitted batch)   */
+    double proj_seconds;       /* their summed GPU durations (CUDA events
+                                  around each pass on its stream; passes that
+                                  share the GPU with other work run longer)  */
 } ms_serve_stats_t;
 
 /* Seconds on the monotonic clock the server stamps results with. */

@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmsgs.so")
 
 MS_OK, MS_ERR_INVALID_ARG, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_TIMEOUT = 0, 1, 2, 3, 4
-MS_ERR_NO_DEVICE, MS_PENDING = 5, 6
+MS_ERR_NO_DEVICE, MS_PENDING, MS_ERR_OOM = 5, 6, 7
 MS_SELECTIVE, MS_ALL_LEVELS, MS_FILTER_SMALL = 0, 1, 2
 MODES = {"selective": MS_SELECTIVE, "all_levels": MS_ALL_LEVELS,
          "filter_small": MS_FILTER_SMALL}
@@ -88,7 +88,8 @@ class ms_serve_cfg_t(ctypes.Structure):
     _fields_ = [("max_gaussians", ctypes.c_int64), ("max_width", ctypes.c_int32),
                 ("max_height", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_size_t),
-                ("initial_capacity", ctypes.c_int64), ("device", ctypes.c_int32)]
+                ("initial_capacity", ctypes.c_int64), ("device", ctypes.c_int32),
+                ("max_batch_views", ctypes.c_int32)]
 
 
 class ms_request_t(ctypes.Structure):
@@ -110,7 +111,8 @@ class ms_serve_stats_t(ctypes.Structure):
                 ("peak_inflight", ctypes.c_int32), ("scenes", ctypes.c_int32),
                 ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
                 ("arena_peak", ctypes.c_size_t), ("renders", ctypes.c_int64),
-                ("issue_seconds", ctypes.c_double)]
+                ("issue_seconds", ctypes.c_double), ("proj_passes", ctypes.c_int64),
+                ("proj_seconds", ctypes.c_double)]
 
 
 # (name, restype, argtypes) of every entry point declared in include/msgs.h
@@ -605,9 +607,9 @@ class Server:
 
     def __init__(self, max_gaussians: int, max_width: int, max_height: int,
                  mem_budget_bytes: int, max_inflight: int = 64, n_streams: int = 16,
-                 initial_capacity: int = 0, device: int = 0):
+                 initial_capacity: int = 0, device: int = 0, max_batch_views: int = 0):
         cfg = ms_serve_cfg_t(max_gaussians, max_width, max_height, max_inflight, n_streams,
-                             mem_budget_bytes, initial_capacity, device)
+                             mem_budget_bytes, initial_capacity, device, max_batch_views)
         self.handle = ms_serve_create(cfg)
         self.scenes = []   # keeps the DeviceScenes (their arrays) alive
 

@@ -4,10 +4,15 @@
 // One scheduler thread owns the queue.  It admits the request at the head
 // of the FIFO when fewer than max_inflight requests are on the device and
 // the request's buffers fit in the arena (first fit over a free list of
-// offset ranges), enqueues ms_project -> ms_bin -> ms_raster plus the
-// copies of the duplicate counts (and, if asked, of the image) on the next
-// stream, and ends the stream's work with a host function that hands the
-// request back.  Host functions run in stream order after the request's
+// offset ranges), together with later queued requests of the same scene
+// and mode whose buffers fit too (up to max_batch_views); while requests
+// are in flight, a head with such company waits until enough slots are
+// free for them all.  The batch's
+// cameras are projected in one ms_project_views pass on the first
+// request's stream; every request then waits for that pass on its own
+// stream and enqueues ms_bin -> ms_raster plus the copies of the duplicate
+// counts (and, if asked, of the image), ending its stream's work with a
+// host function that hands the request back.  Host functions run in stream order after the request's
 // kernels, so the arena range is free for reuse by then.  A completed
 // request that overflowed its duplicate capacity goes back to the head of
 // the queue with the exact count.
@@ -93,6 +98,7 @@ struct RequestKey {
 
 struct Request {
     ms_server *srv = nullptr;
+    bool timed = false;  // first request of its batch: owns the pass's timing events
     uint64_t ticket = 0;
     ms_request_t r{};
     int32_t status = MS_PENDING;
@@ -112,6 +118,8 @@ struct ms_server {
     char *arena_base = nullptr;
     msgs::Arena arena;
     uint64_t *pinned_counts = nullptr;  // [max_inflight][4]
+    std::vector<cudaEvent_t> proj_done;  // per slot: the batch's projection pass is done
+    std::vector<cudaEvent_t> proj_t0, proj_t1;  // per slot: timing of the pass
     std::vector<int> free_slots;
     std::vector<ms_scene_t> scenes;
     std::map<msgs::RequestKey, int64_t> dup_hist;
@@ -123,8 +131,10 @@ struct ms_server {
     uint64_t next_ticket = 1;
     int inflight = 0, peak_inflight = 0, next_stream = 0;
     int64_t submitted = 0, completed = 0, failed = 0, retries = 0, renders = 0;
-    double issue_s = 0;
+    int64_t proj_passes = 0;
+    double issue_s = 0, proj_s = 0;
     bool stop = false;
+    int max_batch = 1;  // requests per projection pass
     std::thread sched;
 };
 
@@ -156,17 +166,15 @@ int64_t capacity_for(ms_server *s, const Request *q) {
     return std::min<int64_t>(std::max<int64_t>(cap, 1024), 1ll << 30);
 }
 
-// Enqueues one request's render on its stream; called without the lock.
-int launch(ms_server *s, Request *q, cudaStream_t st) {
+// The request's buffers inside its arena range.
+bool request_buffers(ms_server *s, const Request *q, ms_proj_t &proj, ms_bins_t &bins,
+                     float *&image, Layout &L) {
     const ms_scene_t &sc = s->scenes[q->r.scene];
     const ms_camera_t &cam = q->r.cam;
     const int64_t tiles = (int64_t)((cam.width + 15) / 16) * ((cam.height + 15) / 16);
     const int64_t pixels = (int64_t)cam.width * cam.height;
-    Layout L;
-    if (!request_layout(sc.n, tiles, q->cap, pixels, q->r.image_dev == nullptr, L))
-        return fail(MS_ERR_INVALID_ARG, "request sizes out of range");
+    if (!request_layout(sc.n, tiles, q->cap, pixels, q->r.image_dev == nullptr, L)) return false;
     char *b = s->arena_base + q->off;
-    ms_proj_t proj;
     proj.rec = reinterpret_cast<float *>(b + L.rec);
     proj.rect = reinterpret_cast<uint32_t *>(b + L.rect);
     proj.n_tiles = reinterpret_cast<uint32_t *>(b + L.n_tiles);
@@ -175,28 +183,70 @@ int launch(ms_server *s, Request *q, cudaStream_t st) {
     proj.mask = nullptr;
     proj.stats = reinterpret_cast<uint32_t *>(b + L.stats);
     proj.n = std::max<int64_t>(sc.n, 1);
-    ms_bins_t bins;
     bins.gauss_idx = reinterpret_cast<uint32_t *>(b + L.gidx);
     bins.ranges = reinterpret_cast<uint32_t *>(b + L.ranges);
     bins.counts = reinterpret_cast<uint64_t *>(b + L.counts);
     bins.dup_capacity = q->cap;
-    float *image = q->r.image_dev ? q->r.image_dev : reinterpret_cast<float *>(b + L.image);
+    image = q->r.image_dev ? q->r.image_dev : reinterpret_cast<float *>(b + L.image);
+    return true;
+}
+
+// Enqueues a batch's renders (requests of one scene and mode, each with its
+// stream): one projection pass for all of their cameras on the first
+// request's stream, then each request's binning, blend and copies on its
+// own stream after that pass.  Called without the lock.
+int launch(ms_server *s, const std::vector<Request *> &batch,
+           const std::vector<cudaStream_t> &st) {
+    const int nb = (int)batch.size();
+    const Request *q0 = batch[0];
+    const ms_scene_t &sc = s->scenes[q0->r.scene];
+    ms_proj_t proj[MS_MAX_PROJ_VIEWS];
+    ms_bins_t bins[MS_MAX_PROJ_VIEWS];
+    ms_camera_t cams[MS_MAX_PROJ_VIEWS];
+    float *image[MS_MAX_PROJ_VIEWS];
+    Layout L[MS_MAX_PROJ_VIEWS];
+    for (int i = 0; i < nb; i++) {
+        if (!request_buffers(s, batch[i], proj[i], bins[i], image[i], L[i]))
+            return fail(MS_ERR_INVALID_ARG, "request sizes out of range");
+        cams[i] = batch[i]->r.cam;
+    }
+    const int slot0 = q0->slot;
     int rc;
-    if ((rc = ms_project(&sc, &cam, (ms_mode_t)q->r.mode, &proj, st))) return rc;
-    if ((rc = ms_bin(&proj, sc.n, &cam, &bins, b + L.bin_ws, L.bin_ws_bytes, st))) return rc;
-    if ((rc = ms_raster(&proj, &bins, &cam, image, nullptr, nullptr, nullptr, b + L.rws,
-                        L.rws_bytes, st)))
+    if ((rc = cuda_check(cudaEventRecord(s->proj_t0[slot0], st[0]), "event record"))) return rc;
+    if (nb == 1) {
+        if ((rc = ms_project(&sc, &cams[0], (ms_mode_t)q0->r.mode, &proj[0], st[0]))) return rc;
+    } else if ((rc = ms_project_views(&sc, cams, nb, (ms_mode_t)q0->r.mode, proj, st[0]))) {
         return rc;
-    if ((rc = cuda_check(cudaMemcpyAsync(s->pinned_counts + 4 * q->slot, bins.counts, 32,
-                                         cudaMemcpyDeviceToHost, st),
-                         "counts copy")))
-        return rc;
-    if (q->r.image_host &&
-        (rc = cuda_check(cudaMemcpyAsync(q->r.image_host, image, (size_t)pixels * 12,
-                                         cudaMemcpyDeviceToHost, st),
-                         "image copy")))
-        return rc;
-    return cuda_check(cudaLaunchHostFunc(st, on_gpu_done, q), "host function");
+    }
+    if ((rc = cuda_check(cudaEventRecord(s->proj_t1[slot0], st[0]), "event record"))) return rc;
+    if ((rc = cuda_check(cudaEventRecord(s->proj_done[slot0], st[0]), "event record"))) return rc;
+    for (int i = 0; i < nb; i++) {
+        Request *q = batch[i];
+        const ms_camera_t &cam = cams[i];
+        const int64_t pixels = (int64_t)cam.width * cam.height;
+        char *b = s->arena_base + q->off;
+        if (st[i] != st[0] &&
+            (rc = cuda_check(cudaStreamWaitEvent(st[i], s->proj_done[slot0], 0), "stream wait")))
+            return rc;
+        if ((rc = ms_bin(&proj[i], sc.n, &cam, &bins[i], b + L[i].bin_ws, L[i].bin_ws_bytes,
+                         st[i])))
+            return rc;
+        if ((rc = ms_raster(&proj[i], &bins[i], &cam, image[i], nullptr, nullptr, nullptr,
+                            b + L[i].rws, L[i].rws_bytes, st[i])))
+            return rc;
+        if ((rc = cuda_check(cudaMemcpyAsync(s->pinned_counts + 4 * q->slot, bins[i].counts, 32,
+                                             cudaMemcpyDeviceToHost, st[i]),
+                             "counts copy")))
+            return rc;
+        if (q->r.image_host &&
+            (rc = cuda_check(cudaMemcpyAsync(q->r.image_host, image[i], (size_t)pixels * 12,
+                                             cudaMemcpyDeviceToHost, st[i]),
+                             "image copy")))
+            return rc;
+        if ((rc = cuda_check(cudaLaunchHostFunc(st[i], on_gpu_done, q), "host function")))
+            return rc;
+    }
+    return MS_OK;
 }
 
 size_t bytes_for(ms_server *s, const Request *q) {
@@ -222,6 +272,14 @@ void reap(ms_server *s) {
     std::vector<Request *> fin;
     fin.swap(s->finished_gpu);
     for (Request *q : fin) {
+        if (q->timed) {
+            // the first request's stream ran the pass before this request's
+            // work, so both events have completed
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, s->proj_t0[q->slot], s->proj_t1[q->slot]) == cudaSuccess)
+                s->proj_s += 1e-3 * ms;
+            q->timed = false;
+        }
         const uint64_t *h = s->pinned_counts + 4 * q->slot;
         const int64_t d = (int64_t)h[kCntDup];
         const uint64_t status = h[kCntStatus];
@@ -261,39 +319,88 @@ void scheduler(ms_server *s) {
             size_t off = 0;
             if (q->bytes == 0 || q->bytes > s->arena.size()) {
                 s->queue.pop_front();
-                finish(s, q, MS_ERR_CAPACITY);  // can never fit
+                finish(s, q, MS_ERR_OOM);  // can never fit
                 s->cv_done.notify_all();
                 progressed = true;
                 continue;
             }
+            if (s->max_batch > 1 && s->inflight > 0) {
+                // when several queued requests share the head's scene and
+                // mode, wait (the GPU busy with the requests in flight) until
+                // enough slots are free to project them in one pass
+                int want = 1;
+                int scanned = 0;
+                for (auto it = std::next(s->queue.begin());
+                     it != s->queue.end() && want < s->max_batch && scanned < 64; ++it, ++scanned)
+                    if ((*it)->r.scene == q->r.scene && (*it)->r.mode == q->r.mode) want++;
+                if (s->cfg.max_inflight - s->inflight < want) break;
+            }
             if (!s->arena.alloc(q->bytes, off)) break;  // wait for memory
             s->queue.pop_front();
             q->off = off;
-            q->slot = s->free_slots.back();
-            s->free_slots.pop_back();
-            s->inflight++;
+            // later queued requests of the same scene and mode whose buffers
+            // fit now join the head's projection pass (FIFO order among them)
+            std::vector<Request *> batch{q};
+            const int maxb = std::min(s->max_batch, s->cfg.max_inflight - s->inflight);
+            for (auto it = s->queue.begin(); it != s->queue.end() && (int)batch.size() < maxb;) {
+                Request *r = *it;
+                if (r->r.scene != q->r.scene || r->r.mode != q->r.mode) {
+                    ++it;
+                    continue;
+                }
+                r->cap = capacity_for(s, r);
+                r->bytes = bytes_for(s, r);
+                size_t roff = 0;
+                if (r->bytes == 0 || r->bytes > s->arena.size() || !s->arena.alloc(r->bytes, roff)) {
+                    ++it;
+                    continue;
+                }
+                r->off = roff;
+                it = s->queue.erase(it);
+                batch.push_back(r);
+            }
+            std::vector<cudaStream_t> sts;
+            for (Request *r : batch) {
+                r->slot = s->free_slots.back();
+                s->free_slots.pop_back();
+                s->inflight++;
+                if (r->t_start == 0) r->t_start = now_s();
+                sts.push_back(s->streams[s->next_stream]);
+                s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
+            }
             s->peak_inflight = std::max(s->peak_inflight, s->inflight);
-            if (q->t_start == 0) q->t_start = now_s();
-            cudaStream_t st = s->streams[s->next_stream];
-            s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
+            batch[0]->timed = true;
             lk.unlock();
             const double t_issue = now_s();
-            const int rc = launch(s, q, st);
+            const int rc = launch(s, batch, sts);
             const double t_issued = now_s();
             lk.lock();
-            s->renders++;
+            s->renders += (int64_t)batch.size();
+            s->proj_passes++;
             s->issue_s += t_issued - t_issue;
             if (rc != MS_OK) {
                 // whatever was enqueued before the failure may still run:
-                // keep the range until the stream has drained
+                // keep the ranges until the streams have drained
                 lk.unlock();
-                cudaStreamSynchronize(st);
+                for (cudaStream_t st : sts) cudaStreamSynchronize(st);
                 lk.lock();
-                s->arena.release(q->off, q->bytes);
-                s->free_slots.push_back(q->slot);
-                q->slot = -1;
-                s->inflight--;
-                finish(s, q, rc);
+                for (Request *r : batch) {
+                    s->arena.release(r->off, r->bytes);
+                    s->free_slots.push_back(r->slot);
+                    r->slot = -1;
+                    r->timed = false;
+                    s->inflight--;
+                    finish(s, r, rc);
+                }
+                // host functions of requests enqueued before the failure
+                // must not hand them back a second time
+                s->finished_gpu.erase(
+                    std::remove_if(s->finished_gpu.begin(), s->finished_gpu.end(),
+                                   [&batch](Request *r) {
+                                       return std::find(batch.begin(), batch.end(), r) !=
+                                              batch.end();
+                                   }),
+                    s->finished_gpu.end());
                 s->cv_done.notify_all();
             }
             progressed = true;
@@ -343,6 +450,8 @@ extern "C" int ms_serve_create(const ms_serve_cfg_t *cfg, ms_server_t **out) {
         return fail(MS_ERR_INVALID_ARG, "mem_budget_bytes must be at least 1 MiB");
     if (cfg->initial_capacity < 0 || cfg->initial_capacity > (1ll << 30))
         return fail(MS_ERR_INVALID_ARG, "initial_capacity must be 0..2^30");
+    if (cfg->max_batch_views < 0 || cfg->max_batch_views > MS_MAX_PROJ_VIEWS)
+        return fail(MS_ERR_INVALID_ARG, "max_batch_views must be 0..MS_MAX_PROJ_VIEWS");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
         return fail(MS_ERR_NO_DEVICE, "no such CUDA device");
@@ -350,20 +459,37 @@ extern "C" int ms_serve_create(const ms_serve_cfg_t *cfg, ms_server_t **out) {
     if ((rc = cuda_check(cudaSetDevice(cfg->device), "set device"))) return rc;
     ms_server *s = new ms_server();
     s->cfg = *cfg;
+    s->max_batch = cfg->max_batch_views > 0 ? cfg->max_batch_views : MS_MAX_PROJ_VIEWS;
     auto cleanup = [s](int code) {
         for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+        for (auto *v : {&s->proj_done, &s->proj_t0, &s->proj_t1})
+            for (cudaEvent_t e : *v) cudaEventDestroy(e);
         if (s->arena_base) cudaFree(s->arena_base);
         if (s->pinned_counts) cudaFreeHost(s->pinned_counts);
         delete s;
         return code;
     };
     const size_t arena = cfg->mem_budget_bytes & ~(kAlign - 1);
-    if ((rc = cuda_check(cudaMalloc(&s->arena_base, arena), "arena allocation"))) return cleanup(rc);
+    if (cudaMalloc(&s->arena_base, arena) != cudaSuccess) {
+        cudaGetLastError();
+        s->arena_base = nullptr;
+        return cleanup(fail(MS_ERR_OOM, "arena allocation of mem_budget_bytes failed"));
+    }
     s->arena.init(arena);
     if ((rc = cuda_check(cudaMallocHost(&s->pinned_counts, (size_t)cfg->max_inflight * 32),
                          "pinned counts")))
         return cleanup(rc);
-    for (int i = 0; i < cfg->max_inflight; i++) s->free_slots.push_back(cfg->max_inflight - 1 - i);
+    for (int i = 0; i < cfg->max_inflight; i++) {
+        s->free_slots.push_back(cfg->max_inflight - 1 - i);
+        cudaEvent_t e0, e1, e2;
+        if ((rc = cuda_check(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming), "event"))) 
+            return cleanup(rc);
+        s->proj_done.push_back(e0);
+        if ((rc = cuda_check(cudaEventCreate(&e1), "event"))) return cleanup(rc);
+        s->proj_t0.push_back(e1);
+        if ((rc = cuda_check(cudaEventCreate(&e2), "event"))) return cleanup(rc);
+        s->proj_t1.push_back(e2);
+    }
     for (int i = 0; i < cfg->n_streams; i++) {
         cudaStream_t st;
         if ((rc = cuda_check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream")))
@@ -460,6 +586,8 @@ extern "C" int ms_serve_stats(ms_server_t *s, ms_serve_stats_t *st) {
     st->arena_peak = s->arena.peak();
     st->renders = s->renders;
     st->issue_seconds = s->issue_s;
+    st->proj_passes = s->proj_passes;
+    st->proj_seconds = s->proj_s;
     return MS_OK;
 }
 
@@ -478,6 +606,8 @@ extern "C" int ms_serve_destroy(ms_server_t *s) {
         cudaStreamDestroy(st);
     }
     for (auto &kv : s->reqs) delete kv.second;
+    for (auto *v : {&s->proj_done, &s->proj_t0, &s->proj_t1})
+        for (cudaEvent_t e : *v) cudaEventDestroy(e);
     if (s->arena_base) cudaFree(s->arena_base);
     if (s->pinned_counts) cudaFreeHost(s->pinned_counts);
     delete s;
