@@ -205,13 +205,15 @@ def alu_peaks(msgs, torch, dev, reps=3):
 # ---------------------------------------------------------- training step
 
 TRAIN_SCALES = (1, 4, 16, 64)
+TRAIN_LEVELS = (1, 2, 3, 4)    # the level whose creation scale each view renders at
 
 
 def train_setup(msgs, torch, ds, sc, dev):
     """Forward + backward of a multi-scale training batch (Sec. 4.1): four
-    orbit cameras at 1x/4x/16x/64x of 1256x832, selective rendering, L1
-    mean loss per view against seeded U(0,1) targets, gradients of every
-    scene parameter accumulated over the batch.  Returns the cameras, the
+    orbit cameras at 1x/4x/16x/64x of 1256x832 (the creation scales of
+    levels 1-4, so each view's projection also applies UpdateRange to its
+    level), selective rendering, L1 mean loss per view against seeded U(0,1)
+    targets, gradients of every scene parameter accumulated over the batch.  Returns the cameras, the
     renderers, forward() (prepare, 4 forwards, 4 loss gradients) and
     backward() (4 backwards), the loss and the gradient buffers."""
     base = inputs.orbit_cameras(4, seed=2, radius=25.0)
@@ -225,7 +227,8 @@ def train_setup(msgs, torch, ds, sc, dev):
     for cam in cams:
         probe.render(ds, cam, "selective")
         rc, d, _ = msgs.ms_bin_counts(probe.bins)
-        caps.append(int(d * 1.05) + 1024)
+        # margin: UpdateRange moves the ranges, and with them the selection
+        caps.append(int(d * 1.5) + 4096)
     del probe
     rs = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, cap, device=dev, with_cover=False,
                         with_mask=False) for c, cap in zip(cams, caps)]
@@ -251,8 +254,10 @@ def train_setup(msgs, torch, ds, sc, dev):
         msgs.ms_scene_prepare(ds.struct)
         loss.zero_()
         main = torch.cuda.current_stream()
-        msgs.ms_project_views(ds.struct, css, msgs.MODES["selective"], [r.proj for r in rs],
-                              main)
+        # view v renders at the creation scale 4^v of level v + 1, whose
+        # coverage ranges it updates after selecting (Alg. 2, Eq. 5)
+        msgs.ms_project_views_update(ds.struct, css, msgs.MODES["selective"],
+                                     list(TRAIN_LEVELS), [r.proj for r in rs], main)
         for r, cam, out, tgt, dl, st in zip(rs, cams, outs, targets, dls, streams):
             st.wait_stream(main)
             with torch.cuda.stream(st):
@@ -273,7 +278,9 @@ def train_setup(msgs, torch, ds, sc, dev):
 
 def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
     """The training step timed as two CUDA graphs per iteration (forward,
-    backward) with events on the launching stream."""
+    backward) with events on the launching stream.  The scene's coverage
+    ranges, which every step updates, are restored afterwards."""
+    saved = (ds.s_max.clone(), ds.s_min.clone())
     cams, rs, forward, backward, loss, grads_t = train_setup(msgs, torch, ds, sc, dev)
     forward()
     backward()
@@ -312,6 +319,8 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
     for r in rs:
         r.check()
     finite = all(bool(torch.isfinite(t).all()) for t in grads_t.values())
+    ds.s_max.copy_(saved[0])
+    ds.s_min.copy_(saved[1])
     launches = 2                                    # prepare; one projection for the views
     for cam in cams:
         tiles = cam.tiles_x * cam.tiles_y
@@ -324,6 +333,8 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
             "config": {"workload": f"train-multiscale-{sc.n // 1000}k-4level-sh3-4views",
                        "views": [[c.width, c.height] for c in cams],
                        "scales": list(TRAIN_SCALES), "mode": "selective",
+                       "update_range": "fused into the projection pass: view v updates "
+                                       "level v + 1 after its selection",
                        "loss": "L1 mean per view, targets U(0,1) seed 1",
                        "launch": "forward (one stream per view) and backward (one batched "
                                  "call over the views) each one CUDA graph"}}

@@ -7,6 +7,7 @@
  *   ms_scene_prepare  per-scene activations (exp(log_scale), ln(255 sigma))
  *   ms_project        EWA splat, pixel coverage, selection, SH colour
  *   ms_project_views  the same for up to MS_MAX_PROJ_VIEWS cameras in one pass
+ *   ms_project_views_update  ... with UpdateRange fused for training renders
  *   ms_select         re-run the selection predicate on stored coverage
  *   ms_update_range   UpdateRange of the coverage bounds
  *   ms_bin            16x16 tile binning with a stable (tile, depth) order
@@ -229,6 +230,26 @@ int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
  */
 int ms_project_views(const ms_scene_t *scene, const ms_camera_t *cams, int32_t n_views,
                      ms_mode_t mode, const ms_proj_t *outs, void *stream);
+
+/*
+ * ms_project_views for a multi-scale training step (Sec. 4.1 "Multi-Scale
+ * Training", Alg. 2): view v with update_levels[v] = l_r >= 1 is rendered at
+ * the creation scale 4^(l_r - 1) of level l_r, and after its selection
+ * (which uses the coverage ranges as they stand) UpdateRange (Eq. 5)
+ * updates, for every valid Gaussian of level l_r whose level-set rectangle
+ * touches that view's image,
+ *   s_max = max(0.95 s_max, S),  s_min = min(1.05 s_min, S)
+ * in scene->s_max / scene->s_min (device arrays the call writes).  Views
+ * are taken in order: view v + 1 selects with the ranges view v left, so
+ * the outputs and the ranges equal those of n_views calls of ms_project,
+ * each followed by ms_update_range for its level.  update_levels (host
+ * array of n_views entries, 0..n_levels; 0 = the view updates nothing) may
+ * be NULL (no view updates: ms_project_views).  Errors as ms_project_views,
+ * and MS_ERR_INVALID_ARG for a level outside 0..n_levels.
+ */
+int ms_project_views_update(const ms_scene_t *scene, const ms_camera_t *cams, int32_t n_views,
+                            ms_mode_t mode, const int32_t *update_levels,
+                            const ms_proj_t *outs, void *stream);
 
 /*
  * Selection predicate alone (Eq. 6, Sec. 4.1 exemptions) on a coverage
@@ -581,6 +602,18 @@ int ms_serve_stats(ms_server_t *srv, ms_serve_stats_t *stats);
 /* Waits for the requests on the device, drops the queued ones, frees
  * everything.  srv may be NULL. */
 int ms_serve_destroy(ms_server_t *srv);
+
+/*
+ * Test hook for the bounded device waits (the paper has no counterpart):
+ * every look-back wait of ms_bin (the radix passes' and the duplication's
+ * decoupled look-back) gives up after `limit` polls of a predecessor that
+ * has not published, instead of the default (about half a second), sets
+ * status bit 2 in ms_bins_t.counts and carries on with in-bounds writes;
+ * ms_bin_counts then returns MS_ERR_TIMEOUT and the lists are not valid.
+ * limit = 0 restores the default.  Process-wide; read when ms_bin enqueues
+ * its kernels.  Only ms_bin is affected.  Returns MS_OK.
+ */
+int ms_debug_set_spin_limit(uint32_t limit);
 
 /*
  * Measurement probes (the paper has no counterpart): the throughput of the

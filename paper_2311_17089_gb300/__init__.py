@@ -125,6 +125,10 @@ _SIGNATURES = [
     ("ms_project_views", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
                                         ctypes.c_int32, ctypes.c_int, ctypes.POINTER(ms_proj_t),
                                         P]),
+    ("ms_project_views_update", ctypes.c_int, [ctypes.POINTER(ms_scene_t),
+                                               ctypes.POINTER(ms_camera_t), ctypes.c_int32,
+                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(ms_proj_t), P]),
     ("ms_select", ctypes.c_int, [ctypes.POINTER(ms_scene_t), P, ctypes.c_int, P, P]),
     ("ms_update_range", ctypes.c_int, [ctypes.POINTER(ms_scene_t),
                                        ctypes.POINTER(ms_camera_t), ctypes.c_int32, P]),
@@ -173,6 +177,7 @@ _SIGNATURES = [
                                      ctypes.POINTER(ms_result_t)]),
     ("ms_serve_stats", ctypes.c_int, [P, ctypes.POINTER(ms_serve_stats_t)]),
     ("ms_serve_destroy", ctypes.c_int, [P]),
+    ("ms_debug_set_spin_limit", ctypes.c_int, [ctypes.c_uint32]),
     ("ms_alu_probe", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]),
     ("ms_alu_probe_ops", ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
 ]
@@ -259,6 +264,21 @@ def ms_project_views(scene: ms_scene_t, cams, mode: int, outs, stream=None):
                                   P(_stream(stream))))
 
 
+def ms_project_views_update(scene: ms_scene_t, cams, mode: int, update_levels, outs,
+                            stream=None):
+    """ms_project_views with UpdateRange (Eq. 5) fused: view v updates the
+    coverage ranges of level update_levels[v] (0: none) after its
+    selection, in view order."""
+    n = len(cams)
+    if len(outs) != n or len(update_levels) != n:
+        raise MsError(MS_ERR_INVALID_ARG, "one ms_proj_t and one update level per camera")
+    ca = (ms_camera_t * max(n, 1))(*cams)
+    oa = (ms_proj_t * max(n, 1))(*outs)
+    la = (ctypes.c_int32 * max(n, 1))(*[int(x) for x in update_levels])
+    _check(lib().ms_project_views_update(ctypes.byref(scene), ca, n, int(mode), la, oa,
+                                         P(_stream(stream))))
+
+
 def ms_select(scene: ms_scene_t, cover_ptr: int, mode: int, mask_ptr: int, stream=None):
     _check(lib().ms_select(ctypes.byref(scene), P(cover_ptr), int(mode), P(mask_ptr),
                            P(_stream(stream))))
@@ -287,6 +307,12 @@ def ms_bin_noalloc(proj: ms_proj_t, n: int, cam: ms_camera_t, out: ms_bins_t, st
 
 
 MS_PROBE_FFMA, MS_PROBE_FFMA2, MS_PROBE_EX2 = 0, 1, 2
+
+
+def ms_debug_set_spin_limit(limit: int):
+    """Test hook: ms_bin's look-back waits give up after `limit` polls
+    (0: the default)."""
+    _check(lib().ms_debug_set_spin_limit(int(limit)))
 
 
 def ms_alu_probe(kind: int, blocks: int, iters: int, out_ptr: int, stream=None):

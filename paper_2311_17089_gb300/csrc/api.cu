@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "common.cuh"
@@ -33,7 +34,19 @@ int num_sms() {
     return n;
 }
 
+static std::atomic<uint32_t> g_bin_spin_limit{0};
+
+uint32_t bin_spin_limit() {
+    const uint32_t v = g_bin_spin_limit.load(std::memory_order_relaxed);
+    return v ? v : kSpinLimit;
+}
+
 }  // namespace msgs
+
+extern "C" int ms_debug_set_spin_limit(uint32_t limit) {
+    msgs::g_bin_spin_limit.store(limit, std::memory_order_relaxed);
+    return MS_OK;
+}
 
 extern "C" const char *ms_last_error(void) { return msgs::g_last_error.c_str(); }
 

@@ -186,7 +186,7 @@ onesweep_pass(PassArgs a) {
                     if (stop) break;
                     k -= i;
                     if (i == 0) {
-                        if (++spins > kSpinLimit) {
+                        if (++spins > a.spin_limit) {
                             atomicOr(a.err, (unsigned long long)kStatusTimeout);
                             break;
                         }
@@ -255,6 +255,7 @@ struct DupArgs {
     uint32_t *tstatus;           // tile-pass look-back words, zeroed here
     uint64_t tstride;            // words per tile pass in tstatus
     uint32_t tpart;              // partition size of the tile passes
+    uint32_t spin_limit;         // look-back polls before a wait gives up
 };
 
 __global__ void __launch_bounds__(kDupThreads)
@@ -348,7 +349,7 @@ duplicate_kernel(DupArgs a) {
                     if (stop) break;
                     k -= i;
                     if (i == 0) {
-                        if (++spins > kSpinLimit) {
+                        if (++spins > a.spin_limit) {
                             atomicOr(a.err, (unsigned long long)kStatusTimeout);
                             break;
                         }
@@ -600,6 +601,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     uint32_t *tickets = U32(L.tickets);
     unsigned long long *err = reinterpret_cast<unsigned long long *>(out->counts) + kCntStatus;
     const int sms = num_sms();
+    const uint32_t spin_limit = bin_spin_limit();
 
     finish_counts_kernel<<<1, 1, 0, st>>>(proj->stats, reinterpret_cast<unsigned long long *>(out->counts),
                                           (uint64_t)out->dup_capacity);
@@ -624,6 +626,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
         a.status = U32(L.dstatus) + (size_t)pass * L.dparts * 256;
         a.ticket = tickets + pass;
         a.err = err;
+        a.spin_limit = spin_limit;
         if ((rc = launch_onesweep(a, (uint64_t)n, st))) return rc;
     }
     // after 4 passes (out: a, b, a, b) the depth-ordered indices are in dv[1]
@@ -647,6 +650,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     da.tstatus = U32(L.tstatus);
     da.tstride = (uint64_t)L.tparts * 256;
     da.tpart = (uint32_t)sort_part((uint64_t)out->dup_capacity);
+    da.spin_limit = spin_limit;
     int dupgrid = (int)std::min<int64_t>(L.dupparts, (int64_t)sms * 4);
     duplicate_kernel<<<dupgrid, kDupThreads, 0, st>>>(da);
     // ---- stable sort by tile id
@@ -669,6 +673,7 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
         a.status = U32(L.tstatus) + (size_t)pass * L.tparts * 256;
         a.ticket = tickets + 5 + pass;
         a.err = err;
+        a.spin_limit = spin_limit;
         if ((rc = launch_onesweep(a, (uint64_t)out->dup_capacity, st))) return rc;
     }
     ranges_kernel<<<sms * 4, 256, 0, st>>>(final_keys, dup64, (uint64_t)out->dup_capacity,

@@ -304,6 +304,8 @@ struct ProjOut {
 template <int MAXV>
 struct ProjViews {
     int n_views;
+    int update_level[MAXV];  // level whose coverage range the view updates (0: none)
+    float *smax_out, *smin_out;  // the scene's ranges, written when a view updates
     int color_src[MAXV];
     CamK cam[MAXV];
     ProjOut out[MAXV];
@@ -429,6 +431,7 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
         float3 col = make_float3(0.0f, 0.0f, 0.0f);
         float op = 0.0f;
         int col_src = -1;  // view whose camera centre col was evaluated towards
+        bool range_dirty = false;
         for (int v = 0; v < nv; v++) {
             const CamK &cam = pv.cam[v];
             const ProjOut &o = pv.out[v];
@@ -438,6 +441,15 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
                 Foot f;
                 footprint_cov(m, S6, cov_ok, lnop_i, cam, f);
                 if (f.valid) sel = select_pred(f.S, level_i, sc.n_levels, smax_i, smin_i, mode);
+                // Alg. 2: a training render at the creation scale of level
+                // l_r updates that level's ranges (Eq. 5) after its
+                // selection used the ranges before the update; the next view
+                // selects with the updated ones
+                if (pv.update_level[v] == level_i && f.valid && f.ntiles > 0) {
+                    smax_i = fmaxf(fm(0.95f, smax_i), f.S);
+                    smin_i = fminf(fm(1.05f, smin_i), f.S);
+                    range_dirty = true;
+                }
                 listed = sel && f.ntiles > 0;
                 ntiles = listed ? f.ntiles : 0u;
                 o.n_tiles[i] = ntiles;
@@ -477,6 +489,10 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
                 atomicAdd(&s_surv[MAXV == 1 ? 0 : v], ws);
                 atomicAdd(&s_dup[MAXV == 1 ? 0 : v], (unsigned long long)wd);
             }
+        }
+        if (range_dirty) {
+            pv.smax_out[i] = smax_i;
+            pv.smin_out[i] = smin_i;
         }
         __syncthreads();  // the buffer is refilled by the next iteration but one
         if ((it + 1) % kHistFlushChunks == 0) {
@@ -560,10 +576,13 @@ int check_proj_out(const ms_scene_t *scene, const ms_proj_t *out) {
 
 template <int MAXV>
 int launch_project(const ms_scene_t *scene, const ms_camera_t *cams, int nv, ms_mode_t mode,
-                   const ms_proj_t *outs, cudaStream_t st) {
+                   const ms_proj_t *outs, const int32_t *update_levels, cudaStream_t st) {
     ProjViews<MAXV> pv;
     pv.n_views = nv;
+    pv.smax_out = scene->s_max;
+    pv.smin_out = scene->s_min;
     for (int v = 0; v < MAXV; v++) {
+        pv.update_level[v] = (update_levels && v < nv) ? update_levels[v] : 0;
         const int u = v < nv ? v : 0;
         pv.cam[v] = make_cam(cams[u]);
         const ms_proj_t &o = outs[u];
@@ -590,9 +609,10 @@ int launch_project(const ms_scene_t *scene, const ms_camera_t *cams, int nv, ms_
 }  // namespace
 }  // namespace msgs
 
-extern "C" int ms_project_views(const ms_scene_t *scene, const ms_camera_t *cams,
-                                int32_t n_views, ms_mode_t mode, const ms_proj_t *outs,
-                                void *stream) {
+extern "C" int ms_project_views_update(const ms_scene_t *scene, const ms_camera_t *cams,
+                                       int32_t n_views, ms_mode_t mode,
+                                       const int32_t *update_levels, const ms_proj_t *outs,
+                                       void *stream) {
     int rc = check_scene(scene, true);
     if (rc) return rc;
     if (n_views < 1 || n_views > MS_MAX_PROJ_VIEWS)
@@ -603,6 +623,8 @@ extern "C" int ms_project_views(const ms_scene_t *scene, const ms_camera_t *cams
     for (int v = 0; v < n_views; v++) {
         if ((rc = check_cam(&cams[v]))) return rc;
         if ((rc = check_proj_out(scene, &outs[v]))) return rc;
+        if (update_levels && (update_levels[v] < 0 || update_levels[v] > scene->n_levels))
+            return fail(MS_ERR_INVALID_ARG, "update_levels[v] must be 0..n_levels");
     }
     cudaStream_t st = as_stream(stream);
     for (int v = 0; v < n_views; v++)
@@ -610,8 +632,14 @@ extern "C" int ms_project_views(const ms_scene_t *scene, const ms_camera_t *cams
                              "stats memset")))
             return rc;
     if (scene->n == 0) return MS_OK;
-    if (n_views == 1) return launch_project<1>(scene, cams, 1, mode, outs, st);
-    return launch_project<MS_MAX_PROJ_VIEWS>(scene, cams, n_views, mode, outs, st);
+    if (n_views == 1) return launch_project<1>(scene, cams, 1, mode, outs, update_levels, st);
+    return launch_project<MS_MAX_PROJ_VIEWS>(scene, cams, n_views, mode, outs, update_levels, st);
+}
+
+extern "C" int ms_project_views(const ms_scene_t *scene, const ms_camera_t *cams,
+                                int32_t n_views, ms_mode_t mode, const ms_proj_t *outs,
+                                void *stream) {
+    return ms_project_views_update(scene, cams, n_views, mode, nullptr, outs, stream);
 }
 
 extern "C" int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,

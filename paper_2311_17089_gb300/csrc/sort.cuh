@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "common.cuh"
+
 namespace msgs {
 
 constexpr int kSortThreads = 256;
@@ -55,6 +57,7 @@ struct PassArgs {
     uint32_t *status;           // [partitions][256]
     uint32_t *ticket;
     unsigned long long *err;    // status word (bit kStatusTimeout)
+    uint32_t spin_limit = kSpinLimit;  // look-back polls before a wait gives up
 };
 
 // One pass: items [0, count) (count from n32 / n64 / n_cap; only items with

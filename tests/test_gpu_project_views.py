@@ -167,3 +167,43 @@ def test_histogram_flush_on_a_30M_scene(cuda):
         for k in ta:
             assert ta[k].equal(tj[k]), k
         del ta, pa
+
+
+@pytest.mark.parametrize("n_views", [1, 4, 6])
+def test_training_projection_updates_ranges_like_the_oracle(cuda, n_views):
+    """Multi-scale training (Alg. 2): ms_project_views_update renders each
+    view with the coverage ranges as they stand, then applies UpdateRange
+    (Eq. 5) for the view's level.  Over three steps of views at the levels'
+    creation scales (1x, 4x, 16x, 64x of orbit cameras, repeated for more
+    than four views), every view's selection mask and coverage and the
+    ranges after every step equal the oracle's sequence of footprints and
+    or_update_range calls, bit for bit; a view with level 0 updates
+    nothing."""
+    sc = inputs.multiscale_scene(n=30_011, seed=5)       # fresh ranges (0, +inf)
+    ds = msgs.DeviceScene(sc)
+    ref = sc.copy()
+    for step in range(3):
+        orbit = inputs.orbit_cameras(n_views, seed=20 + step, radius=25.0, width=628,
+                                     height=416)
+        levels = [(v % 4) + 1 for v in range(n_views)]
+        if n_views == 6:
+            levels[5] = 0                                  # renders, updates nothing
+        cams = [inputs.downscale(c, 4 ** (l - 1) if l else 2) for c, l in zip(orbit, levels)]
+        rs = renderers(sc, cams)
+        msgs.ms_project_views_update(ds.struct, [msgs.camera_struct(c) for c in cams],
+                                     msgs.MODES["selective"], levels, [r.proj for r in rs])
+        cuda.cuda.synchronize()
+        for v, (cam, lv, r) in enumerate(zip(cams, levels, rs)):
+            fp = oracle.footprints(ref, cam, "selective")
+            got_mask = np.unpackbits(r.mask.cpu().numpy().view(np.uint8),
+                                     bitorder="little")[:sc.n].astype(bool)
+            np.testing.assert_array_equal(got_mask, fp["selected"] == 1, err_msg=f"view {v}")
+            np.testing.assert_array_equal(r.cover.cpu().numpy()[:sc.n].view(np.uint32),
+                                          fp["cover"].view(np.uint32))
+            if lv:
+                oracle.update_range(ref, cam, lv)
+        np.testing.assert_array_equal(ds.s_max.cpu().numpy().view(np.uint32),
+                                      np.ascontiguousarray(ref.s_max, np.float32).view(np.uint32))
+        np.testing.assert_array_equal(ds.s_min.cpu().numpy().view(np.uint32),
+                                      np.ascontiguousarray(ref.s_min, np.float32).view(np.uint32))
+    assert np.isfinite(ref.s_max).sum() > 1000 and (ref.s_max > 0).sum() > 1000
