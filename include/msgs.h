@@ -54,8 +54,11 @@ typedef enum {
     MS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up        */
     MS_ERR_NO_DEVICE = 5,   /* no usable sm_103 device                   */
     MS_PENDING = 6,         /* ms_serve_poll: the request has not finished */
-    MS_ERR_OOM = 7          /* serving: a request's buffers can never fit the
+    MS_ERR_OOM = 7,         /* serving: a request's buffers can never fit the
                                arena, or the arena could not be allocated   */
+    MS_ERR_BOUNDS = 8       /* an index check of the debug build (libmsgs
+                               compiled with -DMS_DEBUG) failed; the kernels
+                               clamped or skipped the access (status bit 3) */
 } ms_status_t;
 
 /* Which Gaussians are rendered (Eq. 6 and the "Filter Small" ablation). */
@@ -174,7 +177,7 @@ typedef struct {
  *                 needed, even when it exceeds the capacity), [1] survivor
  *                 count, [2] status bits (1 = capacity overflow, 2 = a
  *                 bounded wait gave up), [3] reserved
- *   dup_capacity  entries gauss_idx can hold, 1 .. 2^30
+ *   dup_capacity  entries gauss_idx can hold, 1 .. 2^30 - 1
  */
 typedef struct {
     uint32_t *gauss_idx;
@@ -273,8 +276,9 @@ int ms_update_range(const ms_scene_t *scene, const ms_camera_t *cam,
 size_t ms_bin_workspace_bytes(int64_t n, int64_t tiles, int64_t dup_capacity);
 
 /*
- * Tile binning (Sec. 3.1: "all 2D Gaussians touching each tile are sorted
- * based on their original depth").  Listed Gaussians are sorted by depth
+ * Tile binning (Sec. 3.1: the Gaussians whose splats touch a tile are
+ * listed for it in the order of their view depth).  n <= 2^30 - 1 (the
+ * radix passes' digit counts are 30-bit).  Listed Gaussians are sorted by depth
  * bits with a stable LSD radix sort (ties keep index order), expanded to
  * one entry per covered tile in that order, and stably radix-sorted by tile
  * id, which yields every tile's list in (depth, index) order.  Fully
@@ -318,9 +322,11 @@ int ms_bin_noalloc(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
 
 /*
  * Copy the counts of a finished ms_bin to the host (synchronises
- * `stream`).  Returns MS_ERR_CAPACITY if D exceeded the capacity
- * (*d_needed tells how many are needed), MS_ERR_TIMEOUT if a bounded wait
- * gave up, else MS_OK.  Either pointer may be NULL.
+ * `stream`).  Returns MS_ERR_BOUNDS if an index check of the debug build
+ * failed (in ms_bin or in an ms_raster that used these bins),
+ * MS_ERR_TIMEOUT if a bounded wait gave up, MS_ERR_CAPACITY if D exceeded
+ * the capacity (*d_needed tells how many are needed), else MS_OK.  Either
+ * pointer may be NULL.
  */
 int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed,
                   int64_t *survivors, void *stream);

@@ -14,7 +14,7 @@
  *     the local affine (Jacobian) approximation of EWA splatting:
  *     V = J W Sigma W^T J^T with Sigma = R diag(s)^2 R^T.
  *   - Sec. 3.2, Eq. 4: the rasterised splat uses V + V^h, V^h a low-pass
- *     filter "determined by the screen pixel size"; the paper gives no
+ *     filter whose size the paper ties to the screen pixel; it gives no
  *     value, this oracle reads it as 0.3 px^2 on each diagonal entry.
  *   - Sec. 4.1 "Pixel Coverage": S is the smaller of the horizontal and
  *     vertical full widths of the splat at the level set

@@ -2,8 +2,8 @@
  * View-dependent colour from spherical-harmonic coefficients, FP64.
  * TEST INFRASTRUCTURE (see oracle.h).
  *
- * The Gaussian's colour c_k (Sec. 3.1) is stored as "spherical harmonics
- * features" (supplementary, "Average Pooling and Enlargement").  The paper
+ * The Gaussian's colour c_k (Sec. 3.1) is stored as spherical-harmonic
+ * coefficients (supplementary, "Average Pooling and Enlargement").  The paper
  * does not give the basis; this oracle uses the real orthonormal basis
  *     Y_l0  = K_l0 P_l^0(cos t)
  *     Y_lm  = sqrt(2) K_lm P_l^m(cos t) cos(m p)      m > 0

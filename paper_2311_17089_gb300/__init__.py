@@ -21,10 +21,12 @@ import numpy as np
 from . import inputs
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmsgs.so")
+# MSGS_DEBUG=1 loads the debug build (index checks reported as MS_ERR_BOUNDS)
+DEBUG = os.environ.get("MSGS_DEBUG", "0") == "1"
+LIB_PATH = os.path.join(_HERE, "libmsgs_debug.so" if DEBUG else "libmsgs.so")
 
 MS_OK, MS_ERR_INVALID_ARG, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_TIMEOUT = 0, 1, 2, 3, 4
-MS_ERR_NO_DEVICE, MS_PENDING, MS_ERR_OOM = 5, 6, 7
+MS_ERR_NO_DEVICE, MS_PENDING, MS_ERR_OOM, MS_ERR_BOUNDS = 5, 6, 7, 8
 MS_SELECTIVE, MS_ALL_LEVELS, MS_FILTER_SMALL = 0, 1, 2
 MODES = {"selective": MS_SELECTIVE, "all_levels": MS_ALL_LEVELS,
          "filter_small": MS_FILTER_SMALL}
@@ -187,7 +189,7 @@ _lib = None
 
 def build(force: bool = False) -> str:
     from . import _build
-    return _build.build(force=force)
+    return _build.build(force=force, debug=DEBUG)
 
 
 def lib():
@@ -195,8 +197,8 @@ def lib():
     global _lib
     if _lib is None:
         from . import _build
-        if not _build.up_to_date():
-            _build.build()
+        if not _build.up_to_date(DEBUG):
+            _build.build(debug=DEBUG)
         L = ctypes.CDLL(LIB_PATH)
         for name, res, args in _SIGNATURES:
             f = getattr(L, name)

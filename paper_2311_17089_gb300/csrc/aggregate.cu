@@ -224,7 +224,7 @@ struct AggLayout {
 };
 
 static bool agg_layout(int64_t n, AggLayout &L) {
-    if (n < 0 || n > INT32_MAX) return false;
+    if (n < 0 || n > kMaxSortItems) return false;
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     L.parts = sort_parts((uint64_t)nn);

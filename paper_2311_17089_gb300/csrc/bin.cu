@@ -97,8 +97,9 @@ onesweep_pass(PassArgs a) {
     __shared__ uint32_t s_total;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // a pass holds fewer than 2^31 items (capacity <= 2^30, scenes < 2^31),
-    // so item indices and scatter positions are 32-bit
+    // a pass holds fewer than 2^30 items (kMaxSortItems), so item indices
+    // and scatter positions are 32-bit and digit counts fit the look-back
+    // words' 30 bits
     const uint32_t n = (uint32_t)pass_count(a);
     const uint32_t parts = (n + kPart - 1) / kPart;
     {
@@ -213,6 +214,7 @@ onesweep_pass(PassArgs a) {
             if (rank[r] == 0xffffffffu) continue;
             uint32_t dd = rank[r] >> 16;
             uint32_t pos = s_excl[dd] + s_whist[warp][dd] + (rank[r] & 0xffffu);
+            MS_DCHECK(pos < (uint32_t)kPart, a.err);
             s_keys[pos] = key[r];
             s_vals[pos] = val[r];
         }
@@ -223,6 +225,7 @@ onesweep_pass(PassArgs a) {
             const uint32_t k = s_keys[j];
             const uint32_t g = s_gofs[(k >> a.shift) & 255u] + j;
             if (g >= n) {  // only reachable after a wait gave up
+                MS_DCHECK(false, a.err);
                 atomicOr(a.err, (unsigned long long)kStatusTimeout);
                 continue;
             }
@@ -305,6 +308,7 @@ duplicate_kernel(DupArgs a) {
                     c = a.n_tiles[g];
                     rc = a.rect[g];
                 } else {
+                    MS_DCHECK(false, a.err);
                     atomicOr(a.err, (unsigned long long)kStatusTimeout);
                 }
             }
@@ -401,6 +405,7 @@ duplicate_kernel(DupArgs a) {
                         yy++;
                     }
                     if (tile >= a.tiles) {
+                        MS_DCHECK(false, a.err);
                         atomicOr(a.err, (unsigned long long)kStatusTimeout);
                         tile = 0xffffffffu;  // not written
                     } else if (base + k < a.cap) {  // the entries the tile passes sort
@@ -528,7 +533,7 @@ struct BinLayout {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bool layout(int64_t n, int64_t cap, BinLayout &L) {
-    if (n < 0 || n > INT32_MAX || cap < 1 || cap > (1ll << 30)) return false;
+    if (n < 0 || n > kMaxSortItems || cap < 1 || cap > kMaxSortItems) return false;
     int64_t nn = n > 0 ? n : 1;
     L.dparts = sort_parts((uint64_t)nn);
     L.tparts = sort_parts((uint64_t)cap);
@@ -693,6 +698,8 @@ extern "C" int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed, int64_t *
     if ((rc = cuda_check(cudaStreamSynchronize(st), "stream sync"))) return rc;
     if (d_needed) *d_needed = (int64_t)h[kCntDup];
     if (survivors) *survivors = (int64_t)h[kCntSurvivors];
+    if (h[kCntStatus] & kStatusBounds)
+        return fail(MS_ERR_BOUNDS, "an index check of the debug build failed");
     if (h[kCntStatus] & kStatusTimeout)
         return fail(MS_ERR_TIMEOUT, "a bounded device wait gave up during ms_bin");
     if (h[kCntStatus] & kStatusOverflow)

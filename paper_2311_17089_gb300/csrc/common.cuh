@@ -39,6 +39,24 @@ constexpr int kCntSurvivors = 1;
 constexpr int kCntStatus = 2;
 constexpr uint64_t kStatusOverflow = 1;
 constexpr uint64_t kStatusTimeout = 2;
+constexpr uint64_t kStatusBounds = 4;  // a debug build's index check failed
+
+// Index checks of the debug build (compiled with -DMS_DEBUG; nothing in the
+// release build): a check that fails sets kStatusBounds in the status word
+// `status` (an unsigned long long * in device memory) and the kernel goes
+// on along the path its release form takes (every such access is guarded
+// or clamped there too); ms_bin_counts then returns MS_ERR_BOUNDS.  No
+// check traps.
+#ifdef MS_DEBUG
+#define MS_DCHECK(cond, status) \
+    do { \
+        if (!(cond)) atomicOr((status), (unsigned long long)kStatusBounds); \
+    } while (0)
+#else
+#define MS_DCHECK(cond, status) \
+    do { \
+    } while (0)
+#endif
 
 // Raster record: three float4 per Gaussian.
 //   r0 = (ux, uy, A, B)      A = -log2(e)/2 conic a, B = -log2(e) conic b

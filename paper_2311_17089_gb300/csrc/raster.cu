@@ -305,10 +305,12 @@ __device__ __forceinline__ void blend_pairs(const WarpPairs &wp, uint32_t n, uin
 // the buffer.
 __device__ __forceinline__ void issue_batch(const RasterArgs &a, uint32_t first, uint32_t cnt,
                                             float4 *buf, uint64_t *bar) {
+    MS_DCHECK(cnt <= (uint32_t)kChunk, a.err);
     if (threadIdx.x == 0) mbar_expect_tx(bar, cnt * kRecBytes);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     for (uint32_t i = threadIdx.x; i < cnt; i += kRasterThreads) {
         uint32_t g = a.gidx[first + i];
+        MS_DCHECK(g < a.n_rec, a.err);
         if (g >= a.n_rec) g = 0;  // unreachable unless binning reported an error
         bulk_copy_g2s(buf + 3 * i, a.rec + 3 * (size_t)g, kRecBytes, bar);
     }
@@ -609,6 +611,7 @@ raster_kernel(RasterArgs a) {
         // by the tile's last segment
         if (inside && !was_term && (s.term || last_seg || redone)) {
             const size_t p = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+            MS_DCHECK(p < plane, a.err);
             a.image[p] = fmaf(s.T, a.bg0, s.C0);
             a.image[plane + p] = fmaf(s.T, a.bg1, s.C1);
             a.image[2 * plane + p] = fmaf(s.T, a.bg2, s.C2);
@@ -745,6 +748,7 @@ extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
         la.seg_off = a.seg_off;
         la.seg_len = a.seg_len;
         la.pre = a.pre;
+        la.err = a.err;
         if ((rc = cuda_check(cudaGetLastError(), "segment offsets launch"))) return rc;
         if (group > 0) return cuda_check(launch_raster_group(la, group, st), "raster group launch");
         return cuda_check(launch_raster_list(la, st), "raster list launch");

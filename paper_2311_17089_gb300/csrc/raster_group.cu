@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(256, 4) raster_group_kernel(ListArgs a) {
     auto stage = [&](int s, uint32_t sb, uint32_t g) {
         const uint32_t pos = sb * kGBatch + threadIdx.x;
         if (pos < len) {
+            MS_DCHECK(g < a.n_rec, a.err);
             if (g >= a.n_rec) g = 0;  // unreachable unless binning reported an error
             const float4 *src = a.rec + 3 * (size_t)g;
             cp_async16(&buf[s][0][my_slot], src);

@@ -68,6 +68,7 @@ constexpr int kListStages = 4;
 
 // Copy the record of Gaussian g (48 bytes) into a stage slot.
 __device__ __forceinline__ void stage_copy(const ListArgs &a, float4 *dst, uint32_t g) {
+    MS_DCHECK(g < a.n_rec, a.err);
     if (g >= a.n_rec) g = 0;  // unreachable unless binning reported an error
     const float4 *src = a.rec + 3 * (size_t)g;
     cp_async16(dst, src);

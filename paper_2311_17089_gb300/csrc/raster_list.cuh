@@ -21,6 +21,7 @@ struct ListArgs {
     const uint32_t *seg_off;  // [tiles + 1] the frame's segmentation (segment_offsets_kernel)
     const uint32_t *seg_len;  // [1] entries per segment
     float4 *pre;              // [max_segs][256] state after each segment, for the backward
+    unsigned long long *err;  // status word (the binning's), for debug-build checks
 };
 
 // Pixels one CTA of the list kernel blends: a row of 8 pixels of a tile,

@@ -46,7 +46,7 @@ __host__ __device__ __forceinline__ int fwd_index(int x, int y) {
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 inline bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {
-    if (tiles < 1 || tiles > 65536 || cap < 1 || cap > (1ll << 30)) return false;
+    if (tiles < 1 || tiles > 65536 || cap < 1 || cap > (1ll << 30) - 1) return false;
     L.max_segs = tiles + std::min(ceil_div(cap, (int64_t)kMinSegment), kMaxResident);
     size_t o = 0;
     L.ticket = o;

@@ -163,7 +163,7 @@ int64_t capacity_for(ms_server *s, const Request *q) {
     } else {
         cap = std::max<int64_t>(65536, 2 * s->scenes[q->r.scene].n);
     }
-    return std::min<int64_t>(std::max<int64_t>(cap, 1024), 1ll << 30);
+    return std::min<int64_t>(std::max<int64_t>(cap, 1024), (1ll << 30) - 1);
 }
 
 // The request's buffers inside its arena range.
@@ -437,8 +437,9 @@ extern "C" int ms_serve_create(const ms_serve_cfg_t *cfg, ms_server_t **out) {
     if (!out) return fail(MS_ERR_INVALID_ARG, "NULL out");
     *out = nullptr;
     if (!cfg) return fail(MS_ERR_INVALID_ARG, "NULL cfg");
-    if (cfg->max_gaussians < 1 || cfg->max_gaussians > INT32_MAX)
-        return fail(MS_ERR_INVALID_ARG, "max_gaussians must be 1..2^31-1");
+    // the binning sorts up to 2^30 - 1 items per pass
+    if (cfg->max_gaussians < 1 || cfg->max_gaussians > (1ll << 30) - 1)
+        return fail(MS_ERR_INVALID_ARG, "max_gaussians must be 1..2^30-1");
     if (cfg->max_width < 1 || cfg->max_height < 1 || cfg->max_width > 32768 ||
         cfg->max_height > 32768)
         return fail(MS_ERR_INVALID_ARG, "max image size must be 1..32768");
@@ -448,8 +449,8 @@ extern "C" int ms_serve_create(const ms_serve_cfg_t *cfg, ms_server_t **out) {
         return fail(MS_ERR_INVALID_ARG, "n_streams must be 1..max_inflight");
     if (cfg->mem_budget_bytes < (1u << 20))
         return fail(MS_ERR_INVALID_ARG, "mem_budget_bytes must be at least 1 MiB");
-    if (cfg->initial_capacity < 0 || cfg->initial_capacity > (1ll << 30))
-        return fail(MS_ERR_INVALID_ARG, "initial_capacity must be 0..2^30");
+    if (cfg->initial_capacity < 0 || cfg->initial_capacity > (1ll << 30) - 1)
+        return fail(MS_ERR_INVALID_ARG, "initial_capacity must be 0..2^30-1");
     if (cfg->max_batch_views < 0 || cfg->max_batch_views > MS_MAX_PROJ_VIEWS)
         return fail(MS_ERR_INVALID_ARG, "max_batch_views must be 0..MS_MAX_PROJ_VIEWS");
     int ndev = 0;

@@ -27,6 +27,8 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPre = 2u << 30;
 constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
+// Most items a pass may sort: the look-back words carry 30-bit digit counts.
+constexpr int64_t kMaxSortItems = (1ll << 30) - 1;
 constexpr int kLookback = 16;  // predecessors polled per look-back step
 
 template <int IPT>
