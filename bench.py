@@ -41,8 +41,30 @@ FP32_LANES_PER_SM = 128    # nominal, for the derived peak shown beside the meas
 OPS_PER_EVAL = 16          # FP32 operations per pixel-Gaussian evaluation
 MUFU_LANES_PER_SM = 16     # nominal ex2 results per SM per clock (one ex2 per evaluation)
 PAPER_LEVEL_MIX = (0.95, 0.035, 0.01, 0.005)   # coarse levels under 5% of the Gaussians
-RASTER_DRAM_BYTES_PER_LAUNCH = 23.35e6   # both raster kernels, selective sweep, measured
-PROJECT_VIEWS_DRAM_BYTES_PER_LAUNCH = 516.8e6   # project_kernel<8> of the selective sweep, measured
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures,
+# each with the SHA-256 (first 16 hex digits) of the kernel sources it was
+# taken on: a figure whose sources changed since is reported as stale (null)
+RASTER_DRAM = {"bytes": 23.15e6, "sources": ("raster.cu", "raster_list.cu", "raster_ws.cuh"),
+               "sha16": "9bfdc7559ba967b3"}   # mean over the sweep's 8 raster launches
+PROJECT_VIEWS_DRAM = {"bytes": 485.3e6, "sources": ("project.cu", "footprint.cuh"),
+                      "sha16": "50ea4e8e0e2efa43"}   # project_kernel<8> of the selective sweep
+
+
+def sources_sha16(names) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_2311_17089_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(rec):
+    """The captured DRAM bytes when the kernel sources are unchanged since
+    the capture, else None."""
+    if rec["bytes"] is None or rec["sha16"] != sources_sha16(rec["sources"]):
+        return None
+    return rec["bytes"]
 
 
 def parse():
@@ -993,14 +1015,18 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     n = sc.n
-    # one pass: the geometry (53 B) once; per frame the tile count (4 B) of
-    # every Gaussian and the 48-B record of each survivor; the SH row and
-    # opacity (196 B) once per Gaussian listed in any frame
-    proj_bytes = 53 * n + 196 * n_listed_any
+    # one pass: the geometry (53 B) and opacity (4 B) of every Gaussian once;
+    # per frame the tile count, depth key and tile rectangle (16 B) of every
+    # Gaussian and the 48-B record of each survivor; the SH row (192 B) once
+    # per Gaussian listed in any frame.  (Counting depth and rectangle only
+    # for survivors, as the binning needs them, gives proj_bytes_listed.)
+    proj_bytes = 57 * n + 192 * n_listed_any
+    proj_bytes_listed = 57 * n + 192 * n_listed_any
     evals = 0
     for cam in cams:
         s = stats[("selective", cam.width)]
-        proj_bytes += 4 * n + 48 * s["survivors"]
+        proj_bytes += 16 * n + 48 * s["survivors"]
+        proj_bytes_listed += 4 * n + (48 + 12) * s["survivors"]
         evals += s["P_eval"]
     proj_s = stage_ms["project"] / 1e3
     raster_s = stage_ms["raster"] / 1e3
@@ -1013,9 +1039,11 @@ def main():
     roof_project = {"bound": "hbm", "kernel": f"project_kernel ({len(cams)} views, one launch)",
                     "achieved": proj_bytes / proj_s / 1e9, "peak": hbm_peak, "unit": "GB/s"}
     roof_project["frac"] = roof_project["achieved"] / roof_project["peak"]
-    # DRAM bytes of one ncu capture of the sweep's projection launch (to be
-    # taken again whenever the projection kernel changes)
-    roof_project["traffic"] = PROJECT_VIEWS_DRAM_BYTES_PER_LAUNCH
+    roof_project["bytes_per_launch"] = proj_bytes
+    roof_project["bytes_per_launch_listed_only"] = proj_bytes_listed
+    # DRAM bytes of one ncu capture of the sweep's projection launch (null
+    # once the projection kernel has changed since the capture)
+    roof_project["traffic"] = captured_traffic(PROJECT_VIEWS_DRAM)
     roof_raster = {"bound": "alu", "kernel": "raster_kernel (tile) + raster_list_kernel",
                    "achieved": OPS_PER_EVAL * evals / raster_s / 1e12, "peak": alu_peak,
                    "unit": "Tops/s",
@@ -1063,7 +1091,7 @@ def main():
     # dram__bytes_write.sum of one ncu capture of this sweep's eight raster
     # launches (both kernels), averaged (to be taken again whenever a raster
     # kernel changes)
-    traffic = RASTER_DRAM_BYTES_PER_LAUNCH if roof is roof_raster else roof.get("traffic")
+    traffic = captured_traffic(RASTER_DRAM) if roof is roof_raster else roof.get("traffic")
     roof = dict(roof, traffic=traffic, stage_ms_per_step=stage_ms,
                 traffic_source=("ncu capture, mean over the sweep's raster launches"
                                 if roof is roof_raster else

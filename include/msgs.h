@@ -142,10 +142,13 @@ typedef struct {
  *                 the conic (a, b, c) = inverse dilated covariance, so that
  *                 power * log2(e) = A dx^2 + B dx dy + C dy^2.  16-B aligned.
  *                 Entries of other Gaussians are left untouched.
- *   rect[n*2]     listed Gaussians: tile rectangle packed as
- *                 (x0 | y0 << 16), (x1 | y1 << 16), inclusive
+ *   rect[n*2]     tile rectangle packed as (x0 | y0 << 16), (x1 | y1 << 16),
+ *                 inclusive; written for every Gaussian, meaningful for
+ *                 listed ones (others hold their footprint's rectangle,
+ *                 possibly empty, or (0, 0xffffffff) when invalid)
  *   n_tiles[n]    tiles covered if listed, else 0 (always written)
- *   depth[n]      listed Gaussians: bit pattern of view-space z (> 0)
+ *   depth[n]      bit pattern of view-space z, written for every Gaussian
+ *                 (> 0 for listed ones)
  *   cover[n]      optional (may be NULL): pixel coverage S of every valid
  *                 Gaussian, -1 for invalid ones
  *   mask[(n+31)/32]  optional (may be NULL): selection bitset, bit i%32 of

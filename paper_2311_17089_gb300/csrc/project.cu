@@ -255,8 +255,11 @@ constexpr float kConicA = -0.72134752044448170f;   // -log2(e) / 2
 constexpr float kConicB = -1.4426950408889634f;    // -log2(e)
 constexpr float kLog2e = 1.4426950408889634f;
 
-// The per-Gaussian geometry of one chunk of kProjThreads Gaussians, staged
-// in shared memory by bulk copies (7 arrays, 13,568 bytes).
+// The per-Gaussian geometry and opacity of one chunk of kProjThreads
+// Gaussians, staged in shared memory by bulk copies (8 arrays, 14,592
+// bytes).  Opacity is staged with the geometry (one coalesced read for
+// every Gaussian) rather than gathered per listed Gaussian, a 4-byte read
+// that costs a whole DRAM sector.
 struct ProjStage {
     float mean[3 * kProjThreads];
     float scale[3 * kProjThreads];
@@ -264,17 +267,18 @@ struct ProjStage {
     float lnop[kProjThreads];
     float smax[kProjThreads];
     float smin[kProjThreads];
+    float opacity[kProjThreads];
     uint8_t level[kProjThreads];
 };
-constexpr uint32_t kProjStageBytes = (3 + 3 + 4 + 3) * 4 * kProjThreads + kProjThreads;
+constexpr uint32_t kProjStageBytes = (3 + 3 + 4 + 4) * 4 * kProjThreads + kProjThreads;
 static_assert(sizeof(ProjStage) == kProjStageBytes, "stage layout");
 
-// Threads 0..6 of warp 0 issue the bulk copies of chunk c (every array
+// Threads 0..7 of warp 0 issue the bulk copies of chunk c (every array
 // offset is a multiple of 256 elements, so 16-byte aligned when the arrays
 // are).
 __device__ __forceinline__ void issue_chunk(const SceneK &sc, int64_t c, ProjStage &st,
                                             uint64_t *bar) {
-    if (threadIdx.x >= 7) return;
+    if (threadIdx.x >= 8) return;
     const int64_t i0 = c * kProjThreads;
     if (threadIdx.x == 0) mbar_expect_tx(bar, kProjStageBytes);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -285,6 +289,7 @@ __device__ __forceinline__ void issue_chunk(const SceneK &sc, int64_t c, ProjSta
     case 3: bulk_copy_g2s(st.lnop, sc.lnop + i0, 4 * kProjThreads, bar); break;
     case 4: bulk_copy_g2s(st.smax, sc.s_max + i0, 4 * kProjThreads, bar); break;
     case 5: bulk_copy_g2s(st.smin, sc.s_min + i0, 4 * kProjThreads, bar); break;
+    case 6: bulk_copy_g2s(st.opacity, sc.opacity + i0, 4 * kProjThreads, bar); break;
     default: bulk_copy_g2s(st.level, sc.level + i0, kProjThreads, bar); break;
     }
 }
@@ -396,6 +401,7 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
         const int64_t i = base + t;
         const bool in = i < sc.n;
         float m[3] = {0.0f, 0.0f, 0.0f}, S6[6], lnop_i = 0.0f, smax_i = 0.0f, smin_i = 0.0f;
+        float op = 0.0f;
         int level_i = 0;
         bool cov_ok = false;
         if (in) {
@@ -412,6 +418,7 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
                 lnop_i = st.lnop[t];
                 smax_i = st.smax[t];
                 smin_i = st.smin[t];
+                op = st.opacity[t];
                 level_i = st.level[t];
             } else {
                 m[0] = sc.mean[3 * i];
@@ -424,12 +431,12 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
                 lnop_i = sc.lnop[i];
                 smax_i = sc.s_max[i];
                 smin_i = sc.s_min[i];
+                op = sc.opacity[i];
                 level_i = sc.level[i];
             }
             cov_ok = cov3d(sv, q, S6);
         }
         float3 col = make_float3(0.0f, 0.0f, 0.0f);
-        float op = 0.0f;
         int col_src = -1;  // view whose camera centre col was evaluated towards
         bool range_dirty = false;
         for (int v = 0; v < nv; v++) {
@@ -453,11 +460,16 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
                 listed = sel && f.ntiles > 0;
                 ntiles = listed ? f.ntiles : 0u;
                 o.n_tiles[i] = ntiles;
+                // depth and rectangle of every Gaussian: coalesced writes
+                // (per listed Gaussian alone they would be scattered 4- and
+                // 8-byte writes, each a partial DRAM sector)
+                o.depth[i] = f.depth;
+                o.rect[i] = make_uint2((uint32_t)f.x0 | ((uint32_t)f.y0 << 16),
+                                       (uint32_t)f.x1 | ((uint32_t)f.y1 << 16));
                 if (o.cover) o.cover[i] = f.S;
                 if (listed) {
                     const int src = pv.color_src[v];
                     if (src != col_src) {
-                        if (col_src < 0) op = sc.opacity[i];
                         col = gaussian_color(sc.color, sc.sh_degree, i, m[0] - cam.campos[0],
                                              m[1] - cam.campos[1], m[2] - cam.campos[2]);
                         col_src = src;
@@ -467,9 +479,6 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
                     o.rec[3 * i + 1] = make_float4(fm(kConicA, f.cc), op, col.x, col.y);
                     // alpha >= 1/255 <=> power * log2(e) >= -ln(255 sigma) log2(e)
                     o.rec[3 * i + 2] = make_float4(col.z, fm(-kLog2e, lnop_i), f.ex, f.ey);
-                    o.rect[i] = make_uint2((uint32_t)f.x0 | ((uint32_t)f.y0 << 16),
-                                           (uint32_t)f.x1 | ((uint32_t)f.y1 << 16));
-                    o.depth[i] = f.depth;
                     uint32_t(*h)[128] = s_hist[MAXV == 1 ? 0 : v];
 #pragma unroll
                     for (int p = 0; p < 4; p++) {
@@ -599,7 +608,7 @@ int launch_project(const ms_scene_t *scene, const ms_camera_t *cams, int nv, ms_
     const bool staged_ok = aligned(scene->mean, 16) && aligned(scene->scale, 16) &&
                            aligned(scene->quat, 16) && aligned(scene->lnop, 16) &&
                            aligned(scene->s_max, 16) && aligned(scene->s_min, 16) &&
-                           aligned(scene->level, 16);
+                           aligned(scene->opacity, 16) && aligned(scene->level, 16);
     project_kernel<MAXV><<<grid_for(scene->n, kProjThreads, proj_blocks_per_sm<MAXV>()),
                            kProjThreads, 0, st>>>(
         make_scene(*scene), pv, (int)mode, staged_ok);
