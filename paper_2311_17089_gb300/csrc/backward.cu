@@ -240,7 +240,7 @@ raster_bwd_kernel(const __grid_constant__ BwdArgs args) {
             }
             __syncthreads();
             const uint32_t jn = wcnt > off ? min(wcnt - off, nb) : 0u;  // warp-uniform
-            // the records whose level-set box (plus 1 px) reaches the warp's
+            // the records whose level-set box reaches the warp's
             // 8x8 block of pixel centres, in list order; any other record has
             // alpha < 1/255 at all of the warp's pixels
             uint32_t nl = 0;
@@ -249,7 +249,9 @@ raster_bwd_kernel(const __grid_constant__ BwdArgs args) {
                 bool rel = false;
                 if (j < jn) {
                     const float4 r0 = s_r0[j], r2 = s_r2[j];
-                    rel = fabsf(r0.x - bcx) <= r2.z + 4.5f && fabsf(r0.y - bcy) <= r2.w + 4.5f;
+                    // half extents of the 8x8 block of pixel centres, plus
+                    // 1/16 px for the FP32 rounding of the level-set box
+                    rel = fabsf(r0.x - bcx) <= r2.z + 3.5625f && fabsf(r0.y - bcy) <= r2.w + 3.5625f;
                 }
                 const uint32_t m = __ballot_sync(0xffffffffu, rel);
                 if (rel) s_list[wid][nl + __popc(m & ((1u << lane) - 1u))] = (uint16_t)j;

@@ -484,14 +484,29 @@ __global__ void ranges_kernel(const uint32_t *__restrict__ keys,
     }
 }
 
-__global__ void finish_counts_kernel(const uint32_t *__restrict__ stats,
-                                     unsigned long long *__restrict__ counts,
-                                     uint64_t cap) {
-    unsigned long long d = *reinterpret_cast<const unsigned long long *>(stats + kStatDup);
-    counts[kCntDup] = d;
-    counts[kCntSurvivors] = stats[kStatSurvivors];
-    if (d > cap) atomicOr(counts + kCntStatus, (unsigned long long)kStatusOverflow);
-    if (stats[kStatStatus]) atomicOr(counts + kCntStatus, (unsigned long long)stats[kStatStatus]);
+// The first kernel of ms_bin: zeroes the workspace's look-back words,
+// tickets and histograms and the caller's tile ranges (grid-stride, 16-byte
+// stores where aligned), and thread 0 writes the counts: D and the survivors
+// from the projection's stats, the status word with the overflow bit and
+// the projection's own status.  Every later kernel of the call only ORs into
+// the status word, after this one.
+__global__ void bin_start_kernel(const uint32_t *__restrict__ stats,
+                                 unsigned long long *__restrict__ counts, uint64_t cap,
+                                 uint4 *__restrict__ zero16, uint64_t n16,
+                                 uint32_t *__restrict__ ranges, uint64_t n_ranges) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (uint64_t i = t; i < n16; i += stride) zero16[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint64_t i = t; i < n_ranges; i += stride) ranges[i] = 0u;
+    if (t == 0) {
+        const unsigned long long d = *reinterpret_cast<const unsigned long long *>(stats + kStatDup);
+        unsigned long long st = stats[kStatStatus];
+        if (d > cap) st |= kStatusOverflow;
+        counts[kCntDup] = d;
+        counts[kCntSurvivors] = stats[kStatSurvivors];
+        counts[kCntStatus] = st;
+        counts[3] = 0ull;
+    }
 }
 
 // ------------------------------------------------------------ launcher
@@ -593,23 +608,25 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     cudaStream_t st = as_stream(stream);
     char *w = static_cast<char *>(ws);
     int rc;
-    if ((rc = cuda_check(cudaMemsetAsync(w + L.zero_begin, 0, L.total - L.zero_begin, st),
-                         "workspace memset")))
-        return rc;
-    if ((rc = cuda_check(cudaMemsetAsync(out->ranges, 0, (size_t)tiles * 2 * sizeof(uint32_t), st),
-                         "ranges memset")))
-        return rc;
-    if ((rc = cuda_check(cudaMemsetAsync(out->counts, 0, 4 * sizeof(uint64_t), st), "counts memset")))
-        return rc;
-    if (n == 0) return MS_OK;
+    const int sms = num_sms();
+    if (n == 0) {
+        if ((rc = cuda_check(cudaMemsetAsync(out->ranges, 0, (size_t)tiles * 2 * sizeof(uint32_t), st),
+                             "ranges memset")))
+            return rc;
+        return cuda_check(cudaMemsetAsync(out->counts, 0, 4 * sizeof(uint64_t), st), "counts memset");
+    }
     auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(w + off); };
     uint32_t *tickets = U32(L.tickets);
     unsigned long long *err = reinterpret_cast<unsigned long long *>(out->counts) + kCntStatus;
-    const int sms = num_sms();
     const uint32_t spin_limit = bin_spin_limit();
 
-    finish_counts_kernel<<<1, 1, 0, st>>>(proj->stats, reinterpret_cast<unsigned long long *>(out->counts),
-                                          (uint64_t)out->dup_capacity);
+    // the zeroed region starts and ends on 256-byte boundaries (layout)
+    const uint64_t n16 = (L.total - L.zero_begin) / 16;
+    bin_start_kernel<<<std::max(1, std::min(sms * 2, (int)ceil_div((int64_t)n16, 256))), 256, 0,
+                       st>>>(proj->stats, reinterpret_cast<unsigned long long *>(out->counts),
+                             (uint64_t)out->dup_capacity,
+                             reinterpret_cast<uint4 *>(w + L.zero_begin), n16, out->ranges,
+                             (uint64_t)tiles * 2);
     // ---- depth sort: 4 passes over the listed Gaussians
     const uint32_t *survivors = proj->stats + kStatSurvivors;
     const unsigned long long *dup64 =

@@ -109,13 +109,17 @@ __device__ __forceinline__ Seg seg_of(const RasterArgs &a, uint32_t c, uint32_t 
 // One block: D = sum of list lengths, segment length L = max(kChunk,
 // ceil(D / resident) rounded up to kChunk), then the number of segments of
 // every tile (at least one, so empty tiles still write the background),
-// exclusive-scanned.
+// exclusive-scanned.  It also zeroes the n_zero16 16-byte words at zero (the
+// tile kernel's ticket, segment flags and tile marks; none for the list
+// kernel), which the raster launch after it reads.
 __global__ void __launch_bounds__(1024)
 segment_offsets_kernel(const uint32_t *__restrict__ ranges, int tiles, uint32_t resident,
-                       uint32_t *__restrict__ off, uint32_t *__restrict__ seg_len) {
+                       uint32_t *__restrict__ off, uint32_t *__restrict__ seg_len,
+                       uint4 *__restrict__ zero, uint32_t n_zero16) {
     __shared__ uint32_t s_warp[32];
     __shared__ unsigned long long s_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t i = tid; i < n_zero16; i += 1024) zero[i] = make_uint4(0u, 0u, 0u, 0u);
     const int per = (tiles + 1023) / 1024;
     const int t0 = tid * per;
     if (tid == 0) s_total = 0;
@@ -182,10 +186,14 @@ struct WarpPairs {
 constexpr int kWarps = kRasterThreads / 32;
 constexpr int kSmemBytes = 2 * kBufBytes + kWarps * (int)sizeof(WarpPairs);
 // Half extents of a warp's block of pixel centres (8 x 4 pixels) plus a
-// 1-pixel margin that covers FP32 rounding of the alpha test near the edge
-// of the level set.
-constexpr float kBlockHalfX = 3.5f + 1.0f;
-constexpr float kBlockHalfY = 1.5f + 1.0f;
+// margin for FP32 rounding: the record's half extents bound the exact
+// alpha >= 1/255 level set, and the rounding of that bound and of the
+// distances is below 1e-4 px at the largest image coordinates.
+#ifndef MS_CULL_MARGIN
+#define MS_CULL_MARGIN 0.0625f
+#endif
+constexpr float kBlockHalfX = 3.5f + MS_CULL_MARGIN;
+constexpr float kBlockHalfY = 1.5f + MS_CULL_MARGIN;
 
 // Compact the records [0, cnt) of the staged sub-batch whose level-set box
 // (centre +- (ex, ey)) can reach the warp's block of pixel centres
@@ -696,9 +704,6 @@ extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
                                                       : 0;
     const bool list = group > 0 || strategy == MS_RASTER_LIST ||
                       (strategy == MS_RASTER_AUTO && tiles < sms);
-    if (!list &&
-        (rc = cuda_check(cudaMemsetAsync(w, 0, L.zero_bytes, st), "raster workspace memset")))
-        return rc;
     RasterArgs a;
     a.ranges = bins->ranges;
     a.gidx = bins->gauss_idx;
@@ -726,8 +731,11 @@ extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
     a.pre2 = reinterpret_cast<uint2 *>(w + L.pre2);
     a.err = reinterpret_cast<unsigned long long *>(bins->counts) + kCntStatus;
     // the segmentation is the same for both kernels: the backward walks it
+    // the tile kernel's ticket, flags and tile marks are zeroed by the first
+    // kernel (the workspace and zero_bytes are 256-byte aligned)
     segment_offsets_kernel<<<1, 1024, 0, st>>>(bins->ranges, (int)tiles, (uint32_t)resident,
-                                               a.seg_off, a.seg_len);
+                                               a.seg_off, a.seg_len, reinterpret_cast<uint4 *>(w),
+                                               list ? 0u : (uint32_t)(L.zero_bytes / 16));
     if (list) {
         ListArgs la;
         la.ranges = a.ranges;
