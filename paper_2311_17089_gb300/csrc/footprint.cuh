@@ -15,6 +15,7 @@ namespace msgs {
 struct CamK {
     float W[9], t[3], campos[3];
     float fx, fy, cx, cy, near_plane;
+    float limx, limy;  // 1.3 x the half field of view as view ratios
     int width, height, tiles_x, tiles_y;
 };
 
@@ -30,6 +31,14 @@ inline CamK make_cam(const ms_camera_t &c) {
     k.cx = c.cx;
     k.cy = c.cy;
     k.near_plane = c.near_plane;
+    // the Jacobian's clamp limits, once per camera: the same single-precision
+    // operations, in the same order, as every Gaussian would perform (host
+    // float arithmetic is IEEE single precision, and no product here can be
+    // contracted into an FMA)
+    const volatile float hw = 0.5f * (float)c.width, hh = 0.5f * (float)c.height;
+    const volatile float qx = hw / c.fx, qy = hh / c.fy;
+    k.limx = 1.3f * qx;
+    k.limy = 1.3f * qy;
     k.width = c.width;
     k.height = c.height;
     k.tiles_x = (c.width + 15) / 16;
@@ -105,8 +114,7 @@ __device__ __forceinline__ void footprint_cov(const float m[3], const float S6[6
     o.depth = __float_as_uint(tz);
     if (!(L > 0.0f) || !fin(L) || !(tz > c.near_plane) || !fin(tz) || !cov_ok) return;
     const float S3[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
-    float limx = fm(1.3f, fdv(fm(0.5f, (float)c.width), c.fx));
-    float limy = fm(1.3f, fdv(fm(0.5f, (float)c.height), c.fy));
+    const float limx = c.limx, limy = c.limy;
     float xr = fdv(tx, tz), yr = fdv(ty, tz);
     float xc = fminf(limx, fmaxf(-limx, xr));
     float yc = fminf(limy, fmaxf(-limy, yr));
