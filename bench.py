@@ -386,8 +386,9 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
     Gaussians (the paper's setting; the main workload puts 30% there):
     the same generator, cameras and calibration with split 95/3.5/1/0.5%.
     One 8-frame sweep (one multi-view projection, then each frame's bin and
-    raster on its own stream) replayed from a CUDA graph; selective and
-    all-levels frames/s."""
+    raster on its own stream, the frames that list most of what the busiest
+    lists binning from one shared depth sort) replayed from a CUDA graph;
+    selective and all-levels frames/s."""
     sc = inputs.multiscale_scene(n=n, seed=0, split=split)
     ds = msgs.DeviceScene(sc, device=dev)
     ds.calibrate(calib)
@@ -396,27 +397,24 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
     out = {"config": {"workload": f"multiscale-{n // 1000}k-levelmix-"
                                   + "/".join(f"{100 * f:g}" for f in split) + "-sweep8",
                       "split": list(split)}}
-    css = [msgs.camera_struct(c) for c in cams]
     streams = [torch.cuda.Stream(device=dev, priority=(-1 if k < 3 else 0))
                for k in range(len(cams))]
+    order = msgs.DepthOrder(n, device=dev)
     for mode in ("selective", "all_levels"):
-        caps = []
+        caps, surv = [], []
         for cam in cams:
             probe.render(ds, cam, mode)
-            caps.append(msgs.ms_bin_counts(probe.bins)[1])
+            _, d, s_ = msgs.ms_bin_counts(probe.bins)
+            caps.append(d)
+            surv.append(s_)
         rs = [msgs.Renderer(n, c.tiles_x * c.tiles_y, int(d * 1.05) + 1024, device=dev,
                             with_cover=False, with_mask=False) for c, d in zip(cams, caps)]
         bufs = [r.images(c, device=dev) for r, c in zip(rs, cams)]
+        ov = msgs.shared_order_views(surv)
 
         def sweep():
-            main = torch.cuda.current_stream()
-            msgs.ms_project_views(ds.struct, css, msgs.MODES[mode], [r.proj for r in rs], main)
-            for r, cam, o, st in zip(rs, cams, bufs, streams):
-                st.wait_stream(main)
-                with torch.cuda.stream(st):
-                    r.bin_raster(ds, cam, out=o, stream=st)
-            for st in streams:
-                main.wait_stream(st)
+            msgs.render_views(ds, rs, cams, mode, outs=bufs, streams=streams, order=order,
+                              order_views=ov)
 
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
@@ -434,7 +432,8 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
         for r in rs:
             r.check()
         out[mode] = {"fps": len(cams) * steps * 1e3 / e0.elapsed_time(e1),
-                     "D": [int(d) for d in caps]}
+                     "D": [int(d) for d in caps],
+                     "shared_depth_order": [f"{cams[k].width}x{cams[k].height}" for k in ov]}
         del rs, bufs, g
     out["selective_over_all_levels"] = out["selective"]["fps"] / out["all_levels"]["fps"]
     return out
@@ -840,15 +839,22 @@ def main():
     # size each frame's duplicate capacity from one pass of both modes
     probe = msgs.Renderer(sc.n, max_tiles, 60_000_000 if sc.n >= 500_000 else 60 * sc.n,
                           device=dev, with_cover=False, with_mask=False)
-    dmax = {}
+    dmax, surv = {}, {}
     for mode in ("selective", "all_levels"):
         for cam in cams:
             probe.render(ds, cam, mode)
-            rc, d, _ = msgs.ms_bin_counts(probe.bins)
+            rc, d, s_ = msgs.ms_bin_counts(probe.bins)
             if rc != msgs.MS_OK:
                 raise msgs.MsError(rc, "probe capacity")
             dmax[(mode, cam.width)] = d
+            surv[(mode, cam.width)] = s_
     del probe
+    # the frames that list most of what the busiest frame lists bin from one
+    # shared depth sort of the union of their lists (the eight frames share
+    # the pose, so the depth keys); the others sort their own lists
+    order = msgs.DepthOrder(sc.n, device=dev)
+    order_views = {m: msgs.shared_order_views([surv[(m, c.width)] for c in cams])
+                   for m in ("selective", "all_levels")}
     # one renderer (projection, tile lists, workspaces) per frame and mode,
     # sized by that frame's duplicate count, and one stream per frame: the
     # frames of a sweep are independent, and the small ones leave most SMs
@@ -868,18 +874,28 @@ def main():
     def step(mode, after=None, scene=None, views=True):
         # views: one projection pass for the eight frames (they share the
         # camera centre, so a Gaussian listed at several scales is coloured
-        # once), then each frame's binning and blend on its own stream;
-        # otherwise each frame projects on its own stream
+        # once) that also forms the union of the lists of the frames in
+        # order_views, whose depth sort runs once on the first one's stream;
+        # then each frame's binning and blend on its own stream; otherwise
+        # each frame projects on its own stream
         main = torch.cuda.current_stream()
         d = scene or ds
+        ov = order_views[mode]
+        sorted_ev = None
         if views:
-            msgs.ms_project_views(d.struct, css, msgs.MODES[mode],
-                                  [r.proj for r in rs_mode[mode]], main)
-        for r, cam, out, st in zip(rs_mode[mode], cams, bufs, streams):
+            order.project(d, rs_mode[mode], cams, mode, main, ov)
+        for k, (r, cam, out, st) in enumerate(zip(rs_mode[mode], cams, bufs, streams)):
             st.wait_stream(main)
+            if views and k in ov:
+                if sorted_ev is None:
+                    order.sort(st)
+                    sorted_ev = torch.cuda.Event()
+                    sorted_ev.record(st)
+                else:
+                    st.wait_event(sorted_ev)
             with torch.cuda.stream(st):
                 if views:
-                    r.bin_raster(d, cam, out=out, stream=st)
+                    r.bin_raster(d, cam, out=out, stream=st, order=order if k in ov else None)
                 else:
                     r.render(d, cam, mode, out=out, stream=st)
                 if after is not None:
@@ -1159,13 +1175,15 @@ def main():
                "pipeline": "scene upload + prepare of step i+1 on a copy stream during "
                            "step i's render (two scene buffers); images read back per frame"}
 
-    # kernels of libmsgs per step: one projection for every frame; per frame
-    # finish_counts, 4 depth passes, duplicate, 1-2 tile passes, ranges;
-    # chunk offsets, raster
-    launches_per_step = 1
-    for cam in cams:
+    # kernels of libmsgs per selective step: one projection for every frame
+    # and 4 passes of the shared depth sort; per frame the start kernel, 4
+    # depth passes (frames outside the shared order), duplicate, 1-2 tile
+    # passes, ranges; segment offsets, raster
+    launches_per_step = 1 + 4
+    for k, cam in enumerate(cams):
         tiles = cam.tiles_x * cam.tiles_y
-        launches_per_step += (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2
+        launches_per_step += (1 + (0 if k in order_views["selective"] else 4) + 1
+                              + (1 if tiles <= 256 else 2) + 1) + 2
 
     train = None
     if not args.no_train:
@@ -1197,7 +1215,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_sel / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config(sc.n), "clocks": clk, "e2e": e2e,
+            "config": dict(config(sc.n), shared_depth_order={
+                m: [f"{cams[k].width}x{cams[k].height}" for k in v]
+                for m, v in order_views.items()}),
+            "clocks": clk, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "roofline": roof,
             "cpu_baseline": cpu,
             "all_levels": {"value": value_all, "unit": "frames/s",

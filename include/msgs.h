@@ -294,6 +294,48 @@ int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
            const ms_bins_t *out, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Binning of several frames of one pose (one camera at several
+ * resolutions, as in a multi-scale sweep) with one shared depth sort.  A
+ * Gaussian's view depth does not depend on the intrinsics, so the Gaussians
+ * listed in any of the frames can be sorted by (depth bits, index) once;
+ * each frame's tile lists then come from that order, skipping the Gaussians
+ * it does not list, and equal ms_bin's bit for bit.
+ *
+ * ms_project_views_union: ms_project_views that also forms the union of
+ * the views whose bit is set in union_views (bit v: view v; at least one,
+ * none at or above n_views; their cameras' R and t equal bitwise, else
+ * MS_ERR_INVALID_ARG).  It writes union_flags[n] (1 if the Gaussian is
+ * listed in any of those views, else 0) and union_stats[MS_STATS_WORDS]
+ * (16-B aligned; the union's count and its depth-digit histograms, zeroed
+ * by the call).  The union's projection for ms_sort_depth is
+ * { depth = outs[f].depth, n_tiles = union_flags, stats = union_stats,
+ * n = outs[f].n }, f any view of the union (other fields unused).  The
+ * other views are projected as by ms_project_views and bin with ms_bin.
+ *
+ * ms_sort_depth: the four stable depth passes of ms_bin over proj's listed
+ * Gaussians (n_tiles > 0); writes their indices in (depth bits, index)
+ * order to order[n] (device, caller-owned; the first union_stats survivors
+ * entries are meaningful).  A wait that gives up is recorded in
+ * proj->stats words 4-5 and reported by every ms_bin_ordered that uses the
+ * order.  `ws` (16-B aligned) of ms_sort_depth_workspace_bytes(n) bytes.
+ *
+ * ms_bin_ordered: ms_bin for one frame, taking the depth order from
+ * ms_sort_depth (order, and order_stats = the sorted projection's stats,
+ * whose survivor count is the order's length) instead of sorting; the
+ * order must cover every Gaussian the frame lists.  Same workspace,
+ * outputs and errors as ms_bin.
+ */
+int ms_project_views_union(const ms_scene_t *scene, const ms_camera_t *cams, int32_t n_views,
+                           ms_mode_t mode, const ms_proj_t *outs, uint32_t union_views,
+                           uint32_t *union_flags, uint32_t *union_stats, void *stream);
+size_t ms_sort_depth_workspace_bytes(int64_t n);
+int ms_sort_depth(const ms_proj_t *proj, int64_t n, uint32_t *order, void *ws, size_t ws_bytes,
+                  void *stream);
+int ms_bin_ordered(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
+                   const ms_bins_t *out, const uint32_t *order, const uint32_t *order_stats,
+                   void *ws, size_t ws_bytes, void *stream);
+
+/*
  * ms_bin for callers that cannot allocate device memory (the paper has no
  * counterpart; this is a deployment aid).  Examples are an engine plugin
  * whose host application owns every device allocation, and a render loop

@@ -131,6 +131,16 @@ _SIGNATURES = [
                                                ctypes.POINTER(ms_camera_t), ctypes.c_int32,
                                                ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                                ctypes.POINTER(ms_proj_t), P]),
+    ("ms_project_views_union", ctypes.c_int, [ctypes.POINTER(ms_scene_t),
+                                              ctypes.POINTER(ms_camera_t), ctypes.c_int32,
+                                              ctypes.c_int, ctypes.POINTER(ms_proj_t),
+                                              ctypes.c_uint32, P, P, P]),
+    ("ms_sort_depth_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64]),
+    ("ms_sort_depth", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.c_int64, P, P,
+                                     ctypes.c_size_t, P]),
+    ("ms_bin_ordered", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.c_int64,
+                                      ctypes.POINTER(ms_camera_t), ctypes.POINTER(ms_bins_t),
+                                      P, P, P, ctypes.c_size_t, P]),
     ("ms_select", ctypes.c_int, [ctypes.POINTER(ms_scene_t), P, ctypes.c_int, P, P]),
     ("ms_update_range", ctypes.c_int, [ctypes.POINTER(ms_scene_t),
                                        ctypes.POINTER(ms_camera_t), ctypes.c_int32, P]),
@@ -279,6 +289,37 @@ def ms_project_views_update(scene: ms_scene_t, cams, mode: int, update_levels, o
     la = (ctypes.c_int32 * max(n, 1))(*[int(x) for x in update_levels])
     _check(lib().ms_project_views_update(ctypes.byref(scene), ca, n, int(mode), la, oa,
                                          P(_stream(stream))))
+
+
+def ms_project_views_union(scene: ms_scene_t, cams, mode: int, outs, union_views: int,
+                           union_flags_ptr: int, union_stats_ptr: int, stream=None):
+    """ms_project_views, also writing the union of the listed Gaussians of
+    the views in the bit mask union_views (one pose) for ms_sort_depth."""
+    n = len(cams)
+    if len(outs) != n:
+        raise MsError(MS_ERR_INVALID_ARG, "one ms_proj_t per camera")
+    ca = (ms_camera_t * max(n, 1))(*cams)
+    oa = (ms_proj_t * max(n, 1))(*outs)
+    _check(lib().ms_project_views_union(ctypes.byref(scene), ca, n, int(mode), oa,
+                                        int(union_views), P(union_flags_ptr),
+                                        P(union_stats_ptr), P(_stream(stream))))
+
+
+def ms_sort_depth_workspace_bytes(n: int) -> int:
+    return int(lib().ms_sort_depth_workspace_bytes(int(n)))
+
+
+def ms_sort_depth(proj: ms_proj_t, n: int, order_ptr: int, ws_ptr: int, ws_bytes: int,
+                  stream=None):
+    _check(lib().ms_sort_depth(ctypes.byref(proj), int(n), P(order_ptr), P(ws_ptr), ws_bytes,
+                               P(_stream(stream))))
+
+
+def ms_bin_ordered(proj: ms_proj_t, n: int, cam: ms_camera_t, out: ms_bins_t, order_ptr: int,
+                   order_stats_ptr: int, ws_ptr: int, ws_bytes: int, stream=None):
+    _check(lib().ms_bin_ordered(ctypes.byref(proj), int(n), ctypes.byref(cam), ctypes.byref(out),
+                                P(order_ptr), P(order_stats_ptr), P(ws_ptr), ws_bytes,
+                                P(_stream(stream))))
 
 
 def ms_select(scene: ms_scene_t, cover_ptr: int, mode: int, mask_ptr: int, stream=None):
@@ -555,13 +596,19 @@ class Renderer:
         return self.bin_raster(scene, cam, out, stream, n_eval, strategy)
 
     def bin_raster(self, scene: DeviceScene, cam: inputs.Camera, out=None, stream=None,
-                   n_eval=None, strategy="auto"):
+                   n_eval=None, strategy="auto", order=None):
         """Enqueue bin -> raster of this renderer's projection (left by
-        ms_project or ms_project_views for `cam`)."""
+        ms_project or ms_project_views for `cam`).  With `order` (a
+        DepthOrder sorted for a pose this frame shares) the binning takes
+        that depth order instead of sorting (ms_bin_ordered)."""
         if cam.tiles_x * cam.tiles_y > self.max_tiles:
             raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
         cs = camera_struct(cam)
-        ms_bin(self.proj, scene.n, cs, self.bins, _ptr(self.ws), self.ws_bytes, stream)
+        if order is None:
+            ms_bin(self.proj, scene.n, cs, self.bins, _ptr(self.ws), self.ws_bytes, stream)
+        else:
+            ms_bin_ordered(self.proj, scene.n, cs, self.bins, _ptr(order.order),
+                           _ptr(order.stats), _ptr(self.ws), self.ws_bytes, stream)
         image, final_t, n_contrib = out if out is not None else self.images(cam)
         ms_raster_ex(self.proj, self.bins, cs, _ptr(image), _ptr(final_t), _ptr(n_contrib),
                      _ptr(n_eval), _ptr(self.rws), self.rws_bytes,
@@ -575,13 +622,65 @@ class Renderer:
         return d, s
 
 
+class DepthOrder:
+    """A depth order shared by the frames of one pose: the union of the
+    Gaussians they list (ms_project_views_union), sorted once
+    (ms_sort_depth) and consumed by each frame's ms_bin_ordered."""
+
+    def __init__(self, n: int, device="cuda"):
+        import torch
+        dev = torch.device(device)
+        nn = max(n, 1)
+        self.n = n
+        self.flags = torch.empty(nn, dtype=torch.int32, device=dev)
+        self.stats = torch.empty(MS_STATS_WORDS, dtype=torch.int32, device=dev)
+        self.order = torch.empty(nn, dtype=torch.int32, device=dev)
+        self.ws_bytes = ms_sort_depth_workspace_bytes(n)
+        if self.ws_bytes == 0:
+            raise MsError(MS_ERR_INVALID_ARG, "invalid sort workspace size")
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+
+    def project(self, scene: "DeviceScene", renderers, cams, mode="selective", stream=None,
+                views=None):
+        """ms_project_views_union of cams (at most MS_MAX_PROJ_VIEWS) into
+        renderers[v].proj, the union over `views` (indices of cameras of one
+        pose; default all).  sort() then orders the union."""
+        views = sorted(set(range(len(cams)) if views is None else views))
+        if not views or views[0] < 0 or views[-1] >= len(cams):
+            raise MsError(MS_ERR_INVALID_ARG, "views must index the cameras")
+        ms_project_views_union(scene.struct, [camera_struct(c) for c in cams],
+                               MODES.get(mode, mode), [r.proj for r in renderers],
+                               sum(1 << v for v in views), _ptr(self.flags), _ptr(self.stats),
+                               stream)
+        u = renderers[views[0]].proj
+        self._union = ms_proj_t(0, 0, _ptr(self.flags), u.depth, 0, 0, _ptr(self.stats), u.n)
+        self._n = scene.n
+
+    def sort(self, stream=None):
+        """ms_sort_depth of the union formed by the last project()."""
+        ms_sort_depth(self._union, self._n, _ptr(self.order), _ptr(self.ws), self.ws_bytes,
+                      stream)
+
+
+def shared_order_views(survivors, frac: float = 0.8):
+    """The frames of a sweep worth binning from one shared depth order: those
+    that list at least `frac` of the most any frame lists (their lists then
+    overlap mostly, and each skips little of the union).  `survivors` are
+    the frames' listed counts from an earlier pass."""
+    top = max(survivors) if len(survivors) else 0
+    return [v for v, s in enumerate(survivors) if top > 0 and s >= frac * top]
+
+
 def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=None,
-                 streams=None, strategy="auto"):
+                 streams=None, strategy="auto", order=None, order_views=None):
     """Several frames of one scene: one ms_project_views pass for every
     (up to MS_MAX_PROJ_VIEWS) cameras on the current stream, then each
     frame's bin -> raster on its own stream (streams[v], or the current
     stream), which the current stream waits for.  renderers[v] holds frame
-    v's buffers.  Returns the (image, final_t, n_contrib) of every frame."""
+    v's buffers.  With `order` (a DepthOrder; at most MS_MAX_PROJ_VIEWS
+    cameras) the frames in order_views (default all; cameras of one pose)
+    bin from one shared depth sort, the others sort their own lists.
+    Returns the (image, final_t, n_contrib) of every frame."""
     import torch
     n = len(cams)
     if (len(renderers) != n or (outs is not None and len(outs) != n)
@@ -592,18 +691,37 @@ def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=Non
             raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
     main = torch.cuda.current_stream()
     m = MODES.get(mode, mode)
-    for v0 in range(0, n, MS_MAX_PROJ_VIEWS):
-        sl = slice(v0, min(n, v0 + MS_MAX_PROJ_VIEWS))
-        ms_project_views(scene.struct, [camera_struct(c) for c in cams[sl]], m,
-                         [r.proj for r in renderers[sl]], main)
+    if order is not None:
+        if n > MS_MAX_PROJ_VIEWS:
+            raise MsError(MS_ERR_INVALID_ARG, "a shared depth order covers at most "
+                          f"{MS_MAX_PROJ_VIEWS} cameras")
+        order_views = set(range(n) if order_views is None else order_views)
+        order.project(scene, renderers, cams, m, main, order_views)
+        sorted_ev = None
+    else:
+        for v0 in range(0, n, MS_MAX_PROJ_VIEWS):
+            sl = slice(v0, min(n, v0 + MS_MAX_PROJ_VIEWS))
+            ms_project_views(scene.struct, [camera_struct(c) for c in cams[sl]], m,
+                             [r.proj for r in renderers[sl]], main)
     res = []
     for v, (r, cam) in enumerate(zip(renderers, cams)):
         st = streams[v] if streams is not None else main
         if st is not main:
             st.wait_stream(main)
+        if order is not None and v in order_views:
+            # the union is sorted on the stream of its first frame; the
+            # union's other frames wait for the sort, the rest do not
+            if sorted_ev is None:
+                order.sort(st)
+                sorted_ev = torch.cuda.Event()
+                sorted_ev.record(st)
+            else:
+                st.wait_event(sorted_ev)
         with torch.cuda.stream(st):
             res.append(r.bin_raster(scene, cam, None if outs is None else outs[v], st,
-                                    strategy=strategy))
+                                    strategy=strategy,
+                                    order=order if order is not None and v in order_views
+                                    else None))
     if streams is not None:
         for st in streams:
             if st is not main:

@@ -261,6 +261,9 @@ struct DupArgs {
     uint32_t spin_limit;         // look-back polls before a wait gives up
 };
 
+// kSparse: the order may hold Gaussians without tiles in this frame (a depth
+// order shared by several frames); their rectangles are not loaded.
+template <bool kSparse>
 __global__ void __launch_bounds__(kDupThreads)
 duplicate_kernel(DupArgs a) {
     __shared__ uint32_t s_off[kDupPart + 1];
@@ -306,7 +309,7 @@ duplicate_kernel(DupArgs a) {
             if (g != 0xffffffffu) {
                 if (g < a.n_max) {
                     c = a.n_tiles[g];
-                    rc = a.rect[g];
+                    if (!kSparse || c) rc = a.rect[g];
                 } else {
                     MS_DCHECK(false, a.err);
                     atomicOr(a.err, (unsigned long long)kStatusTimeout);
@@ -487,10 +490,12 @@ __global__ void ranges_kernel(const uint32_t *__restrict__ keys,
 // The first kernel of ms_bin: zeroes the workspace's look-back words,
 // tickets and histograms and the caller's tile ranges (grid-stride, 16-byte
 // stores where aligned), and thread 0 writes the counts: D and the survivors
-// from the projection's stats, the status word with the overflow bit and
-// the projection's own status.  Every later kernel of the call only ORs into
+// from the projection's stats, the status word with the overflow bit, the
+// projection's own status and (ms_bin_ordered) the status of the depth sort
+// it takes its order from.  Every later kernel of the call only ORs into
 // the status word, after this one.
 __global__ void bin_start_kernel(const uint32_t *__restrict__ stats,
+                                 const uint32_t *__restrict__ order_stats,
                                  unsigned long long *__restrict__ counts, uint64_t cap,
                                  uint4 *__restrict__ zero16, uint64_t n16,
                                  uint32_t *__restrict__ ranges, uint64_t n_ranges) {
@@ -501,6 +506,7 @@ __global__ void bin_start_kernel(const uint32_t *__restrict__ stats,
     if (t == 0) {
         const unsigned long long d = *reinterpret_cast<const unsigned long long *>(stats + kStatDup);
         unsigned long long st = stats[kStatStatus];
+        if (order_stats) st |= order_stats[kStatStatus];  // the shared depth sort's waits
         if (d > cap) st |= kStatusOverflow;
         counts[kCntDup] = d;
         counts[kCntSurvivors] = stats[kStatSurvivors];
@@ -587,15 +593,51 @@ extern "C" size_t ms_bin_workspace_bytes(int64_t n, int64_t tiles, int64_t dup_c
     return L.total;
 }
 
-extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
-                      const ms_bins_t *out, void *ws, size_t ws_bytes, void *stream) {
+namespace msgs {
+namespace {
+
+// The four stable depth passes over proj's listed Gaussians (pass 0 takes
+// the items with n_tiles > 0, compacting them in index order); the depth
+// order's indices end in vals_final.
+int depth_passes(const ms_proj_t *proj, int64_t n, const BinLayout &L, char *w,
+                 uint32_t *vals_final, unsigned long long *err, uint32_t spin_limit,
+                 cudaStream_t st) {
+    auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(w + off); };
+    uint32_t *tickets = U32(L.tickets);
+    const uint32_t *survivors = proj->stats + kStatSurvivors;
+    uint32_t *dk[2] = {U32(L.dkeys_a), U32(L.dkeys_b)};
+    uint32_t *dv[2] = {U32(L.dvals_a), U32(L.dvals_b)};
+    int rc;
+    for (int pass = 0; pass < 4; pass++) {
+        PassArgs a;
+        a.keys_in = pass == 0 ? proj->depth : dk[(pass - 1) & 1];
+        a.vals_in = pass == 0 ? nullptr : dv[(pass - 1) & 1];
+        a.filter = pass == 0 ? proj->n_tiles : nullptr;
+        a.keys_out = pass == 3 ? nullptr : dk[pass & 1];
+        a.vals_out = pass == 3 ? vals_final : dv[pass & 1];
+        a.n32 = pass == 0 ? nullptr : survivors;
+        a.n64 = nullptr;
+        a.n_cap = (uint64_t)n;
+        a.shift = 8 * pass;
+        a.hist = proj->stats + kStatHist + 256 * pass;
+        a.status = U32(L.dstatus) + (size_t)pass * L.dparts * 256;
+        a.ticket = tickets + pass;
+        a.err = err;
+        a.spin_limit = spin_limit;
+        if ((rc = launch_onesweep(a, (uint64_t)n, st))) return rc;
+    }
+    return MS_OK;
+}
+
+int check_bin_args(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam, const ms_bins_t *out,
+                   void *ws, size_t ws_bytes, BinLayout &L, int64_t &tiles, int &tiles_x) {
     if (!proj || !out || !cam) return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
         return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
-    const int tiles_x = (cam->width + 15) / 16, tiles_y = (cam->height + 15) / 16;
-    const int64_t tiles = (int64_t)tiles_x * tiles_y;
+    tiles_x = (cam->width + 15) / 16;
+    const int tiles_y = (cam->height + 15) / 16;
+    tiles = (int64_t)tiles_x * tiles_y;
     if (tiles > 65536) return fail(MS_ERR_INVALID_ARG, "more than 65536 tiles");
-    BinLayout L;
     if (!layout(n, out->dup_capacity, L))
         return fail(MS_ERR_INVALID_ARG, "n or dup_capacity out of range");
     if (!ws || ws_bytes < L.total || !aligned(ws, 16))
@@ -605,9 +647,22 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     if (n > 0 && (!proj->n_tiles || !proj->depth || !proj->rect || !proj->stats))
         return fail(MS_ERR_INVALID_ARG, "ms_proj_t has a NULL buffer");
     if (proj->n < n) return fail(MS_ERR_INVALID_ARG, "ms_proj_t holds fewer Gaussians than n");
+    return MS_OK;
+}
+
+// ms_bin, or with `order` (a depth order of a superset of proj's listed
+// Gaussians; its count and the sort's status in order_stats) the same
+// without the depth passes.
+int bin_impl(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam, const ms_bins_t *out,
+             const uint32_t *order, const uint32_t *order_stats, void *ws, size_t ws_bytes,
+             void *stream) {
+    BinLayout L;
+    int64_t tiles = 0;
+    int tiles_x = 0;
+    int rc = check_bin_args(proj, n, cam, out, ws, ws_bytes, L, tiles, tiles_x);
+    if (rc) return rc;
     cudaStream_t st = as_stream(stream);
     char *w = static_cast<char *>(ws);
-    int rc;
     const int sms = num_sms();
     if (n == 0) {
         if ((rc = cuda_check(cudaMemsetAsync(out->ranges, 0, (size_t)tiles * 2 * sizeof(uint32_t), st),
@@ -623,41 +678,27 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     // the zeroed region starts and ends on 256-byte boundaries (layout)
     const uint64_t n16 = (L.total - L.zero_begin) / 16;
     bin_start_kernel<<<std::max(1, std::min(sms * 2, (int)ceil_div((int64_t)n16, 256))), 256, 0,
-                       st>>>(proj->stats, reinterpret_cast<unsigned long long *>(out->counts),
+                       st>>>(proj->stats, order ? order_stats : nullptr,
+                             reinterpret_cast<unsigned long long *>(out->counts),
                              (uint64_t)out->dup_capacity,
                              reinterpret_cast<uint4 *>(w + L.zero_begin), n16, out->ranges,
                              (uint64_t)tiles * 2);
-    // ---- depth sort: 4 passes over the listed Gaussians
     const uint32_t *survivors = proj->stats + kStatSurvivors;
     const unsigned long long *dup64 =
         reinterpret_cast<const unsigned long long *>(proj->stats + kStatDup);
-    uint32_t *dk[2] = {U32(L.dkeys_a), U32(L.dkeys_b)};
-    uint32_t *dv[2] = {U32(L.dvals_a), U32(L.dvals_b)};
-    for (int pass = 0; pass < 4; pass++) {
-        PassArgs a;
-        a.keys_in = pass == 0 ? proj->depth : dk[(pass - 1) & 1];
-        a.vals_in = pass == 0 ? nullptr : dv[(pass - 1) & 1];
-        a.filter = pass == 0 ? proj->n_tiles : nullptr;
-        a.keys_out = pass == 3 ? nullptr : dk[pass & 1];
-        a.vals_out = dv[pass & 1];
-        a.n32 = pass == 0 ? nullptr : survivors;
-        a.n64 = nullptr;
-        a.n_cap = (uint64_t)n;
-        a.shift = 8 * pass;
-        a.hist = proj->stats + kStatHist + 256 * pass;
-        a.status = U32(L.dstatus) + (size_t)pass * L.dparts * 256;
-        a.ticket = tickets + pass;
-        a.err = err;
-        a.spin_limit = spin_limit;
-        if ((rc = launch_onesweep(a, (uint64_t)n, st))) return rc;
+    const uint32_t *order_n = order ? order_stats + kStatSurvivors : survivors;
+    if (!order) {
+        // ---- depth sort: 4 passes over the listed Gaussians; after them
+        // (out: a, b, a, b) the depth-ordered indices are in dvals_b
+        if ((rc = depth_passes(proj, n, L, w, U32(L.dvals_b), err, spin_limit, st))) return rc;
+        order = U32(L.dvals_b);
     }
-    // after 4 passes (out: a, b, a, b) the depth-ordered indices are in dv[1]
     // ---- duplicate into (tile, index) entries
     DupArgs da;
-    da.order = dv[1];
+    da.order = order;
     da.n_tiles = proj->n_tiles;
     da.rect = reinterpret_cast<const uint2 *>(proj->rect);
-    da.n32 = survivors;
+    da.n32 = order_n;
     da.n_max = (uint64_t)n;
     da.tiles_x = tiles_x;
     da.tiles = (uint32_t)tiles;
@@ -674,7 +715,8 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     da.tpart = (uint32_t)sort_part((uint64_t)out->dup_capacity);
     da.spin_limit = spin_limit;
     int dupgrid = (int)std::min<int64_t>(L.dupparts, (int64_t)sms * 4);
-    duplicate_kernel<<<dupgrid, kDupThreads, 0, st>>>(da);
+    if (order_stats) duplicate_kernel<true><<<dupgrid, kDupThreads, 0, st>>>(da);
+    else duplicate_kernel<false><<<dupgrid, kDupThreads, 0, st>>>(da);
     // ---- stable sort by tile id
     const int tpasses = tiles <= 256 ? 1 : 2;
     uint32_t *final_keys = U32(L.tkeys_b);
@@ -701,6 +743,52 @@ extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
     ranges_kernel<<<sms * 4, 256, 0, st>>>(final_keys, dup64, (uint64_t)out->dup_capacity,
                                            (uint32_t)tiles, out->ranges);
     return cuda_check(cudaGetLastError(), "ms_bin launches");
+}
+
+}  // namespace
+}  // namespace msgs
+
+extern "C" int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
+                      const ms_bins_t *out, void *ws, size_t ws_bytes, void *stream) {
+    return bin_impl(proj, n, cam, out, nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+extern "C" int ms_bin_ordered(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
+                              const ms_bins_t *out, const uint32_t *order,
+                              const uint32_t *order_stats, void *ws, size_t ws_bytes,
+                              void *stream) {
+    if (!order || !order_stats) return fail(MS_ERR_INVALID_ARG, "order / order_stats is NULL");
+    return bin_impl(proj, n, cam, out, order, order_stats, ws, ws_bytes, stream);
+}
+
+extern "C" size_t ms_sort_depth_workspace_bytes(int64_t n) {
+    BinLayout L;
+    if (!layout(n, 1, L)) return 0;
+    return L.total;
+}
+
+extern "C" int ms_sort_depth(const ms_proj_t *proj, int64_t n, uint32_t *order, void *ws,
+                             size_t ws_bytes, void *stream) {
+    BinLayout L;
+    if (!proj || !order) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (!layout(n, 1, L)) return fail(MS_ERR_INVALID_ARG, "n out of range");
+    if (!ws || ws_bytes < L.total || !aligned(ws, 16))
+        return fail(MS_ERR_INVALID_ARG, "workspace missing, too small or misaligned");
+    if (n > 0 && (!proj->n_tiles || !proj->depth || !proj->stats))
+        return fail(MS_ERR_INVALID_ARG, "ms_proj_t has a NULL buffer");
+    if (proj->n < n) return fail(MS_ERR_INVALID_ARG, "ms_proj_t holds fewer Gaussians than n");
+    if (n == 0) return MS_OK;
+    cudaStream_t st = as_stream(stream);
+    char *w = static_cast<char *>(ws);
+    int rc;
+    if ((rc = cuda_check(cudaMemsetAsync(w + L.zero_begin, 0, L.total - L.zero_begin, st),
+                         "workspace memset")))
+        return rc;
+    // a wait that gives up is recorded in the sorted projection's status
+    // word (stats words 4-5), where ms_bin_ordered picks it up
+    unsigned long long *err = reinterpret_cast<unsigned long long *>(proj->stats + kStatStatus);
+    if ((rc = depth_passes(proj, n, L, w, order, err, bin_spin_limit(), st))) return rc;
+    return cuda_check(cudaGetLastError(), "ms_sort_depth launches");
 }
 
 extern "C" int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed, int64_t *survivors,

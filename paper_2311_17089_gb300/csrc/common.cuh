@@ -29,7 +29,8 @@ __device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
 // ms_proj_t::stats words
 constexpr int kStatSurvivors = 0;  // uint32 listed Gaussians
 constexpr int kStatDup = 2;        // uint64 (words 2-3) sum of n_tiles
-constexpr int kStatStatus = 4;     // uint32 status bits of ms_project (kStatusTimeout)
+constexpr int kStatStatus = 4;     // status bits (kStatusTimeout): uint32 of ms_project; words
+                                   // 4-5 as a uint64 where ms_sort_depth records its waits
 constexpr int kStatHist = 16;      // 4 x 256 uint32 depth-digit histograms
 static_assert(kStatHist + 1024 <= MS_STATS_WORDS, "stats layout");
 

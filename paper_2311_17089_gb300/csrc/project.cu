@@ -310,6 +310,13 @@ template <int MAXV>
 struct ProjViews {
     int n_views;
     int update_level[MAXV];  // level whose coverage range the view updates (0: none)
+    // the union of the views in union_mask (all with one pose, so one depth
+    // per Gaussian, taken in view union_first): per Gaussian 1 if listed in
+    // any of them else 0, and stats with the union's count and depth-digit
+    // histograms; NULL: not formed
+    uint32_t *union_flags, *union_stats;
+    uint32_t union_mask;
+    int union_first;
     float *smax_out, *smin_out;  // the scene's ranges, written when a view updates
     int color_src[MAXV];
     CamK cam[MAXV];
@@ -323,15 +330,23 @@ struct ProjViews {
 constexpr int kHistFlushChunks = 255;
 static_assert(kHistFlushChunks * kProjThreads < 65536, "16-bit digit counts");
 
+// Histogram slots in shared memory: one per view, and for MAXV > 1 one
+// more (slot MAXV) for the union of the views.
+template <int MAXV>
+__host__ __device__ constexpr int hist_slots() { return MAXV == 1 ? 1 : MAXV + 1; }
+
 template <int MAXV>
 __device__ __forceinline__ void flush_hist(uint32_t (*s_hist)[4][128], const ProjViews<MAXV> &pv) {
-    for (int k = threadIdx.x; k < pv.n_views * 512; k += blockDim.x) {
+    const int nv = MAXV == 1 ? 1 : pv.n_views;
+    const int slots = nv + (MAXV > 1 && pv.union_stats ? 1 : 0);
+    for (int k = threadIdx.x; k < slots * 512; k += blockDim.x) {
         const int v = k >> 9, w = k & 511;
-        uint32_t &word = (&s_hist[v][0][0])[w];
+        const int slot = v < nv ? v : MAXV;
+        uint32_t &word = (&s_hist[slot][0][0])[w];
         const uint32_t x = word;
         if (x) {
             const int pass = w >> 7, d = (w & 127) * 2;
-            uint32_t *g = pv.out[v].stats + kStatHist + 256 * pass + d;
+            uint32_t *g = (v < nv ? pv.out[v].stats : pv.union_stats) + kStatHist + 256 * pass + d;
             if (x & 0xffffu) atomicAdd(g, x & 0xffffu);
             if (x >> 16) atomicAdd(g + 1, x >> 16);
             word = 0;
@@ -356,16 +371,15 @@ constexpr int proj_blocks_per_sm() { return MAXV == 1 ? kProjBlocksPerSM : 3; }
 template <int MAXV>
 __global__ void __launch_bounds__(kProjThreads, proj_blocks_per_sm<MAXV>())
 project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, bool staged_ok) {
-    __shared__ uint32_t s_hist[MAXV][4][128];
-    __shared__ uint32_t s_surv[MAXV];
+    __shared__ uint32_t s_hist[hist_slots<MAXV>()][4][128];
+    __shared__ uint32_t s_surv[MAXV + 1];
     __shared__ unsigned long long s_dup[MAXV];
     __shared__ __align__(128) ProjStage s_st[2];
     __shared__ __align__(8) uint64_t s_bar[2];
-    for (int i = threadIdx.x; i < MAXV * 512; i += blockDim.x) (&s_hist[0][0][0])[i] = 0;
-    if (threadIdx.x < MAXV) {
-        s_surv[threadIdx.x] = 0;
-        s_dup[threadIdx.x] = 0;
-    }
+    for (int i = threadIdx.x; i < hist_slots<MAXV>() * 512; i += blockDim.x)
+        (&s_hist[0][0][0])[i] = 0;
+    if (threadIdx.x <= MAXV) s_surv[threadIdx.x] = 0;
+    if (threadIdx.x < MAXV) s_dup[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
@@ -439,6 +453,8 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
         float3 col = make_float3(0.0f, 0.0f, 0.0f);
         int col_src = -1;  // view whose camera centre col was evaluated towards
         bool range_dirty = false;
+        bool any_listed = false;  // listed in some view (the union)
+        uint32_t depth0 = 0u;     // depth key in the pose the union's views share
         for (int v = 0; v < nv; v++) {
             const CamK &cam = pv.cam[v];
             const ProjOut &o = pv.out[v];
@@ -459,6 +475,8 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
                 }
                 listed = sel && f.ntiles > 0;
                 ntiles = listed ? f.ntiles : 0u;
+                if ((pv.union_mask >> v) & 1u) any_listed |= listed;
+                if (v == pv.union_first) depth0 = f.depth;
                 o.n_tiles[i] = ntiles;
                 // depth and rectangle of every Gaussian: coalesced writes
                 // (per listed Gaussian alone they would be scattered 4- and
@@ -503,6 +521,18 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
             pv.smax_out[i] = smax_i;
             pv.smin_out[i] = smin_i;
         }
+        if (MAXV > 1 && pv.union_flags) {
+            if (in) pv.union_flags[i] = any_listed ? 1u : 0u;
+            if (any_listed) {
+#pragma unroll
+                for (int p = 0; p < 4; p++) {
+                    const uint32_t d = (depth0 >> (8 * p)) & 255u;
+                    atomicAdd(&s_hist[MAXV > 1 ? MAXV : 0][p][d >> 1], 1u << (16 * (d & 1u)));
+                }
+            }
+            const uint32_t wu = __reduce_add_sync(0xffffffffu, any_listed ? 1u : 0u);
+            if ((threadIdx.x & 31) == 0 && wu) atomicAdd(&s_surv[MAXV], wu);
+        }
         __syncthreads();  // the buffer is refilled by the next iteration but one
         if ((it + 1) % kHistFlushChunks == 0) {
             flush_hist<MAXV>(s_hist, pv);
@@ -517,6 +547,8 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
         if (s_surv[v]) atomicAdd(&stats[kStatSurvivors], s_surv[v]);
         if (s_dup[v]) atomicAdd(reinterpret_cast<unsigned long long *>(stats + kStatDup), s_dup[v]);
     }
+    if (MAXV > 1 && pv.union_stats && threadIdx.x == 0 && s_surv[MAXV])
+        atomicAdd(&pv.union_stats[kStatSurvivors], s_surv[MAXV]);
 }
 
 __global__ void select_kernel(int64_t n, const float *__restrict__ cover,
@@ -585,9 +617,15 @@ int check_proj_out(const ms_scene_t *scene, const ms_proj_t *out) {
 
 template <int MAXV>
 int launch_project(const ms_scene_t *scene, const ms_camera_t *cams, int nv, ms_mode_t mode,
-                   const ms_proj_t *outs, const int32_t *update_levels, cudaStream_t st) {
+                   const ms_proj_t *outs, const int32_t *update_levels, uint32_t *union_flags,
+                   uint32_t *union_stats, uint32_t union_mask, cudaStream_t st) {
     ProjViews<MAXV> pv;
     pv.n_views = nv;
+    pv.union_flags = union_flags;
+    pv.union_stats = union_stats;
+    pv.union_mask = union_mask;
+    pv.union_first = 0;
+    while (pv.union_first < nv - 1 && !((union_mask >> pv.union_first) & 1u)) pv.union_first++;
     pv.smax_out = scene->s_max;
     pv.smin_out = scene->s_min;
     for (int v = 0; v < MAXV; v++) {
@@ -618,10 +656,13 @@ int launch_project(const ms_scene_t *scene, const ms_camera_t *cams, int nv, ms_
 }  // namespace
 }  // namespace msgs
 
-extern "C" int ms_project_views_update(const ms_scene_t *scene, const ms_camera_t *cams,
-                                       int32_t n_views, ms_mode_t mode,
-                                       const int32_t *update_levels, const ms_proj_t *outs,
-                                       void *stream) {
+namespace msgs {
+namespace {
+
+int project_views(const ms_scene_t *scene, const ms_camera_t *cams, int32_t n_views,
+                  ms_mode_t mode, const int32_t *update_levels, const ms_proj_t *outs,
+                  uint32_t *union_flags, uint32_t *union_stats, uint32_t union_mask,
+                  void *stream) {
     int rc = check_scene(scene, true);
     if (rc) return rc;
     if (n_views < 1 || n_views > MS_MAX_PROJ_VIEWS)
@@ -640,9 +681,49 @@ extern "C" int ms_project_views_update(const ms_scene_t *scene, const ms_camera_
         if ((rc = cuda_check(cudaMemsetAsync(outs[v].stats, 0, MS_STATS_WORDS * sizeof(uint32_t), st),
                              "stats memset")))
             return rc;
+    if (union_stats &&
+        (rc = cuda_check(cudaMemsetAsync(union_stats, 0, MS_STATS_WORDS * sizeof(uint32_t), st),
+                         "union stats memset")))
+        return rc;
     if (scene->n == 0) return MS_OK;
-    if (n_views == 1) return launch_project<1>(scene, cams, 1, mode, outs, update_levels, st);
-    return launch_project<MS_MAX_PROJ_VIEWS>(scene, cams, n_views, mode, outs, update_levels, st);
+    if (n_views == 1 && !union_flags)
+        return launch_project<1>(scene, cams, 1, mode, outs, update_levels, nullptr, nullptr, 0u,
+                                 st);
+    return launch_project<MS_MAX_PROJ_VIEWS>(scene, cams, n_views, mode, outs, update_levels,
+                                             union_flags, union_stats, union_mask, st);
+}
+
+}  // namespace
+}  // namespace msgs
+
+extern "C" int ms_project_views_update(const ms_scene_t *scene, const ms_camera_t *cams,
+                                       int32_t n_views, ms_mode_t mode,
+                                       const int32_t *update_levels, const ms_proj_t *outs,
+                                       void *stream) {
+    return project_views(scene, cams, n_views, mode, update_levels, outs, nullptr, nullptr, 0u,
+                         stream);
+}
+
+extern "C" int ms_project_views_union(const ms_scene_t *scene, const ms_camera_t *cams,
+                                      int32_t n_views, ms_mode_t mode, const ms_proj_t *outs,
+                                      uint32_t union_views, uint32_t *union_flags,
+                                      uint32_t *union_stats, void *stream) {
+    if (!union_flags || !union_stats || !aligned(union_stats, 16))
+        return fail(MS_ERR_INVALID_ARG, "union_flags / union_stats NULL or stats misaligned");
+    if (!cams || n_views < 1 || n_views > MS_MAX_PROJ_VIEWS)
+        return fail(MS_ERR_INVALID_ARG, "cams is NULL or n_views not 1..MS_MAX_PROJ_VIEWS");
+    if (union_views == 0 || (union_views >> n_views) != 0)
+        return fail(MS_ERR_INVALID_ARG, "union_views must name 1 or more of the n_views views");
+    int first = 0;
+    while (!((union_views >> first) & 1u)) first++;
+    for (int v = first + 1; v < n_views; v++)
+        if (((union_views >> v) & 1u) &&
+            (std::memcmp(cams[v].R, cams[first].R, sizeof(cams[0].R)) != 0 ||
+             std::memcmp(cams[v].t, cams[first].t, sizeof(cams[0].t)) != 0))
+            return fail(MS_ERR_INVALID_ARG,
+                        "the union needs one pose: the R and t of its views equal, bitwise");
+    return project_views(scene, cams, n_views, mode, nullptr, outs, union_flags, union_stats,
+                         union_views, stream);
 }
 
 extern "C" int ms_project_views(const ms_scene_t *scene, const ms_camera_t *cams,
