@@ -44,10 +44,10 @@ PAPER_LEVEL_MIX = (0.95, 0.035, 0.01, 0.005)   # coarse levels under 5% of the G
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures,
 # each with the SHA-256 (first 16 hex digits) of the kernel sources it was
 # taken on: a figure whose sources changed since is reported as stale (null)
-RASTER_DRAM = {"bytes": 23.15e6, "sources": ("raster.cu", "raster_list.cu", "raster_ws.cuh"),
-               "sha16": "9bfdc7559ba967b3"}   # mean over the sweep's 8 raster launches
-PROJECT_VIEWS_DRAM = {"bytes": 485.3e6, "sources": ("project.cu", "footprint.cuh"),
-                      "sha16": "50ea4e8e0e2efa43"}   # project_kernel<8> of the selective sweep
+RASTER_DRAM = {"bytes": 23.21e6, "sources": ("raster.cu", "raster_list.cu", "raster_ws.cuh"),
+               "sha16": "18fbc639d89438b6"}   # mean over the sweep's 8 raster launches
+PROJECT_VIEWS_DRAM = {"bytes": 504.1e6, "sources": ("project.cu", "footprint.cuh"),
+                      "sha16": "bfb76a3c1f792bf4"}   # the selective sweep's projection launch
 
 
 def sources_sha16(names) -> str:
@@ -937,8 +937,9 @@ def main():
         return g
 
     g_step = {m: capture(lambda m=m: step(m)) for m in ("selective", "all_levels")}
-    g_views = capture(lambda: msgs.ms_project_views(ds.struct, css, msgs.MODES["selective"],
-                                                    [r.proj for r in rs_mode["selective"]]))
+    # the sweep's projection launch as the step issues it (with the union)
+    g_views = capture(lambda: order.project(ds, rs_mode["selective"], cams, "selective",
+                                            views=order_views["selective"]))
     # Gaussians listed in at least one frame: each reads its SH row once
     listed_any = torch.zeros(sc.n, dtype=torch.bool, device=dev)
     g_views.replay()
@@ -1036,8 +1037,10 @@ def main():
     # Gaussian and the 48-B record of each survivor; the SH row (192 B) once
     # per Gaussian listed in any frame.  (Counting depth and rectangle only
     # for survivors, as the binning needs them, gives proj_bytes_listed.)
-    proj_bytes = 57 * n + 192 * n_listed_any
-    proj_bytes_listed = 57 * n + 192 * n_listed_any
+    # The launch also writes the 4-B union flag of every Gaussian for the
+    # shared depth sort.
+    proj_bytes = 57 * n + 192 * n_listed_any + 4 * n
+    proj_bytes_listed = 57 * n + 192 * n_listed_any + 4 * n
     evals = 0
     for cam in cams:
         s = stats[("selective", cam.width)]
@@ -1052,7 +1055,8 @@ def main():
     mufu_peak = peaks_alu["ex2"]
     # the unit-count figure at the maximum clock, for context
     alu_nominal = sms * FP32_LANES_PER_SM * 2070.0e6 / 1e12
-    roof_project = {"bound": "hbm", "kernel": f"project_kernel ({len(cams)} views, one launch)",
+    roof_project = {"bound": "hbm", "kernel": f"project_pruned_kernel ({len(cams)} views of "
+                                              "one pose, one launch)",
                     "achieved": proj_bytes / proj_s / 1e9, "peak": hbm_peak, "unit": "GB/s"}
     roof_project["frac"] = roof_project["achieved"] / roof_project["peak"]
     roof_project["bytes_per_launch"] = proj_bytes

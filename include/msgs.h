@@ -145,7 +145,8 @@ typedef struct {
  *   rect[n*2]     tile rectangle packed as (x0 | y0 << 16), (x1 | y1 << 16),
  *                 inclusive; written for every Gaussian, meaningful for
  *                 listed ones (others hold their footprint's rectangle,
- *                 possibly empty, or (0, 0xffffffff) when invalid)
+ *                 possibly empty, or (0, 0xffffffff) when invalid or, in
+ *                 ms_project_views, when the footprint was left out)
  *   n_tiles[n]    tiles covered if listed, else 0 (always written)
  *   depth[n]      bit pattern of view-space z, written for every Gaussian
  *                 (> 0 for listed ones)
@@ -223,11 +224,17 @@ int ms_project(const ms_scene_t *scene, const ms_camera_t *cam,
 /*
  * ms_project for n_views cameras at once (1..MS_MAX_PROJ_VIEWS): outs[v]
  * receives, bit for bit, what ms_project(scene, &cams[v], mode, &outs[v])
- * writes.  One pass over the scene reads each Gaussian's geometry once and
- * forms its 3D covariance once; the camera-dependent steps run per view,
- * and views whose cameras share a centre (campos) share the listed
- * Gaussians' SH colour (the multi-scale setting of Sec. 4: one pose at
- * several resolutions).  cams and outs are host arrays of n_views entries
+ * writes, except the rectangles of Gaussians that are not listed (below).
+ * One pass over the scene reads each Gaussian's geometry once and forms its
+ * 3D covariance once; the camera-dependent steps run per view, and views
+ * whose cameras share a centre (campos) share the listed Gaussians' SH
+ * colour (the multi-scale setting of Sec. 4: one pose at several
+ * resolutions).  When every view is a selective render with the first
+ * view's R, t and campos, no cover output and no range update, the pass
+ * leaves out the footprints that a bound on the coverage S (from one
+ * covariance per Gaussian for all the views) shows cannot pass Eq. 6;
+ * there, as for every Gaussian a view does not list, the rectangle is
+ * (0, 0xffffffff).  cams and outs are host arrays of n_views entries
  * (read during the call only); the device buffers of the outs[v] are the
  * caller's and must not overlap one another.  Errors: MS_ERR_INVALID_ARG
  * for n_views outside 1..MS_MAX_PROJ_VIEWS, NULL cams/outs, or any camera

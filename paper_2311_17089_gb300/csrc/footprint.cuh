@@ -97,25 +97,35 @@ __device__ __forceinline__ bool cov3d(const float s[3], float4 q, float S6[6]) {
     return true;
 }
 
+// The view-space point of a mean in camera c: depth tz and the view ratios
+// xr = tx / tz, yr = ty / tz (the first steps of the footprint; cameras of
+// one pose give the same bits).
+__device__ __forceinline__ void view_point(const float m[3], const CamK &c, float &tz, float &xr,
+                                           float &yr) {
+    const float *W = c.W;
+    const float tx = fa(fa(fa(fm(W[0], m[0]), fm(W[1], m[1])), fm(W[2], m[2])), c.t[0]);
+    const float ty = fa(fa(fa(fm(W[3], m[0]), fm(W[4], m[1])), fm(W[5], m[2])), c.t[1]);
+    tz = fa(fa(fa(fm(W[6], m[0]), fm(W[7], m[1])), fm(W[8], m[2])), c.t[2]);
+    xr = fdv(tx, tz);
+    yr = fdv(ty, tz);
+}
+
 // FP32 footprint in one camera (Sec. 3.1 EWA splat, Eq. 4 dilation by
-// 0.3 px^2, Sec. 4.1 pixel coverage, Sec. 3.1 16x16 tiles) from the mean,
-// the 3D covariance of cov3d (cov_ok its result) and L = ln(255 sigma).
-__device__ __forceinline__ void footprint_cov(const float m[3], const float S6[6], bool cov_ok,
-                                              float L, const CamK &c, Foot &o) {
+// 0.3 px^2, Sec. 4.1 pixel coverage, Sec. 3.1 16x16 tiles) from the
+// view-space point (view_point), the 3D covariance of cov3d (cov_ok its
+// result) and L = ln(255 sigma).
+__device__ __forceinline__ void footprint_vp(float tz, float xr, float yr, const float S6[6],
+                                             bool cov_ok, float L, const CamK &c, Foot &o) {
     o.valid = false;
     o.S = -1.0f;
     o.ntiles = 0;
     o.x0 = o.y0 = 0;
     o.x1 = o.y1 = -1;
-    const float *W = c.W;
-    float tx = fa(fa(fa(fm(W[0], m[0]), fm(W[1], m[1])), fm(W[2], m[2])), c.t[0]);
-    float ty = fa(fa(fa(fm(W[3], m[0]), fm(W[4], m[1])), fm(W[5], m[2])), c.t[1]);
-    float tz = fa(fa(fa(fm(W[6], m[0]), fm(W[7], m[1])), fm(W[8], m[2])), c.t[2]);
     o.depth = __float_as_uint(tz);
     if (!(L > 0.0f) || !fin(L) || !(tz > c.near_plane) || !fin(tz) || !cov_ok) return;
+    const float *W = c.W;
     const float S3[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
     const float limx = c.limx, limy = c.limy;
-    float xr = fdv(tx, tz), yr = fdv(ty, tz);
     float xc = fminf(limx, fmaxf(-limx, xr));
     float yc = fminf(limy, fmaxf(-limy, yr));
     float J00 = fdv(c.fx, tz);
@@ -175,12 +185,116 @@ __device__ __forceinline__ void footprint_cov(const float m[3], const float S6[6
     }
 }
 
+// The footprint from the mean.
+__device__ __forceinline__ void footprint_cov(const float m[3], const float S6[6], bool cov_ok,
+                                              float L, const CamK &c, Foot &o) {
+    float tz, xr, yr;
+    view_point(m, c, tz, xr, yr);
+    footprint_vp(tz, xr, yr, S6, cov_ok, L, c, o);
+}
+
 // The footprint of one Gaussian in one camera.
 __device__ __forceinline__ void footprint(const float m[3], const float s[3], float4 q,
                                           float L, const CamK &c, Foot &o) {
     float S6[6];
     const bool ok = cov3d(s, q, S6);
     footprint_cov(m, S6, ok, L, c, o);
+}
+
+// A bound on the pixel coverage S of one Gaussian in every camera of one
+// pose (R, t), without that camera's footprint.  The pose fixes the
+// view-space mean (tx, ty, tz) and the view ratios (xr, yr); where the
+// Jacobian's clamp leaves them unchanged, a camera with focal lengths
+// (fx, fy) has J = diag(fx, fy) J1, J1 the Jacobian for unit focal
+// lengths, so its undilated 2D covariance is V = diag(fx, fy) V1 diag(fx, fy)
+// and S^2 = 8 L fx^2 fy^2 det V1 / max(fx^2 V1_xx, fy^2 V1_yy).
+// Error bound (u = 2^-24): the FP32 chain J -> J W -> J W Sigma ->
+// J W Sigma W^T J^T leaves each entry of V within 20u of the same product
+// taken over absolute values (|J||W| |Sigma| |W|^T|J|^T = Va; 16u for the
+// footprint's correctly rounded Jacobian, 20u for V1's, whose 1 / tz comes
+// from the approximate reciprocal), so det V is within
+// 50u (Va_xx Va_yy + Va_xy^2) and max(V_xx, V_yy) within
+// 20u max(Va_xx / V_xx, Va_yy / V_yy) relative; with the last few roundings
+// S^2 from the camera's own fixed-order footprint and S^2 from V1 below
+// each lie within eps = u (50 P / det + 20 q + 8) of the exact value
+// (P, q those ratios' terms, the same for every camera of the pose), so
+// within 2 eps (1 + eps) of each other.  The bound is kept only where V1 is
+// well conditioned (eps < 1e-3; P / det and q need only a few correct
+// digits); mu2 = 1 + 4 eps + 1e-6 covers the rest of the rounding of the
+// comparisons.
+struct CoverBound {
+    bool ok;           // the bound holds
+    float tz, xr, yr;  // view-space depth and view ratios of the pose
+    float s2_unit;     // 8 L det V1
+    float v00, v11;    // diagonal of V1
+    float mu2;         // margin on squared coverage
+};
+
+__device__ __forceinline__ void cover_bound(float tz, float xr, float yr, const float S6[6],
+                                            bool cov_ok, float L, const CamK &c, CoverBound &b) {
+    const float *W = c.W;
+    b.ok = false;
+    b.tz = tz;
+    b.xr = xr;
+    b.yr = yr;
+    if (!cov_ok || !(L > 0.0f) || !fin(L) || !(tz > 0.0f) || !fin(tz) || !fin(xr) || !fin(yr))
+        return;
+    const float r = __fdividef(1.0f, tz);
+    const float j2 = -xr * r, k2 = -yr * r;  // J1 = [[r, 0, j2], [0, r, k2]]
+    float T0[3], T1[3], A0[3], A1[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        T0[k] = r * W[k] + j2 * W[6 + k];
+        T1[k] = r * W[3 + k] + k2 * W[6 + k];
+        A0[k] = fabsf(r * W[k]) + fabsf(j2 * W[6 + k]);
+        A1[k] = fabsf(r * W[3 + k]) + fabsf(k2 * W[6 + k]);
+    }
+    const float S3[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
+    float U0[3], U1[3], B0[3], B1[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        U0[k] = T0[0] * S3[k] + T0[1] * S3[3 + k] + T0[2] * S3[6 + k];
+        U1[k] = T1[0] * S3[k] + T1[1] * S3[3 + k] + T1[2] * S3[6 + k];
+        B0[k] = A0[0] * fabsf(S3[k]) + A0[1] * fabsf(S3[3 + k]) + A0[2] * fabsf(S3[6 + k]);
+        B1[k] = A1[0] * fabsf(S3[k]) + A1[1] * fabsf(S3[3 + k]) + A1[2] * fabsf(S3[6 + k]);
+    }
+    const float v00 = U0[0] * T0[0] + U0[1] * T0[1] + U0[2] * T0[2];
+    const float v01 = U0[0] * T1[0] + U0[1] * T1[1] + U0[2] * T1[2];
+    const float v11 = U1[0] * T1[0] + U1[1] * T1[1] + U1[2] * T1[2];
+    const float a00 = B0[0] * A0[0] + B0[1] * A0[1] + B0[2] * A0[2];
+    const float a01 = B0[0] * A1[0] + B0[1] * A1[1] + B0[2] * A1[2];
+    const float a11 = B1[0] * A1[0] + B1[1] * A1[1] + B1[2] * A1[2];
+    const float det = v00 * v11 - v01 * v01;
+    if (!(det > 0.0f) || !(v00 > 0.0f) || !(v11 > 0.0f)) return;
+    const float P = a00 * a11 + a01 * a01;
+    const float q = fmaxf(__fdividef(a00, v00), __fdividef(a11, v11));
+    const float eps = 5.9604645e-8f * (50.0f * __fdividef(P, det) + 20.0f * q + 8.0f);
+    if (!(eps < 1e-3f)) return;  // also false for NaN and infinity
+    b.s2_unit = 8.0f * L * det;
+    b.v00 = v00;
+    b.v11 = v11;
+    b.mu2 = 1.0f + 4.0f * eps + 1e-6f;
+    b.ok = fin(b.s2_unit) && b.s2_unit > 0.0f;
+}
+
+// True only if the camera (focal lengths squared fx2, fy2; the pose of the
+// bound) is sure to reject the Gaussian in selective mode (Eq. 6 with the
+// exemptions of Sec. 4.1): too large for a level above the finest, or too
+// small for a level below the coarsest, by more than the bound's margin.
+// False where the camera's clamp would change the view ratios.
+__device__ __forceinline__ bool surely_unselected(const CoverBound &b, float fx2, float fy2,
+                                                  const CamK &c, int level, int n_levels,
+                                                  float smax, float smin) {
+    if (!(fabsf(b.xr) <= c.limx) || !(fabsf(b.yr) <= c.limy)) return false;
+    // S^2 = num / den, compared without dividing
+    const float num = b.s2_unit * fx2 * fy2, den = fmaxf(fx2 * b.v00, fy2 * b.v11);
+    if (!fin(num) || !(den > 0.0f) || !fin(den)) return false;
+    const float lo = num * (2.0f - b.mu2), hi = num * b.mu2;
+    if (level != 1 && smax > 0.0f && fin(smax) && lo > 2.25f * smax * smax * den) return true;
+    if (level != n_levels && smin > 0.0f && fin(smin) && hi < 4.0f * den &&
+        hi < 0.25f * smin * smin * den)
+        return true;
+    return false;
 }
 
 struct SceneK {

@@ -319,6 +319,7 @@ struct ProjViews {
     int union_first;
     float *smax_out, *smin_out;  // the scene's ranges, written when a view updates
     int color_src[MAXV];
+    float fx2[MAXV], fy2[MAXV];  // squared focal lengths (the coverage bound)
     CamK cam[MAXV];
     ProjOut out[MAXV];
 };
@@ -551,6 +552,271 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
         atomicAdd(&pv.union_stats[kStatSurvivors], s_surv[MAXV]);
 }
 
+// Position of the set bit of rank r (0-based, from the least significant)
+// in m, which has more than r set bits.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (r >= c) {
+            r -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// K1 for selective renders of one pose at several resolutions (every view
+// with view 0's R, t and camera centre, no coverage output, no range
+// update), leaving out the footprints that cannot be selected.  Per
+// Gaussian the coverage bound (cover_bound) marks the views whose exact
+// footprint is needed; the warp packs its (Gaussian, view) pairs that need
+// one, 32 per round, each lane taking the pair's Gaussian (view-space
+// point, covariance, colour) from the owner lane by shuffles and the
+// camera and outputs from shared memory.  A pair left out holds n_tiles 0,
+// the depth key and the empty rectangle (0, 0xffffffff); every other pair
+// writes what project_kernel writes, so the lists, records, masks and stats
+// are the same bit for bit.
+template <int MAXV>
+__global__ void __launch_bounds__(kProjThreads, 3)
+project_pruned_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, bool staged_ok) {
+    constexpr int kWarps = kProjThreads / 32;
+    __shared__ uint32_t s_hist[MAXV + 1][4][128];
+    __shared__ uint32_t s_surv[MAXV + 1];
+    __shared__ unsigned long long s_dup[MAXV];
+    __shared__ __align__(128) ProjStage s_st[2];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ CamK s_cam[MAXV];
+    __shared__ ProjOut s_out[MAXV];
+    __shared__ uint32_t s_bits[kProjThreads];  // per Gaussian: bit v selected, bit 8 + v listed
+    __shared__ uint32_t s_vlanes[kWarps][MAXV];  // per warp and view: lanes needing the footprint
+    __shared__ int s_voff[kWarps][MAXV];         // first pair of each view in the warp's packing
+    for (int k = threadIdx.x; k < (MAXV + 1) * 512; k += blockDim.x) (&s_hist[0][0][0])[k] = 0;
+    for (int k = threadIdx.x; k < (int)(MAXV * sizeof(CamK) / 4); k += blockDim.x)
+        reinterpret_cast<uint32_t *>(s_cam)[k] = reinterpret_cast<const uint32_t *>(pv.cam)[k];
+    if (threadIdx.x < MAXV) s_out[threadIdx.x] = pv.out[threadIdx.x];
+    s_bits[threadIdx.x] = 0u;
+    if (threadIdx.x <= MAXV) s_surv[threadIdx.x] = 0;
+    if (threadIdx.x < MAXV) s_dup[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int nv = pv.n_views;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nchunks = (sc.n + kProjThreads - 1) / kProjThreads;
+    auto full = [&](int64_t c) { return staged_ok && (c + 1) * kProjThreads <= sc.n; };
+    if ((int64_t)blockIdx.x < nchunks && full(blockIdx.x)) issue_chunk(sc, blockIdx.x, s_st[0], &s_bar[0]);
+    uint32_t par = 0;
+    int it = 0;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x, it++) {
+        const int b = it & 1;
+        const int64_t cn = c + gridDim.x;
+        if (cn < nchunks && full(cn)) issue_chunk(sc, cn, s_st[b ^ 1], &s_bar[b ^ 1]);
+        bool staged = full(c);
+        if (staged) {
+            bool ok = false;
+            for (uint32_t spins = 0; spins < kSpinLimit && !ok; spins++)
+                ok = mbar_try_wait(&s_bar[b], (par >> b) & 1u);
+            par ^= 1u << b;
+            if (!ok) {  // copies still out: this chunk reads global memory
+                staged = false;
+                for (int v = 0; v < nv; v++)
+                    atomicOr(pv.out[v].stats + kStatStatus, (uint32_t)kStatusTimeout);
+            }
+        }
+        const ProjStage &st = s_st[b];
+        const int64_t base = c * kProjThreads;
+        const int t = threadIdx.x;
+        const int64_t i = base + t;
+        const bool in = i < sc.n;
+        float m[3] = {0.0f, 0.0f, 0.0f}, S6[6], lnop_i = 0.0f, smax_i = 0.0f, smin_i = 0.0f;
+        float op = 0.0f;
+        int level_i = 0;
+        bool cov_ok = false;
+        if (in) {
+            float sv[3];
+            float4 q;
+            if (staged) {
+                m[0] = st.mean[3 * t];
+                m[1] = st.mean[3 * t + 1];
+                m[2] = st.mean[3 * t + 2];
+                sv[0] = st.scale[3 * t];
+                sv[1] = st.scale[3 * t + 1];
+                sv[2] = st.scale[3 * t + 2];
+                q = st.quat[t];
+                lnop_i = st.lnop[t];
+                smax_i = st.smax[t];
+                smin_i = st.smin[t];
+                op = st.opacity[t];
+                level_i = st.level[t];
+            } else {
+                m[0] = sc.mean[3 * i];
+                m[1] = sc.mean[3 * i + 1];
+                m[2] = sc.mean[3 * i + 2];
+                sv[0] = sc.scale[3 * i];
+                sv[1] = sc.scale[3 * i + 1];
+                sv[2] = sc.scale[3 * i + 2];
+                q = reinterpret_cast<const float4 *>(sc.quat)[i];
+                lnop_i = sc.lnop[i];
+                smax_i = sc.s_max[i];
+                smin_i = sc.s_min[i];
+                op = sc.opacity[i];
+                level_i = sc.level[i];
+            }
+            cov_ok = cov3d(sv, q, S6);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 6; k++) S6[k] = 0.0f;
+        }
+        // the views whose exact footprint is needed
+        float tz, xr, yr;
+        view_point(m, s_cam[0], tz, xr, yr);
+        CoverBound cb;
+        cover_bound(tz, xr, yr, S6, cov_ok, lnop_i, s_cam[0], cb);
+        uint32_t need = 0u;
+        if (in)
+            for (int v = 0; v < nv; v++)
+                if (!(cb.ok && surely_unselected(cb, pv.fx2[v], pv.fy2[v], s_cam[v], level_i,
+                                                 sc.n_levels, smax_i, smin_i)))
+                    need |= 1u << v;
+        // the colour, evaluated once towards the centre every view shares,
+        // for a Gaussian that some view may list
+        float3 col = make_float3(0.0f, 0.0f, 0.0f);
+        if (need)
+            col = gaussian_color(sc.color, sc.sh_degree, i, m[0] - s_cam[0].campos[0],
+                                 m[1] - s_cam[0].campos[1], m[2] - s_cam[0].campos[2]);
+        const int lc = level_i | (cov_ok ? 0x100 : 0);
+        // every pair's tile count, depth key and empty rectangle first, in
+        // whole-warp stores (full DRAM sectors); the pairs that need a
+        // footprint overwrite theirs below
+        const uint32_t depth_key = __float_as_uint(tz);
+        if (in)
+            for (int v = 0; v < nv; v++) {
+                const ProjOut &o = pv.out[v];
+                o.n_tiles[i] = 0u;
+                o.depth[i] = depth_key;
+                o.rect[i] = make_uint2(0u, 0xffffffffu);
+            }
+        // pack the warp's (Gaussian, view) pairs, view by view
+        int total = 0;
+        for (int v = 0; v < nv; v++) {
+            const uint32_t bl = __ballot_sync(0xffffffffu, (need >> v) & 1u);
+            if (lane == 0) {
+                s_vlanes[warp][v] = bl;
+                s_voff[warp][v] = total;
+            }
+            total += __popc(bl);
+        }
+        __syncwarp();
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + lane;
+            const bool act = k < total;
+            int v = 0;
+            for (int u = 1; u < nv; u++)
+                if (k >= s_voff[warp][u]) v = u;
+            const int src = act ? nth_set_bit(s_vlanes[warp][v], k - s_voff[warp][v]) : lane;
+            float ss[6];
+#pragma unroll
+            for (int j = 0; j < 6; j++) ss[j] = __shfl_sync(0xffffffffu, S6[j], src);
+            const float ptz = __shfl_sync(0xffffffffu, tz, src);
+            const float pxr = __shfl_sync(0xffffffffu, xr, src);
+            const float pyr = __shfl_sync(0xffffffffu, yr, src);
+            const float L = __shfl_sync(0xffffffffu, lnop_i, src);
+            const float smx = __shfl_sync(0xffffffffu, smax_i, src);
+            const float smn = __shfl_sync(0xffffffffu, smin_i, src);
+            const float opv = __shfl_sync(0xffffffffu, op, src);
+            const float cr = __shfl_sync(0xffffffffu, col.x, src);
+            const float cg = __shfl_sync(0xffffffffu, col.y, src);
+            const float cbl = __shfl_sync(0xffffffffu, col.z, src);
+            const int plc = __shfl_sync(0xffffffffu, lc, src);
+            bool listed = false;
+            uint32_t nt = 0u;
+            if (act) {
+                const int lev = plc & 0xff;
+                const bool cok = (plc & 0x100) != 0;
+                const ProjOut &o = s_out[v];
+                const int64_t gi = base + warp * 32 + src;
+                Foot f;
+                footprint_vp(ptz, pxr, pyr, ss, cok, L, s_cam[v], f);
+                const bool sel = f.valid && select_pred(f.S, lev, sc.n_levels, smx, smn, MS_SELECTIVE);
+                listed = sel && f.ntiles > 0;
+                nt = listed ? f.ntiles : 0u;
+                if (listed) {  // the rest keeps the prefilled values
+                    o.n_tiles[gi] = nt;
+                    o.rect[gi] = make_uint2((uint32_t)f.x0 | ((uint32_t)f.y0 << 16),
+                                            (uint32_t)f.x1 | ((uint32_t)f.y1 << 16));
+                    o.rec[3 * gi + 0] = make_float4(f.ux, f.uy, fm(kConicA, f.ca), fm(kConicB, f.cb));
+                    o.rec[3 * gi + 1] = make_float4(fm(kConicA, f.cc), opv, cr, cg);
+                    o.rec[3 * gi + 2] = make_float4(cbl, fm(-kLog2e, L), f.ex, f.ey);
+#pragma unroll
+                    for (int p = 0; p < 4; p++) {
+                        const uint32_t d = (f.depth >> (8 * p)) & 255u;
+                        atomicAdd(&s_hist[v][p][d >> 1], 1u << (16 * (d & 1u)));
+                    }
+                }
+                const uint32_t fl = (sel ? 1u << v : 0u) | (listed ? 1u << (8 + v) : 0u);
+                if (fl) atomicOr(&s_bits[warp * 32 + src], fl);
+            }
+            // survivor and duplicate counts of the round's views (its pairs
+            // are in view order, so one contiguous range of views)
+            const int vlo = __shfl_sync(0xffffffffu, v, 0);
+            const int vhi = __shfl_sync(0xffffffffu, v, min(31, total - 1 - k0));
+            for (int u = vlo; u <= vhi; u++) {
+                const bool mine = act && v == u;
+                const uint32_t ws = __reduce_add_sync(0xffffffffu, mine && listed ? 1u : 0u);
+                const uint32_t wd = __reduce_add_sync(0xffffffffu, mine ? nt : 0u);
+                if (lane == 0 && ws) {
+                    atomicAdd(&s_surv[u], ws);
+                    atomicAdd(&s_dup[u], (unsigned long long)wd);
+                }
+            }
+        }
+        __syncwarp();
+        const uint32_t bits = s_bits[t];
+        s_bits[t] = 0u;
+        for (int v = 0; v < nv; v++) {
+            const ProjOut &o = pv.out[v];
+            if (o.mask) {
+                const uint32_t mb = __ballot_sync(0xffffffffu, in && ((bits >> v) & 1u));
+                if (lane == 0 && in) o.mask[i >> 5] = mb;
+            }
+        }
+        if (pv.union_flags) {
+            const bool any_listed = ((bits >> 8) & pv.union_mask) != 0u;
+            if (in) pv.union_flags[i] = any_listed ? 1u : 0u;
+            if (any_listed) {
+#pragma unroll
+                for (int p = 0; p < 4; p++) {
+                    const uint32_t d = (depth_key >> (8 * p)) & 255u;
+                    atomicAdd(&s_hist[MAXV][p][d >> 1], 1u << (16 * (d & 1u)));
+                }
+            }
+            const uint32_t wu = __reduce_add_sync(0xffffffffu, any_listed ? 1u : 0u);
+            if (lane == 0 && wu) atomicAdd(&s_surv[MAXV], wu);
+        }
+        __syncthreads();  // the buffer is refilled by the next iteration but one
+        if ((it + 1) % kHistFlushChunks == 0) {
+            flush_hist<MAXV>(s_hist, pv);
+            __syncthreads();
+        }
+    }
+    flush_hist<MAXV>(s_hist, pv);
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        const int v = threadIdx.x;
+        uint32_t *stats = pv.out[v].stats;
+        if (s_surv[v]) atomicAdd(&stats[kStatSurvivors], s_surv[v]);
+        if (s_dup[v]) atomicAdd(reinterpret_cast<unsigned long long *>(stats + kStatDup), s_dup[v]);
+    }
+    if (pv.union_stats && threadIdx.x == 0 && s_surv[MAXV])
+        atomicAdd(&pv.union_stats[kStatSurvivors], s_surv[MAXV]);
+}
+
 __global__ void select_kernel(int64_t n, const float *__restrict__ cover,
                               const uint8_t *__restrict__ level, int n_levels,
                               const float *__restrict__ smax,
@@ -647,9 +913,28 @@ int launch_project(const ms_scene_t *scene, const ms_camera_t *cams, int nv, ms_
                            aligned(scene->quat, 16) && aligned(scene->lnop, 16) &&
                            aligned(scene->s_max, 16) && aligned(scene->s_min, 16) &&
                            aligned(scene->opacity, 16) && aligned(scene->level, 16);
-    project_kernel<MAXV><<<grid_for(scene->n, kProjThreads, proj_blocks_per_sm<MAXV>()),
-                           kProjThreads, 0, st>>>(
-        make_scene(*scene), pv, (int)mode, staged_ok);
+    // selective views of one pose without coverage output or range updates
+    // leave out the footprints their coverage bound rules out
+    bool prune = MAXV > 1 && nv >= 2 && mode == MS_SELECTIVE;
+    for (int v = 0; v < nv && prune; v++)
+        prune = !outs[v].cover && pv.update_level[v] == 0 && pv.color_src[v] == 0 &&
+                std::memcmp(cams[v].R, cams[0].R, sizeof(cams[0].R)) == 0 &&
+                std::memcmp(cams[v].t, cams[0].t, sizeof(cams[0].t)) == 0;
+    for (int v = 0; v < MAXV; v++) {
+        const ms_camera_t &c = cams[v < nv ? v : 0];
+        pv.fx2[v] = (float)((double)c.fx * (double)c.fx);
+        pv.fy2[v] = (float)((double)c.fy * (double)c.fy);
+    }
+    const int grid = grid_for(scene->n, kProjThreads, proj_blocks_per_sm<MAXV>());
+    if constexpr (MAXV > 1) {
+        if (prune) {
+            project_pruned_kernel<MAXV><<<grid, kProjThreads, 0, st>>>(make_scene(*scene), pv,
+                                                                      staged_ok);
+            return cuda_check(cudaGetLastError(), "project_pruned_kernel launch");
+        }
+    }
+    project_kernel<MAXV><<<grid, kProjThreads, 0, st>>>(make_scene(*scene), pv, (int)mode,
+                                                       staged_ok);
     return cuda_check(cudaGetLastError(), "project_kernel launch");
 }
 

@@ -93,6 +93,68 @@ def test_mixed_centres_any_view_count(cuda, ms_scene_50k, n_views):
     assert_views_equal(alone, joint)
 
 
+def pruned_both(torch, sc, cams, ds=None):
+    """Selective views of one pose without coverage output (the launch that
+    leaves out footprints its coverage bound rules out) against each camera
+    projected alone."""
+    ds = ds or msgs.DeviceScene(sc)
+    n = sc.n
+
+    def rs():
+        out = [msgs.Renderer(n, c.tiles_x * c.tiles_y, 16, with_cover=False) for c in cams]
+        for r in out:
+            for b in ("rec", "rect", "n_tiles", "depth", "mask", "stats"):
+                getattr(r, b).zero_()
+        return out
+    alone, joint = rs(), rs()
+    m = msgs.MODES["selective"]
+    for r, c in zip(alone, cams):
+        msgs.ms_project(ds.struct, msgs.camera_struct(c), m, r.proj)
+    msgs.ms_project_views(ds.struct, [msgs.camera_struct(c) for c in cams], m,
+                          [r.proj for r in joint])
+    torch.cuda.synchronize()
+    pruned = 0
+    for v, (a, j) in enumerate(zip(alone, joint)):
+        for b in ("rec", "n_tiles", "depth", "mask", "stats"):
+            assert getattr(a, b).equal(getattr(j, b)), (v, b)
+        listed = a.n_tiles[:n] != 0
+        ra, rj = a.rect.view(-1, 2)[:n], j.rect.view(-1, 2)[:n]
+        assert ra[listed].equal(rj[listed]), v
+        # a pair left out holds the empty rectangle
+        empty = (rj[:, 0] == 0) & (rj[:, 1] == -1)
+        assert bool((empty | (ra == rj).all(1)).all()), v
+        pruned += int((~(ra == rj).all(1)).sum())
+    return pruned
+
+
+def test_pruned_views_equal_single_views(cuda, ms_scene_50k):
+    """The eight scales of one pose: the views' footprints the coverage
+    bound rules out are left out, and every list, record, mask and stat
+    still equals the camera's own ms_project bit for bit."""
+    pruned = pruned_both(cuda, ms_scene_50k, shared_centre_cams())
+    assert pruned > 10_000
+
+
+def test_pruned_views_on_the_1M_sweep(cuda):
+    """The 1M four-level scene with its calibrated ranges (many Gaussians
+    near a range's edge) at the eight scales of the bench sweep."""
+    sc = inputs.multiscale_scene(n=1_000_000, seed=0)
+    ds = msgs.DeviceScene(sc)
+    ds.calibrate(inputs.orbit_cameras(8, seed=1, radius=25.0))
+    cams = [inputs.downscale(inputs.config2_camera(), s) for s in inputs.SCALES]
+    assert pruned_both(cuda, sc, cams, ds) > 1_000_000
+
+
+def test_pruned_views_ragged_invalid(cuda):
+    sc = degenerate_scene()
+    sc.level[:] = np.arange(sc.n) % 3 + 1
+    sc.n_levels = 3
+    ds = msgs.DeviceScene(sc)
+    ds.calibrate([inputs.config1_camera()])
+    cams = [inputs.downscale(inputs.config1_camera(400, 300), s) for s in (1, 2, 4, 8, 16)]
+    pruned_both(cuda, sc, cams, ds)
+
+
 def test_invalid_gaussians_and_ragged_chunk(cuda):
     sc = degenerate_scene()
     cams = [inputs.config1_camera(96, 80), inputs.config1_camera(48, 40),
@@ -134,11 +196,14 @@ def test_render_views_equals_frames_rendered_alone(cuda, ms_scene_50k):
             assert a.equal(b), v
 
 
-def test_histogram_flush_on_a_30M_scene(cuda):
+@pytest.mark.parametrize("mode", ["all_levels", "selective"])
+def test_histogram_flush_on_a_30M_scene(cuda, mode):
     """30M Gaussians: with two views (456 CTAs of 256 threads) every CTA
     processes more than 255 chunks, so its 16-bit digit counts are flushed
     mid-launch; one view (608 CTAs) never flushes early.  Counters,
-    histograms and footprints still agree bit for bit."""
+    histograms and footprints still agree bit for bit, in both the plain
+    multi-view launch and the pruning one (one level: nothing is left
+    out, every pair is packed)."""
     torch = cuda
     sc = inputs.single_level_scene(n=30_000_000, seed=9)
     ds = msgs.DeviceScene(sc)
@@ -155,7 +220,7 @@ def test_histogram_flush_on_a_30M_scene(cuda):
                            msgs._ptr(t["depth"]), 0, 0, msgs._ptr(t["stats"]), n)
         return t, p
 
-    m = msgs.MODES["all_levels"]
+    m = msgs.MODES[mode]  # selective: views of one pose, the pruning launch
     joint = [proj() for _ in cams]
     msgs.ms_project_views(ds.struct, [msgs.camera_struct(c) for c in cams], m,
                           [p for _, p in joint])

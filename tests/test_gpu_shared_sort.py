@@ -42,8 +42,11 @@ def sweep_cams(scales=inputs.SCALES):
     return [inputs.downscale(inputs.config2_camera(), s) for s in scales]
 
 
-def renderers(n, cams):
-    return [msgs.Renderer(n, c.tiles_x * c.tiles_y, 16 * n + 4096) for c in cams]
+def renderers(n, cams, cover=True):
+    # without coverage output, selective views of one pose take the
+    # projection launch that leaves out footprints ruled out by the bound
+    return [msgs.Renderer(n, c.tiles_x * c.tiles_y, 16 * n + 4096, with_cover=cover)
+            for c in cams]
 
 
 def bins_of(torch, r):
@@ -52,9 +55,9 @@ def bins_of(torch, r):
     return (r.gauss_idx[:d].cpu().numpy(), r.ranges.cpu().numpy().copy(), counts.copy())
 
 
-def run_both(torch, sc, cams, mode, views=None):
+def run_both(torch, sc, cams, mode, views=None, cover=True):
     ds = msgs.DeviceScene(sc)
-    own, shared = renderers(sc.n, cams), renderers(sc.n, cams)
+    own, shared = renderers(sc.n, cams), renderers(sc.n, cams, cover)
     order = msgs.DepthOrder(sc.n)
     out_own = msgs.render_views(ds, own, cams, mode)
     out_shared = msgs.render_views(ds, shared, cams, mode, order=order, order_views=views)
@@ -74,12 +77,13 @@ def expected_order(own, n, views=None):
     return idx[np.argsort(depth[idx], kind="stable")], listed
 
 
-@pytest.mark.parametrize("mode", ["selective", "all_levels"])
-def test_shared_order_bins_like_own_sort(cuda, ms_scene_50k, mode):
+@pytest.mark.parametrize("mode,cover", [("selective", True), ("selective", False),
+                                        ("all_levels", True)])
+def test_shared_order_bins_like_own_sort(cuda, ms_scene_50k, mode, cover):
     torch = cuda
     cams = sweep_cams()
     sc = ms_scene_50k
-    _, own, shared, order, out_own, out_shared = run_both(torch, sc, cams, mode)
+    _, own, shared, order, out_own, out_shared = run_both(torch, sc, cams, mode, cover=cover)
     want, listed = expected_order(own, sc.n)
     stats = order.stats.cpu().numpy()
     assert int(stats[0]) == len(want)
@@ -134,7 +138,8 @@ def test_union_of_some_views(cuda, ms_scene_50k, views):
     torch = cuda
     cams = sweep_cams()
     sc = ms_scene_50k
-    _, own, shared, order, out_own, out_shared = run_both(torch, sc, cams, "selective", views)
+    _, own, shared, order, out_own, out_shared = run_both(torch, sc, cams, "selective", views,
+                                                          cover=False)
     want, _ = expected_order(own, sc.n, views)
     assert int(order.stats[0].item()) == len(want)
     assert np.array_equal(order.order[:len(want)].cpu().numpy(), want.astype(np.int32))
