@@ -145,6 +145,40 @@ def test_pruned_views_on_the_1M_sweep(cuda):
     assert pruned_both(cuda, sc, cams, ds) > 1_000_000
 
 
+def test_pruned_views_at_the_range_edges(cuda):
+    """Ranges placed on the selection thresholds of Eq. 6: every Gaussian's
+    s_max puts S / s_max within a few ulps of 1.5 in one view and its s_min
+    puts S / s_min within a few ulps of 0.5 in another, and a third of the
+    Gaussians are needles (one axis 400x shorter, so their 2D covariance is
+    badly conditioned).  The bound must leave out no footprint that the
+    exact comparison would select."""
+    torch = cuda
+    sc = inputs.multiscale_scene(n=20_000, seed=3)
+    sc.log_scale[::3, 2] -= 6.0
+    ds = msgs.DeviceScene(sc)
+    cams = shared_centre_cams()
+    n = sc.n
+    rs = [msgs.Renderer(n, c.tiles_x * c.tiles_y, 16) for c in cams]
+    msgs.ms_project_views(ds.struct, [msgs.camera_struct(c) for c in cams],
+                          msgs.MODES["all_levels"], [r.proj for r in rs])
+    torch.cuda.synchronize()
+    S = torch.stack([r.cover[:n] for r in rs], 1).double()          # n x 8, exact FP32 S
+    rng = np.random.default_rng(11)
+    va = torch.from_numpy(rng.integers(0, 4, n)).cuda()             # views 1x .. 8x
+    vb = torch.from_numpy(rng.integers(3, 8, n)).cuda()             # views 8x .. 128x
+    ka = torch.from_numpy(rng.integers(-3, 4, n).astype(np.float64)).cuda()
+    kb = torch.from_numpy(rng.integers(-3, 4, n).astype(np.float64)).cuda()
+    u = 2.0 ** -24
+    sa = S.gather(1, va[:, None])[:, 0]
+    sb = S.gather(1, vb[:, None])[:, 0]
+    smax = sa / 1.5 * (1.0 + ka * u)
+    smin = sb / 0.5 * (1.0 + kb * u)
+    ok = (sa > 0) & (sb > 0)
+    ds.s_max[:n] = torch.where(ok, smax, torch.ones_like(smax)).float()
+    ds.s_min[:n] = torch.where(ok, smin, torch.ones_like(smin)).float()
+    assert pruned_both(torch, sc, cams, ds) > 1000
+
+
 def test_pruned_views_ragged_invalid(cuda):
     sc = degenerate_scene()
     sc.level[:] = np.arange(sc.n) % 3 + 1
