@@ -305,14 +305,16 @@ int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
  * resolutions, as in a multi-scale sweep) with one shared depth sort.  A
  * Gaussian's view depth does not depend on the intrinsics, so the Gaussians
  * listed in any of the frames can be sorted by (depth bits, index) once;
- * each frame's tile lists then come from that order, skipping the Gaussians
- * it does not list, and equal ms_bin's bit for bit.
+ * each frame's tile lists then come from that order (directly, skipping the
+ * Gaussians it does not list, or from its own part split off by
+ * ms_split_order), and equal ms_bin's bit for bit.
  *
  * ms_project_views_union: ms_project_views that also forms the union of
  * the views whose bit is set in union_views (bit v: view v; at least one,
  * none at or above n_views; their cameras' R and t equal bitwise, else
- * MS_ERR_INVALID_ARG).  It writes union_flags[n] (1 if the Gaussian is
- * listed in any of those views, else 0) and union_stats[MS_STATS_WORDS]
+ * MS_ERR_INVALID_ARG).  It writes union_flags[n] (the mask of those views
+ * that list the Gaussian, bit v for view v; 0 if none) and
+ * union_stats[MS_STATS_WORDS]
  * (16-B aligned; the union's count and its depth-digit histograms, zeroed
  * by the call).  The union's projection for ms_sort_depth is
  * { depth = outs[f].depth, n_tiles = union_flags, stats = union_stats,
@@ -326,11 +328,21 @@ int ms_bin(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
  * proj->stats words 4-5 and reported by every ms_bin_ordered that uses the
  * order.  `ws` (16-B aligned) of ms_sort_depth_workspace_bytes(n) bytes.
  *
- * ms_bin_ordered: ms_bin for one frame, taking the depth order from
- * ms_sort_depth (order, and order_stats = the sorted projection's stats,
- * whose survivor count is the order's length) instead of sorting; the
- * order must cover every Gaussian the frame lists.  Same workspace,
- * outputs and errors as ms_bin.
+ * ms_split_order: the order of ms_sort_depth restricted to each view of
+ * the union, in one pass: orders[v][0..s_v) receives, in the same order,
+ * the Gaussians whose union_flags bit v is set (s_v = what view v lists),
+ * and view_stats[v] (MS_STATS_WORDS words, 16-B aligned) receives s_v as
+ * its survivor count and the union's status (the sort's waits and this
+ * pass's) as its status.  union_proj is the sorted union (n_tiles =
+ * union_flags, stats = union_stats); orders and view_stats are host arrays
+ * of n_views (1..MS_MAX_PROJ_VIEWS) device pointers, each order of n
+ * entries.  `ws` (16-B aligned) of ms_split_order_workspace_bytes(n) bytes.
+ *
+ * ms_bin_ordered: ms_bin for one frame, taking the depth order instead of
+ * sorting: either the union's (order from ms_sort_depth, order_stats = the
+ * union's stats) or the frame's own (orders[v] and view_stats[v] of
+ * ms_split_order); the order must cover every Gaussian the frame lists.
+ * Same workspace, outputs and errors as ms_bin.
  */
 int ms_project_views_union(const ms_scene_t *scene, const ms_camera_t *cams, int32_t n_views,
                            ms_mode_t mode, const ms_proj_t *outs, uint32_t union_views,
@@ -338,6 +350,10 @@ int ms_project_views_union(const ms_scene_t *scene, const ms_camera_t *cams, int
 size_t ms_sort_depth_workspace_bytes(int64_t n);
 int ms_sort_depth(const ms_proj_t *proj, int64_t n, uint32_t *order, void *ws, size_t ws_bytes,
                   void *stream);
+size_t ms_split_order_workspace_bytes(int64_t n);
+int ms_split_order(const ms_proj_t *union_proj, int64_t n, const uint32_t *order,
+                   int32_t n_views, uint32_t *const *orders, uint32_t *const *view_stats,
+                   void *ws, size_t ws_bytes, void *stream);
 int ms_bin_ordered(const ms_proj_t *proj, int64_t n, const ms_camera_t *cam,
                    const ms_bins_t *out, const uint32_t *order, const uint32_t *order_stats,
                    void *ws, size_t ws_bytes, void *stream);

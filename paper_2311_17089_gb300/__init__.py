@@ -138,6 +138,9 @@ _SIGNATURES = [
     ("ms_sort_depth_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64]),
     ("ms_sort_depth", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.c_int64, P, P,
                                      ctypes.c_size_t, P]),
+    ("ms_split_order_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64]),
+    ("ms_split_order", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.c_int64, P,
+                                      ctypes.c_int32, P, P, P, ctypes.c_size_t, P]),
     ("ms_bin_ordered", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.c_int64,
                                       ctypes.POINTER(ms_camera_t), ctypes.POINTER(ms_bins_t),
                                       P, P, P, ctypes.c_size_t, P]),
@@ -313,6 +316,23 @@ def ms_sort_depth(proj: ms_proj_t, n: int, order_ptr: int, ws_ptr: int, ws_bytes
                   stream=None):
     _check(lib().ms_sort_depth(ctypes.byref(proj), int(n), P(order_ptr), P(ws_ptr), ws_bytes,
                                P(_stream(stream))))
+
+
+def ms_split_order_workspace_bytes(n: int) -> int:
+    return int(lib().ms_split_order_workspace_bytes(int(n)))
+
+
+def ms_split_order(union_proj: ms_proj_t, n: int, order_ptr: int, order_ptrs, stats_ptrs,
+                   ws_ptr: int, ws_bytes: int, stream=None):
+    """The union's depth order restricted to each view (orders[v], with the
+    view's count and the union's status in view_stats[v])."""
+    k = len(order_ptrs)
+    if len(stats_ptrs) != k:
+        raise MsError(MS_ERR_INVALID_ARG, "one stats array per order")
+    oa = (ctypes.c_void_p * max(k, 1))(*order_ptrs)
+    sa = (ctypes.c_void_p * max(k, 1))(*stats_ptrs)
+    _check(lib().ms_split_order(ctypes.byref(union_proj), int(n), P(order_ptr), k, oa, sa,
+                                P(ws_ptr), ws_bytes, P(_stream(stream))))
 
 
 def ms_bin_ordered(proj: ms_proj_t, n: int, cam: ms_camera_t, out: ms_bins_t, order_ptr: int,
@@ -599,16 +619,19 @@ class Renderer:
                    n_eval=None, strategy="auto", order=None):
         """Enqueue bin -> raster of this renderer's projection (left by
         ms_project or ms_project_views for `cam`).  With `order` (a
-        DepthOrder sorted for a pose this frame shares) the binning takes
-        that depth order instead of sorting (ms_bin_ordered)."""
+        DepthOrder sorted for a pose this frame shares, or (DepthOrder, v)
+        for frame v of a split order) the binning takes that depth order
+        instead of sorting (ms_bin_ordered)."""
         if cam.tiles_x * cam.tiles_y > self.max_tiles:
             raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
         cs = camera_struct(cam)
         if order is None:
             ms_bin(self.proj, scene.n, cs, self.bins, _ptr(self.ws), self.ws_bytes, stream)
         else:
-            ms_bin_ordered(self.proj, scene.n, cs, self.bins, _ptr(order.order),
-                           _ptr(order.stats), _ptr(self.ws), self.ws_bytes, stream)
+            order, v = order if isinstance(order, tuple) else (order, 0)
+            o, st = order.view_order(v)
+            ms_bin_ordered(self.proj, scene.n, cs, self.bins, o, st, _ptr(self.ws),
+                           self.ws_bytes, stream)
         image, final_t, n_contrib = out if out is not None else self.images(cam)
         ms_raster_ex(self.proj, self.bins, cs, _ptr(image), _ptr(final_t), _ptr(n_contrib),
                      _ptr(n_eval), _ptr(self.rws), self.rws_bytes,
@@ -627,7 +650,7 @@ class DepthOrder:
     Gaussians they list (ms_project_views_union), sorted once
     (ms_sort_depth) and consumed by each frame's ms_bin_ordered."""
 
-    def __init__(self, n: int, device="cuda"):
+    def __init__(self, n: int, device="cuda", split_views: int = 0):
         import torch
         dev = torch.device(device)
         nn = max(n, 1)
@@ -639,6 +662,15 @@ class DepthOrder:
         if self.ws_bytes == 0:
             raise MsError(MS_ERR_INVALID_ARG, "invalid sort workspace size")
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        # with split_views > 0: each view's own part of the order (ms_split_order)
+        self.split_views = split_views
+        self.view_orders = [torch.empty(nn, dtype=torch.int32, device=dev)
+                            for _ in range(split_views)]
+        self.view_stats = [torch.empty(MS_STATS_WORDS, dtype=torch.int32, device=dev)
+                           for _ in range(split_views)]
+        self.split_ws_bytes = ms_split_order_workspace_bytes(n) if split_views else 0
+        self.split_ws = (torch.empty(max(self.split_ws_bytes, 16), dtype=torch.uint8, device=dev)
+                         if split_views else None)
 
     def project(self, scene: "DeviceScene", renderers, cams, mode="selective", stream=None,
                 views=None):
@@ -657,9 +689,22 @@ class DepthOrder:
         self._n = scene.n
 
     def sort(self, stream=None):
-        """ms_sort_depth of the union formed by the last project()."""
+        """ms_sort_depth of the union formed by the last project(), then
+        (split_views > 0) every view's own part of the order."""
         ms_sort_depth(self._union, self._n, _ptr(self.order), _ptr(self.ws), self.ws_bytes,
                       stream)
+        if self.split_views:
+            k = self.split_views
+            ms_split_order(self._union, self._n, _ptr(self.order),
+                           [_ptr(o) for o in self.view_orders[:k]],
+                           [_ptr(t) for t in self.view_stats[:k]], _ptr(self.split_ws),
+                           self.split_ws_bytes, stream)
+
+    def view_order(self, v: int):
+        """(order, order_stats) device pointers frame v bins from."""
+        if self.split_views:
+            return _ptr(self.view_orders[v]), _ptr(self.view_stats[v])
+        return _ptr(self.order), _ptr(self.stats)
 
 
 def shared_order_views(survivors, frac: float = 0.8):
@@ -720,7 +765,7 @@ def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=Non
         with torch.cuda.stream(st):
             res.append(r.bin_raster(scene, cam, None if outs is None else outs[v], st,
                                     strategy=strategy,
-                                    order=order if order is not None and v in order_views
+                                    order=(order, v) if order is not None and v in order_views
                                     else None))
     if streams is not None:
         for st in streams:

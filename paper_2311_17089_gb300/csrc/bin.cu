@@ -540,6 +540,162 @@ int launch_onesweep(const PassArgs &a, uint64_t bound, cudaStream_t st) {
                                     : launch_pass<kLargeIPT>(a, bound, st);
 }
 
+// ------------------------------------------------------------ split
+
+// The shared depth order restricted to each view (ms_split_order): one pass
+// over the union's order in partitions of kSplitPart positions (8
+// consecutive ones per thread, so a thread's items stay in order), each item
+// appended to the order of every view whose bit its mask holds.  Per view,
+// the partition's count is found by a block scan of per-thread counts
+// (four views per 64-bit word, 16 bits each) and its offset by a decoupled
+// look-back over the earlier partitions' counts (thread v for view v).
+constexpr int kSplitThreads = 256;
+constexpr int kSplitIPT = 8;
+constexpr int kSplitPart = kSplitThreads * kSplitIPT;
+
+struct SplitArgs {
+    const uint32_t *order;   // union order (Gaussian indices)
+    const uint32_t *flags;   // per Gaussian: bit v set if listed in view v
+    const uint32_t *n32;     // union count (device)
+    uint64_t n_max;          // length of flags and order
+    int n_views;
+    uint32_t *out[MS_MAX_PROJ_VIEWS];         // per-view orders
+    uint32_t *view_stats[MS_MAX_PROJ_VIEWS];  // per-view count and status
+    uint32_t *status;        // [partitions][MS_MAX_PROJ_VIEWS] look-back words, zeroed
+    uint32_t *ticket;        // [2] zeroed: partitions taken, CTAs finished
+    unsigned long long *err;  // the union's status word (the sort's waits and this pass's)
+    uint32_t spin_limit;
+};
+
+__device__ __forceinline__ uint64_t block_excl_scan256_u64(uint64_t v, uint64_t *s_warp,
+                                                           uint64_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint64_t wpre = 0;
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < kSplitThreads / 32; w++) {
+        const uint64_t t = s_warp[w];
+        if (w < warp) wpre += t;
+        total += t;
+    }
+    __syncthreads();
+    return wpre + x - v;
+}
+
+__global__ void __launch_bounds__(kSplitThreads) split_kernel(SplitArgs a) {
+    __shared__ uint64_t s_warp[kSplitThreads / 32];
+    __shared__ uint32_t s_prefix[MS_MAX_PROJ_VIEWS];
+    __shared__ uint32_t s_part;
+    const int tid = threadIdx.x;
+    const uint32_t n = (uint32_t)umin64(*a.n32, a.n_max);
+    const uint32_t parts = (n + kSplitPart - 1) / kSplitPart;
+    if (blockIdx.x == 0 && tid < a.n_views && n == 0) a.view_stats[tid][kStatSurvivors] = 0u;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_part = atomicAdd(a.ticket, 1u);
+        __syncthreads();
+        const uint32_t p = s_part;
+        if (p >= parts) break;
+        uint32_t g[kSplitIPT], m[kSplitIPT];
+        const uint32_t j0 = p * (uint32_t)kSplitPart + (uint32_t)tid * kSplitIPT;
+#pragma unroll
+        for (int r = 0; r < kSplitIPT; r++) g[r] = j0 + r < n ? a.order[j0 + r] : 0xffffffffu;
+#pragma unroll
+        for (int r = 0; r < kSplitIPT; r++) {
+            m[r] = 0u;
+            if (g[r] < a.n_max) m[r] = a.flags[g[r]];
+            else if (g[r] != 0xffffffffu) {
+                MS_DCHECK(false, a.err);
+                atomicOr(a.err, (unsigned long long)kStatusTimeout);
+            }
+        }
+        // per-thread counts of views 0-3 and 4-7, 16 bits each
+        uint64_t c_lo = 0, c_hi = 0;
+#pragma unroll
+        for (int r = 0; r < kSplitIPT; r++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                c_lo += (uint64_t)((m[r] >> v) & 1u) << (16 * v);
+                c_hi += (uint64_t)((m[r] >> (v + 4)) & 1u) << (16 * v);
+            }
+        uint64_t t_lo, t_hi;
+        const uint64_t e_lo = block_excl_scan256_u64(c_lo, s_warp, t_lo);
+        const uint64_t e_hi = block_excl_scan256_u64(c_hi, s_warp, t_hi);
+        if (tid < a.n_views) {
+            const int v = tid;
+            const uint32_t local =
+                (uint32_t)(((v < 4 ? t_lo : t_hi) >> (16 * (v & 3))) & 0xffffu);
+            uint32_t *st = a.status + (uint64_t)p * MS_MAX_PROJ_VIEWS + v;
+            uint32_t excl = 0;
+            if (p == 0) {
+                st_relaxed(st, kFlagPre | local);
+            } else {
+                st_relaxed(st, kFlagAgg | local);
+                int64_t k = (int64_t)p - 1;
+                uint32_t spins = 0;
+                while (k >= 0) {
+                    const uint32_t w = ld_relaxed(a.status + (uint64_t)k * MS_MAX_PROJ_VIEWS + v);
+                    if ((w & kFlagMask) == 0) {  // not published yet: poll again
+                        if (++spins > a.spin_limit) {
+                            atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    excl += w & kValMask;
+                    if (w & kFlagPre) break;
+                    k--;
+                }
+                st_relaxed(st, kFlagPre | ((excl + local) & kValMask));
+            }
+            s_prefix[v] = excl;
+            if (p + 1 == parts) a.view_stats[v][kStatSurvivors] = excl + local;
+        }
+        __syncthreads();
+        // append each item to the order of every view it is listed in
+        uint32_t pos[MS_MAX_PROJ_VIEWS];
+#pragma unroll
+        for (int v = 0; v < MS_MAX_PROJ_VIEWS; v++)
+            pos[v] = (v < a.n_views ? s_prefix[v] : 0u) +
+                     (uint32_t)(((v < 4 ? e_lo : e_hi) >> (16 * (v & 3))) & 0xffffu);
+#pragma unroll
+        for (int r = 0; r < kSplitIPT; r++) {
+            const uint32_t mr = m[r];
+#pragma unroll
+            for (int v = 0; v < MS_MAX_PROJ_VIEWS; v++)
+                if (v < a.n_views && ((mr >> v) & 1u)) {
+                    const uint32_t q = pos[v]++;
+                    if (q < a.n_max) a.out[v][q] = g[r];
+                    else atomicOr(a.err, (unsigned long long)kStatusTimeout);
+                }
+        }
+    }
+    // the last CTA to finish copies the union's status (the sort's waits and
+    // this pass's) to every view
+    __shared__ bool s_last;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(a.ticket + 1, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && tid < a.n_views) {
+        __threadfence();
+        const uint32_t st = (uint32_t)ld_relaxed64(a.err);
+        a.view_stats[tid][kStatStatus] = st;
+        a.view_stats[tid][kStatStatus + 1] = 0u;
+    }
+}
+
 // ------------------------------------------------------------ workspace
 
 struct BinLayout {
@@ -789,6 +945,57 @@ extern "C" int ms_sort_depth(const ms_proj_t *proj, int64_t n, uint32_t *order, 
     unsigned long long *err = reinterpret_cast<unsigned long long *>(proj->stats + kStatStatus);
     if ((rc = depth_passes(proj, n, L, w, order, err, bin_spin_limit(), st))) return rc;
     return cuda_check(cudaGetLastError(), "ms_sort_depth launches");
+}
+
+extern "C" size_t ms_split_order_workspace_bytes(int64_t n) {
+    if (n < 0 || n > kMaxSortItems) return 0;
+    const int64_t parts = ceil_div(n > 0 ? n : 1, (int64_t)kSplitPart);
+    return 256 + (size_t)parts * MS_MAX_PROJ_VIEWS * 4;
+}
+
+extern "C" int ms_split_order(const ms_proj_t *union_proj, int64_t n, const uint32_t *order,
+                              int32_t n_views, uint32_t *const *orders,
+                              uint32_t *const *view_stats, void *ws, size_t ws_bytes,
+                              void *stream) {
+    if (!union_proj || !order || !orders || !view_stats)
+        return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (n_views < 1 || n_views > MS_MAX_PROJ_VIEWS)
+        return fail(MS_ERR_INVALID_ARG, "n_views must be 1..MS_MAX_PROJ_VIEWS");
+    if (n < 0 || n > kMaxSortItems) return fail(MS_ERR_INVALID_ARG, "n out of range");
+    const size_t need = ms_split_order_workspace_bytes(n);
+    if (!ws || ws_bytes < need || !aligned(ws, 16))
+        return fail(MS_ERR_INVALID_ARG, "workspace missing, too small or misaligned");
+    if (!union_proj->n_tiles || !union_proj->stats || !aligned(union_proj->stats, 16))
+        return fail(MS_ERR_INVALID_ARG, "union flags / stats NULL or stats misaligned");
+    if (union_proj->n < n) return fail(MS_ERR_INVALID_ARG, "the union holds fewer Gaussians than n");
+    SplitArgs a;
+    for (int v = 0; v < MS_MAX_PROJ_VIEWS; v++) {
+        a.out[v] = nullptr;
+        a.view_stats[v] = nullptr;
+    }
+    for (int v = 0; v < n_views; v++) {
+        if (!orders[v] || !view_stats[v] || !aligned(view_stats[v], 16))
+            return fail(MS_ERR_INVALID_ARG, "orders[v] / view_stats[v] NULL or stats misaligned");
+        a.out[v] = orders[v];
+        a.view_stats[v] = view_stats[v];
+    }
+    cudaStream_t st = as_stream(stream);
+    int rc;
+    if ((rc = cuda_check(cudaMemsetAsync(ws, 0, need, st), "split workspace memset"))) return rc;
+    char *w = static_cast<char *>(ws);
+    a.order = order;
+    a.flags = union_proj->n_tiles;
+    a.n32 = union_proj->stats + kStatSurvivors;
+    a.n_max = (uint64_t)n;
+    a.n_views = n_views;
+    a.ticket = reinterpret_cast<uint32_t *>(w);
+    a.status = reinterpret_cast<uint32_t *>(w + 256);
+    a.err = reinterpret_cast<unsigned long long *>(union_proj->stats + kStatStatus);
+    a.spin_limit = bin_spin_limit();
+    const int64_t parts = ceil_div(n > 0 ? n : 1, (int64_t)kSplitPart);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(parts, (int64_t)num_sms() * 2));
+    split_kernel<<<grid, kSplitThreads, 0, st>>>(a);
+    return cuda_check(cudaGetLastError(), "split_kernel launch");
 }
 
 extern "C" int ms_bin_counts(const ms_bins_t *bins, int64_t *d_needed, int64_t *survivors,

@@ -311,9 +311,9 @@ struct ProjViews {
     int n_views;
     int update_level[MAXV];  // level whose coverage range the view updates (0: none)
     // the union of the views in union_mask (all with one pose, so one depth
-    // per Gaussian, taken in view union_first): per Gaussian 1 if listed in
-    // any of them else 0, and stats with the union's count and depth-digit
-    // histograms; NULL: not formed
+    // per Gaussian, taken in view union_first): per Gaussian the mask of
+    // those views that list it (bit v: view v), and stats with the union's
+    // count and depth-digit histograms; NULL: not formed
     uint32_t *union_flags, *union_stats;
     uint32_t union_mask;
     int union_first;
@@ -454,7 +454,7 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
         float3 col = make_float3(0.0f, 0.0f, 0.0f);
         int col_src = -1;  // view whose camera centre col was evaluated towards
         bool range_dirty = false;
-        bool any_listed = false;  // listed in some view (the union)
+        uint32_t umask = 0u;      // the union's views that list it
         uint32_t depth0 = 0u;     // depth key in the pose the union's views share
         for (int v = 0; v < nv; v++) {
             const CamK &cam = pv.cam[v];
@@ -476,7 +476,7 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
                 }
                 listed = sel && f.ntiles > 0;
                 ntiles = listed ? f.ntiles : 0u;
-                if ((pv.union_mask >> v) & 1u) any_listed |= listed;
+                if (listed && ((pv.union_mask >> v) & 1u)) umask |= 1u << v;
                 if (v == pv.union_first) depth0 = f.depth;
                 o.n_tiles[i] = ntiles;
                 // depth and rectangle of every Gaussian: coalesced writes
@@ -523,7 +523,8 @@ project_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, int mode, 
             pv.smin_out[i] = smin_i;
         }
         if (MAXV > 1 && pv.union_flags) {
-            if (in) pv.union_flags[i] = any_listed ? 1u : 0u;
+            const bool any_listed = umask != 0u;
+            if (in) pv.union_flags[i] = umask;
             if (any_listed) {
 #pragma unroll
                 for (int p = 0; p < 4; p++) {
@@ -787,8 +788,9 @@ project_pruned_kernel(SceneK sc, const __grid_constant__ ProjViews<MAXV> pv, boo
             }
         }
         if (pv.union_flags) {
-            const bool any_listed = ((bits >> 8) & pv.union_mask) != 0u;
-            if (in) pv.union_flags[i] = any_listed ? 1u : 0u;
+            const uint32_t umask = (bits >> 8) & pv.union_mask;
+            const bool any_listed = umask != 0u;
+            if (in) pv.union_flags[i] = umask;
             if (any_listed) {
 #pragma unroll
                 for (int p = 0; p < 4; p++) {

@@ -55,10 +55,10 @@ def bins_of(torch, r):
     return (r.gauss_idx[:d].cpu().numpy(), r.ranges.cpu().numpy().copy(), counts.copy())
 
 
-def run_both(torch, sc, cams, mode, views=None, cover=True):
+def run_both(torch, sc, cams, mode, views=None, cover=True, split=False):
     ds = msgs.DeviceScene(sc)
     own, shared = renderers(sc.n, cams), renderers(sc.n, cams, cover)
-    order = msgs.DepthOrder(sc.n)
+    order = msgs.DepthOrder(sc.n, split_views=len(cams) if split else 0)
     out_own = msgs.render_views(ds, own, cams, mode)
     out_shared = msgs.render_views(ds, shared, cams, mode, order=order, order_views=views)
     torch.cuda.synchronize()
@@ -72,6 +72,7 @@ def expected_order(own, n, views=None):
     listed = np.zeros(n, dtype=bool)
     for v in views:
         listed |= own[v].n_tiles[:n].cpu().numpy() > 0
+    # (the union's flags hold, per Gaussian, the mask of the views listing it)
     depth = own[views[0]].depth[:n].cpu().numpy().view(np.uint32)
     idx = np.nonzero(listed)[0]
     return idx[np.argsort(depth[idx], kind="stable")], listed
@@ -88,6 +89,10 @@ def test_shared_order_bins_like_own_sort(cuda, ms_scene_50k, mode, cover):
     stats = order.stats.cpu().numpy()
     assert int(stats[0]) == len(want)
     assert np.array_equal(order.flags[:sc.n].cpu().numpy() > 0, listed)
+    mask = np.zeros(sc.n, dtype=np.int64)
+    for v, r in enumerate(own):
+        mask |= (r.n_tiles[:sc.n].cpu().numpy() > 0).astype(np.int64) << v
+    assert np.array_equal(order.flags[:sc.n].cpu().numpy().astype(np.int64), mask)
     assert np.array_equal(order.order[:len(want)].cpu().numpy(), want.astype(np.int32))
     # the union is larger than the finest frame's list (coarse levels are
     # listed in the coarse frames only), so the skipping path is exercised
@@ -101,6 +106,51 @@ def test_shared_order_bins_like_own_sort(cuda, ms_scene_50k, mode, cover):
     for v, (x, y) in enumerate(zip(out_own, out_shared)):
         for k in range(3):
             assert x[k].equal(y[k]), (v, k)
+
+
+@pytest.mark.parametrize("mode", ["selective", "all_levels"])
+def test_split_order_bins_like_own_sort(cuda, ms_scene_50k, mode):
+    """ms_split_order gives every frame its own part of the shared order:
+    exactly the frame's listed Gaussians in (depth bits, index) order, its
+    count in the view stats, and lists, ranges, counts and images equal to
+    ms_bin's."""
+    torch = cuda
+    cams = sweep_cams()
+    sc = ms_scene_50k
+    _, own, shared, order, out_own, out_shared = run_both(torch, sc, cams, mode, cover=False,
+                                                          split=True)
+    depth = own[0].depth[:sc.n].cpu().numpy().view(np.uint32)
+    for v, r in enumerate(own):
+        idx = np.nonzero(r.n_tiles[:sc.n].cpu().numpy() > 0)[0]
+        want = idx[np.argsort(depth[idx], kind="stable")]
+        st = order.view_stats[v].cpu().numpy()
+        assert int(st[0]) == len(want), v
+        assert int(st[4]) == 0 and int(st[5]) == 0, v
+        assert np.array_equal(order.view_orders[v][:len(want)].cpu().numpy(),
+                              want.astype(np.int32)), v
+    for v, (a, b) in enumerate(zip(own, shared)):
+        for x, y in zip(bins_of(torch, a), bins_of(torch, b)):
+            assert np.array_equal(x, y), v
+    for v, (x, y) in enumerate(zip(out_own, out_shared)):
+        for k in range(3):
+            assert x[k].equal(y[k]), (v, k)
+
+
+def test_split_order_ragged_and_subsets(cuda):
+    """A ragged scene with invalid Gaussians, the union over some of the
+    views (the others sort their own lists), and an empty view."""
+    torch = cuda
+    sc = degenerate_scene()
+    cams = [inputs.downscale(inputs.config1_camera(), s) for s in (1, 2, 4, 8)]
+    for views in (None, (1, 3)):
+        _, own, shared, order, out_own, out_shared = run_both(torch, sc, cams, "selective",
+                                                              views, split=True)
+        for a, b in zip(own, shared):
+            for x, y in zip(bins_of(torch, a), bins_of(torch, b)):
+                assert np.array_equal(x, y)
+        for x, y in zip(out_own, out_shared):
+            for k in range(3):
+                assert x[k].equal(y[k])
 
 
 def test_shared_order_ragged_invalid_scene(cuda):
