@@ -386,9 +386,8 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
     Gaussians (the paper's setting; the main workload puts 30% there):
     the same generator, cameras and calibration with split 95/3.5/1/0.5%.
     One 8-frame sweep (one multi-view projection, then each frame's bin and
-    raster on its own stream, the frames that list most of what the busiest
-    lists binning from one shared depth sort) replayed from a CUDA graph;
-    selective and all-levels frames/s."""
+    raster on its own stream, all frames binning from one shared depth sort)
+    replayed from a CUDA graph; selective and all-levels frames/s."""
     sc = inputs.multiscale_scene(n=n, seed=0, split=split)
     ds = msgs.DeviceScene(sc, device=dev)
     ds.calibrate(calib)
@@ -399,7 +398,8 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
                       "split": list(split)}}
     streams = [torch.cuda.Stream(device=dev, priority=(-1 if k < 3 else 0))
                for k in range(len(cams))]
-    order = msgs.DepthOrder(n, device=dev)
+    orders = {True: msgs.DepthOrder(n, device=dev, split_views=len(cams)),
+              False: msgs.DepthOrder(n, device=dev)}
     for mode in ("selective", "all_levels"):
         caps, surv = [], []
         for cam in cams:
@@ -410,11 +410,11 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
         rs = [msgs.Renderer(n, c.tiles_x * c.tiles_y, int(d * 1.05) + 1024, device=dev,
                             with_cover=False, with_mask=False) for c, d in zip(cams, caps)]
         bufs = [r.images(c, device=dev) for r, c in zip(rs, cams)]
-        ov = msgs.shared_order_views(surv)
+        ov, split = msgs.depth_order_plan(surv)
 
         def sweep():
-            msgs.render_views(ds, rs, cams, mode, outs=bufs, streams=streams, order=order,
-                              order_views=ov)
+            msgs.render_views(ds, rs, cams, mode, outs=bufs, streams=streams,
+                              order=orders[split], order_views=ov)
 
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
@@ -433,7 +433,8 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
             r.check()
         out[mode] = {"fps": len(cams) * steps * 1e3 / e0.elapsed_time(e1),
                      "D": [int(d) for d in caps],
-                     "shared_depth_order": [f"{cams[k].width}x{cams[k].height}" for k in ov]}
+                     "shared_depth_order": {"frames": [f"{cams[k].width}x{cams[k].height}"
+                                                       for k in ov], "split": bool(split)}}
         del rs, bufs, g
     out["selective_over_all_levels"] = out["selective"]["fps"] / out["all_levels"]["fps"]
     return out
@@ -849,12 +850,15 @@ def main():
             dmax[(mode, cam.width)] = d
             surv[(mode, cam.width)] = s_
     del probe
-    # the frames that list most of what the busiest frame lists bin from one
-    # shared depth sort of the union of their lists (the eight frames share
-    # the pose, so the depth keys); the others sort their own lists
-    order = msgs.DepthOrder(sc.n, device=dev)
-    order_views = {m: msgs.shared_order_views([surv[(m, c.width)] for c in cams])
-                   for m in ("selective", "all_levels")}
+    # the eight frames share the pose, so the depth keys: one depth sort of
+    # the union of their lists serves them all, split into every frame's
+    # own order when the frames list very different numbers of Gaussians
+    # (selective), taken as it is when they list nearly the same ones (all
+    # levels)
+    orders = {True: msgs.DepthOrder(sc.n, device=dev, split_views=len(cams)),
+              False: msgs.DepthOrder(sc.n, device=dev)}
+    plan = {m: msgs.depth_order_plan([surv[(m, c.width)] for c in cams])
+            for m in ("selective", "all_levels")}
     # one renderer (projection, tile lists, workspaces) per frame and mode,
     # sized by that frame's duplicate count, and one stream per frame: the
     # frames of a sweep are independent, and the small ones leave most SMs
@@ -874,13 +878,14 @@ def main():
     def step(mode, after=None, scene=None, views=True):
         # views: one projection pass for the eight frames (they share the
         # camera centre, so a Gaussian listed at several scales is coloured
-        # once) that also forms the union of the lists of the frames in
-        # order_views, whose depth sort runs once on the first one's stream;
-        # then each frame's binning and blend on its own stream; otherwise
-        # each frame projects on its own stream
+        # once) that also forms the union of their lists, whose depth sort
+        # (and split) runs once on the first frame's stream; then each
+        # frame's binning and blend on its own stream; otherwise each frame
+        # projects and sorts on its own stream
         main = torch.cuda.current_stream()
         d = scene or ds
-        ov = order_views[mode]
+        ov, split = plan[mode]
+        order = orders[split]
         sorted_ev = None
         if views:
             order.project(d, rs_mode[mode], cams, mode, main, ov)
@@ -895,7 +900,8 @@ def main():
                     st.wait_event(sorted_ev)
             with torch.cuda.stream(st):
                 if views:
-                    r.bin_raster(d, cam, out=out, stream=st, order=order if k in ov else None)
+                    r.bin_raster(d, cam, out=out, stream=st,
+                                 order=(order, k) if k in ov else None)
                 else:
                     r.render(d, cam, mode, out=out, stream=st)
                 if after is not None:
@@ -937,9 +943,25 @@ def main():
         return g
 
     g_step = {m: capture(lambda m=m: step(m)) for m in ("selective", "all_levels")}
-    # the sweep's projection launch as the step issues it (with the union)
-    g_views = capture(lambda: order.project(ds, rs_mode["selective"], cams, "selective",
-                                            views=order_views["selective"]))
+    # the sweep's projection launch as the step issues it (with the union),
+    # and the step's binning (the shared sort and split, every frame's
+    # binning) on one stream
+    sel_views, sel_split = plan["selective"]
+    g_views = capture(lambda: orders[sel_split].project(ds, rs_mode["selective"], cams,
+                                                        "selective", views=sel_views))
+
+    def bin_step():
+        o = orders[sel_split]
+        o.sort()
+        for k, (r, cam) in enumerate(zip(rs_mode["selective"], cams)):
+            cs = msgs.camera_struct(cam)
+            if k in sel_views:
+                po, pst = o.view_order(k)
+                msgs.ms_bin_ordered(r.proj, sc.n, cs, r.bins, po, pst, msgs._ptr(r.ws),
+                                    r.ws_bytes)
+            else:
+                msgs.ms_bin(r.proj, sc.n, cs, r.bins, msgs._ptr(r.ws), r.ws_bytes)
+    g_bin_step = capture(bin_step)
     # Gaussians listed in at least one frame: each reads its SH row once
     listed_any = torch.zeros(sc.n, dtype=torch.bool, device=dev)
     g_views.replay()
@@ -991,7 +1013,7 @@ def main():
 
     # per-scale and per-stage timing (events on the launching stream)
     per_scale = {"selective": {}, "all_levels": {}}
-    stage_ms = {"project": 0.0, "bin": 0.0, "raster": 0.0}
+    stage_ms = {"project": 0.0, "bin": 0.0, "raster": 0.0, "bin_frames_alone": 0.0}
     reps = max(20, args.steps)
     for mode in ("selective", "all_levels"):
         for cam in cams:
@@ -1011,9 +1033,10 @@ def main():
                 "fps": 1e3 / sum(ms), "project_ms": ms[0], "bin_ms": ms[1],
                 "raster_ms": ms[2], **stats[(mode, cam.width)]}
             if mode == "selective":
-                for k, name in (1, "bin"), (2, "raster"):
-                    stage_ms[name] += ms[k]
-    # the sweep projects its eight frames in one launch
+                for k, name in (1, "bin_frames_alone"), (2, "raster"):
+                    stage_ms[name] = stage_ms.get(name, 0.0) + ms[k]
+    # the sweep projects its eight frames in one launch, then bins them from
+    # one shared depth sort (timed here on one stream, every kernel in turn)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
     for _ in range(reps):
@@ -1021,6 +1044,12 @@ def main():
     ev[1].record(stream)
     torch.cuda.synchronize()
     stage_ms["project"] = ev[0].elapsed_time(ev[1]) / reps
+    ev[0].record(stream)
+    for _ in range(reps):
+        g_bin_step.replay()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    stage_ms["bin"] = ev[0].elapsed_time(ev[1]) / reps
     clk = clocks.stop()
 
     # roofline of the dominant stage of the selective step
@@ -1097,12 +1126,13 @@ def main():
     for cam in cams:
         st_ = stats[("selective", cam.width)]
         bin_bytes += 44 * st_["survivors"] + 44 * st_["D"]
-    roof_bin = {"bound": "hbm", "kernel": "binning (finish counts, 4 depth passes, duplicate, "
-                                          "1-2 tile passes, ranges), 8 frames each timed alone",
+    roof_bin = {"bound": "hbm", "kernel": "the step's binning on one stream (the shared depth "
+                                          "sort and split, per frame start, duplicate, 1-2 tile "
+                                          "passes, ranges)",
                 "achieved": bin_bytes / (stage_ms["bin"] / 1e3) / 1e9, "peak": hbm_peak,
                 "unit": "GB/s", "bytes_per_step": bin_bytes}
     roof_bin["frac"] = roof_bin["achieved"] / hbm_peak
-    dominant = max(stage_ms, key=stage_ms.get)
+    dominant = max(("project", "bin", "raster"), key=stage_ms.get)
     roof = roof_raster if dominant == "raster" else roof_project
     if dominant == "bin":
         roof = dict(roof_project)
@@ -1179,14 +1209,14 @@ def main():
                "pipeline": "scene upload + prepare of step i+1 on a copy stream during "
                            "step i's render (two scene buffers); images read back per frame"}
 
-    # kernels of libmsgs per selective step: one projection for every frame
-    # and 4 passes of the shared depth sort; per frame the start kernel, 4
-    # depth passes (frames outside the shared order), duplicate, 1-2 tile
-    # passes, ranges; segment offsets, raster
-    launches_per_step = 1 + 4
+    # kernels of libmsgs per selective step: one projection for every frame,
+    # 4 passes of the shared depth sort and its split; per frame the start
+    # kernel, 4 depth passes (frames outside the shared order), duplicate,
+    # 1-2 tile passes, ranges; segment offsets, raster
+    launches_per_step = 1 + 4 + (1 if sel_split else 0)
     for k, cam in enumerate(cams):
         tiles = cam.tiles_x * cam.tiles_y
-        launches_per_step += (1 + (0 if k in order_views["selective"] else 4) + 1
+        launches_per_step += (1 + (0 if k in sel_views else 4) + 1
                               + (1 if tiles <= 256 else 2) + 1) + 2
 
     train = None
@@ -1220,8 +1250,8 @@ def main():
             "ms_per_step": 1e3 * t_sel / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(config(sc.n), shared_depth_order={
-                m: [f"{cams[k].width}x{cams[k].height}" for k in v]
-                for m, v in order_views.items()}),
+                m: {"frames": [f"{cams[k].width}x{cams[k].height}" for k in v],
+                    "split": bool(sp)} for m, (v, sp) in plan.items()}),
             "clocks": clk, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "roofline": roof,
             "cpu_baseline": cpu,

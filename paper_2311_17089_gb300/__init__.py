@@ -707,6 +707,20 @@ class DepthOrder:
         return _ptr(self.order), _ptr(self.stats)
 
 
+def depth_order_plan(survivors, frac: float = 0.8):
+    """How the frames of one pose (survivors: their listed counts from an
+    earlier pass) share one depth sort: (views, split).  When every frame
+    lists at least `frac` of what the busiest lists, they all bin straight
+    from the sorted union (split False: each skips the few Gaussians it
+    does not list); otherwise the sorted union is split into every frame's
+    own order (split True) rather than making the small frames skip through
+    it."""
+    views = list(range(len(survivors)))
+    top = max(survivors) if len(survivors) else 0
+    dense = top > 0 and min(survivors) >= frac * top
+    return views, not dense
+
+
 def shared_order_views(survivors, frac: float = 0.8):
     """The frames of a sweep worth binning from one shared depth order: those
     that list at least `frac` of the most any frame lists (their lists then
