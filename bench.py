@@ -39,6 +39,13 @@ METRIC = ("frames/s at 1x-128x downscale, selective vs all-levels; "
 N_GAUSS = 1_000_000
 FP32_LANES_PER_SM = 128    # nominal, for the derived peak shown beside the measured one
 OPS_PER_EVAL = 16          # FP32 operations per pixel-Gaussian evaluation
+# FP32 operations per pixel-Gaussian evaluation of the raster backward (an
+# FMA counting as one): the forward's alpha again (power 6, test 2, ex2 and
+# clamp 3), the colour and transmittance recurrences (F 3, T 2, 1 / (1 -
+# alpha) 2), dL/dalpha over the three channels (13), the opacity and power
+# terms (4), the centre and conic terms (18) and the pixel's share of the
+# warp's reduce-scatter of the 2D gradients (6)
+OPS_PER_BWD_EVAL = 60
 MUFU_LANES_PER_SM = 16     # nominal ex2 results per SM per clock (one ex2 per evaluation)
 PAPER_LEVEL_MIX = (0.95, 0.035, 0.01, 0.005)   # coarse levels under 5% of the Gaussians
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures,
@@ -290,11 +297,13 @@ def train_setup(msgs, torch, ds, sc, dev):
         for st in streams:
             main.wait_stream(st)
 
-    def backward():
+    def backward(passes=0):
         # all views in one batched backward: one raster pass over every
-        # view's segments, one projection pass summing the views
-        msgs.ms_raster_bwd_views(ds.struct, views, grads, 0, msgs._ptr(bwd_ws), bwd_bytes)
+        # view's segments, one projection pass summing the views (`passes`
+        # picks one of them, for timing them apart)
+        msgs.ms_raster_bwd_views(ds.struct, views, grads, passes, msgs._ptr(bwd_ws), bwd_bytes)
 
+    backward.outs = outs
     return cams, rs, forward, backward, loss, grads_t
 
 
@@ -338,6 +347,32 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
         torch.cuda.synchronize()
         fwd += ev[0].elapsed_time(ev[1])
         bwd += ev[1].elapsed_time(ev[2])
+    # the backward's two passes timed apart (after a forward, the raster pass
+    # then the projection pass from the 2D gradients it left)
+    g_pass = []
+    for flag in (msgs.MS_BWD_RASTER_PASS, msgs.MS_BWD_PROJECT_PASS):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            backward(flag)
+        g_pass.append(g)
+    t_pass = [0.0, 0.0]
+    for _ in range(steps):
+        graphs[0].replay()
+        ev[0].record(stream)
+        g_pass[0].replay()
+        ev[1].record(stream)
+        g_pass[1].replay()
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        t_pass[0] += ev[0].elapsed_time(ev[1]) / steps
+        t_pass[1] += ev[1].elapsed_time(ev[2]) / steps
+    # evaluations the raster backward walks: every pixel's list up to its
+    # last contributor (the forward's n_contrib), over the views
+    n_walk = sum(int(o[2].sum(dtype=torch.int64).item()) for o in backward.outs)
+    listed_any = torch.zeros(sc.n, dtype=torch.bool, device=dev)
+    for r in rs:
+        listed_any |= r.n_tiles[:sc.n] != 0
+    n_blended = int(listed_any.sum().item())
     for r in rs:
         r.check()
     finite = all(bool(torch.isfinite(t).all()) for t in grads_t.values())
@@ -348,8 +383,23 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
         tiles = cam.tiles_x * cam.tiles_y
         launches += (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2 + 1
     launches += 2                                   # batched backward: raster, projection
+    nv = len(cams)
+    # the projection pass: per Gaussian its geometry (44 B), the 2D gradients
+    # of every view (36 B each) and the gradients written (236 B), plus the
+    # SH row (192 B) of every Gaussian some view blended
+    proj_bwd_bytes = sc.n * (44 + 36 * nv + 236) + 192 * n_blended
+    rast_s, proj_s = t_pass[0] / 1e3, t_pass[1] / 1e3
+    roof_bwd = {
+        "raster_bwd": {"bound": "alu", "kernel": "raster_bwd_kernel (the four views' segments)",
+                       "evaluations": n_walk, "ops_per_evaluation": OPS_PER_BWD_EVAL,
+                       "ms": t_pass[0], "unit": "Tops/s",
+                       "achieved": OPS_PER_BWD_EVAL * n_walk / rast_s / 1e12},
+        "project_bwd": {"bound": "hbm", "kernel": "project_bwd_kernel<3> (the views summed)",
+                        "bytes_per_launch": proj_bwd_bytes, "ms": t_pass[1], "unit": "GB/s",
+                        "achieved": proj_bwd_bytes / proj_s / 1e9}}
     return {"metric": "bwd it/s", "value": 1.0 / t_step, "unit": "it/s",
             "ms_per_step": 1e3 * t_step, "fwd_ms": fwd / steps, "bwd_ms": bwd / steps,
+            "roofline_bwd": roof_bwd,
             "loss": float(loss.item()), "grads_finite": finite,
             "gpu_launches": launches * steps,
             "config": {"workload": f"train-multiscale-{sc.n // 1000}k-4level-sh3-4views",
@@ -1239,6 +1289,13 @@ def main():
         train = train_step_bench(msgs, torch, ds, sc, dev, max(10, args.steps // 2),
                                  args.warmup)
         train["value"] *= world
+
+    if train is not None:
+        rb = train["roofline_bwd"]
+        rb["raster_bwd"]["peak"] = alu_peak
+        rb["raster_bwd"]["frac"] = rb["raster_bwd"]["achieved"] / alu_peak
+        rb["project_bwd"]["peak"] = hbm_peak
+        rb["project_bwd"]["frac"] = rb["project_bwd"]["achieved"] / hbm_peak
 
     aggregate = aggregate_bench(msgs, torch, ds, sc, dev)
     single_level = single_level_bench(msgs, torch, dev, max(50, args.steps))

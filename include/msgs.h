@@ -517,8 +517,14 @@ size_t ms_raster_bwd_views_workspace_bytes(int64_t n, int32_t n_views);
  * segments of every view by ticket, each view's 2D gradients going to its
  * own part of `ws`; one projection pass then applies, per Gaussian, the
  * chain rule of every view that blended it and writes the sum once.
- * `flags` as for ms_raster_bwd.
+ * `flags` as for ms_raster_bwd, plus the pass selection: with
+ * MS_BWD_RASTER_PASS alone only the raster pass runs (zeroing `ws` and
+ * leaving the views' 2D gradients in it), with MS_BWD_PROJECT_PASS alone
+ * only the projection pass (from the 2D gradients a raster pass left in
+ * the same `ws`); neither or both: the two passes.
  */
+#define MS_BWD_RASTER_PASS 2u
+#define MS_BWD_PROJECT_PASS 4u
 int ms_raster_bwd_views(const ms_scene_t *scene, const ms_bwd_view_t *views, int32_t n_views,
                         const ms_grads_t *grads, uint32_t flags, void *ws, size_t ws_bytes,
                         void *stream);

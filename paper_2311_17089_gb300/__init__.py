@@ -37,6 +37,8 @@ STRATEGIES = {"auto": MS_RASTER_AUTO, "tile": MS_RASTER_TILE, "list": MS_RASTER_
               "group32": MS_RASTER_GROUP32}
 MS_STATS_WORDS = 1040
 MS_BWD_ACCUMULATE = 1
+MS_BWD_RASTER_PASS = 2
+MS_BWD_PROJECT_PASS = 4
 MS_MAX_BWD_VIEWS = 8
 REC_FLOATS = 12
 

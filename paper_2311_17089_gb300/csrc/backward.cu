@@ -822,8 +822,12 @@ extern "C" int ms_raster_bwd_views(const ms_scene_t *scene, const ms_bwd_view_t 
         return fail(MS_ERR_INVALID_ARG, "scene mean/quat/scale/color is NULL");
     if (scene->sh_degree < -1 || scene->sh_degree > 3)
         return fail(MS_ERR_INVALID_ARG, "sh_degree must be in -1..3");
-    if (flags & ~MS_BWD_ACCUMULATE) return fail(MS_ERR_INVALID_ARG, "unknown flags");
+    if (flags & ~(MS_BWD_ACCUMULATE | MS_BWD_RASTER_PASS | MS_BWD_PROJECT_PASS))
+        return fail(MS_ERR_INVALID_ARG, "unknown flags");
     const bool accumulate = (flags & MS_BWD_ACCUMULATE) != 0;
+    const uint32_t passes = flags & (MS_BWD_RASTER_PASS | MS_BWD_PROJECT_PASS);
+    const bool raster_pass = passes == 0 || (passes & MS_BWD_RASTER_PASS);
+    const bool project_pass = passes == 0 || (passes & MS_BWD_PROJECT_PASS);
     const size_t need = ms_raster_bwd_views_workspace_bytes(scene->n, n_views);
     if (!ws || ws_bytes < need || !aligned(ws, 16))
         return fail(MS_ERR_INVALID_ARG, "backward workspace missing, too small or misaligned");
@@ -884,9 +888,12 @@ extern "C" int ms_raster_bwd_views(const ms_scene_t *scene, const ms_bwd_view_t 
     cudaStream_t st = as_stream(stream);
     const int64_t n = scene->n;
     int rc;
-    if ((rc = cuda_check(cudaMemsetAsync(ws, 0, need, st), "bwd workspace memset"))) return rc;
-    raster_bwd_kernel<<<raster_bwd_blocks_per_sm() * num_sms(), kBwdThreads, 0, st>>>(a);
-    if (n > 0) {
+    if (raster_pass) {
+        if ((rc = cuda_check(cudaMemsetAsync(ws, 0, need, st), "bwd workspace memset")))
+            return rc;
+        raster_bwd_kernel<<<raster_bwd_blocks_per_sm() * num_sms(), kBwdThreads, 0, st>>>(a);
+    }
+    if (n > 0 && project_pass) {
         pb.sc.n = n;
         pb.sc.sh_degree = scene->sh_degree;
         pb.sc.mean = scene->mean;

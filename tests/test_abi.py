@@ -134,7 +134,7 @@ def test_backward_argument_errors_need_no_device():
         return lib.ms_raster_bwd(ctypes.byref(s), ctypes.byref(cam), ctypes.byref(proj),
                                  ctypes.byref(bins), fake, fake, fake, rws_bytes, fake,
                                  ctypes.byref(g), flags, fake, ws_bytes, None)
-    assert bwd(2) == msgs.MS_ERR_INVALID_ARG and b"flags" in lib.ms_last_error()
+    assert bwd(8) == msgs.MS_ERR_INVALID_ARG and b"flags" in lib.ms_last_error()
     assert bwd(msgs.MS_BWD_ACCUMULATE, ws - 4) == msgs.MS_ERR_INVALID_ARG
     assert bwd(0, g=msgs.ms_grads_t(fake, fake, 0, fake, fake)) == msgs.MS_ERR_INVALID_ARG
     bad_deg = msgs.ms_scene_t(10, 1, 4, *([fake] * 10))

@@ -292,6 +292,18 @@ def test_batched_views_backward_matches_oracle_sum():
         g1 = oracle.grad64(sc, cam, off, idx, w)
         go = {k: go[k] + g1[k] for k in NAMES}
     compare(gg, go)
+    # the two passes run by themselves, one after the other (the raster
+    # pass's 2D gradients stay in the workspace for the projection pass)
+    for k in NAMES:
+        g[k].fill_(float("nan"))
+    msgs.ms_raster_bwd_views(ds.struct, views, grads, msgs.MS_BWD_RASTER_PASS,
+                             msgs._ptr(wsd), wsb)
+    msgs.ms_raster_bwd_views(ds.struct, views, grads, msgs.MS_BWD_PROJECT_PASS,
+                             msgs._ptr(wsd), wsb)
+    torch.cuda.synchronize()
+    compare({k: g[k].cpu().numpy().astype(np.float64) for k in NAMES}, go)
+    with pytest.raises(msgs.MsError):
+        msgs.ms_raster_bwd_views(ds.struct, views, grads, 8, msgs._ptr(wsd), wsb)
 
 
 def test_autograd_views_equals_sum_of_single_views():
