@@ -33,6 +33,24 @@ o = oracle.render(sc, cam, "selective")
 for strategy in ("tile", "list", "group16"):
     g = gpu_frame(sc, cam, "selective", strategy=strategy)   # asserts MS_OK
     assert_image_close(g, o)
+# the sweep's path (pruned multi-view projection, shared sort split into
+# per-frame orders, ordered binning) under the debug checks: silent, and the
+# frames equal the frames rendered one by one
+cams = [inputs.downscale(cam, s) for s in (1, 2, 4)]
+ds0 = msgs.DeviceScene(sc)
+for mode in ("selective", "all_levels"):
+    alone = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, 64 * sc.n) for c in cams]
+    want = [r.render(ds0, c, mode) for r, c in zip(alone, cams)]
+    rs = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, 64 * sc.n, with_cover=False)
+          for c in cams]
+    order = msgs.DepthOrder(sc.n, split_views=len(cams))
+    got = msgs.render_views(ds0, rs, cams, mode, order=order)
+    for r in alone + rs:
+        r.check()                                  # MS_OK, no index check fired
+    torch.cuda.synchronize()
+    for w, gimg in zip(want, got):
+        for a, b in zip(w, gimg):
+            assert a.equal(b)
 # a tile list entry beyond the projection's Gaussians: each raster kernel
 # clamps it and the debug checks report it
 ds = msgs.DeviceScene(sc)
