@@ -1070,6 +1070,7 @@ def main():
             graphs = g_stage[(mode, cam.width)]
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             tot = [0.0, 0.0, 0.0]
+            frame_ms = []
             for _ in range(reps):
                 for k in range(3):
                     ev[k].record(stream)
@@ -1078,10 +1079,13 @@ def main():
                 torch.cuda.synchronize()
                 for k in range(3):
                     tot[k] += ev[k].elapsed_time(ev[k + 1])
+                frame_ms.append(ev[0].elapsed_time(ev[3]))
             ms = [t / reps for t in tot]
             per_scale[mode][f"{cam.width}x{cam.height}"] = {
                 "fps": 1e3 / sum(ms), "project_ms": ms[0], "bin_ms": ms[1],
-                "raster_ms": ms[2], **stats[(mode, cam.width)]}
+                "raster_ms": ms[2], "frame_ms_median": float(np.median(frame_ms)),
+                "frame_ms_p99": float(np.percentile(frame_ms, 99)),
+                **stats[(mode, cam.width)]}
             if mode == "selective":
                 for k, name in (1, "bin_frames_alone"), (2, "raster"):
                     stage_ms[name] = stage_ms.get(name, 0.0) + ms[k]
