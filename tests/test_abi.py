@@ -200,3 +200,54 @@ def test_serve_argument_errors_need_no_device():
     assert lib.ms_serve_poll(None, 1, ctypes.byref(r)) == msgs.MS_ERR_INVALID_ARG
     assert lib.ms_serve_submit(None, None, None) == msgs.MS_ERR_INVALID_ARG
     assert lib.ms_serve_clock() > 0.0
+
+
+def test_shared_sort_argument_errors_need_no_device():
+    """The shared depth sort's calls reject bad arguments on the host."""
+    lib = msgs.lib()
+    fake = 1 << 20                      # never dereferenced: the checks fail first
+    E = msgs.MS_ERR_INVALID_ARG
+    up = msgs.ms_proj_t(0, 0, fake, fake, 0, 0, fake, 1000)
+    assert msgs.ms_sort_depth_workspace_bytes(1000) > 0
+    assert msgs.ms_sort_depth_workspace_bytes(-1) == 0
+    assert msgs.ms_split_order_workspace_bytes(1000) >= 256
+    assert msgs.ms_split_order_workspace_bytes(-1) == 0
+    ws = msgs.ms_split_order_workspace_bytes(1000)
+    orders = (ctypes.c_void_p * 8)(*([fake] * 8))
+    stats = (ctypes.c_void_p * 8)(*([fake] * 8))
+
+    def split(n_views, ws_bytes=ws, o=orders, s=stats, order=fake, n=1000):
+        return lib.ms_split_order(ctypes.byref(up), n, order, n_views, o, s, fake, ws_bytes,
+                                  None)
+    assert split(0) == E and split(9) == E                   # n_views outside 1..8
+    assert split(2, ws_bytes=ws - 16) == E                   # workspace too small
+    assert split(2, order=None) == E
+    assert split(2, n=2000) == E                             # the union holds 1000
+    bad = (ctypes.c_void_p * 8)(fake, 0, *([fake] * 6))
+    assert split(2, o=bad) == E                              # a NULL view order
+    assert lib.ms_sort_depth(ctypes.byref(up), 1000, None, fake, 1 << 30, None) == E
+    assert lib.ms_sort_depth(ctypes.byref(up), 1000, fake, fake, 16, None) == E
+    cam = msgs.camera_struct(inputs.config1_camera())
+    bins = msgs.ms_bins_t(fake, fake, fake, 16)
+    assert lib.ms_bin_ordered(ctypes.byref(up), 1000, ctypes.byref(cam), ctypes.byref(bins),
+                              None, fake, fake, 1 << 30, None) == E
+    sc = msgs.ms_scene_t(10, 1, -1, *([fake] * 10))
+    cams = (msgs.ms_camera_t * 2)(cam, cam)
+    outs = (msgs.ms_proj_t * 2)(up, up)
+    for mask in (0, 4):                                      # none, or a view beyond n_views
+        assert lib.ms_project_views_union(ctypes.byref(sc), cams, 2, 0, outs, mask, fake,
+                                          fake, None) == E
+    assert lib.ms_project_views_union(ctypes.byref(sc), cams, 2, 0, outs, 3, None, fake,
+                                      None) == E
+
+
+def test_depth_order_plan():
+    """Frames that list nearly the same Gaussians bin straight from the
+    sorted union; frames of very different list sizes get it split."""
+    views, split = msgs.depth_order_plan([900, 950, 1000])
+    assert views == [0, 1, 2] and not split
+    views, split = msgs.depth_order_plan([600_000, 650_000, 34_000])
+    assert views == [0, 1, 2] and split
+    assert msgs.depth_order_plan([0, 0])[1]                  # nothing listed: split (trivial)
+    assert msgs.shared_order_views([614, 649, 417, 34]) == [0, 1]
+    assert msgs.shared_order_views([]) == []
