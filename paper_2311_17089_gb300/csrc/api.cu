@@ -3,7 +3,10 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
+#include <set>
 #include <string>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -24,14 +27,38 @@ int cuda_check(cudaError_t e, const char *what) {
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 int num_sms() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];  // zero-initialised (static storage)
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    if (dev >= 0 && dev < 64) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
     if (n < 1) n = 1;
-    if (dev >= 0 && dev < 64) cached[dev] = n;
+    if (dev >= 0 && dev < 64) cached[dev].store(n, std::memory_order_relaxed);
     return n;
+}
+
+int ensure_smem_attr(const void *func, int bytes) {
+    // the attribute belongs to the function on the current device: set once
+    // per (device, function, size), from any host thread
+    static std::mutex mu;
+    static std::set<std::tuple<int, const void *, int>> done;
+    int dev = 0;
+    int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    const auto key = std::make_tuple(dev, func, bytes);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (done.count(key)) return MS_OK;
+    }
+    rc = cuda_check(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+                    "shared memory attribute");
+    if (rc) return rc;
+    std::lock_guard<std::mutex> g(mu);
+    done.insert(key);
+    return MS_OK;
 }
 
 static std::atomic<uint32_t> g_bin_spin_limit{0};

@@ -24,6 +24,8 @@
 // Jacobian, Sigma = R diag(e^s)^2 R^T, the normalised quaternion and the
 // SH colour (basis derivatives in closed form, projected on the sphere).
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <math.h>
 #include <stdint.h>
 
@@ -714,14 +716,8 @@ template <int DEG>
 static int launch_project_bwd(const ProjBwdArgs &pb, cudaStream_t st) {
     using CR = ColorRows<DEG>;
     const int smem = kProjBwdWarps * CR::WARP_FLOATS * (int)sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        int rc = cuda_check(cudaFuncSetAttribute(project_bwd_kernel<DEG>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-                            "project_bwd smem attribute");
-        if (rc) return rc;
-        attr = true;
-    }
+    int rc = ensure_smem_attr(reinterpret_cast<const void *>(project_bwd_kernel<DEG>), smem);
+    if (rc) return rc;
     const int64_t warps = ceil_div(pb.sc.n, 32);
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(ceil_div(warps, kProjBwdWarps), (int64_t)num_sms() * 16));
@@ -796,16 +792,16 @@ extern "C" size_t ms_raster_bwd_workspace_bytes(int64_t n) {
 }
 
 static int raster_bwd_blocks_per_sm() {
-    static int v = 0;
-    if (v == 0) {
-        int b = 0;
+    static std::atomic<int> v{0};
+    int b = v.load(std::memory_order_relaxed);
+    if (b == 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, raster_bwd_kernel, kBwdThreads, 0) !=
                 cudaSuccess ||
             b < 1)
             b = 1;
-        v = b;
+        v.store(b, std::memory_order_relaxed);
     }
-    return v;
+    return b;
 }
 
 extern "C" int ms_raster_bwd_views(const ms_scene_t *scene, const ms_bwd_view_t *views,

@@ -519,15 +519,9 @@ __global__ void bin_start_kernel(const uint32_t *__restrict__ stats,
 
 template <int IPT>
 static int launch_pass(const PassArgs &a, uint64_t bound, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        int rc = cuda_check(cudaFuncSetAttribute(onesweep_pass<IPT>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 SortCfg<IPT>::kSmem),
-                            "radix smem attribute");
-        if (rc) return rc;
-        attr = true;
-    }
+    int rc = ensure_smem_attr(reinterpret_cast<const void *>(onesweep_pass<IPT>),
+                              SortCfg<IPT>::kSmem);
+    if (rc) return rc;
     const int64_t parts = (int64_t)((bound + SortCfg<IPT>::kPart - 1) / SortCfg<IPT>::kPart);
     const int per_sm = bound <= kSmallPassItems ? kSmallPassCtasPerSm : kLargePassCtasPerSm;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(parts, (int64_t)num_sms() * per_sm));

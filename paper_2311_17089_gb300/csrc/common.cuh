@@ -111,6 +111,9 @@ __device__ __forceinline__ void fence_acquire() {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 int num_sms();
+// cudaFuncAttributeMaxDynamicSharedMemorySize = bytes for func on the
+// current device, once per (device, function, size); thread-safe
+int ensure_smem_attr(const void *func, int bytes);
 // Polls the binning's look-back waits make before giving up: kSpinLimit,
 // unless a test lowered it (ms_debug_set_spin_limit).
 uint32_t bin_spin_limit();

@@ -29,6 +29,8 @@
 // mark.  Every wait is bounded; a wait that gives
 // up sets a status bit and the CTA carries on.
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -631,16 +633,17 @@ raster_kernel(RasterArgs a) {
 }
 
 static int raster_blocks_per_sm() {
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0) {
-        int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_kernel, kRasterThreads,
+    // the same for every device of the one architecture this library targets
+    static std::atomic<int> blocks_per_sm{0};
+    int b = blocks_per_sm.load(std::memory_order_relaxed);
+    if (b == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, raster_kernel, kRasterThreads,
                                                           kSmemBytes) != cudaSuccess ||
-            v < 1)
-            v = 1;
-        blocks_per_sm = v;
+            b < 1)
+            b = 1;
+        blocks_per_sm.store(b, std::memory_order_relaxed);
     }
-    return blocks_per_sm;
+    return b;
 }
 
 }  // namespace msgs
@@ -677,15 +680,8 @@ extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
     cudaStream_t st = as_stream(stream);
     char *w = static_cast<char *>(ws);
     int rc;
-    static bool attr_set = false;
-    if (!attr_set) {
-        if ((rc = cuda_check(cudaFuncSetAttribute(raster_kernel,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  kSmemBytes),
-                             "raster smem attribute")))
-            return rc;
-        attr_set = true;
-    }
+    if ((rc = ensure_smem_attr(reinterpret_cast<const void *>(raster_kernel), kSmemBytes)))
+        return rc;
     const int resident = (int)std::min<int64_t>((int64_t)raster_blocks_per_sm() * num_sms(),
                                                 kMaxResident);
     // a frame with fewer tiles than SMs would leave SMs without a tile: the
