@@ -436,8 +436,10 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
     Gaussians (the paper's setting; the main workload puts 30% there):
     the same generator, cameras and calibration with split 95/3.5/1/0.5%.
     One 8-frame sweep (one multi-view projection, then each frame's bin and
-    raster on its own stream, all frames binning from one shared depth sort)
-    replayed from a CUDA graph; selective and all-levels frames/s."""
+    raster on its own stream, all frames binning from one shared depth sort,
+    with or without the SMs shared between the fine and coarse frames,
+    whichever a short trial finds faster) replayed from a CUDA graph;
+    selective and all-levels frames/s."""
     sc = inputs.multiscale_scene(n=n, seed=0, split=split)
     ds = msgs.DeviceScene(sc, device=dev)
     ds.calibrate(calib)
@@ -462,13 +464,28 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
         bufs = [r.images(c, device=dev) for r, c in zip(rs, cams)]
         ov, split = msgs.depth_order_plan(surv)
 
-        def sweep():
+        def sweep(share):
             msgs.render_views(ds, rs, cams, mode, outs=bufs, streams=streams,
-                              order=orders[split], order_views=ov)
+                              order=orders[split], order_views=ov, share_sms=share)
 
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            sweep()
+        # with and without the SMs shared; the faster is timed
+        cand, trial = {}, {}
+        for share in (False, True):
+            gc_ = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gc_):
+                sweep(share)
+            for _ in range(3):
+                gc_.replay()
+            torch.cuda.synchronize()
+            t0_, t1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0_.record()
+            for _ in range(10):
+                gc_.replay()
+            t1_.record()
+            torch.cuda.synchronize()
+            cand[share], trial[share] = gc_, t0_.elapsed_time(t1_) / 10
+        shared = trial[True] < trial[False]
+        g = cand[shared]
         for _ in range(3):
             g.replay()
         stream = torch.cuda.current_stream()
@@ -484,8 +501,10 @@ def level_mix_bench(msgs, torch, dev, n, cams, calib, steps, split=PAPER_LEVEL_M
         out[mode] = {"fps": len(cams) * steps * 1e3 / e0.elapsed_time(e1),
                      "D": [int(d) for d in caps],
                      "shared_depth_order": {"frames": [f"{cams[k].width}x{cams[k].height}"
-                                                       for k in ov], "split": bool(split)}}
-        del rs, bufs, g
+                                                       for k in ov], "split": bool(split)},
+                     "share_sms": {"chosen": bool(shared), "shared_ms": trial[True],
+                                   "not_shared_ms": trial[False]}}
+        del rs, bufs, g, cand
     out["selective_over_all_levels"] = out["selective"]["fps"] / out["all_levels"]["fps"]
     return out
 
@@ -909,6 +928,14 @@ def main():
               False: msgs.DepthOrder(sc.n, device=dev)}
     plan = {m: msgs.depth_order_plan([surv[(m, c.width)] for c in cams])
             for m in ("selective", "all_levels")}
+    # frames the tile kernel blends; whether a mode's sweep shares the SMs
+    # between them and the coarse frames is decided below by timing both
+    # schedules (it helps where the coarse frames carry much of the work and
+    # the fine frames bin quickly: selective 1.051 vs 1.088 ms, all levels
+    # 2.484 vs 2.447 ms)
+    sms_dev = torch.cuda.get_device_properties(dev).multi_processor_count
+    fine = [c.tiles_x * c.tiles_y >= sms_dev for c in cams]
+    share_plan = {"selective": True, "all_levels": False}
     # one renderer (projection, tile lists, workspaces) per frame and mode,
     # sized by that frame's duplicate count, and one stream per frame: the
     # frames of a sweep are independent, and the small ones leave most SMs
@@ -925,21 +952,27 @@ def main():
 
     css = [msgs.camera_struct(cam) for cam in cams]
 
-    def step(mode, after=None, scene=None, views=True):
+    def step(mode, after=None, scene=None, views=True, share=None):
         # views: one projection pass for the eight frames (they share the
         # camera centre, so a Gaussian listed at several scales is coloured
         # once) that also forms the union of their lists, whose depth sort
         # (and split) runs once on the first frame's stream; then each
         # frame's binning and blend on its own stream; otherwise each frame
-        # projects and sorts on its own stream
+        # projects and sorts on its own stream.  In selective mode the frames
+        # the tile kernel blends share the SMs: their blends run on
+        # SHARE_CTAS_PER_SM CTAs per SM and the coarse frames start once
+        # they have binned (as render_views with share_sms)
         main = torch.cuda.current_stream()
         d = scene or ds
         ov, split = plan[mode]
         order = orders[split]
+        share = views and (share_plan[mode] if share is None else share)
         sorted_ev = None
+        binned = []
         if views:
             order.project(d, rs_mode[mode], cams, mode, main, ov)
-        for k, (r, cam, out, st) in enumerate(zip(rs_mode[mode], cams, bufs, streams)):
+        for k in sorted(range(len(cams)), key=lambda k: not (share and fine[k])):
+            r, cam, out, st = rs_mode[mode][k], cams[k], bufs[k], streams[k]
             st.wait_stream(main)
             if views and k in ov:
                 if sorted_ev is None:
@@ -948,14 +981,21 @@ def main():
                     sorted_ev.record(st)
                 else:
                     st.wait_event(sorted_ev)
+            if share and not fine[k]:
+                for e in binned:
+                    st.wait_event(e)
             with torch.cuda.stream(st):
                 if views:
-                    r.bin_raster(d, cam, out=out, stream=st,
-                                 order=(order, k) if k in ov else None)
+                    r.bin(d, cam, st, (order, k) if k in ov else None)
+                    if share and fine[k]:
+                        binned.append(torch.cuda.Event())
+                        binned[-1].record(st)
+                    r.raster(cam, out, st, max_ctas_per_sm=(msgs.SHARE_CTAS_PER_SM
+                                                            if share and fine[k] else 0))
                 else:
                     r.render(d, cam, mode, out=out, stream=st)
                 if after is not None:
-                    after(out, st)
+                    after(k, out, st)
         for st in streams:
             main.wait_stream(st)
 
@@ -992,7 +1032,26 @@ def main():
             fn()
         return g
 
-    g_step = {m: capture(lambda m=m: step(m)) for m in ("selective", "all_levels")}
+    # each mode's sweep with and without the SMs shared; the faster is timed
+    share_trial = {}
+    g_step = {}
+    for m in ("selective", "all_levels"):
+        cand = {sh: capture(lambda m=m, sh=sh: step(m, share=sh)) for sh in (False, True)}
+        trial = {}
+        for sh, g in cand.items():
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            trial[sh] = e0.elapsed_time(e1) / 20
+        share_plan[m] = trial[True] < trial[False]
+        g_step[m] = cand[share_plan[m]]
+        share_trial[m] = {"shared_ms": trial[True], "not_shared_ms": trial[False]}
     # the sweep's projection launch as the step issues it (with the union),
     # and the step's binning (the shared sort and split, every frame's
     # binning) on one stream
@@ -1235,8 +1294,8 @@ def main():
             # the sweep as the timed step runs it (one projection launch, one
             # shared depth sort) from scene buffer j, each image read back
             # into pinned host memory as its frame ends
-            hb = iter(outs)
-            step("selective", after=lambda out, st: next(hb).copy_(out[0], non_blocking=True),
+            step("selective",
+                 after=lambda k, out, st: outs[k].copy_(out[0], non_blocking=True),
                  scene=scenes[j])
 
         # the public calls of each buffer's render captured once as a CUDA
@@ -1333,7 +1392,12 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(config(sc.n), shared_depth_order={
                 m: {"frames": [f"{cams[k].width}x{cams[k].height}" for k in v],
-                    "split": bool(sp)} for m, (v, sp) in plan.items()}),
+                    "split": bool(sp)} for m, (v, sp) in plan.items()},
+                share_sms={m: {"chosen": bool(share_plan[m]),
+                               "fine_frames": [f"{c.width}x{c.height}"
+                                               for c, f in zip(cams, fine) if f],
+                               "ctas_per_sm": msgs.SHARE_CTAS_PER_SM, **share_trial[m]}
+                           for m in share_plan}),
             "clocks": clk, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "roofline": roof,
             "cpu_baseline": cpu,

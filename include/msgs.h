@@ -437,6 +437,20 @@ int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
                  size_t ws_bytes, int strategy, void *stream);
 
 /*
+ * ms_raster_ex with the tile kernel's persistent CTAs capped at
+ * max_ctas_per_sm per SM (0: as many as fit, as ms_raster_ex), so that the
+ * kernels of other frames blended at the same time on other streams find
+ * room beside it.  The frame's segmentation follows the number of CTAs (the
+ * backward reads it from the workspace), so the blend's transmittance
+ * products may round differently from ms_raster_ex's.  Negative values:
+ * MS_ERR_INVALID_ARG.  The list and group kernels ignore the cap.
+ */
+int ms_raster_ex2(const ms_proj_t *proj, const ms_bins_t *bins,
+                  const ms_camera_t *cam, float *image, float *final_t,
+                  uint32_t *n_contrib, uint32_t *n_eval, void *ws,
+                  size_t ws_bytes, int strategy, int32_t max_ctas_per_sm, void *stream);
+
+/*
  * Gradients of a loss with respect to the scene parameters, outputs of
  * ms_raster_bwd; device buffers with the scene's shapes: dmean[n*3],
  * dlog_scale[n*3], dquat[n*4] (with respect to the unnormalised

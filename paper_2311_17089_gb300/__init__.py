@@ -178,6 +178,9 @@ _SIGNATURES = [
     ("ms_raster_ex", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
                                     ctypes.POINTER(ms_camera_t), P, P, P, P, P,
                                     ctypes.c_size_t, ctypes.c_int, P]),
+    ("ms_raster_ex2", ctypes.c_int, [ctypes.POINTER(ms_proj_t), ctypes.POINTER(ms_bins_t),
+                                     ctypes.POINTER(ms_camera_t), P, P, P, P, P,
+                                     ctypes.c_size_t, ctypes.c_int, ctypes.c_int32, P]),
     ("ms_aggregate_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64]),
     ("ms_aggregate", ctypes.c_int, [ctypes.POINTER(ms_scene_t), ctypes.POINTER(ms_camera_t),
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
@@ -421,6 +424,15 @@ def ms_raster_ex(proj: ms_proj_t, bins: ms_bins_t, cam: ms_camera_t, image_ptr: 
                               P(ws_ptr), ws_bytes, int(strategy), P(_stream(stream))))
 
 
+def ms_raster_ex2(proj: ms_proj_t, bins: ms_bins_t, cam: ms_camera_t, image_ptr: int,
+                  final_t_ptr: int, n_contrib_ptr: int, n_eval_ptr: int, ws_ptr: int,
+                  ws_bytes: int, strategy: int, max_ctas_per_sm: int, stream=None):
+    _check(lib().ms_raster_ex2(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(cam),
+                               P(image_ptr), P(final_t_ptr), P(n_contrib_ptr), P(n_eval_ptr),
+                               P(ws_ptr), ws_bytes, int(strategy), int(max_ctas_per_sm),
+                               P(_stream(stream))))
+
+
 def ms_raster_bwd_workspace_bytes(n: int) -> int:
     return int(lib().ms_raster_bwd_workspace_bytes(n))
 
@@ -607,23 +619,24 @@ class Renderer:
                 torch.empty((H, W), dtype=torch.int32, device=device))
 
     def render(self, scene: DeviceScene, cam: inputs.Camera, mode="selective", out=None,
-               stream=None, n_eval=None, strategy="auto"):
+               stream=None, n_eval=None, strategy="auto", max_ctas_per_sm=0):
         """Enqueue project -> bin -> raster.  Returns (image, final_t,
         n_contrib) device tensors; call `check()` after to learn D and
         whether the capacity sufficed.  `strategy` picks the raster kernel
-        ("auto", "tile" or "list", see ms_raster_ex)."""
+        ("auto", "tile", "list", "group8/16/32", see ms_raster_ex) and
+        max_ctas_per_sm caps the tile kernel's CTAs (ms_raster_ex2)."""
         if cam.tiles_x * cam.tiles_y > self.max_tiles:
             raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
         ms_project(scene.struct, camera_struct(cam), MODES.get(mode, mode), self.proj, stream)
-        return self.bin_raster(scene, cam, out, stream, n_eval, strategy)
+        return self.bin_raster(scene, cam, out, stream, n_eval, strategy,
+                               max_ctas_per_sm=max_ctas_per_sm)
 
-    def bin_raster(self, scene: DeviceScene, cam: inputs.Camera, out=None, stream=None,
-                   n_eval=None, strategy="auto", order=None):
-        """Enqueue bin -> raster of this renderer's projection (left by
+    def bin(self, scene: DeviceScene, cam: inputs.Camera, stream=None, order=None):
+        """Enqueue the binning of this renderer's projection (left by
         ms_project or ms_project_views for `cam`).  With `order` (a
         DepthOrder sorted for a pose this frame shares, or (DepthOrder, v)
-        for frame v of a split order) the binning takes that depth order
-        instead of sorting (ms_bin_ordered)."""
+        for frame v of a split order) it takes that depth order instead of
+        sorting (ms_bin_ordered)."""
         if cam.tiles_x * cam.tiles_y > self.max_tiles:
             raise MsError(MS_ERR_INVALID_ARG, "camera has more tiles than max_tiles")
         cs = camera_struct(cam)
@@ -634,11 +647,24 @@ class Renderer:
             o, st = order.view_order(v)
             ms_bin_ordered(self.proj, scene.n, cs, self.bins, o, st, _ptr(self.ws),
                            self.ws_bytes, stream)
+
+    def raster(self, cam: inputs.Camera, out=None, stream=None, n_eval=None, strategy="auto",
+               max_ctas_per_sm=0):
+        """Enqueue the blend of this renderer's bins (ms_raster_ex2).
+        Returns the (image, final_t, n_contrib) device tensors."""
+        cs = camera_struct(cam)
         image, final_t, n_contrib = out if out is not None else self.images(cam)
-        ms_raster_ex(self.proj, self.bins, cs, _ptr(image), _ptr(final_t), _ptr(n_contrib),
-                     _ptr(n_eval), _ptr(self.rws), self.rws_bytes,
-                     STRATEGIES.get(strategy, strategy), stream)
+        ms_raster_ex2(self.proj, self.bins, cs, _ptr(image), _ptr(final_t), _ptr(n_contrib),
+                      _ptr(n_eval), _ptr(self.rws), self.rws_bytes,
+                      STRATEGIES.get(strategy, strategy), max_ctas_per_sm, stream)
         return image, final_t, n_contrib
+
+    def bin_raster(self, scene: DeviceScene, cam: inputs.Camera, out=None, stream=None,
+                   n_eval=None, strategy="auto", order=None, max_ctas_per_sm=0):
+        """Enqueue bin -> raster of this renderer's projection (see bin()
+        and raster())."""
+        self.bin(scene, cam, stream, order)
+        return self.raster(cam, out, stream, n_eval, strategy, max_ctas_per_sm)
 
     def check(self, stream=None):
         rc, d, s = ms_bin_counts(self.bins, stream)
@@ -732,8 +758,14 @@ def shared_order_views(survivors, frac: float = 0.8):
     return [v for v, s in enumerate(survivors) if top > 0 and s >= frac * top]
 
 
+# CTAs per SM of the tile kernel when frames share the GPU (render_views
+# with share_sms): the blends of the fine frames leave room for the others
+SHARE_CTAS_PER_SM = 2
+
+
 def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=None,
-                 streams=None, strategy="auto", order=None, order_views=None):
+                 streams=None, strategy="auto", order=None, order_views=None,
+                 share_sms=False):
     """Several frames of one scene: one ms_project_views pass for every
     (up to MS_MAX_PROJ_VIEWS) cameras on the current stream, then each
     frame's bin -> raster on its own stream (streams[v], or the current
@@ -741,6 +773,10 @@ def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=Non
     v's buffers.  With `order` (a DepthOrder; at most MS_MAX_PROJ_VIEWS
     cameras) the frames in order_views (default all; cameras of one pose)
     bin from one shared depth sort, the others sort their own lists.
+    With share_sms (and streams), the frames the tile kernel blends (at
+    least as many tiles as SMs) blend on SHARE_CTAS_PER_SM CTAs per SM, and
+    the other frames start once those have binned, so that their binning and
+    blending fill the SM room the fine frames' blends leave.
     Returns the (image, final_t, n_contrib) of every frame."""
     import torch
     n = len(cams)
@@ -764,8 +800,13 @@ def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=Non
             sl = slice(v0, min(n, v0 + MS_MAX_PROJ_VIEWS))
             ms_project_views(scene.struct, [camera_struct(c) for c in cams[sl]], m,
                              [r.proj for r in renderers[sl]], main)
-    res = []
-    for v, (r, cam) in enumerate(zip(renderers, cams)):
+    share = share_sms and streams is not None and strategy == "auto"
+    sms = torch.cuda.get_device_properties(main.device).multi_processor_count if share else 0
+    fine = [share and c.tiles_x * c.tiles_y >= sms for c in cams]
+    binned = []   # events: the fine frames' binning done
+    res = [None] * n
+    for v in sorted(range(n), key=lambda k: not fine[k]):   # fine frames first
+        r, cam = renderers[v], cams[v]
         st = streams[v] if streams is not None else main
         if st is not main:
             st.wait_stream(main)
@@ -778,11 +819,17 @@ def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=Non
                 sorted_ev.record(st)
             else:
                 st.wait_event(sorted_ev)
+        if share and not fine[v]:
+            for e in binned:
+                st.wait_event(e)
         with torch.cuda.stream(st):
-            res.append(r.bin_raster(scene, cam, None if outs is None else outs[v], st,
-                                    strategy=strategy,
-                                    order=(order, v) if order is not None and v in order_views
-                                    else None))
+            r.bin(scene, cam, st, (order, v) if order is not None and v in order_views
+                  else None)
+            if fine[v]:
+                binned.append(torch.cuda.Event())
+                binned[-1].record(st)
+            res[v] = r.raster(cam, None if outs is None else outs[v], st, strategy=strategy,
+                              max_ctas_per_sm=SHARE_CTAS_PER_SM if fine[v] else 0)
     if streams is not None:
         for st in streams:
             if st is not main:

@@ -11,7 +11,7 @@ from __future__ import annotations
 import torch
 
 from . import (MODES, STRATEGIES, MsError, MS_OK, MS_MAX_BWD_VIEWS, Renderer, _ptr, bwd_view,
-               camera_struct, ms_bin, ms_bin_counts, ms_grads_t, ms_project, ms_raster_ex,
+               camera_struct, ms_bin, ms_bin_counts, ms_grads_t, ms_project, ms_raster_ex2,
                ms_raster_bwd, ms_raster_bwd_views, ms_raster_bwd_views_workspace_bytes,
                ms_raster_bwd_workspace_bytes, ms_scene_prepare, ms_scene_t)
 from . import inputs
@@ -19,13 +19,16 @@ from . import inputs
 
 class Frame:
     """Buffers for rendering and differentiating one view.  `strategy`
-    picks the forward's raster kernel ("auto", "tile" or "list",
-    ms_raster_ex); the backward reads either one's segment states."""
+    picks the forward's raster kernel ("auto", "tile", "list", "group8/16/32",
+    ms_raster_ex; "tile@K": the tile kernel on at most K CTAs per SM,
+    ms_raster_ex2); the backward reads any one's segment states."""
 
     def __init__(self, n: int, cam: inputs.Camera, dup_capacity: int, device="cuda",
                  strategy="auto"):
         self.cam = cam
-        self.strategy = STRATEGIES.get(strategy, strategy)
+        name, _, ctas = strategy.partition("@") if isinstance(strategy, str) else (strategy, "", "")
+        self.strategy = STRATEGIES.get(name, name)
+        self.max_ctas_per_sm = int(ctas) if ctas else 0
         self.renderer = Renderer(n, cam.tiles_x * cam.tiles_y, dup_capacity, device=device,
                                  with_cover=False, with_mask=False)
         self.image, self.final_t, self.n_contrib = self.renderer.images(cam, device=device)
@@ -61,8 +64,9 @@ class GaussianRender(torch.autograd.Function):
         cs = camera_struct(frame.cam)
         ms_project(sc, cs, MODES.get(mode, mode), r.proj)
         ms_bin(r.proj, n, cs, r.bins, _ptr(r.ws), r.ws_bytes)
-        ms_raster_ex(r.proj, r.bins, cs, _ptr(frame.image), _ptr(frame.final_t),
-                     _ptr(frame.n_contrib), 0, _ptr(r.rws), r.rws_bytes, frame.strategy)
+        ms_raster_ex2(r.proj, r.bins, cs, _ptr(frame.image), _ptr(frame.final_t),
+                      _ptr(frame.n_contrib), 0, _ptr(r.rws), r.rws_bytes, frame.strategy,
+                      frame.max_ctas_per_sm)
         ctx.frame = frame
         ctx.meta = (n, n_levels, sh_degree)
         ctx.save_for_backward(mean, log_scale, quat, opacity, color, level, s_max, s_min,
@@ -115,8 +119,9 @@ class GaussianRenderViews(torch.autograd.Function):
             cs = camera_struct(frame.cam)
             ms_project(sc, cs, MODES.get(mode, mode), r.proj)
             ms_bin(r.proj, n, cs, r.bins, _ptr(r.ws), r.ws_bytes)
-            ms_raster_ex(r.proj, r.bins, cs, _ptr(frame.image), _ptr(frame.final_t),
-                         _ptr(frame.n_contrib), 0, _ptr(r.rws), r.rws_bytes, frame.strategy)
+            ms_raster_ex2(r.proj, r.bins, cs, _ptr(frame.image), _ptr(frame.final_t),
+                          _ptr(frame.n_contrib), 0, _ptr(r.rws), r.rws_bytes, frame.strategy,
+                          frame.max_ctas_per_sm)
             outs.append(frame.image.clone())
         ctx.frames = frames
         ctx.meta = (n, n_levels, sh_degree)

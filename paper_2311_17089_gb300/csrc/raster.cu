@@ -656,12 +656,13 @@ extern "C" size_t ms_raster_workspace_bytes(int64_t tiles, int64_t dup_capacity)
     return L.total;
 }
 
-extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
-                            const ms_camera_t *cam, float *image, float *final_t,
-                            uint32_t *n_contrib, uint32_t *n_eval, void *ws, size_t ws_bytes,
-                            int strategy, void *stream) {
+extern "C" int ms_raster_ex2(const ms_proj_t *proj, const ms_bins_t *bins,
+                             const ms_camera_t *cam, float *image, float *final_t,
+                             uint32_t *n_contrib, uint32_t *n_eval, void *ws, size_t ws_bytes,
+                             int strategy, int32_t max_ctas_per_sm, void *stream) {
     if (strategy < MS_RASTER_AUTO || strategy > MS_RASTER_GROUP32)
         return fail(MS_ERR_INVALID_ARG, "unknown raster strategy");
+    if (max_ctas_per_sm < 0) return fail(MS_ERR_INVALID_ARG, "max_ctas_per_sm must be >= 0");
     if (!proj || !bins || !cam || !image) return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
         return fail(MS_ERR_INVALID_ARG, "image size must be 1..32768");
@@ -682,8 +683,11 @@ extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
     int rc;
     if ((rc = ensure_smem_attr(reinterpret_cast<const void *>(raster_kernel), kSmemBytes)))
         return rc;
-    const int resident = (int)std::min<int64_t>((int64_t)raster_blocks_per_sm() * num_sms(),
-                                                kMaxResident);
+    // the tile kernel's persistent CTAs: as many as fit, or at most
+    // max_ctas_per_sm per SM so that other frames' kernels find room beside it
+    const int per_sm = max_ctas_per_sm > 0 ? std::min(raster_blocks_per_sm(), (int)max_ctas_per_sm)
+                                           : raster_blocks_per_sm();
+    const int resident = (int)std::min<int64_t>((int64_t)per_sm * num_sms(), kMaxResident);
     // a frame with fewer tiles than SMs would leave SMs without a tile: the
     // tile kernel then splits every list into many segments, most of them
     // blended speculatively, and the list-parallel kernel is faster (it
@@ -759,6 +763,14 @@ extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
     }
     raster_kernel<<<resident, kRasterThreads, kSmemBytes, st>>>(a);
     return cuda_check(cudaGetLastError(), "raster launches");
+}
+
+extern "C" int ms_raster_ex(const ms_proj_t *proj, const ms_bins_t *bins,
+                            const ms_camera_t *cam, float *image, float *final_t,
+                            uint32_t *n_contrib, uint32_t *n_eval, void *ws, size_t ws_bytes,
+                            int strategy, void *stream) {
+    return ms_raster_ex2(proj, bins, cam, image, final_t, n_contrib, n_eval, ws, ws_bytes,
+                         strategy, 0, stream);
 }
 
 extern "C" int ms_raster(const ms_proj_t *proj, const ms_bins_t *bins, const ms_camera_t *cam,

@@ -24,17 +24,21 @@ def calibrated(scene, cams):
 
 
 def gpu_frame(scene, cam, mode="selective", cap=None, ds=None, strategy="auto"):
-    """Run ms_project -> ms_bin -> ms_raster_ex(strategy); return host copies."""
+    """Run ms_project -> ms_bin -> ms_raster_ex2(strategy); return host
+    copies.  A strategy "tile@K" is the tile kernel on at most K CTAs per SM."""
     torch = require_cuda()
     ds = ds or msgs.DeviceScene(scene)
     cap = cap or max(4096, 16 * scene.n)
+    strategy, _, ctas = strategy.partition("@")
+    ctas = int(ctas) if ctas else 0
     r = msgs.Renderer(scene.n, cam.tiles_x * cam.tiles_y, cap)
     ne = torch.empty((cam.height, cam.width), dtype=torch.int32, device=ds.mean.device)
-    img, ft, nc = r.render(ds, cam, mode, strategy=strategy, n_eval=ne)
+    img, ft, nc = r.render(ds, cam, mode, strategy=strategy, n_eval=ne, max_ctas_per_sm=ctas)
     rc, d, surv = msgs.ms_bin_counts(r.bins)
     if rc == msgs.MS_ERR_CAPACITY:
         r = msgs.Renderer(scene.n, cam.tiles_x * cam.tiles_y, max(d, 1))
-        img, ft, nc = r.render(ds, cam, mode, strategy=strategy, n_eval=ne)
+        img, ft, nc = r.render(ds, cam, mode, strategy=strategy, n_eval=ne,
+                               max_ctas_per_sm=ctas)
         rc, d, surv = msgs.ms_bin_counts(r.bins)
     assert rc == msgs.MS_OK, rc
     torch.cuda.synchronize()

@@ -52,7 +52,7 @@ def compare(gg, go, rel=1e-3, floor=1e-4):
         GRAD_LOG.append((case, k, int(a.size), int((err > rel * np.abs(b)).sum())))
 
 
-@pytest.mark.parametrize("strategy", ["tile", "list", "group8", "group16", "group32"])
+@pytest.mark.parametrize("strategy", ["tile", "tile@1", "list", "group8", "group16", "group32"])
 @pytest.mark.parametrize("seed,deg,n,size", [(0, -1, 64, 64), (1, 3, 64, 64), (2, 1, 400, 96),
                                               (3, 3, 3000, 160)])
 def test_backward_matches_oracle_gradient(seed, deg, n, size, strategy):
@@ -68,7 +68,8 @@ def test_backward_matches_oracle_gradient(seed, deg, n, size, strategy):
     compare(gg, go)
 
 
-@pytest.mark.parametrize("strategy", ["tile", "list", "group8", "group16", "group32"])
+@pytest.mark.parametrize("strategy", ["tile", "tile@1", "tile@2", "list", "group8", "group16",
+                                      "group32"])
 def test_backward_long_lists_many_segments(strategy):
     """Thousands of faint, wide Gaussians on a 48x32 frame (6 tiles): every
     tile's list spans several segments, so the backward starts most

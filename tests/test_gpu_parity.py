@@ -36,7 +36,9 @@ def test_scene_prepare_matches_oracle(cuda):
     np.testing.assert_array_equal(ds.lnop.cpu().numpy(), lnop)
 
 
-STRATEGIES = ["tile", "list", "group8", "group16", "group32"]
+# "tile@K": the tile kernel on at most K CTAs per SM (ms_raster_ex2), which
+# also changes the frame's segmentation
+STRATEGIES = ["tile", "tile@1", "tile@2", "list", "group8", "group16", "group32"]
 
 
 @pytest.mark.parametrize("strategy", STRATEGIES)

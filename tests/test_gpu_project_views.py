@@ -230,6 +230,37 @@ def test_render_views_equals_frames_rendered_alone(cuda, ms_scene_50k):
             assert a.equal(b), v
 
 
+@pytest.mark.parametrize("split", [False, True])
+def test_render_views_sharing_the_sms_equals_frames_rendered_alone(cuda, ms_scene_50k, split):
+    """render_views with share_sms: the frames the tile kernel blends run on
+    SHARE_CTAS_PER_SM CTAs per SM and the others start once those have
+    binned; every frame equals the frame rendered alone with the same
+    kernel and CTA count, bit for bit (also from a shared, split depth
+    order)."""
+    torch = cuda
+    sc = ms_scene_50k
+    cams = shared_centre_cams()
+    ds = msgs.DeviceScene(sc)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    alone = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, 16 * sc.n) for c in cams]
+    want = [r.render(ds, c, "selective",
+                     max_ctas_per_sm=msgs.SHARE_CTAS_PER_SM if c.tiles_x * c.tiles_y >= sms else 0)
+            for r, c in zip(alone, cams)]
+    joint = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, 16 * sc.n, with_cover=False)
+             for c in cams]
+    streams = [torch.cuda.Stream() for _ in cams]
+    order = msgs.DepthOrder(sc.n, split_views=len(cams)) if split else None
+    got = msgs.render_views(ds, joint, cams, "selective", streams=streams, order=order,
+                            share_sms=True)
+    torch.cuda.synchronize()
+    assert sum(c.tiles_x * c.tiles_y >= sms for c in cams) >= 2
+    for r in alone + joint:
+        r.check()
+    for v, (w, g) in enumerate(zip(want, got)):
+        for a, b in zip(w, g):
+            assert a.equal(b), v
+
+
 @pytest.mark.parametrize("mode", ["all_levels", "selective"])
 def test_histogram_flush_on_a_30M_scene(cuda, mode):
     """30M Gaussians: with two views (456 CTAs of 256 threads) every CTA
