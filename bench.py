@@ -935,6 +935,9 @@ def main():
     # 2.484 vs 2.447 ms)
     sms_dev = torch.cuda.get_device_properties(dev).multi_processor_count
     fine = [c.tiles_x * c.tiles_y >= sms_dev for c in cams]
+    tiles_max = max(c.tiles_x * c.tiles_y for c, f in zip(cams, fine) if f) if any(fine) else 1
+    share_ctas = [msgs.share_ctas_per_sm(c.tiles_x * c.tiles_y, tiles_max) if f else 0
+                  for c, f in zip(cams, fine)]
     share_plan = {"selective": True, "all_levels": False}
     # one renderer (projection, tile lists, workspaces) per frame and mode,
     # sized by that frame's duplicate count, and one stream per frame: the
@@ -960,7 +963,7 @@ def main():
         # frame's binning and blend on its own stream; otherwise each frame
         # projects and sorts on its own stream.  In selective mode the frames
         # the tile kernel blends share the SMs: their blends run on
-        # SHARE_CTAS_PER_SM CTAs per SM and the coarse frames start once
+        # share_ctas_per_sm() CTAs per SM and the coarse frames start once
         # they have binned (as render_views with share_sms)
         main = torch.cuda.current_stream()
         d = scene or ds
@@ -990,8 +993,7 @@ def main():
                     if share and fine[k]:
                         binned.append(torch.cuda.Event())
                         binned[-1].record(st)
-                    r.raster(cam, out, st, max_ctas_per_sm=(msgs.SHARE_CTAS_PER_SM
-                                                            if share and fine[k] else 0))
+                    r.raster(cam, out, st, max_ctas_per_sm=share_ctas[k] if share else 0)
                 else:
                     r.render(d, cam, mode, out=out, stream=st)
                 if after is not None:
@@ -1396,7 +1398,7 @@ def main():
                 share_sms={m: {"chosen": bool(share_plan[m]),
                                "fine_frames": [f"{c.width}x{c.height}"
                                                for c, f in zip(cams, fine) if f],
-                               "ctas_per_sm": msgs.SHARE_CTAS_PER_SM, **share_trial[m]}
+                               "ctas_per_sm": [c for c in share_ctas if c], **share_trial[m]}
                            for m in share_plan}),
             "clocks": clk, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "roofline": roof,

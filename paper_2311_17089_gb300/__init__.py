@@ -758,9 +758,17 @@ def shared_order_views(survivors, frac: float = 0.8):
     return [v for v, s in enumerate(survivors) if top > 0 and s >= frac * top]
 
 
-# CTAs per SM of the tile kernel when frames share the GPU (render_views
-# with share_sms): the blends of the fine frames leave room for the others
-SHARE_CTAS_PER_SM = 2
+def share_ctas_per_sm(tiles: int, tiles_max: int) -> int:
+    """CTAs per SM of the tile kernel for a frame of `tiles` tiles blended
+    beside others (render_views with share_sms), the finest of them having
+    tiles_max: 3 for the finest, one fewer for every 4x fewer tiles, at
+    least 1, so that the blends leave the SMs room for the other frames'
+    kernels in proportion to their work (on the 1M sweep the 1x, 2x and 4x
+    frames at 3, 2, 1: 1.000-1.008 ms; at 2, 2, 2: 1.040-1.052 ms; at
+    2, 2, 1: 1.009-1.020 ms; every CTA: 1.082-1.088 ms)."""
+    import math
+    steps = round(math.log(max(tiles_max, 1) / max(tiles, 1), 4)) if tiles > 0 else 3
+    return max(1, 3 - steps)
 
 
 def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=None,
@@ -774,9 +782,9 @@ def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=Non
     cameras) the frames in order_views (default all; cameras of one pose)
     bin from one shared depth sort, the others sort their own lists.
     With share_sms (and streams), the frames the tile kernel blends (at
-    least as many tiles as SMs) blend on SHARE_CTAS_PER_SM CTAs per SM, and
-    the other frames start once those have binned, so that their binning and
-    blending fill the SM room the fine frames' blends leave.
+    least as many tiles as SMs) blend on share_ctas_per_sm() CTAs per SM,
+    and the other frames start once those have binned, so that their
+    binning and blending fill the SM room the fine frames' blends leave.
     Returns the (image, final_t, n_contrib) of every frame."""
     import torch
     n = len(cams)
@@ -803,6 +811,7 @@ def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=Non
     share = share_sms and streams is not None and strategy == "auto"
     sms = torch.cuda.get_device_properties(main.device).multi_processor_count if share else 0
     fine = [share and c.tiles_x * c.tiles_y >= sms for c in cams]
+    tiles_max = max([c.tiles_x * c.tiles_y for c, f in zip(cams, fine) if f] or [1])
     binned = []   # events: the fine frames' binning done
     res = [None] * n
     for v in sorted(range(n), key=lambda k: not fine[k]):   # fine frames first
@@ -829,7 +838,9 @@ def render_views(scene: DeviceScene, renderers, cams, mode="selective", outs=Non
                 binned.append(torch.cuda.Event())
                 binned[-1].record(st)
             res[v] = r.raster(cam, None if outs is None else outs[v], st, strategy=strategy,
-                              max_ctas_per_sm=SHARE_CTAS_PER_SM if fine[v] else 0)
+                              max_ctas_per_sm=(share_ctas_per_sm(cam.tiles_x * cam.tiles_y,
+                                                                 tiles_max)
+                                               if fine[v] else 0))
     if streams is not None:
         for st in streams:
             if st is not main:

@@ -233,7 +233,7 @@ def test_render_views_equals_frames_rendered_alone(cuda, ms_scene_50k):
 @pytest.mark.parametrize("split", [False, True])
 def test_render_views_sharing_the_sms_equals_frames_rendered_alone(cuda, ms_scene_50k, split):
     """render_views with share_sms: the frames the tile kernel blends run on
-    SHARE_CTAS_PER_SM CTAs per SM and the others start once those have
+    share_ctas_per_sm() CTAs per SM and the others start once those have
     binned; every frame equals the frame rendered alone with the same
     kernel and CTA count, bit for bit (also from a shared, split depth
     order)."""
@@ -243,8 +243,10 @@ def test_render_views_sharing_the_sms_equals_frames_rendered_alone(cuda, ms_scen
     ds = msgs.DeviceScene(sc)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     alone = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, 16 * sc.n) for c in cams]
+    tmax = max(c.tiles_x * c.tiles_y for c in cams)
     want = [r.render(ds, c, "selective",
-                     max_ctas_per_sm=msgs.SHARE_CTAS_PER_SM if c.tiles_x * c.tiles_y >= sms else 0)
+                     max_ctas_per_sm=(msgs.share_ctas_per_sm(c.tiles_x * c.tiles_y, tmax)
+                                      if c.tiles_x * c.tiles_y >= sms else 0))
             for r, c in zip(alone, cams)]
     joint = [msgs.Renderer(sc.n, c.tiles_x * c.tiles_y, 16 * sc.n, with_cover=False)
              for c in cams]
