@@ -51,8 +51,8 @@ PAPER_LEVEL_MIX = (0.95, 0.035, 0.01, 0.005)   # coarse levels under 5% of the G
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures,
 # each with the SHA-256 (first 16 hex digits) of the kernel sources it was
 # taken on: a figure whose sources changed since is reported as stale (null)
-RASTER_DRAM = {"bytes": 21.56e6, "sources": ("raster.cu", "raster_list.cu", "raster_ws.cuh"),
-               "sha16": "9ce07e9f2be9af79"}   # mean over the sweep's 8 raster launches
+RASTER_DRAM = {"bytes": 23.37e6, "sources": ("raster.cu", "raster_list.cu", "raster_ws.cuh"),
+               "sha16": "9ce07e9f2be9af79"}   # mean over the 8 frames' raster launches, each frame alone
 PROJECT_VIEWS_DRAM = {"bytes": 505.1e6, "sources": ("project.cu", "footprint.cuh"),
                       "sha16": "1e94d3f932b66c6a"}   # the selective sweep's projection launch
 
@@ -93,7 +93,8 @@ def parse():
                     help="run the serving leg alone and print its JSON (the full bench runs "
                          "it this way, in a fresh process)")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
-    ap.add_argument("--profile", default=None, choices=["selective", "all_levels", "train"],
+    ap.add_argument("--profile", default=None,
+                    choices=["selective", "all_levels", "train", "selective_frames"],
                     help="for profilers: two warm-up sweeps (training steps), then one "
                          "of this mode inside the NVTX range 'sweep'; prints no JSON")
     return ap.parse_args()
@@ -1027,15 +1028,24 @@ def main():
             main.wait_stream(st)
 
     if args.profile:
+        # selective_frames: each selective frame projected, binned and
+        # blended alone with every CTA (the per-frame stage timings the
+        # raster roofline divides by); otherwise one sweep as timed
+        frames_alone = args.profile == "selective_frames"
+        prof_mode = "selective" if frames_alone else args.profile
         for it in range(3):
             torch.cuda.synchronize()
             if it == 2:
                 torch.cuda.nvtx.range_push("sweep")
-            step(args.profile)
+            if frames_alone:
+                for r, cam, out in zip(rs_mode[prof_mode], cams, bufs):
+                    r.render(ds, cam, prof_mode, out=out)
+            else:
+                step(prof_mode)
             torch.cuda.synchronize()
             if it == 2:
                 torch.cuda.nvtx.range_pop()
-        for r in rs_mode[args.profile]:
+        for r in rs_mode[prof_mode]:
             r.check()
         return
     neval = [torch.empty((c.height, c.width), dtype=torch.int32, device=dev) for c in cams]
@@ -1278,12 +1288,14 @@ def main():
         roof = dict(roof_project)
         roof["note"] = "binning dominates; project roofline shown"
     # DRAM bytes per launch of the dominant stage: dram__bytes_read.sum +
-    # dram__bytes_write.sum of one ncu capture of this sweep's eight raster
-    # launches (both kernels), averaged (to be taken again whenever a raster
-    # kernel changes)
+    # dram__bytes_write.sum of one ncu capture of the eight frames' raster
+    # launches (both kernels), each frame rendered alone with every CTA as
+    # in the per-frame stage timings, averaged (to be taken again whenever a
+    # raster kernel changes)
     traffic = captured_traffic(RASTER_DRAM) if roof is roof_raster else roof.get("traffic")
     roof = dict(roof, traffic=traffic, stage_ms_per_step=stage_ms,
-                traffic_source=("ncu capture, mean over the sweep's raster launches"
+                traffic_source=("ncu capture, mean over the eight frames' raster launches, "
+                                "each frame alone (bench.py --profile selective_frames)"
                                 if roof is roof_raster else
                                 "ncu capture of the sweep's projection launch")
                 if traffic else None)
