@@ -523,7 +523,8 @@ static int launch_pass(const PassArgs &a, uint64_t bound, cudaStream_t st) {
                               SortCfg<IPT>::kSmem);
     if (rc) return rc;
     const int64_t parts = (int64_t)((bound + SortCfg<IPT>::kPart - 1) / SortCfg<IPT>::kPart);
-    const int per_sm = bound <= kSmallPassItems ? kSmallPassCtasPerSm : kLargePassCtasPerSm;
+    const int per_sm = a.ctas_per_sm > 0 ? a.ctas_per_sm
+                       : bound <= kSmallPassItems ? kSmallPassCtasPerSm : kLargePassCtasPerSm;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(parts, (int64_t)num_sms() * per_sm));
     onesweep_pass<IPT><<<grid, kSortThreads, SortCfg<IPT>::kSmem, st>>>(a);
     return MS_OK;
@@ -751,7 +752,7 @@ namespace {
 // order's indices end in vals_final.
 int depth_passes(const ms_proj_t *proj, int64_t n, const BinLayout &L, char *w,
                  uint32_t *vals_final, unsigned long long *err, uint32_t spin_limit,
-                 cudaStream_t st) {
+                 cudaStream_t st, int ctas_per_sm = 0) {
     auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(w + off); };
     uint32_t *tickets = U32(L.tickets);
     const uint32_t *survivors = proj->stats + kStatSurvivors;
@@ -774,6 +775,7 @@ int depth_passes(const ms_proj_t *proj, int64_t n, const BinLayout &L, char *w,
         a.ticket = tickets + pass;
         a.err = err;
         a.spin_limit = spin_limit;
+        a.ctas_per_sm = ctas_per_sm;
         if ((rc = launch_onesweep(a, (uint64_t)n, st))) return rc;
     }
     return MS_OK;
@@ -937,7 +939,11 @@ extern "C" int ms_sort_depth(const ms_proj_t *proj, int64_t n, uint32_t *order, 
     // a wait that gives up is recorded in the sorted projection's status
     // word (stats words 4-5), where ms_bin_ordered picks it up
     unsigned long long *err = reinterpret_cast<unsigned long long *>(proj->stats + kStatStatus);
-    if ((rc = depth_passes(proj, n, L, w, order, err, bin_spin_limit(), st))) return rc;
+    // the shared sort runs ahead of every frame that takes its order: its
+    // passes take every CTA the SMs hold (a frame's own sort leaves room for
+    // the frames sorting beside it)
+    if ((rc = depth_passes(proj, n, L, w, order, err, bin_spin_limit(), st, kLargePassCtasPerSm)))
+        return rc;
     return cuda_check(cudaGetLastError(), "ms_sort_depth launches");
 }
 
@@ -987,7 +993,7 @@ extern "C" int ms_split_order(const ms_proj_t *union_proj, int64_t n, const uint
     a.err = reinterpret_cast<unsigned long long *>(union_proj->stats + kStatStatus);
     a.spin_limit = bin_spin_limit();
     const int64_t parts = ceil_div(n > 0 ? n : 1, (int64_t)kSplitPart);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(parts, (int64_t)num_sms() * 2));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(parts, (int64_t)num_sms() * 4));
     split_kernel<<<grid, kSplitThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "split_kernel launch");
 }

@@ -60,6 +60,7 @@ struct PassArgs {
     uint32_t *ticket;
     unsigned long long *err;    // status word (bit kStatusTimeout)
     uint32_t spin_limit = kSpinLimit;  // look-back polls before a wait gives up
+    int ctas_per_sm = 0;               // 0: by the pass's size (below); else this many
 };
 
 // One pass: items [0, count) (count from n32 / n64 / n_cap; only items with
