@@ -51,8 +51,8 @@ PAPER_LEVEL_MIX = (0.95, 0.035, 0.01, 0.005)   # coarse levels under 5% of the G
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures,
 # each with the SHA-256 (first 16 hex digits) of the kernel sources it was
 # taken on: a figure whose sources changed since is reported as stale (null)
-RASTER_DRAM = {"bytes": 23.37e6, "sources": ("raster.cu", "raster_list.cu", "raster_ws.cuh"),
-               "sha16": "9ce07e9f2be9af79"}   # mean over the 8 frames' raster launches, each frame alone
+RASTER_DRAM = {"bytes": 33.95e6, "sources": ("raster.cu", "raster_list.cu", "raster_ws.cuh"),
+               "sha16": "3f2f568be902bbd9"}   # mean over the 8 frames' raster stages, each frame alone
 PROJECT_VIEWS_DRAM = {"bytes": 505.1e6, "sources": ("project.cu", "footprint.cuh"),
                       "sha16": "1e94d3f932b66c6a"}   # the selective sweep's projection launch
 
@@ -1243,7 +1243,8 @@ def main():
     # DRAM bytes of one ncu capture of the sweep's projection launch (null
     # once the projection kernel has changed since the capture)
     roof_project["traffic"] = captured_traffic(PROJECT_VIEWS_DRAM)
-    roof_raster = {"bound": "alu", "kernel": "raster_kernel (tile) + raster_list_kernel",
+    roof_raster = {"bound": "alu", "kernel": "raster_kernel (tile) + raster_list_kernel "
+                                              "(with its row_mask_kernel pass)",
                    "achieved": OPS_PER_EVAL * evals / raster_s / 1e12, "peak": alu_peak,
                    "unit": "Tops/s",
                    "peak_source": "measured: the faster of the scalar FFMA and packed FFMA2 "
@@ -1254,12 +1255,16 @@ def main():
     roof_raster["co_bound"] = {"bound": "mufu", "achieved": evals / raster_s / 1e12,
                                "peak": mufu_peak, "unit": "T ex2/s",
                                "frac": evals / raster_s / 1e12 / mufu_peak}
-    # the same split by kernel: ms_raster blends frames with at least as many
-    # tiles as SMs with the tile kernel, the others with the list kernel
+    # the same split by kernel, by ms_raster's own rule (MS_RASTER_AUTO, no
+    # cap: the frames are timed alone): the list kernel (with its mask pass)
+    # for frames with fewer tiles than SMs, and up to 4x as many when the
+    # mean list length is 1024-8192; the tile kernel otherwise
     by_kernel = {}
     for cam in cams:
         nt = cam.tiles_x * cam.tiles_y
-        name = "raster_kernel" if nt >= sms else "raster_list_kernel"
+        d_ = stats[("selective", cam.width)]["D"]
+        list_k = nt < sms or (nt < 4 * sms and 1024 * nt <= d_ <= 8192 * nt)
+        name = "raster_list_kernel" if list_k else "raster_kernel"
         e = by_kernel.setdefault(name, {"frames": [], "P_eval": 0, "ms": 0.0})
         e["frames"].append(f"{cam.width}x{cam.height}")
         e["P_eval"] += stats[("selective", cam.width)]["P_eval"]
@@ -1287,15 +1292,16 @@ def main():
     if dominant == "bin":
         roof = dict(roof_project)
         roof["note"] = "binning dominates; project roofline shown"
-    # DRAM bytes per launch of the dominant stage: dram__bytes_read.sum +
+    # DRAM bytes per frame of the dominant stage: dram__bytes_read.sum +
     # dram__bytes_write.sum of one ncu capture of the eight frames' raster
-    # launches (both kernels), each frame rendered alone with every CTA as
-    # in the per-frame stage timings, averaged (to be taken again whenever a
-    # raster kernel changes)
+    # launches (the tile kernel, or the list kernel's mask pass and blend),
+    # each frame rendered alone with every CTA as in the per-frame stage
+    # timings, averaged (to be taken again whenever a raster kernel changes)
     traffic = captured_traffic(RASTER_DRAM) if roof is roof_raster else roof.get("traffic")
     roof = dict(roof, traffic=traffic, stage_ms_per_step=stage_ms,
-                traffic_source=("ncu capture, mean over the eight frames' raster launches, "
-                                "each frame alone (bench.py --profile selective_frames)"
+                traffic_source=("ncu capture, mean over the eight frames' raster stages "
+                                "(tile kernel, or mask pass + list kernel), each frame alone "
+                                "(bench.py --profile selective_frames)"
                                 if roof is roof_raster else
                                 "ncu capture of the sweep's projection launch")
                 if traffic else None)

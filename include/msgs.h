@@ -71,13 +71,18 @@ typedef enum {
 /* How ms_raster_ex spreads a frame's blend over the GPU (the result is the
  * same blend either way, up to FP32 rounding). */
 typedef enum {
-    MS_RASTER_AUTO = 0,  /* TILE when the frame has at least as many tiles as
-                            the GPU has SMs, else LIST                       */
+    MS_RASTER_AUTO = 0,  /* LIST when the frame has fewer tiles than the GPU
+                            has SMs; TILE from 4x as many, or when
+                            ms_raster_ex2 caps the tile kernel's CTAs; in
+                            between the frame's mean list length decides on
+                            the device (LIST for 1024-8192 entries per
+                            tile)                                           */
     MS_RASTER_TILE = 1,  /* one thread per pixel; long lists split into
                             segments merged exactly across CTAs             */
-    MS_RASTER_LIST = 2,  /* one warp per pixel; lanes take consecutive list
-                            entries, a product scan of (1 - alpha) decides
-                            termination                                     */
+    MS_RASTER_LIST = 2,  /* one warp per pixel; only the list entries whose
+                            level-set box reaches the pixel's half row are
+                            blended, lanes take consecutive ones, a product
+                            scan of (1 - alpha) decides termination        */
     MS_RASTER_GROUP8 = 3,  /* G = 8, 16 or 32 lanes per pixel, 4 consecutive */
     MS_RASTER_GROUP16 = 4, /* list entries per lane, one product scan over   */
     MS_RASTER_GROUP32 = 5  /* the group's lanes per 4 G entries              */

@@ -62,8 +62,9 @@ constexpr uint64_t kStatusBounds = 4;  // a debug build's index check failed
 // Raster record: three float4 per Gaussian.
 //   r0 = (ux, uy, A, B)      A = -log2(e)/2 conic a, B = -log2(e) conic b
 //   r1 = (C, opacity, r, g)  C = -log2(e)/2 conic c
-//   r2 = (b, thr, 0, 0)     thr = -log2(e) ln(255 opacity): alpha >= 1/255
-//                            exactly when power * log2(e) >= thr
+//   r2 = (b, thr, ex, ey)   thr = -log2(e) ln(255 opacity): alpha >= 1/255
+//                            exactly when power * log2(e) >= thr; (ex, ey)
+//                            the half extents of that level set's box
 constexpr int kRecFloats = 12;
 
 // Bounded waits: spin iterations before giving up (each ~100 ns).

@@ -56,6 +56,13 @@ constexpr float kTStop = 1e-4f;
 constexpr uint32_t kWindow = MS_RASTER_WINDOW;
 constexpr uint32_t kAgg = 1u;                // segment flag: local aggregate published
 constexpr uint32_t kPre = 2u;                // segment flag: inclusive prefix published
+// ms_raster (AUTO) launches both blend kernels for frames with at least as
+// many tiles as SMs and fewer than kListBandSms times as many, and the list
+// kernel takes the frame when its mean list length lies in kListMeanMin ..
+// kListMeanMax.
+constexpr int64_t kListBandSms = 4;
+constexpr uint32_t kListMeanMin = 1024;
+constexpr uint32_t kListMeanMax = 8192;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -83,6 +90,7 @@ struct RasterArgs {
     uint2 *agg2;          // [max_segs][256] (n_contrib, n_eval | term bit)
     float4 *pre;          // [max_segs][256] inclusive (C0, C1, C2, T)
     uint2 *pre2;          // [max_segs][256] (n_contrib, n_eval | term bit)
+    const uint32_t *use_list;  // NULL, or nonzero when the list kernel blends this frame instead
     unsigned long long *err;
 };
 
@@ -113,11 +121,16 @@ __device__ __forceinline__ Seg seg_of(const RasterArgs &a, uint32_t c, uint32_t 
 // every tile (at least one, so empty tiles still write the background),
 // exclusive-scanned.  It also zeroes the n_zero16 16-byte words at zero (the
 // tile kernel's ticket, segment flags and tile marks; none for the list
-// kernel), which the raster launch after it reads.
+// kernel), which the raster launch after it reads.  With use_list, it
+// writes there which blend kernel takes the frame: the list kernel when the
+// mean list length D / tiles lies in list_mean_min .. list_mean_max, else
+// the tile kernel.
 __global__ void __launch_bounds__(1024)
 segment_offsets_kernel(const uint32_t *__restrict__ ranges, int tiles, uint32_t resident,
                        uint32_t *__restrict__ off, uint32_t *__restrict__ seg_len,
-                       uint4 *__restrict__ zero, uint32_t n_zero16) {
+                       uint4 *__restrict__ zero, uint32_t n_zero16,
+                       uint32_t *__restrict__ use_list, uint32_t list_mean_min,
+                       uint32_t list_mean_max) {
     __shared__ uint32_t s_warp[32];
     __shared__ unsigned long long s_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -164,6 +177,9 @@ segment_offsets_kernel(const uint32_t *__restrict__ ranges, int tiles, uint32_t 
     if (tid == 1023) {
         off[tiles] = run;
         seg_len[0] = L;
+        if (use_list)
+            use_list[0] = s_total >= (unsigned long long)list_mean_min * (unsigned long long)tiles &&
+                          s_total <= (unsigned long long)list_mean_max * (unsigned long long)tiles;
     }
 }
 
@@ -438,6 +454,7 @@ raster_kernel(RasterArgs a) {
     __shared__ uint32_t s_flag;
     __shared__ uint32_t s_wait;
     __shared__ uint32_t s_abort[2];
+    if (a.use_list && *a.use_list) return;  // the list kernel blends this frame
     float4 *aos = reinterpret_cast<float4 *>(smem);
     WarpPairs &wp = reinterpret_cast<WarpPairs *>(smem + 2 * kBufBytes)[threadIdx.x >> 5];
     const int tid = threadIdx.x;
@@ -688,11 +705,21 @@ extern "C" int ms_raster_ex2(const ms_proj_t *proj, const ms_bins_t *bins,
     const int per_sm = max_ctas_per_sm > 0 ? std::min(raster_blocks_per_sm(), (int)max_ctas_per_sm)
                                            : raster_blocks_per_sm();
     const int resident = (int)std::min<int64_t>((int64_t)per_sm * num_sms(), kMaxResident);
-    // a frame with fewer tiles than SMs would leave SMs without a tile: the
+    // A frame with fewer tiles than SMs would leave SMs without a tile: the
     // tile kernel then splits every list into many segments, most of them
-    // blended speculatively, and the list-parallel kernel is faster (it
-    // costs about twice the instructions per evaluation, but none is
-    // speculative; measured crossover between 70 and 260 tiles on GB300).
+    // blended speculatively, and the list kernel is faster.  Up to
+    // kListBandSms x SMs tiles (and no cap on the tile kernel's CTAs), the
+    // frame's mean list length decides on the device (both kernels are
+    // launched, the one not chosen returns at once): lists of
+    // kListMeanMin .. kListMeanMax entries per tile (selective frames, whose
+    // pixels walk deep into them) go to the list kernel; short ones, which
+    // the tile kernel walks quickly, and long ones (all levels, whose
+    // pixels end early in lists whose first kMaskPrefix entries the list
+    // kernel's mask pass covers whole) to the tile kernel.  Measured on
+    // GB300, 314x208 frames of the 1M-Gaussian scene: selective (3.5k
+    // entries per tile) list 120 against tile 184 us; all levels (19k per
+    // tile) tile 60 us against list 173; the 256x256 single-level frame (70
+    // per tile) is faster on the tile kernel.
     // The group kernels are chosen only explicitly: the 8-lane one blends a
     // 314x208 frame alone faster than the tile kernel (176 against 200 us on
     // GB300) but costs more SM time, and the concurrent 8-frame sweep was
@@ -702,8 +729,12 @@ extern "C" int ms_raster_ex2(const ms_proj_t *proj, const ms_bins_t *bins,
                       : strategy == MS_RASTER_GROUP16 ? 16
                       : strategy == MS_RASTER_GROUP32 ? 32
                                                       : 0;
-    const bool list = group > 0 || strategy == MS_RASTER_LIST ||
-                      (strategy == MS_RASTER_AUTO && tiles < sms);
+    const bool auto_list = strategy == MS_RASTER_AUTO && tiles < sms;
+    // a cap on the tile kernel's CTAs (frames blended side by side) keeps
+    // the tile kernel: the list kernel cannot leave SMs to other frames
+    const bool band = strategy == MS_RASTER_AUTO && !auto_list && max_ctas_per_sm == 0 &&
+                      tiles < kListBandSms * sms;
+    const bool list = group > 0 || strategy == MS_RASTER_LIST || auto_list;
     RasterArgs a;
     a.ranges = bins->ranges;
     a.gidx = bins->gauss_idx;
@@ -729,14 +760,17 @@ extern "C" int ms_raster_ex2(const ms_proj_t *proj, const ms_bins_t *bins,
     a.agg2 = reinterpret_cast<uint2 *>(w + L.agg2);
     a.pre = reinterpret_cast<float4 *>(w + L.pre);
     a.pre2 = reinterpret_cast<uint2 *>(w + L.pre2);
+    uint32_t *use_list = band ? reinterpret_cast<uint32_t *>(w + L.use_list) : nullptr;
+    a.use_list = use_list;
     a.err = reinterpret_cast<unsigned long long *>(bins->counts) + kCntStatus;
     // the segmentation is the same for both kernels: the backward walks it
     // the tile kernel's ticket, flags and tile marks are zeroed by the first
     // kernel (the workspace and zero_bytes are 256-byte aligned)
     segment_offsets_kernel<<<1, 1024, 0, st>>>(bins->ranges, (int)tiles, (uint32_t)resident,
                                                a.seg_off, a.seg_len, reinterpret_cast<uint4 *>(w),
-                                               list ? 0u : (uint32_t)(L.zero_bytes / 16));
-    if (list) {
+                                               list ? 0u : (uint32_t)(L.zero_bytes / 16),
+                                               use_list, kListMeanMin, kListMeanMax);
+    if (list || band) {
         ListArgs la;
         la.ranges = a.ranges;
         la.gidx = a.gidx;
@@ -756,10 +790,14 @@ extern "C" int ms_raster_ex2(const ms_proj_t *proj, const ms_bins_t *bins,
         la.seg_off = a.seg_off;
         la.seg_len = a.seg_len;
         la.pre = a.pre;
+        la.rowmask = reinterpret_cast<uint32_t *>(w + L.rowmask);
+        la.use_list = use_list;
+        la.max_segs = (uint32_t)L.max_segs;
         la.err = a.err;
         if ((rc = cuda_check(cudaGetLastError(), "segment offsets launch"))) return rc;
         if (group > 0) return cuda_check(launch_raster_group(la, group, st), "raster group launch");
-        return cuda_check(launch_raster_list(la, st), "raster list launch");
+        if ((rc = cuda_check(launch_raster_list(la, st), "raster list launch"))) return rc;
+        if (!band) return MS_OK;
     }
     raster_kernel<<<resident, kRasterThreads, kSmemBytes, st>>>(a);
     return cuda_check(cudaGetLastError(), "raster launches");

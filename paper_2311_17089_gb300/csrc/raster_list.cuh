@@ -21,6 +21,9 @@ struct ListArgs {
     const uint32_t *seg_off;  // [tiles + 1] the frame's segmentation (segment_offsets_kernel)
     const uint32_t *seg_len;  // [1] entries per segment
     float4 *pre;              // [max_segs][256] state after each segment, for the backward
+    uint32_t *rowmask;        // [dup_capacity] half rows each list entry reaches (workspace)
+    const uint32_t *use_list; // NULL, or 0 when the tile kernel blends this frame instead
+    uint32_t max_segs;        // upper bound of the frame's segment count
     unsigned long long *err;  // status word (the binning's), for debug-build checks
 };
 
@@ -29,8 +32,9 @@ struct ListArgs {
 constexpr int kListPixelsPerCta = 8;
 constexpr int kListCtasPerTile = 256 / kListPixelsPerCta;
 
-// Enqueue the list-parallel blend of every tile on `st` (no waits, no
-// workspace zeroing needed).
+// Enqueue the list-parallel blend of every tile on `st`: the half-row masks
+// of every list entry, then the blend (no waits, no workspace zeroing
+// needed).
 cudaError_t launch_raster_list(const ListArgs &a, cudaStream_t st);
 
 // Enqueue the group blend (raster_group.cu): each pixel's list walked by a

@@ -25,12 +25,16 @@ constexpr uint32_t kTermBit = 0x80000000u;   // pixel terminated (in the n_eval 
 constexpr int64_t kMaxResident = 4096;
 
 // Byte offsets inside the workspace.  ticket, flags and tile_done are zeroed
-// by every ms_raster call (zero_bytes); seg_len and seg_off are written by
-// its first kernel; agg/agg2 hold segment-local aggregates and pre/pre2 the
+// by every ms_raster call (zero_bytes); seg_len, use_list (which of the two
+// blend kernels a frame takes when both are launched) and seg_off are
+// written by its first kernel; agg/agg2 hold segment-local aggregates and pre/pre2 the
 // inclusive prefix state (C0, C1, C2, T) / (n_contrib, n_eval | term) per
-// segment and pixel, for every segment but a tile's last.
+// segment and pixel, for every segment but a tile's last; rowmask holds,
+// for the list kernel, one word per tile-list entry: bit 2 r + h set when
+// the entry's level-set box reaches half h of the tile's pixel row r.
 struct RasterLayout {
-    size_t ticket, seg_len, flags, tile_done, seg_off, agg, agg2, pre, pre2, total, zero_bytes;
+    size_t ticket, seg_len, use_list, flags, tile_done, seg_off, agg, agg2, pre, pre2, rowmask,
+        total, zero_bytes;
     int64_t max_segs;
 };
 
@@ -57,7 +61,8 @@ inline bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {
     o = al256(o + (size_t)tiles * 4);
     L.zero_bytes = o;
     L.seg_len = o;
-    o = al256(o + 4);
+    L.use_list = o + 4;
+    o = al256(o + 8);
     L.seg_off = o;
     o = al256(o + (size_t)(tiles + 1) * 4);
     const size_t per4 = (size_t)L.max_segs * kRasterThreads * 16;
@@ -70,6 +75,8 @@ inline bool raster_layout(int64_t tiles, int64_t cap, RasterLayout &L) {
     o = al256(o + per4);
     L.pre2 = o;
     o = al256(o + per2);
+    L.rowmask = o;
+    o = al256(o + (size_t)cap * 4);
     L.total = o;
     return true;
 }

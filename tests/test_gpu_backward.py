@@ -113,6 +113,22 @@ def test_backward_deep_lists(strategy):
     compare(gg, go)
 
 
+def test_backward_lists_past_the_mask_prefix():
+    """The backward after the list kernel on lists longer than its mask
+    pass's 16384-entry prefix (the forward's prefix states past it come
+    from entries whose masks the blend formed itself)."""
+    from test_gpu_parity import deep_lists_scene
+    sc = deep_lists_scene(seed=36, nb=110_000)
+    cam = inputs.config1_camera(48, 32)
+    w = np.random.default_rng(37).standard_normal((3, 32, 48))
+    gg, _ = gpu_grads(sc, cam, w, strategy="list")
+    fp = oracle.footprints(sc, cam, "all_levels")
+    off, idx = oracle.tile_lists(fp, cam)
+    assert np.diff(off).min() > 16384 + 1024
+    go = oracle.grad64(sc, cam, off, idx, w)
+    compare(gg, go)
+
+
 def test_backward_multiscale_selective():
     sc = inputs.multiscale_scene(n=20_000, seed=2, box=2.0, cluster_sigma=0.5, n_clusters=16)
     cam = inputs.config2_camera(256, 192, distance=6.0)

@@ -37,8 +37,10 @@ def test_scene_prepare_matches_oracle(cuda):
 
 
 # "tile@K": the tile kernel on at most K CTAs per SM (ms_raster_ex2), which
-# also changes the frame's segmentation
-STRATEGIES = ["tile", "tile@1", "tile@2", "list", "group8", "group16", "group32"]
+# also changes the frame's segmentation; "auto" launches both the tile and
+# the list kernel for frames of 1-4x as many tiles as SMs and lets the
+# device pick one
+STRATEGIES = ["auto", "tile", "tile@1", "tile@2", "list", "group8", "group16", "group32"]
 
 
 @pytest.mark.parametrize("strategy", STRATEGIES)
@@ -117,7 +119,9 @@ def test_full_size_multiscale_sampled(cuda):
     sc = calibrated(sc, inputs.orbit_cameras(8, seed=1, radius=25.0))
     rng = np.random.default_rng(0)
     for mode in ("selective", "all_levels"):
-        for s in (1, 16, 128):
+        # 4x: 260 tiles, where the device picks the list kernel for the
+        # selective frame (short lists) and the tile kernel at all levels
+        for s in (1, 4, 16, 128):
             cam = inputs.downscale(inputs.config2_camera(), s)
             g = gpu_frame(sc, cam, mode)
             fp = oracle.footprints(sc, cam, mode)
@@ -282,15 +286,15 @@ def test_long_lists_split_across_ctas(cuda, wh, n, op, strategy):
     assert_image_close(g, o)
 
 
-def deep_lists_scene(seed=31):
-    """A 48x32 frame whose tile lists hold more than 4096 entries: 40k
+def deep_lists_scene(seed=31, nb=40_000):
+    """A 48x32 frame whose tile lists hold more than 4096 entries: nb (40k)
     faint Gaussians about 2 px wide spread over the whole view (each pixel
     sees a few percent of its tile's list, so most pixels never terminate
     and blend entries past 4096), and 400 large, fairly opaque ones in
     front of the left half (those pixels terminate within the first few
     dozen entries)."""
     rng = np.random.default_rng(seed)
-    nf, nb = 400, 40_000
+    nf = 400
     n = nf + nb
     mean = np.empty((n, 3), np.float32)
     mean[:nf] = np.stack([rng.uniform(-0.75, 0.0, nf), rng.uniform(-0.5, 0.5, nf),
@@ -320,6 +324,22 @@ def test_long_lists_early_and_deep_pixels(cuda, strategy):
     early = (o["final_t"] < 1e-3) & (o["n_contrib"] < 2048)
     deep = o["n_contrib"] > 4096 + 512
     assert early.mean() > 0.2 and deep.mean() > 0.2, (early.mean(), deep.mean())
+    g = gpu_frame(sc, cam, "all_levels", strategy=strategy)
+    assert_lists_equal(g, o["offsets"], o["idx"])
+    assert_image_close(g, o)
+
+
+@pytest.mark.parametrize("strategy", ["auto", "list"])
+def test_lists_past_the_mask_prefix(cuda, strategy):
+    """Lists of 19k-22k entries, with deep pixels blending entries past the
+    first 16384 of their tile's list: the list kernel's mask pass covers
+    only that prefix, and past it each thread forms its entries' half-row
+    masks itself."""
+    sc = deep_lists_scene(seed=35, nb=110_000)
+    cam = inputs.config1_camera(48, 32)
+    o = oracle.render(sc, cam, "all_levels")
+    assert np.diff(o["offsets"]).min() > 16384 + 1024
+    assert (o["n_contrib"] > 16384 + 512).mean() > 0.2
     g = gpu_frame(sc, cam, "all_levels", strategy=strategy)
     assert_lists_equal(g, o["offsets"], o["idx"])
     assert_image_close(g, o)
@@ -383,3 +403,34 @@ def test_scene_prepare_bit_exact_many_values(cuda):
         nan = np.isnan(want)          # NaN payloads may differ; positions may not
         np.testing.assert_array_equal(np.isnan(got), nan)
         np.testing.assert_array_equal(got[~nan].view(np.uint32), want[~nan].view(np.uint32))
+
+
+def band_scene(seed=41, n=36_000):
+    """36k faint Gaussians about 10 px wide over a 320x240 frame (300
+    tiles, 1.2k-2.6k entries per tile list): a frame with 1-4x as many
+    tiles as SMs and a mean list length of 1024-8192, which ms_raster
+    (MS_RASTER_AUTO) hands to the list kernel on the device."""
+    rng = np.random.default_rng(seed)
+    mean = np.stack([rng.uniform(-1.9, 1.9, n), rng.uniform(-1.4, 1.4, n),
+                     rng.uniform(-0.5, 0.5, n)], 1).astype(np.float32)
+    log_scale = rng.normal(np.log(0.12), 0.15, (n, 3)).astype(np.float32)
+    quat = rng.standard_normal((n, 4)).astype(np.float32)
+    opacity = rng.uniform(0.02, 0.10, n).astype(np.float32)
+    color = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    return inputs.Scene(mean, log_scale, quat, opacity, color, np.ones(n, np.uint8), 1, -1,
+                        np.zeros(n, np.float32), np.full(n, np.inf, np.float32))
+
+
+@pytest.mark.parametrize("strategy", ["auto", "tile", "list"])
+def test_band_frame(cuda, strategy):
+    """The frame where ms_raster launches both blend kernels and the device
+    picks one: the same lists and image whichever blends it."""
+    sc = band_scene()
+    cam = inputs.config1_camera(320, 240)
+    o = oracle.render(sc, cam, "all_levels")
+    tiles = cam.tiles_x * cam.tiles_y
+    assert 152 <= tiles < 4 * 152
+    assert 1024 * tiles <= len(o["idx"]) <= 8192 * tiles
+    g = gpu_frame(sc, cam, "all_levels", strategy=strategy)
+    assert_lists_equal(g, o["offsets"], o["idx"])
+    assert_image_close(g, o)
