@@ -72,11 +72,12 @@ typedef enum {
  * same blend either way, up to FP32 rounding). */
 typedef enum {
     MS_RASTER_AUTO = 0,  /* LIST when the frame has fewer tiles than the GPU
-                            has SMs; TILE from 4x as many, or when
-                            ms_raster_ex2 caps the tile kernel's CTAs; in
-                            between the frame's mean list length decides on
-                            the device (LIST for 1024-8192 entries per
-                            tile)                                           */
+                            has SMs; TILE from 4x as many, when
+                            ms_raster_ex2 caps the tile kernel's CTAs, or
+                            when the duplicate capacity is below 1024 per
+                            tile; in between the frame's mean list length
+                            decides on the device (LIST for 1024-8192
+                            entries per tile)                               */
     MS_RASTER_TILE = 1,  /* one thread per pixel; long lists split into
                             segments merged exactly across CTAs             */
     MS_RASTER_LIST = 2,  /* one warp per pixel; only the list entries whose

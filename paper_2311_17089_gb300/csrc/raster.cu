@@ -731,9 +731,12 @@ extern "C" int ms_raster_ex2(const ms_proj_t *proj, const ms_bins_t *bins,
                                                       : 0;
     const bool auto_list = strategy == MS_RASTER_AUTO && tiles < sms;
     // a cap on the tile kernel's CTAs (frames blended side by side) keeps
-    // the tile kernel: the list kernel cannot leave SMs to other frames
+    // the tile kernel: the list kernel cannot leave SMs to other frames; so
+    // does a duplicate capacity below kListMeanMin entries per tile, which
+    // rules the list kernel out before the lists are known
     const bool band = strategy == MS_RASTER_AUTO && !auto_list && max_ctas_per_sm == 0 &&
-                      tiles < kListBandSms * sms;
+                      tiles < kListBandSms * sms &&
+                      bins->dup_capacity >= (int64_t)kListMeanMin * tiles;
     const bool list = group > 0 || strategy == MS_RASTER_LIST || auto_list;
     RasterArgs a;
     a.ranges = bins->ranges;
