@@ -386,9 +386,14 @@ def train_step_bench(msgs, torch, ds, sc, dev, steps, warmup):
     ds.s_max.copy_(saved[0])
     ds.s_min.copy_(saved[1])
     launches = 2                                    # prepare; one projection for the views
-    for cam in cams:
+    sms_dev = torch.cuda.get_device_properties(dev).multi_processor_count
+    for r, cam in zip(rs, cams):
         tiles = cam.tiles_x * cam.tiles_y
-        launches += (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 2 + 1
+        # segment offsets, then the blend as ms_raster launches it (mask pass
+        # and list kernel; tile kernel; or, in between, both and the mask pass)
+        blend = (2 if tiles < sms_dev else
+                 3 if tiles < 4 * sms_dev and r.dup_capacity >= 1024 * tiles else 1)
+        launches += (1 + 4 + 1 + (1 if tiles <= 256 else 2) + 1) + 1 + blend + 1
     launches += 2                                   # batched backward: raster, projection
     nv = len(cams)
     # the projection pass: per Gaussian its geometry (44 B), the 2D gradients
@@ -1393,12 +1398,19 @@ def main():
     # kernels of libmsgs per selective step: one projection for every frame,
     # 4 passes of the shared depth sort and its split; per frame the start
     # kernel, 4 depth passes (frames outside the shared order), duplicate,
-    # 1-2 tile passes, ranges; segment offsets, raster
+    # 1-2 tile passes, ranges; segment offsets, then the blend as ms_raster
+    # launches it: the mask pass and the list kernel (fewer tiles than SMs),
+    # the tile kernel alone (capped, or 4x as many tiles, or a capacity below
+    # 1024 per tile), or both kernels and the mask pass (in between)
     launches_per_step = 1 + 4 + (1 if sel_split else 0)
     for k, cam in enumerate(cams):
         tiles = cam.tiles_x * cam.tiles_y
+        capped = share_plan["selective"] and share_ctas[k] > 0
+        cap_ok = rs_mode["selective"][k].dup_capacity >= 1024 * tiles
+        blend = (2 if tiles < sms_dev else
+                 3 if (not capped and tiles < 4 * sms_dev and cap_ok) else 1)
         launches_per_step += (1 + (0 if k in sel_views else 4) + 1
-                              + (1 if tiles <= 256 else 2) + 1) + 2
+                              + (1 if tiles <= 256 else 2) + 1) + 1 + blend
 
     serve = None
     if not args.no_serve:
