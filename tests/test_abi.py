@@ -47,6 +47,14 @@ def test_workspace_sizes():
     assert msgs.ms_bin_workspace_bytes(10, 1, 0) == 0          # no capacity
     assert msgs.ms_bin_workspace_bytes(10, 1, 1 << 31) == 0    # capacity > 2^30
     assert msgs.ms_bin_workspace_bytes(-1, 1, 1) == 0
+    # the raster workspace holds, besides the segment states, one half-row
+    # mask word per tile-list entry for the list kernel
+    a = msgs.ms_raster_workspace_bytes(260, 1_000_000)
+    b = msgs.ms_raster_workspace_bytes(260, 2_000_000)
+    assert a > 4 * 1_000_000 and b - a >= 4 * 1_000_000
+    assert msgs.ms_raster_workspace_bytes(0, 1) == 0
+    assert msgs.ms_raster_workspace_bytes(65537, 1) == 0
+    assert msgs.ms_raster_workspace_bytes(1, 1 << 30) == 0
 
 
 def test_argument_errors_need_no_device():
