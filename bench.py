@@ -52,10 +52,11 @@ PAPER_LEVEL_MIX = (0.95, 0.035, 0.01, 0.005)   # coarse levels under 5% of the G
 # each with the SHA-256 (first 16 hex digits) of the kernel sources it was
 # taken on: a figure whose sources changed since is reported as stale (null)
 # (the raster figure was taken on sources whose kernels are those of the
-# current ones; the host's launch choice changed since only for duplicate
-# capacities below 1024 per tile, which no profiled frame has)
+# current ones: since then only comments and the host's launch choice for
+# duplicate capacities below 1024 per tile, which no profiled frame has,
+# changed)
 RASTER_DRAM = {"bytes": 33.95e6, "sources": ("raster.cu", "raster_list.cu", "raster_ws.cuh"),
-               "sha16": "290261e29046cac3"}   # mean over the 8 frames' raster stages, each frame alone
+               "sha16": "d0db282cefbd654c"}   # mean over the 8 frames' raster stages, each frame alone
 PROJECT_VIEWS_DRAM = {"bytes": 505.1e6, "sources": ("project.cu", "footprint.cuh"),
                       "sha16": "1e94d3f932b66c6a"}   # the selective sweep's projection launch
 

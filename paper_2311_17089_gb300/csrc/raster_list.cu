@@ -6,10 +6,12 @@
 // leaves most of the GPU idle, and splitting the list across CTAs blends
 // segments that the pixels never reach.  Here one warp blends one pixel,
 // and a CTA the eight pixels of one half row of a tile:
-//   - A first pass gives every entry of every tile list a 32-bit mask of the
-//     tile's half rows its alpha >= 1/255 level-set box (the record's half
-//     extents) reaches.  Any entry whose bit is clear has alpha below 1/255
-//     at every pixel of that half row, so leaving it out changes no result.
+//   - A first pass gives every entry of every tile list (its first
+//     kMaskPrefix entries; past them the blend's own threads do it) a 32-bit
+//     mask of the tile's half rows its alpha >= 1/255 level-set box (the
+//     record's half extents) reaches.  Any entry whose bit is clear has
+//     alpha below 1/255 at every pixel of that half row, so leaving it out
+//     changes no result.
 //     On coarse frames about a fifth of a tile's entries reach a given half
 //     row, and a pixel that never terminates (an image edge with no surface
 //     behind it) walks its whole list.
